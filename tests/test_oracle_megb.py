@@ -1,0 +1,111 @@
+"""Pins of the oracle's ball solvers (CPU only).
+
+* exact ball: Welzl's recursion equals brute force over support sets;
+  the ball of a rectangle's corners is its circumcircle (Fig. 2 example);
+* translation GGD (Badoiu-Clarkson): r* <= d_K <= (1 + 1/sqrt(K)) r* and
+  |c_K - c*| <= r*/sqrt(K) against the exact ball;
+* rotation GGD: on samples along one geodesic the ball is known in closed
+  form (centre at the middle of the arc, radius half its length) and the
+  one-dimensional Badoiu-Clarkson bound holds; on the six rotations
+  Exp(+-theta e_k) C the centre is C and the radius theta;
+* invariants: containment, diam/2 <= radius <= diam, sign invariance.
+"""
+import numpy as np
+import pytest
+
+from oracle import megb, so3
+
+rng = np.random.default_rng(11)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 7), (3, 9), (4, 9), (3, 3)])
+def test_welzl_equals_bruteforce(dim, n):
+    for trial in range(5):
+        P = rng.normal(size=(n, dim))
+        c1, r1 = megb.welzl_meb(P)
+        c2, r2 = megb.meb_bruteforce(P)
+        assert abs(r1 - r2) < 1e-10 * max(1, r2)
+        assert np.allclose(c1, c2, atol=1e-9)
+        assert np.all(np.linalg.norm(P - c1, axis=1) <= r1 + 1e-12)
+
+
+def test_rectangle_corners():
+    w, h = 3.0, 1.0
+    P = np.array([[0, 0, 0], [w, 0, 0], [0, h, 0], [w, h, 0]], float) + 5.0
+    c, r = megb.welzl_meb(P)
+    assert np.allclose(c, [w / 2 + 5, h / 2 + 5, 5])
+    assert abs(r - 0.5 * np.hypot(w, h)) < 1e-12
+    for K in [10, 100, 1000]:
+        cK, dK, _ = megb.megb_translation(P, K)
+        assert r - 1e-12 <= dK <= r * (1 + 1 / np.sqrt(K))
+
+
+@pytest.mark.parametrize("n", [20, 200, 2000])
+def test_translation_ggd_badoiu_clarkson_bound(n):
+    P = rng.normal(size=(n, 3)) * np.array([0.01, 0.02, 0.05]) + rng.normal(size=3)
+    cs, rs = megb.welzl_meb(P)
+    for K in [1, 10, 50, 200]:
+        cK, dK, f = megb.megb_translation(P, K)
+        assert rs * (1 - 1e-12) <= dK <= rs * (1 + 1 / np.sqrt(K)) + 1e-15
+        assert np.linalg.norm(cK - cs) <= rs / np.sqrt(K) + 1e-15
+        # containment and the farthest points are real samples
+        assert np.all(np.linalg.norm(P - cK, axis=1) <= dK + 1e-15)
+        assert f.min() >= 0 and f.max() < n
+    diam = max(np.linalg.norm(P - p, axis=1).max() for p in P)
+    assert diam / 2 - 1e-15 <= dK <= diam
+
+
+def test_rotation_ggd_on_one_geodesic():
+    C0 = so3.quat_from_R(so3.exp_so3(rng.normal(size=3)))
+    u = rng.normal(size=3)
+    u /= np.linalg.norm(u)
+    ang = rng.uniform(-0.4, 0.9, 300)
+    qs = so3.quat_mul(so3.quat_exp(ang[:, None] * u), C0[None])
+    mid, half = 0.5 * (ang.max() + ang.min()), 0.5 * (ang.max() - ang.min())
+    Cstar = so3.quat_mul(so3.quat_exp(mid * u), C0)
+    for K in [1, 10, 100, 400]:
+        C, D, f = megb.megb_rotation(qs, K)
+        assert half * (1 - 1e-12) <= D <= half * (1 + 1 / np.sqrt(K)) + 1e-12
+        assert so3.dist_quat(C, Cstar) <= half / np.sqrt(K) + 1e-12
+
+
+def test_rotation_ggd_octahedral_configuration():
+    C0 = so3.quat_from_R(so3.exp_so3(rng.normal(size=3)))
+    theta = 0.2
+    axes = np.concatenate([np.eye(3), -np.eye(3)])
+    qs = so3.quat_mul(so3.quat_exp(theta * axes), C0[None])
+    qs = np.concatenate([qs, so3.quat_mul(so3.quat_exp(rng.normal(size=(50, 3)) * 0.03), C0[None])])
+    K = 400
+    C, D, f = megb.megb_rotation(qs, K)
+    assert theta * (1 - 1e-12) <= D <= theta * (1 + 1 / np.sqrt(K))
+    assert so3.dist_quat(C, C0) <= theta / np.sqrt(K)
+
+
+def test_rotation_ggd_invariants_and_sign_invariance():
+    C0 = so3.quat_from_R(so3.exp_so3(rng.normal(size=3)))
+    qs = so3.quat_mul(so3.quat_exp(rng.normal(size=(500, 3)) * np.array([0.02, 0.05, 0.1])), C0[None])
+    C, D, f = megb.megb_rotation(qs, 200)
+    d = so3.dist_quat(C[None], qs)
+    assert np.all(d <= D + 1e-15)
+    diam = max(so3.dist_quat(q[None], qs).max() for q in qs)
+    assert diam / 2 <= D <= diam
+    flip = qs * np.where(rng.random(len(qs)) < 0.5, -1.0, 1.0)[:, None]
+    C2, D2, f2 = megb.megb_rotation(flip, 200)
+    assert np.array_equal(f, f2) and abs(D - D2) < 1e-14
+    # near-flat cluster: the ball of the quaternions in R^4 (Step III embedding)
+    # projected to the sphere is a centre no better than the GGD one by more than the bound
+    cw, rw = megb.welzl_meb(megb.canonical(qs))
+    cw /= np.linalg.norm(cw)
+    Dw = so3.dist_quat(cw[None], qs).max()
+    assert D <= Dw * (1 + 1 / np.sqrt(200))
+    assert Dw <= D * (1 + 1 / np.sqrt(200))
+
+
+def test_replay_reproduces_free_run():
+    qs = so3.quat_from_R(so3.exp_so3(rng.normal(size=(100, 3)) * 0.1))
+    C, D, f = megb.megb_rotation(qs, 50)
+    Cs = megb.megb_rotation_replay(qs, f)
+    assert np.allclose(Cs[-1], C, atol=1e-15)
+    ts = rng.normal(size=(100, 3))
+    c, d, g = megb.megb_translation(ts, 50)
+    assert np.allclose(megb.megb_translation_replay(ts, g)[-1], c, atol=1e-15)
