@@ -18,11 +18,13 @@ the three constraint indices, j = 1, 2, 3 the three points drawn inside
 the chosen noise balls).
 A batched PURSE p uses key = seed + p (mod 2^64).
 
-Uniform ball points are drawn by integer rejection so both sides take the
-same accept decisions: three words give X_c = (word >> 8) - 2^23 and the
-attempt is accepted when sum X_c^2 <= 2^46 (int64); the point is X * 2^-23.
-Random unit vectors accept 2^40 <= sum X_c^2 <= 2^46 and return X / |X|.
-After MAX_ATTEMPTS rejections the draw is the zero vector.
+Uniform ball points are drawn by integer rejection on a symmetric lattice so
+both sides take the same accept decisions: attempt a uses word a of the
+stream and X_c = 2 ((word >> 10c) & 1023) - 1023 for c = 0, 1, 2 (odd
+integers in [-1023, 1023]); it is accepted when sum X_c^2 <= 2^20 and the
+point is X / 1024.  Random unit vectors accept 2^14 <= sum X_c^2 <= 2^20
+and return X / |X|.  After MAX_ATTEMPTS rejections the draw is the zero
+vector.
 """
 from __future__ import annotations
 
@@ -41,8 +43,8 @@ PHASE_V = 4
 PHASE_RANSAG = 5
 
 MAX_ATTEMPTS = 64
-BALL_R2 = 1 << 46
-UNIT_R2_MIN = 1 << 40
+BALL_R2 = 1 << 20
+UNIT_R2_MIN = 1 << 14
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):
@@ -87,8 +89,10 @@ def stream_words(seed: int, phase: int, j, i, w, n_words: int, start: int = 0) -
     return out
 
 
-def _centered(words: np.ndarray) -> np.ndarray:
-    return (words >> np.uint64(8)).astype(np.int64) - (1 << 23)
+def lattice_point(words: np.ndarray) -> np.ndarray:
+    """Odd-integer lattice coordinates (..., 3) of each word."""
+    w = np.asarray(words, dtype=np.int64)
+    return np.stack([2 * ((w >> (10 * c)) & 1023) - 1023 for c in range(3)], axis=-1)
 
 
 def ball_points(seed: int, phase: int, j, i, w, unit: bool = False):
@@ -99,14 +103,13 @@ def ball_points(seed: int, phase: int, j, i, w, unit: bool = False):
     """
     shape = np.broadcast_shapes(np.shape(j), np.shape(i), np.shape(w))
     pts = np.zeros(shape + (3,))
-    used = np.full(shape, 3 * MAX_ATTEMPTS, dtype=np.int64)
+    used = np.full(shape, MAX_ATTEMPTS, dtype=np.int64)
     done = np.zeros(shape, dtype=bool)
-    chunk = 8  # attempts per batch of words
+    chunk = 8  # attempts (words) per batch
     for a0 in range(0, MAX_ATTEMPTS, chunk):
         if done.all():
             break
-        words = stream_words(seed, phase, j, i, w, 3 * chunk, start=3 * a0)
-        X = _centered(words).reshape(shape + (chunk, 3))
+        X = lattice_point(stream_words(seed, phase, j, i, w, chunk, start=a0))   # (..., chunk, 3)
         r2 = (X * X).sum(axis=-1)
         ok = r2 <= BALL_R2
         if unit:
@@ -118,9 +121,9 @@ def ball_points(seed: int, phase: int, j, i, w, unit: bool = False):
                 if unit:
                     val = Xa / np.sqrt(r2[..., a].astype(np.float64))[..., None]
                 else:
-                    val = Xa * 2.0 ** -23
+                    val = Xa / 1024.0
                 pts[take] = val[take]
-                used[take] = 3 * (a0 + a + 1)
+                used[take] = a0 + a + 1
                 done |= take
     return pts, used
 

@@ -44,12 +44,20 @@ def test_ball_points_uniform_in_ball():
     r2 = (pts ** 2).sum(1)
     assert r2.max() <= 1.0
     # acceptance rate of a cube -> ball rejection is pi/6
-    rate = len(w) / (used / 3).sum()
+    rate = len(w) / used.sum()
     assert abs(rate - np.pi / 6) < 0.005
     # uniform in the unit 3-ball: E|x|^2 = 3/5, mean 0, isotropic
     assert abs(r2.mean() - 0.6) < 0.005
     assert np.abs(pts.mean(0)).max() < 0.005
     assert np.abs((pts ** 2).mean(0) - 0.2).max() < 0.005
+
+
+def test_lattice_is_symmetric_and_decodes_each_word():
+    words = np.array([0, 0x3FFFFFFF, (5 << 20) | (7 << 10) | 1023])
+    X = philox.lattice_point(words)
+    assert X.tolist() == [[-1023, -1023, -1023], [1023, 1023, 1023], [1023, 2 * 7 - 1023, 2 * 5 - 1023]]
+    all_vals = 2 * np.arange(1024) - 1023
+    assert all_vals.sum() == 0 and np.all(all_vals % 2 == 1)
 
 
 def test_unit_vectors():
