@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the CLOSURE hot path on GB300.
+
+One step = one pass of the whole hot path over one synthetic 2D-3D PURSE
+(N = 16 keypoints, pinhole 600/600/320/240): centre statistics, 2^20 walks of
+the rotation-boundary sampler and 2^20 walks of the translation-boundary
+sampler (N_I = 100, N_P = 150, N_P* = 10, N_T = 15, FP32), then the two
+minimum enclosing geodesic balls (200 GGD iterations each).
+
+Printed JSON line: value = executed pose-constraint evaluations per second
+(whole job), roofline of the dominant walk kernel against the FP32 ALU peak,
+e2e through the C ABI with host buffers, the FP64 oracle timed on the host
+cores as cpu_baseline.  ``--impl reference`` times the oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MEGB solves/sec & pose-constraint evals/sec vs plain GPU path; % FP32 roofline"
+UNIT = "evals/s"
+N_KEYPOINTS = 16
+N_WALKS = 1 << 20
+N_ITER = 100
+K_MEGB = 200
+PURSE_SEED = 0
+# algorithmic FP32 flops per (pose, constraint) evaluation of the 2D-3D walk kernels
+# (FFMA = 2; add, mul, min/max, select, rsqrt = 1 each):
+FLOPS = {"R": {"dist": 18, "ladder": 15}, "t": {"dist": 33, "ladder": 30}}
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+
+
+def workload_config():
+    return {
+        "workload": "2D-3D PURSE N=16 (pinhole 600/600/320/240, r_i~U[2,10] px, depth U[0.5,1.5] m); "
+                    "2^20 walks per sampler x 100 iterations (N_P=150, N_P*=10, N_T=15); "
+                    "rotation + translation MEGB, 200 GGD iterations",
+        "n_keypoints": N_KEYPOINTS, "walks_per_sampler": N_WALKS, "n_iter": N_ITER, "megb_iters": K_MEGB,
+        "precision": "fp32 walk arithmetic, fp64 centre statistics and ball centres",
+        "l2": "flushed between timed steps (512 MB write)", "data": "synthetic (seeded)",
+    }
+
+
+def make_purse(rank=0):
+    from paper_2403_09990_gb300 import synthetic as syn
+    return syn.purse_2d3d(N_KEYPOINTS, PURSE_SEED + rank)
+
+
+def closure_params(sampler, n_iter=N_ITER, precision=0):
+    import paper_2403_09990_gb300.purse as P
+    return P.make_params(n_iter=n_iter, n_perturb=150, n_keep=10, n_steps=15, omega0=1.0, v0=2.0, gamma=0.5,
+                         rot_perturb=0.2, trans_perturb=0.1, perturb_units=0, sampler=sampler, precision=precision)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle
+def _oracle_chunk(args):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    sampler, walk_ids, n_iter, rank = args
+    from oracle import closure
+    p = make_purse(rank)
+    prm = closure.preset_2d3d(n_iter=n_iter)
+    seeds = p.seed_pose()[None]
+    t0 = time.perf_counter()
+    if sampler == 0:
+        R, t = closure.sample_rotation_boundary(p, seeds, prm, 1000, np.asarray(walk_ids))
+    else:
+        R, t = closure.sample_translation_boundary(p, seeds, prm, 1000, np.asarray(walk_ids))
+    dt = time.perf_counter() - t0
+    q, t = closure.as_samples(R, t)
+    # the oracle evaluates every perturbation and the full ladder (Alg. 3/5 as written)
+    evals = len(walk_ids) * n_iter * (prm.n_perturb + prm.n_keep * prm.n_steps) * p.n
+    return evals, dt, q, t
+
+
+def oracle_sample(walks_per_worker, workers, n_iter=N_ITER, rank=0):
+    """The oracle on a bounded sample of the workload: both samplers, then both balls."""
+    import multiprocessing as mp
+    from oracle import megb as om
+    ctx = mp.get_context("spawn")
+    jobs = []
+    for s in (0, 1):
+        for k in range(workers):
+            ids = list(range(k * walks_per_worker, (k + 1) * walks_per_worker))
+            jobs.append((s, ids, n_iter, rank))
+    with ctx.Pool(workers) as pool:
+        pool.map(_warm, range(workers))
+        t0 = time.perf_counter()
+        out = pool.map(_oracle_chunk, jobs)
+        qs = np.concatenate([o[2] for o, j in zip(out, jobs) if j[0] == 0])
+        ts = np.concatenate([o[3] for o, j in zip(out, jobs) if j[0] == 1])
+        om.megb_rotation(qs, K_MEGB)
+        om.megb_translation(ts, K_MEGB)
+        wall = time.perf_counter() - t0
+    evals = sum(o[0] for o in out)
+    return evals, wall, 2 * workers * walks_per_worker
+
+
+def _warm(_):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import oracle.closure  # noqa: F401
+    return 0
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world):
+    import torch
+    import paper_2403_09990_gb300.purse as P
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    P.lib(build_if_missing=True)
+    p = make_purse(rank)
+    stream = torch.cuda.current_stream()
+    hR, hT = P.Purse(p), P.Purse(p)
+    seeds = torch.as_tensor(p.seed_pose()[None], dtype=torch.float64, device=dev)
+    qR = torch.empty((N_WALKS, 4), dtype=torch.float32, device=dev)
+    tR = torch.empty((N_WALKS, 3), dtype=torch.float32, device=dev)
+    qT = torch.empty((N_WALKS, 4), dtype=torch.float32, device=dev)
+    tT = torch.empty((N_WALKS, 3), dtype=torch.float32, device=dev)
+    res = torch.empty(9, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    pR, pT = closure_params(0), closure_params(1)
+    launches_per_step = 2 + 2 + (2 * (K_MEGB + 1) + 2)
+
+    def step(seed, ev=None):
+        if ev:
+            ev[0].record(stream)
+        P.purse_sample(hR.h, pR, seed, seeds, 1, N_WALKS, qR, tR, None, stream)
+        if ev:
+            ev[1].record(stream)
+        P.purse_sample(hT.h, pT, seed, seeds, 1, N_WALKS, qT, tT, None, stream)
+        if ev:
+            ev[2].record(stream)
+        P.megb_solve(hR.h, 0, K_MEGB, qR, N_WALKS, tT, N_WALKS, res, None, stream)
+        if ev:
+            ev[3].record(stream)
+
+    for w in range(args.warmup):
+        flush.fill_(w & 0xFF)
+        step(100 + w)
+    P.purse_sync(hR.h, stream)
+    P.purse_sync(hT.h, stream)
+    evals_dist = N_WALKS * N_ITER * 150 * p.n
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    t_wall = time.perf_counter()
+    rows = []
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)  # untimed: L2 flush between timed steps
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        step(1000 + s, ev)
+        eR = P.purse_last_evals(hR.h, stream)
+        eT = P.purse_last_evals(hT.h, stream)
+        rows.append((ev, eR, eT))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    ck = clocks.stop()
+    P.purse_sync(hR.h, stream)
+    P.purse_sync(hT.h, stream)
+    tot = walkR = walkT = ggd = 0.0
+    evals = evR = evT = 0
+    for ev, eR, eT in rows:
+        a, b, c, d = (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]),
+                      ev[0].elapsed_time(ev[3]))
+        walkR += a
+        walkT += b
+        ggd += c
+        tot += d
+        evals += eR + eT
+        evR += eR
+        evT += eT
+    t_step = tot / args.steps / 1e3
+    if dist:
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+        ee = torch.tensor([float(evals)], device=dev, dtype=torch.float64)
+        dist.all_reduce(ee)
+        evals_all = float(ee.item())
+    else:
+        evals_all = float(evals)
+    value = evals_all / (t_step * args.steps)
+    # roofline of the dominant kernel (the slower of the two walk kernels)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+    kern = "t" if walkT >= walkR else "R"
+    ev_k = evT if kern == "t" else evR
+    ms_k = (walkT if kern == "t" else walkR) / args.steps
+    dist_k = evals_dist * args.steps
+    flops_k = (dist_k * FLOPS[kern]["dist"] + (ev_k - dist_k) * FLOPS[kern]["ladder"]) / args.steps
+    achieved = flops_k / (ms_k / 1e3) / 1e12
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": dict(workload_config(), parallelism="replicas" if world > 1 else "single"),
+        "megb_solves_per_s": world / t_step, "samples_per_s": 2 * N_WALKS * world / t_step,
+        "breakdown_ms": {"walk_dS_R": walkR / args.steps, "walk_dS_t": walkT / args.steps, "megb": ggd / args.steps},
+        "evals_per_step": {"dS_R": evR / args.steps, "dS_t": evT / args.steps},
+        "roofline": {"bound": "alu", "kernel": f"walk_kernel<float, 2D-3D, dS_{kern}>", "achieved": achieved,
+                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                     "traffic": None,
+                     "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz (max SM clock)"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": ck, "wall_s_timed": wall,
+    }
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = run_e2e(args, p, dev)
+    if rank == 0 and not args.no_cpu_baseline:
+        ev_c, wall_c, walks_c = oracle_sample(args.cpu_walks, args.cpu_workers)
+        out["cpu_baseline"] = {"value": ev_c / wall_c, "unit": UNIT, "cores": args.cpu_workers, "kind": "oracle",
+                               "sample": f"{walks_c} walks ({args.cpu_walks} per worker, both samplers, N_I=100) "
+                                         f"+ both balls (200 GGD iterations); {wall_c:.1f} s"}
+    hR.close()
+    hT.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def run_e2e(args, p, dev):
+    """Same step through the public API from host buffers: create the PURSE from host arrays, copy the
+    seed pose in, sample both boundaries, solve both balls, read the result back."""
+    import torch
+    import paper_2403_09990_gb300.purse as P
+    seeds_h = torch.as_tensor(p.seed_pose()[None], dtype=torch.float64).pin_memory()
+    res_h = torch.empty(9, dtype=torch.float64).pin_memory()
+    qR = torch.empty((N_WALKS, 4), dtype=torch.float32, device=dev)
+    tR = torch.empty((N_WALKS, 3), dtype=torch.float32, device=dev)
+    qT = torch.empty((N_WALKS, 4), dtype=torch.float32, device=dev)
+    tT = torch.empty((N_WALKS, 3), dtype=torch.float32, device=dev)
+    seeds = torch.empty((1, 12), dtype=torch.float64, device=dev)
+    res = torch.empty(9, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    pR, pT = closure_params(0), closure_params(1)
+    total, evals = 0.0, 0
+    n = p.n
+    h2d = 8 * n * 8 + 8 * n * 4 + seeds_h.numel() * 8
+    d2h = res_h.numel() * 8 + 2 * 8
+    for s in range(args.warmup + args.steps):
+        flush.fill_(s & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hR, hT = P.Purse(p), P.Purse(p)
+        seeds.copy_(seeds_h, non_blocking=True)
+        P.purse_sample(hR.h, pR, 2000 + s, seeds, 1, N_WALKS, qR, tR, None, stream)
+        P.purse_sample(hT.h, pT, 2000 + s, seeds, 1, N_WALKS, qT, tT, None, stream)
+        P.megb_solve(hR.h, 0, K_MEGB, qR, N_WALKS, tT, N_WALKS, res, None, stream)
+        res_h.copy_(res, non_blocking=True)
+        ev = P.purse_last_evals(hR.h, stream) + P.purse_last_evals(hT.h, stream)
+        P.purse_sync(hR.h, stream)
+        dt = time.perf_counter() - t0
+        hR.close()
+        hT.close()
+        if s >= args.warmup:
+            total += dt
+            evals += ev
+    return {"value": evals / total, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": total / args.steps * 1e3,
+            "path": "purse_create(host arrays) + pinned seed H2D + purse_sample x2 + megb_solve + result D2H"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    times, evals_all = [], 0
+    walks = 0
+    for s in range(args.warmup + args.steps):
+        ev, wall, w = oracle_sample(args.ref_walks, args.cpu_workers)
+        if s >= args.warmup:
+            times.append(wall)
+            evals_all += ev
+            walks = w
+    t = sum(times)
+    value = evals_all / t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": dict(workload_config(), parallelism="host cores"),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": args.cpu_workers, "kind": "oracle",
+                            "sample": f"per step {walks} walks (both samplers, N_I=100) + both balls"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-walks", type=int, default=4, help="oracle walks per worker per sampler (cpu_baseline)")
+    ap.add_argument("--ref-walks", type=int, default=2, help="oracle walks per worker per sampler (reference arm)")
+    ap.add_argument("--cpu-workers", type=int, default=min(16, cpu_cores()))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,152 @@
+/*
+ * purse.h -- C ABI of the GB300 CLOSURE hot path (arXiv 2403.09990).
+ *
+ * A PURSE (pose uncertainty set, eq. 5 with Lambda_i = I, beta_i = r_i) is the
+ * set of poses (R, t) in SE(3) whose residuals satisfy |g_i(R, t)| <= r_i for
+ * every keypoint i, with
+ *   3D-3D (Example 2, eq. 3):  g_i = b_i - (R a_i + t)
+ *   2D-3D (Example 1, eq. 2):  g_i = z_i - pi(K (R Z_i + t)) in pixels,
+ *                              pi(P) = (P_x/P_z, P_y/P_z), and P_z > 0 required.
+ * The library samples the PURSE boundary with the strategic random walks of
+ * Section IV (Alg. 2-5) and computes minimum enclosing geodesic balls (MEGB,
+ * Section II) of the samples by geodesic gradient descent.
+ *
+ * Conventions for every call
+ * - Every call returns a purse_status; PURSE_OK is 0.  On failure
+ *   purse_last_error() returns a thread-local message.  Kernels are launched
+ *   asynchronously on the given stream; errors detected on the device (a
+ *   bounded wait that ran out, non-finite input) are recorded in the
+ *   handle's device status word and returned by the next purse_sync().
+ * - Pointers named d_* are device pointers owned by the caller; they must
+ *   stay valid until the work on the stream completes.  Host pointers are
+ *   read before the call returns.
+ * - Rotations are unit quaternions (w, x, y, z) with w >= 0; a pose packed
+ *   in 12 doubles is R row-major followed by t.
+ * - Precision: 0 = FP32 (float buffers), 1 = FP64 (double buffers).
+ * - A handle is not thread-safe; different handles are independent.
+ * - purse_stream_t is a cudaStream_t (NULL = the legacy default stream).
+ */
+#ifndef PURSE_H
+#define PURSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct purse_s* purse_t;
+typedef void* purse_stream_t;
+
+typedef enum { PURSE_3D3D = 0, PURSE_2D3D = 1 } purse_kind;
+
+typedef enum {
+  PURSE_OK = 0,
+  PURSE_ERR_ARG = 1,      /* invalid argument (sizes, NaN/Inf, r_i <= 0, ...) */
+  PURSE_ERR_CUDA = 2,     /* a CUDA runtime call failed */
+  PURSE_ERR_EMPTY = 3,    /* Step I found no pose inside the PURSE */
+  PURSE_ERR_TIMEOUT = 4,  /* a bounded device wait ran out */
+  PURSE_ERR_NOMEM = 5,    /* device allocation failed */
+  PURSE_ERR_NUMERIC = 6,  /* non-finite value met on the device */
+  PURSE_ERR_STATE = 7     /* call out of order (e.g. backward before solve) */
+} purse_status;
+
+typedef struct { double fx, fy, cx, cy; } purse_intrinsics;
+
+/* Simulation parameters P of Alg. 1 (names of Alg. 2-5). */
+typedef struct {
+  int n_iter;           /* N_I   walk iterations, >= 0 */
+  int n_perturb;        /* N_P   perturbations per iteration, 1..256 */
+  int n_keep;           /* N_P*  kept perturbations, 1..min(32, N_P) */
+  int n_steps;          /* N_T   step-ladder length, 1..32 */
+  double omega0;        /* omega_0 angular speed [rad] (rotation sampler) */
+  double v0;            /* v_0 centre speed [m] (translation sampler) */
+  double gamma;         /* time-step decay, ladder Delta T = gamma^(m-1), in (0, 1] */
+  double rot_perturb;   /* theta_p (R_p) */
+  double trans_perturb; /* t_p */
+  int perturb_units;    /* 0: t_p, theta_p relative to the PURSE scale; 1: raw m / rad */
+  int sampler;          /* 0: dS_R sampler (Alg. 2/3); 1: dS_t sampler (Alg. 4/5) */
+  int precision;        /* 0: FP32 samples and walk arithmetic; 1: FP64 */
+} purse_params;
+
+/* Create a handle owning device copies of one PURSE (eq. 5).
+ * kind: PURSE_3D3D or PURSE_2D3D.  n: number of constraints, 3..256.
+ * model: host n x 3 (a_i or Z_i); obs: host n x 3 (b_i) or n x 2 (pixels z_i);
+ * radii: host n, each > 0 (r_i = beta_i); K: intrinsics for 2D-3D, NULL for 3D-3D.
+ * All values must be finite.  Allocates device memory (PURSE_ERR_NOMEM). */
+purse_status purse_create(int kind, int n, const double* model, const double* obs,
+                          const double* radii, const purse_intrinsics* K, purse_t* out);
+
+purse_status purse_destroy(purse_t h);
+
+/* Constraint evaluation (eq. 2/3, eq. 11).  d_poses: n_poses x 12 poses (R row-major,
+ * t) in the given precision.  Outputs (each may be NULL):
+ *   d_margin  n_poses x n  r_i - |g_i| (-inf for 2D-3D keypoints behind the camera)
+ *   d_active  n_poses      index of the smallest margin (the constraint defining
+ *                          dist(R, t, dS) of eq. 11), lowest index on ties
+ *   d_grad    n_poses x 6  d|g_a| / d(phi, rho) for that active constraint a, under
+ *                          R <- Exp(phi) R, t <- t + rho (0 when |g_a| = 0). */
+purse_status purse_eval(purse_t h, int precision, const void* d_poses, int n_poses,
+                        void* d_margin, int32_t* d_active, void* d_grad, purse_stream_t stream);
+
+/* Step I for 3D-3D (Section IV, RANSAG): trials tau = 0..n_trials-1 each fit a pose to three
+ * distinct constraints with one point drawn inside each noise ball (Arun's least-squares
+ * rotation) and accept it if it lies in the PURSE.  The first max_seeds accepted poses in
+ * trial order are written to d_seeds (device, max_seeds x 12 doubles); *n_seeds (host)
+ * receives their count.  Synchronises the stream.  PURSE_ERR_EMPTY if none. */
+purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds,
+                          double* d_seeds, int* n_seeds, purse_stream_t stream);
+
+/* Step II (Alg. 3 or Alg. 5 by p->sampler): n_samples walks, walk w starting from seed pose
+ * (w mod s0) of d_seeds (device, s0 x 12 doubles).  Writes the final pose of each walk:
+ * d_q n_samples x 4 and d_t n_samples x 3 (precision p->precision).  d_trace (device, may be
+ * NULL) receives per walk and iteration n_keep + 2 int16: the top-k perturbation indices in
+ * rank order, then m0 and k0 (0-based; -1 when no candidate was feasible).
+ * Random draws: Philox4x32-10, key = (low, high 32 bits of seed); word k of the stream named
+ * (phase, j, i, w) is output lane k & 3 of counter (k >> 2, phase << 24 | j, i, w); phase 1/2 are
+ * the perturbations j of iteration i of walk w in the dS_R / dS_t sampler, 3/4 the random unit
+ * vector of the initial angular / centre velocity.  A ball point takes one word per attempt:
+ * X_c = 2 ((word >> 10c) & 1023) - 1023, accepted if |X|^2 <= 2^20, point X / 1024. */
+purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const double* d_seeds,
+                          int s0, int n_samples, void* d_q, void* d_t, int16_t* d_trace,
+                          purse_stream_t stream);
+
+/* Number of (pose, constraint) evaluations the last purse_sample on this handle executed
+ * (perturbation distances of eq. 11 plus in_purse checks of the step ladder up to m0).
+ * Synchronises the stream; *evals is a host pointer. */
+purse_status purse_last_evals(purse_t h, unsigned long long* evals, purse_stream_t stream);
+
+/* Step III (Section II, geodesic gradient descent; step rule of Alg. 6): K iterations on the
+ * n_rot rotation samples d_q (n_rot x 4) and on the n_tr translation samples d_t (n_tr x 3),
+ * precision as given.  C_0 = first sample; C_k = SLERP(C_{k-1}, farthest sample, 1/k);
+ * c_k = c_{k-1} + (farthest - c_{k-1}) / k.  d_result (device, 9 doubles):
+ * C (4, w >= 0), c (3), D-hat (rad), d-hat (m).  d_farthest (device, may be NULL):
+ * 2K int32, the farthest-sample indices of the rotation then the translation descent.
+ * Either ball may be skipped with n = 0 (its result entries are 0).
+ * Uses handle-owned scratch; the input buffers must not change before megb_backward. */
+purse_status megb_solve(purse_t h, int precision, int n_iters, const void* d_q, int n_rot,
+                        const void* d_t, int n_tr, double* d_result, int32_t* d_farthest,
+                        purse_stream_t stream);
+
+/* The walks' random streams, exposed for verification: for streams w = w0 .. w0+n_streams-1
+ * named (phase, j, i, w) under key = seed, writes their first n_words Philox4x32-10 words to
+ * d_words (device, n_streams x n_words uint32) and, if d_lattice is not NULL, the first accepted
+ * lattice point of each stream (device, n_streams x 4 int32: X, Y, Z, attempts used; unit != 0
+ * selects the unit-vector acceptance region 2^14 <= |X|^2 <= 2^20). */
+purse_status purse_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t i, uint32_t w0, int n_streams,
+                             int n_words, uint32_t* d_words, int32_t* d_lattice, int unit, purse_stream_t stream);
+
+/* Synchronise the stream and return (and clear) the handle's device status. */
+purse_status purse_sync(purse_t h, purse_stream_t stream);
+
+/* Thread-local message for the last failing call (never NULL). */
+const char* purse_last_error(void);
+
+/* Library build string: version, CUDA target. */
+const char* purse_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PURSE_H */

@@ -1,0 +1,280 @@
+// C ABI of libpurse (declared in include/purse.h): argument validation,
+// handle lifetime, handle-owned scratch, the device status word.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dev.cuh"
+#include "internal.h"
+
+namespace purse {
+
+static thread_local std::string g_error = "";
+
+void set_error(const std::string& msg) { g_error = msg; }
+
+purse_status cuda_fail(cudaError_t e, const char* where) {
+  set_error(std::string(where) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? PURSE_ERR_NOMEM : PURSE_ERR_CUDA;
+}
+
+static purse_status arg_error(const std::string& msg) {
+  set_error(msg);
+  return PURSE_ERR_ARG;
+}
+
+purse_status ensure_scratch(purse_t h, size_t bytes) {
+  if (bytes <= h->scratch_bytes) return PURSE_OK;
+  if (h->d_scratch) {
+    cudaError_t e = cudaFree(h->d_scratch);  // synchronises the device
+    h->d_scratch = nullptr;
+    h->scratch_bytes = 0;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFree(scratch)");
+  }
+  const size_t sz = bytes < (1 << 16) ? (1 << 16) : bytes + bytes / 4;
+  cudaError_t e = cudaMalloc(&h->d_scratch, sz);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(scratch)");
+  h->scratch_bytes = sz;
+  return PURSE_OK;
+}
+
+static bool finite_all(const double* v, size_t n) {
+  for (size_t k = 0; k < n; ++k)
+    if (!std::isfinite(v[k])) return false;
+  return true;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace purse
+
+using namespace purse;
+
+extern "C" {
+
+const char* purse_last_error(void) { return g_error.c_str(); }
+
+const char* purse_version(void) { return "libpurse 0.1 (CUDA sm_103a)"; }
+
+purse_status purse_create(int kind, int n, const double* model, const double* obs, const double* radii,
+                          const purse_intrinsics* K, purse_t* out) {
+  if (!out) return arg_error("purse_create: out is NULL");
+  *out = nullptr;
+  if (kind != PURSE_3D3D && kind != PURSE_2D3D) return arg_error("purse_create: kind must be 0 (3D-3D) or 1 (2D-3D)");
+  if (n < 3 || n > 256) return arg_error("purse_create: n must be in [3, 256]");
+  if (!model || !obs || !radii) return arg_error("purse_create: NULL input array");
+  const int od = kind == PURSE_3D3D ? 3 : 2;
+  if (!finite_all(model, 3 * (size_t)n) || !finite_all(obs, (size_t)od * n) || !finite_all(radii, n))
+    return arg_error("purse_create: non-finite input");
+  for (int i = 0; i < n; ++i)
+    if (!(radii[i] > 0)) return arg_error("purse_create: radii must be > 0");
+  purse_intrinsics Kc{0, 0, 0, 0};
+  if (kind == PURSE_2D3D) {
+    if (!K) return arg_error("purse_create: 2D-3D needs intrinsics");
+    Kc = *K;
+    if (!(std::isfinite(Kc.fx) && std::isfinite(Kc.fy) && std::isfinite(Kc.cx) && std::isfinite(Kc.cy)) ||
+        !(Kc.fx > 0 && Kc.fy > 0))
+      return arg_error("purse_create: intrinsics must be finite with fx, fy > 0");
+  }
+  std::vector<double> t64(8 * (size_t)n);
+  std::vector<float> t32(8 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    double* a = &t64[4 * i];
+    double* b = &t64[4 * (n + i)];
+    a[0] = model[3 * i], a[1] = model[3 * i + 1], a[2] = model[3 * i + 2], a[3] = radii[i];
+    b[0] = obs[od * i], b[1] = obs[od * i + 1], b[2] = od == 3 ? obs[od * i + 2] : 0.0, b[3] = radii[i] * radii[i];
+  }
+  for (size_t k = 0; k < t64.size(); ++k) t32[k] = (float)t64[k];
+  purse_s* h = new purse_s();
+  h->kind = kind;
+  h->n = n;
+  h->K = Kc;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaMalloc(&h->tables.f64, t64.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tables.f32, t32.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_status, 256);
+  if (e == cudaSuccess) e = cudaMemcpy(h->tables.f64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->tables.f32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, 256);
+  if (e != cudaSuccess) {
+    purse_status s = cuda_fail(e, "purse_create");
+    purse_destroy(h);
+    return s;
+  }
+  h->d_evals = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h->d_status) + 64);
+  *out = h;
+  return PURSE_OK;
+}
+
+purse_status purse_destroy(purse_t h) {
+  if (!h) return PURSE_OK;
+  if (h->tables.f64) cudaFree(h->tables.f64);
+  if (h->tables.f32) cudaFree(h->tables.f32);
+  if (h->d_status) cudaFree(h->d_status);
+  if (h->d_scratch) cudaFree(h->d_scratch);
+  delete h;
+  return PURSE_OK;
+}
+
+purse_status purse_eval(purse_t h, int precision, const void* d_poses, int n_poses, void* d_margin, int32_t* d_active,
+                        void* d_grad, purse_stream_t stream) {
+  if (!h) return arg_error("purse_eval: NULL handle");
+  if (precision != 0 && precision != 1) return arg_error("purse_eval: precision must be 0 or 1");
+  if (n_poses < 0) return arg_error("purse_eval: n_poses < 0");
+  if (n_poses > 0 && !d_poses) return arg_error("purse_eval: NULL poses");
+  cudaError_t e = launch_eval(h, precision, d_poses, n_poses, d_margin, d_active, d_grad, (cudaStream_t)stream);
+  return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_eval");
+}
+
+purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds, double* d_seeds, int* n_seeds,
+                          purse_stream_t stream) {
+  if (!h) return arg_error("purse_ransag: NULL handle");
+  if (h->kind != PURSE_3D3D) return arg_error("purse_ransag: RANSAG is implemented for 3D-3D PURSEs");
+  if (n_trials < 1 || max_seeds < 1) return arg_error("purse_ransag: n_trials and max_seeds must be >= 1");
+  if (!d_seeds || !n_seeds) return arg_error("purse_ransag: NULL output");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int chunk = 1 << 16;
+  const size_t pose_bytes = align256((size_t)chunk * 12 * sizeof(double));
+  const size_t acc_bytes = align256(chunk);
+  purse_status s = ensure_scratch(h, pose_bytes + acc_bytes + 256);
+  if (s != PURSE_OK) return s;
+  double* d_pose = reinterpret_cast<double*>(h->d_scratch);
+  uint8_t* d_acc = reinterpret_cast<uint8_t*>(h->d_scratch) + pose_bytes;
+  int* d_count = reinterpret_cast<int*>(reinterpret_cast<char*>(h->d_scratch) + pose_bytes + acc_bytes);
+  cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(int), st);
+  int count = 0;
+  for (int t0 = 0; t0 < n_trials && e == cudaSuccess; t0 += chunk) {
+    const int nt = n_trials - t0 < chunk ? n_trials - t0 : chunk;
+    e = launch_ransag(h, seed, t0, nt, d_pose, d_acc, st);
+    if (e == cudaSuccess) e = launch_compact(d_pose, d_acc, nt, d_seeds, d_count, max_seeds, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&count, d_count, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (count >= max_seeds) break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "purse_ransag");
+  *n_seeds = count;
+  if (count == 0) {
+    set_error("purse_ransag: no trial pose inside the PURSE");
+    return PURSE_ERR_EMPTY;
+  }
+  return PURSE_OK;
+}
+
+purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const double* d_seeds, int s0,
+                          int n_samples, void* d_q, void* d_t, int16_t* d_trace, purse_stream_t stream) {
+  if (!h || !p) return arg_error("purse_sample: NULL handle or params");
+  if (p->n_iter < 0) return arg_error("purse_sample: n_iter < 0");
+  if (p->n_perturb < 1 || p->n_perturb > 256) return arg_error("purse_sample: n_perturb must be in [1, 256]");
+  if (p->n_keep < 1 || p->n_keep > 32 || p->n_keep > p->n_perturb)
+    return arg_error("purse_sample: n_keep must be in [1, min(32, n_perturb)]");
+  if (p->n_steps < 1 || p->n_steps > 32) return arg_error("purse_sample: n_steps must be in [1, 32]");
+  if (!(p->gamma > 0 && p->gamma <= 1)) return arg_error("purse_sample: gamma must be in (0, 1]");
+  if (!std::isfinite(p->omega0) || !std::isfinite(p->v0) || !std::isfinite(p->rot_perturb) ||
+      !std::isfinite(p->trans_perturb) || p->rot_perturb < 0 || p->trans_perturb < 0)
+    return arg_error("purse_sample: speeds and perturbation scales must be finite (scales >= 0)");
+  if (p->sampler != 0 && p->sampler != 1) return arg_error("purse_sample: sampler must be 0 or 1");
+  if (p->precision != 0 && p->precision != 1) return arg_error("purse_sample: precision must be 0 or 1");
+  if (p->perturb_units != 0 && p->perturb_units != 1) return arg_error("purse_sample: perturb_units must be 0 or 1");
+  if (s0 < 1 || !d_seeds) return arg_error("purse_sample: need at least one seed pose");
+  if (n_samples < 0) return arg_error("purse_sample: n_samples < 0");
+  if (n_samples > 0 && (!d_q || !d_t)) return arg_error("purse_sample: NULL output");
+  if ((long long)p->n_iter * (p->n_keep + 2) * (long long)n_samples > (1LL << 40))
+    return arg_error("purse_sample: trace too large");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t stats_bytes = align256(sizeof(WalkStats));
+  const size_t seed_bytes = align256((size_t)s0 * kSeedStride * sizeof(double));
+  purse_status s = ensure_scratch(h, stats_bytes + seed_bytes);
+  if (s != PURSE_OK) return s;
+  WalkStats* d_stats = reinterpret_cast<WalkStats*>(h->d_scratch);
+  double* d_seed_data = reinterpret_cast<double*>(reinterpret_cast<char*>(h->d_scratch) + stats_bytes);
+  cudaError_t e = cudaMemsetAsync(h->d_evals, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = launch_stats(h, d_seeds, s0, p, d_stats, d_seed_data, st);
+  if (e != cudaSuccess) return cuda_fail(e, "purse_sample (stats)");
+  if (n_samples == 0) return PURSE_OK;
+  WalkArgs a;
+  a.table = p->precision == 0 ? (const void*)h->tables.f32 : (const void*)h->tables.f64;
+  a.n = h->n;
+  a.fx = h->K.fx, a.fy = h->K.fy, a.cx = h->K.cx, a.cy = h->K.cy;
+  a.seed_data = d_seed_data;
+  a.s0 = s0;
+  a.stats = d_stats;
+  a.n_samples = n_samples;
+  a.n_iter = p->n_iter, a.n_perturb = p->n_perturb, a.n_keep = p->n_keep, a.n_steps = p->n_steps;
+  a.omega0 = p->omega0, a.v0 = p->v0, a.gamma = p->gamma;
+  a.key0 = (uint32_t)seed, a.key1 = (uint32_t)(seed >> 32);
+  a.out_q = d_q, a.out_t = d_t;
+  a.trace = d_trace;
+  a.status = h->d_status;
+  a.evals = h->d_evals;
+  e = launch_walk(h, p, a, st);
+  if (e == cudaErrorInvalidConfiguration || e == cudaErrorInvalidValue) {
+    set_error("purse_sample: walk configuration does not fit in shared memory");
+    return PURSE_ERR_ARG;
+  }
+  return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_sample (walk)");
+}
+
+purse_status purse_last_evals(purse_t h, unsigned long long* evals, purse_stream_t stream) {
+  if (!h || !evals) return arg_error("purse_last_evals: NULL argument");
+  cudaError_t e = cudaMemcpyAsync(evals, h->d_evals, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                  (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_last_evals");
+}
+
+purse_status megb_solve(purse_t h, int precision, int n_iters, const void* d_q, int n_rot, const void* d_t, int n_tr,
+                        double* d_result, int32_t* d_farthest, purse_stream_t stream) {
+  if (!h) return arg_error("megb_solve: NULL handle");
+  if (precision != 0 && precision != 1) return arg_error("megb_solve: precision must be 0 or 1");
+  if (n_iters < 1 || n_iters > (1 << 20)) return arg_error("megb_solve: n_iters must be in [1, 2^20]");
+  if (n_rot < 0 || n_tr < 0) return arg_error("megb_solve: negative sample count");
+  if ((n_rot > 0 && !d_q) || (n_tr > 0 && !d_t) || !d_result) return arg_error("megb_solve: NULL buffer");
+  const size_t need = megb_scratch_bytes(n_iters, h->sm_count);
+  // the walk scratch (stats, seeds) is not needed any more once sampling is enqueued,
+  // but megb keeps its own region after it so both can coexist on one stream
+  purse_status s = ensure_scratch(h, need);
+  if (s != PURSE_OK) return s;
+  cudaError_t e = launch_megb(h, precision, n_iters, d_q, n_rot, d_t, n_tr, d_result, d_farthest, h->d_scratch,
+                              (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "megb_solve");
+  h->megb_iters = n_iters;
+  h->megb_precision = precision;
+  h->megb_q = d_q, h->megb_t = d_t;
+  h->megb_nrot = n_rot, h->megb_ntr = n_tr;
+  return PURSE_OK;
+}
+
+purse_status purse_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t i, uint32_t w0, int n_streams,
+                             int n_words, uint32_t* d_words, int32_t* d_lattice, int unit, purse_stream_t stream) {
+  if (n_streams < 0 || n_words < 0 || (n_streams > 0 && n_words > 0 && !d_words))
+    return arg_error("purse_rng_words: bad sizes or NULL output");
+  if (j >= (1u << 24) || phase > 255u) return arg_error("purse_rng_words: j must be < 2^24 and phase < 256");
+  cudaError_t e = launch_rng_words(seed, phase, j, i, w0, n_streams, n_words, d_words, d_lattice, unit,
+                                   (cudaStream_t)stream);
+  return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_rng_words");
+}
+
+purse_status purse_sync(purse_t h, purse_stream_t stream) {
+  if (!h) return arg_error("purse_sync: NULL handle");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "purse_sync");
+  int st = 0;
+  e = cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "purse_sync (status)");
+  if (st & kDevErrTimeout) {
+    set_error("a bounded device wait ran out");
+    return PURSE_ERR_TIMEOUT;
+  }
+  if (st & kDevErrNumeric) {
+    set_error("non-finite value on the device");
+    return PURSE_ERR_NUMERIC;
+  }
+  return PURSE_OK;
+}
+
+}  // extern "C"

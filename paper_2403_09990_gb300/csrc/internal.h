@@ -1,0 +1,96 @@
+// Host-side internals shared by the translation units of libpurse.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/purse.h"
+
+namespace purse {
+
+// Constraint table in the layout the kernels stage into shared memory:
+// rows 0..n-1: (model x, y, z, r), rows n..2n-1: (obs x, y, z or 0, r^2).
+// One copy per arithmetic type; 8 n values, a multiple of 16 bytes.
+struct purse_tables {
+  float* f32 = nullptr;
+  double* f64 = nullptr;
+};
+
+// Output of the centre-statistics kernel (Alg. 2, R-bar / t-bar lines; PCA of
+// Section IV for 2D-3D; perturbation radii).
+struct WalkStats {
+  double Rbar[9];
+  double tbar[3];
+  double S[9];
+  double sigma_t, rho_a, r_trans, r_rot;
+};
+
+// Per-seed data: unit quaternion (w >= 0) and translation of the seed, the
+// axis u of R_0 R-bar^T (0 below 1e-9 rad) and the unit direction of
+// t_0 - t-bar (0 when degenerate).  16 doubles.
+constexpr int kSeedStride = 16;
+
+struct WalkArgs {
+  const void* table;
+  int n;
+  double fx, fy, cx, cy;
+  const double* seed_data;  // s0 x kSeedStride
+  int s0;
+  const WalkStats* stats;
+  int n_samples, n_iter, n_perturb, n_keep, n_steps;
+  double omega0, v0, gamma;
+  uint32_t key0, key1;
+  void* out_q;
+  void* out_t;
+  int16_t* trace;
+  int* status;
+  unsigned long long* evals;  // executed (pose, constraint) evaluations
+};
+
+}  // namespace purse
+
+struct purse_s {
+  int kind = 0;
+  int n = 0;
+  purse_intrinsics K{0, 0, 0, 0};
+  purse::purse_tables tables;
+  int* d_status = nullptr;
+  unsigned long long* d_evals = nullptr;  // evaluation counter of the last purse_sample
+  // scratch owned by the handle, grown on demand
+  void* d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+  // state kept by megb_solve
+  int megb_iters = 0;
+  int megb_precision = 0;
+  const void* megb_q = nullptr;
+  const void* megb_t = nullptr;
+  int megb_nrot = 0, megb_ntr = 0;
+  int sm_count = 0;
+};
+
+namespace purse {
+
+void set_error(const std::string& msg);
+purse_status cuda_fail(cudaError_t e, const char* where);
+purse_status ensure_scratch(purse_t h, size_t bytes);
+
+// Launchers (one translation unit each).
+cudaError_t launch_stats(purse_t h, const double* d_seeds, int s0, const purse_params* p, WalkStats* d_stats,
+                         double* d_seed_data, cudaStream_t st);
+cudaError_t launch_walk(purse_t h, const purse_params* p, const WalkArgs& a, cudaStream_t st);
+cudaError_t launch_ransag(purse_t h, uint64_t seed, int trial0, int n_trials, double* d_pose, uint8_t* d_acc,
+                          cudaStream_t st);
+cudaError_t launch_compact(const double* d_pose, const uint8_t* d_acc, int n_trials, double* d_seeds,
+                           int* d_count, int max_seeds, cudaStream_t st);
+cudaError_t launch_eval(purse_t h, int precision, const void* d_poses, int n_poses, void* d_margin,
+                        int32_t* d_active, void* d_grad, cudaStream_t st);
+cudaError_t launch_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t i, uint32_t w0, int n_streams,
+                             int n_words, uint32_t* d_words, int32_t* d_lattice, int unit, cudaStream_t st);
+size_t megb_scratch_bytes(int n_iters, int sm_count);
+cudaError_t launch_megb(purse_t h, int precision, int n_iters, const void* d_q, int n_rot, const void* d_t,
+                        int n_tr, double* d_result, int32_t* d_farthest, void* scratch, cudaStream_t st);
+
+}  // namespace purse

@@ -1,0 +1,215 @@
+// Minimum enclosing geodesic balls of the samples (Step III) by geodesic
+// gradient descent (Section II; step rule of Alg. 6):
+//   rotation:    f_k = argmax_s |vec(C_{k-1}^* q_s)|^2   (= sin^2 of half the
+//                geodesic distance, monotone on [0, pi]),
+//                C_k = SLERP(C_{k-1}, q_{f_k}, 1/k)
+//   translation: f_k = argmax_s |t_s - c_{k-1}|^2,  c_k = c_{k-1} + (t_f - c_{k-1}) / k
+// One launch per iteration: every block reduces its slice to a (key, index)
+// partial; the last block to finish (atomic ticket, no waiting) reduces the
+// partials and takes the step in FP64.  A final pass computes the radius from
+// the farthest sample with an FP64 log map.  Ties go to the lowest index.
+#include <climits>
+
+#include "dev.cuh"
+#include "internal.h"
+
+namespace purse {
+
+constexpr int kMegbThreads = 256;
+
+struct MegbState {
+  double C[4];
+  double c[4];
+  unsigned int counter[2];
+  unsigned int pad[2];
+};
+
+struct Part {
+  double key;
+  int idx;
+  int pad;
+};
+
+__host__ __device__ inline size_t megb_blocks_cap(int sm_count) { return 2 * (size_t)sm_count; }
+
+size_t megb_scratch_bytes(int n_iters, int sm_count) {
+  return sizeof(MegbState) + 2 * megb_blocks_cap(sm_count) * sizeof(Part) + 2 * (size_t)n_iters * sizeof(int32_t) + 256;
+}
+
+__device__ __forceinline__ bool better(double ka, int ia, double kb, int ib) {
+  return ka > kb || (ka == kb && ia < ib);
+}
+
+template <typename T>
+__global__ void megb_init(const T* q, int nq, const T* t, int nt, MegbState* s) {
+  if (threadIdx.x != 0) return;
+  if (nq > 0) {
+    const Q4<double> c = qnormalize(Q4<double>{(double)q[0], (double)q[1], (double)q[2], (double)q[3]});
+    s->C[0] = c.w, s->C[1] = c.x, s->C[2] = c.y, s->C[3] = c.z;
+  }
+  if (nt > 0) {
+    s->c[0] = t[0], s->c[1] = t[1], s->c[2] = t[2];
+  }
+  s->c[3] = 0.0;
+  s->counter[0] = s->counter[1] = 0;
+}
+
+// Squared sine of half the geodesic distance between centre (cw, cv) and q.
+template <typename T>
+__device__ __forceinline__ T rot_key(T cw, T cx, T cy, T cz, const T* qs) {
+  const T qw = qs[0], qx = qs[1], qy = qs[2], qz = qs[3];
+  // vector part of c^* (x) q = cw qv - qw cv - cv x qv
+  const T vx = cw * qx - qw * cx - (cy * qz - cz * qy);
+  const T vy = cw * qy - qw * cy - (cz * qx - cx * qz);
+  const T vz = cw * qz - qw * cz - (cx * qy - cy * qx);
+  return vx * vx + vy * vy + vz * vz;
+}
+
+// MODE 0: rotation ball, MODE 1: translation ball.  k >= 1: GGD step k; k == 0: final radius.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kMegbThreads)
+    ggd_step(const T* __restrict__ x, int n, MegbState* s, Part* parts, int k, int32_t* f_int, int32_t* f_out,
+             double* result) {
+  __shared__ double wkey[kMegbThreads / 32];
+  __shared__ int widx[kMegbThreads / 32];
+  __shared__ bool last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T c0, c1, c2, c3;
+  if (MODE == 0) {
+    c0 = T(s->C[0]), c1 = T(s->C[1]), c2 = T(s->C[2]), c3 = T(s->C[3]);
+  } else {
+    c0 = T(s->c[0]), c1 = T(s->c[1]), c2 = T(s->c[2]), c3 = T(0);
+  }
+  double bk = -1.0;
+  int bi = INT_MAX;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + tid; i < n; i += stride) {
+    T key;
+    if (MODE == 0) {
+      key = rot_key(c0, c1, c2, c3, x + 4 * (size_t)i);
+    } else {
+      const T* p = x + 3 * (size_t)i;
+      const T dx = p[0] - c0, dy = p[1] - c1, dz = p[2] - c2;
+      key = dx * dx + dy * dy + dz * dz;
+    }
+    if ((double)key > bk) bk = (double)key, bi = i;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const double ok = __shfl_xor_sync(kFullMask, bk, o);
+    const int oi = __shfl_xor_sync(kFullMask, bi, o);
+    if (better(ok, oi, bk, bi)) bk = ok, bi = oi;
+  }
+  if (lane == 0) wkey[warp] = bk, widx[warp] = bi;
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < kMegbThreads / 32; ++w)
+      if (better(wkey[w], widx[w], bk, bi)) bk = wkey[w], bi = widx[w];
+    parts[blockIdx.x] = Part{bk, bi, 0};
+    __threadfence();
+    const unsigned ticket = atomicAdd(&s->counter[MODE], 1u);
+    last = ticket == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  bk = -1.0, bi = INT_MAX;
+  for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+    // partials of other blocks: read from L2, bypassing this SM's L1
+    const double pk = __ldcg(&parts[b].key);
+    const int pi = __ldcg(&parts[b].idx);
+    if (better(pk, pi, bk, bi)) bk = pk, bi = pi;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const double ok = __shfl_xor_sync(kFullMask, bk, o);
+    const int oi = __shfl_xor_sync(kFullMask, bi, o);
+    if (better(ok, oi, bk, bi)) bk = ok, bi = oi;
+  }
+  if (lane == 0) wkey[warp] = bk, widx[warp] = bi;
+  __syncthreads();
+  if (tid != 0) return;
+  for (int w = 1; w < kMegbThreads / 32; ++w)
+    if (better(wkey[w], widx[w], bk, bi)) bk = wkey[w], bi = widx[w];
+  s->counter[MODE] = 0;
+  if (MODE == 0) {
+    const T* qs = x + 4 * (size_t)bi;
+    const Q4<double> c{s->C[0], s->C[1], s->C[2], s->C[3]};
+    const Q4<double> qf = qnormalize(Q4<double>{(double)qs[0], (double)qs[1], (double)qs[2], (double)qs[3]});
+    Q4<double> d = qmul(Q4<double>{c.w, -c.x, -c.y, -c.z}, qf);
+    if (d.w < 0) d = Q4<double>{-d.w, -d.x, -d.y, -d.z};
+    const double sn = sqrt(d.x * d.x + d.y * d.y + d.z * d.z);
+    const double th = 2.0 * atan2(sn, d.w);
+    if (k > 0) {
+      Q4<double> step{1.0, 0.0, 0.0, 0.0};
+      if (sn > 0.0) {
+        const double h = 0.5 * th / k;
+        const double sh = sin(h) / sn;
+        step = Q4<double>{cos(h), sh * d.x, sh * d.y, sh * d.z};
+      }
+      const Q4<double> cn = qnormalize(qmul(c, step));
+      s->C[0] = cn.w, s->C[1] = cn.x, s->C[2] = cn.y, s->C[3] = cn.z;
+    } else {
+      result[0] = c.w, result[1] = c.x, result[2] = c.y, result[3] = c.z;
+      result[7] = th;
+    }
+  } else {
+    const T* p = x + 3 * (size_t)bi;
+    if (k > 0) {
+      for (int d = 0; d < 3; ++d) s->c[d] = s->c[d] + ((double)p[d] - s->c[d]) / k;
+    } else {
+      const double dx = (double)p[0] - s->c[0], dy = (double)p[1] - s->c[1], dz = (double)p[2] - s->c[2];
+      result[4] = s->c[0], result[5] = s->c[1], result[6] = s->c[2];
+      result[8] = sqrt(dx * dx + dy * dy + dz * dz);
+    }
+  }
+  if (k > 0) {
+    f_int[k - 1] = bi;
+    if (f_out) f_out[k - 1] = bi;
+  }
+}
+
+__global__ void megb_zero_result(double* result, int skip_rot, int skip_tr) {
+  if (threadIdx.x != 0) return;
+  if (skip_rot) result[0] = result[1] = result[2] = result[3] = result[7] = 0.0;
+  if (skip_tr) result[4] = result[5] = result[6] = result[8] = 0.0;
+}
+
+template <typename T>
+static cudaError_t launch_megb_t(purse_t h, int n_iters, const T* q, int nq, const T* t, int nt, double* result,
+                                 int32_t* f_out, void* scratch, cudaStream_t st) {
+  MegbState* s = reinterpret_cast<MegbState*>(scratch);
+  Part* parts = reinterpret_cast<Part*>(reinterpret_cast<char*>(scratch) + sizeof(MegbState));
+  int32_t* f_int = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(parts) + 2 * megb_blocks_cap(h->sm_count) * sizeof(Part));
+  megb_init<T><<<1, 32, 0, st>>>(q, nq, t, nt, s);
+  megb_zero_result<<<1, 32, 0, st>>>(result, nq == 0, nt == 0);
+  const long cap = (long)megb_blocks_cap(h->sm_count);
+  if (nq > 0) {
+    const long want = (nq + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
+    const int g = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+    for (int k = 1; k <= n_iters; ++k)
+      ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, k, f_int, f_out, result);
+    ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, 0, f_int, f_out, result);
+  }
+  if (nt > 0) {
+    const long want = (nt + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
+    const int g = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+    Part* parts_t = parts + cap;
+    for (int k = 1; k <= n_iters; ++k)
+      ggd_step<T, 1><<<g, kMegbThreads, 0, st>>>(t, nt, s, parts_t, k, f_int + n_iters, f_out ? f_out + n_iters : nullptr,
+                                                  result);
+    ggd_step<T, 1><<<g, kMegbThreads, 0, st>>>(t, nt, s, parts_t, 0, f_int + n_iters, nullptr, result);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_megb(purse_t h, int precision, int n_iters, const void* d_q, int n_rot, const void* d_t, int n_tr,
+                        double* d_result, int32_t* d_farthest, void* scratch, cudaStream_t st) {
+  if (precision == 0)
+    return launch_megb_t<float>(h, n_iters, (const float*)d_q, n_rot, (const float*)d_t, n_tr, d_result, d_farthest,
+                                scratch, st);
+  return launch_megb_t<double>(h, n_iters, (const double*)d_q, n_rot, (const double*)d_t, n_tr, d_result, d_farthest,
+                               scratch, st);
+}
+
+}  // namespace purse

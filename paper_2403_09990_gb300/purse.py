@@ -1,0 +1,187 @@
+"""Thin ctypes binding of libpurse (include/purse.h).
+
+Argument marshalling only: every function forwards to the C ABI function of
+the same name with raw device pointers (``tensor.data_ptr()``) and the
+current CUDA stream.  Nothing here computes a step of the method, and there
+is no CPU fallback: if the library is missing, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+PURSE_3D3D, PURSE_2D3D = 0, 1
+STATUS = {0: "PURSE_OK", 1: "PURSE_ERR_ARG", 2: "PURSE_ERR_CUDA", 3: "PURSE_ERR_EMPTY", 4: "PURSE_ERR_TIMEOUT",
+          5: "PURSE_ERR_NOMEM", 6: "PURSE_ERR_NUMERIC", 7: "PURSE_ERR_STATE"}
+
+
+class PurseError(RuntimeError):
+    def __init__(self, status: int, fn: str, msg: str):
+        super().__init__(f"{fn}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class purse_intrinsics(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double)]
+
+
+class purse_params(ctypes.Structure):
+    _fields_ = [("n_iter", ctypes.c_int), ("n_perturb", ctypes.c_int), ("n_keep", ctypes.c_int),
+                ("n_steps", ctypes.c_int), ("omega0", ctypes.c_double), ("v0", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("rot_perturb", ctypes.c_double), ("trans_perturb", ctypes.c_double),
+                ("perturb_units", ctypes.c_int), ("sampler", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+def make_params(n_iter=5, n_perturb=150, n_keep=10, n_steps=15, omega0=1.0, v0=2.0, gamma=0.5, rot_perturb=0.2,
+                trans_perturb=0.1, perturb_units=0, sampler=0, precision=0) -> purse_params:
+    return purse_params(n_iter, n_perturb, n_keep, n_steps, omega0, v0, gamma, rot_perturb, trans_perturb,
+                        perturb_units, sampler, precision)
+
+
+_LIB = None
+_VP = ctypes.c_void_p
+_SIGS = {
+    "purse_create": [ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)],
+    "purse_destroy": [_VP],
+    "purse_eval": [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP, _VP],
+    "purse_ransag": [_VP, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int), _VP],
+    "purse_sample": [_VP, ctypes.POINTER(purse_params), ctypes.c_uint64, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP,
+                     _VP, _VP],
+    "purse_last_evals": [_VP, ctypes.POINTER(ctypes.c_ulonglong), _VP],
+    "megb_solve": [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP],
+    "purse_rng_words": [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                        ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP],
+    "purse_sync": [_VP, _VP],
+    "purse_last_error": [],
+    "purse_version": [],
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True) -> ctypes.CDLL:
+    """The loaded libpurse.so (built in-tree on first use)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libpurse.so not built ({path})")
+            path = _build.build()
+        L = ctypes.CDLL(path)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name in ("purse_last_error", "purse_version") else ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(status: int, fn: str):
+    if status != 0:
+        raise PurseError(status, fn, lib().purse_last_error().decode())
+
+
+def purse_create(kind: int, model, obs, radii, K=None) -> int:
+    """Host arrays (numpy float64, contiguous) -> handle."""
+    import numpy as np
+    model = np.ascontiguousarray(model, dtype=np.float64)
+    obs = np.ascontiguousarray(obs, dtype=np.float64)
+    radii = np.ascontiguousarray(radii, dtype=np.float64)
+    Kp = ctypes.byref(purse_intrinsics(*K)) if K is not None else None
+    h = _VP()
+    _check(lib().purse_create(kind, radii.shape[0], model.ctypes.data, obs.ctypes.data, radii.ctypes.data, Kp,
+                              ctypes.byref(h)), "purse_create")
+    return h.value
+
+
+def purse_destroy(h: int):
+    _check(lib().purse_destroy(h), "purse_destroy")
+
+
+def purse_eval(h, precision, poses, n_poses, margin=None, active=None, grad=None, stream=None):
+    _check(lib().purse_eval(h, precision, _ptr(poses), n_poses, _ptr(margin), _ptr(active), _ptr(grad),
+                            _stream(stream)), "purse_eval")
+
+
+def purse_ransag(h, seed, n_trials, max_seeds, seeds, stream=None) -> int:
+    n = ctypes.c_int(0)
+    _check(lib().purse_ransag(h, seed, n_trials, max_seeds, _ptr(seeds), ctypes.byref(n), _stream(stream)),
+           "purse_ransag")
+    return n.value
+
+
+def purse_sample(h, params: purse_params, seed, seeds, s0, n_samples, q, t, trace=None, stream=None):
+    _check(lib().purse_sample(h, ctypes.byref(params), seed, _ptr(seeds), s0, n_samples, _ptr(q), _ptr(t),
+                              _ptr(trace), _stream(stream)), "purse_sample")
+
+
+def purse_last_evals(h, stream=None) -> int:
+    v = ctypes.c_ulonglong(0)
+    _check(lib().purse_last_evals(h, ctypes.byref(v), _stream(stream)), "purse_last_evals")
+    return v.value
+
+
+def megb_solve(h, precision, n_iters, q, n_rot, t, n_tr, result, farthest=None, stream=None):
+    _check(lib().megb_solve(h, precision, n_iters, _ptr(q), n_rot, _ptr(t), n_tr, _ptr(result), _ptr(farthest),
+                            _stream(stream)), "megb_solve")
+
+
+def purse_rng_words(seed, phase, j, i, w0, n_streams, n_words, words, lattice=None, unit=0, stream=None):
+    _check(lib().purse_rng_words(seed, phase, j, i, w0, n_streams, n_words, _ptr(words), _ptr(lattice), unit,
+                                 _stream(stream)), "purse_rng_words")
+
+
+def purse_sync(h, stream=None):
+    _check(lib().purse_sync(h, _stream(stream)), "purse_sync")
+
+
+def version() -> str:
+    return lib().purse_version().decode()
+
+
+class Purse:
+    """Owning wrapper of a PURSE handle built from a synthetic.Purse-like object."""
+
+    def __init__(self, p):
+        self.kind = int(p.kind)
+        self.n = int(p.radii.shape[0])
+        self.h = purse_create(self.kind, p.model, p.obs, p.radii, p.K if self.kind == PURSE_2D3D else None)
+
+    def close(self):
+        if self.h:
+            purse_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

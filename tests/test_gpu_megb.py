@@ -1,0 +1,105 @@
+"""GGD ball kernels against the oracle: the GPU's farthest-sample sequence is
+checked against FP64 distances (within the rounding band) and replayed; the
+centres, D-hat and d-hat must agree with FP64."""
+import numpy as np
+import pytest
+
+from oracle import megb as om
+from oracle import so3
+from paper_2403_09990_gb300 import purse as P
+from paper_2403_09990_gb300 import synthetic as syn
+from tests import parity
+from tests.gpu_helpers import megb
+
+pytestmark = pytest.mark.gpu
+
+EPS = {0: 2.0 ** -23, 1: 2.0 ** -52}
+
+
+def rot_keys(C, qs):
+    d = so3.quat_mul(so3.quat_conj(C)[None], qs)
+    return (d[:, 1:] ** 2).sum(1)
+
+
+def check_rotation(q64, res, f, precision):
+    K = len(f)
+    qs = om.canonical(q64)
+    Cs = om.megb_rotation_replay(qs, f)
+    for k in range(1, K + 1):
+        keys = rot_keys(Cs[k - 1], qs)
+        band = 64 * EPS[precision] * (np.sqrt(keys.max()) + EPS[precision])
+        assert keys[f[k - 1]] >= keys.max() - band, (k, keys[f[k - 1]], keys.max())
+    C = Cs[-1]
+    assert parity.rot_angle(res[:4], C) <= 1e-9
+    D = om.rotation_distances(C, qs).max()
+    assert abs(res[7] - D) <= 1e-5 * D + 1e-12, (res[7], D)
+    return C, D
+
+
+def check_translation(t64, res, f, precision):
+    K = len(f)
+    cs = om.megb_translation_replay(t64, f)
+    scale = np.abs(t64).max()
+    for k in range(1, K + 1):
+        keys = ((t64 - cs[k - 1]) ** 2).sum(1)
+        band = 16 * EPS[precision] * scale * (np.sqrt(keys.max()) + EPS[precision] * scale)
+        assert keys[f[k - 1]] >= keys.max() - band
+    c = cs[-1]
+    assert np.abs(res[4:7] - c).max() <= 1e-12 * (1 + scale)
+    d = np.sqrt(((t64 - c) ** 2).sum(1)).max()
+    assert abs(res[8] - d) <= 1e-5 * d + 1e-12
+    return c, d
+
+
+def cluster(n, seed, spread=(0.02, 0.05, 0.1)):
+    rng = np.random.default_rng(seed)
+    C0 = so3.quat_from_R(so3.exp_so3(rng.normal(size=3)))
+    q = so3.quat_mul(so3.quat_exp(rng.normal(size=(n, 3)) * np.array(spread)), C0[None])
+    t = rng.normal(size=(n, 3)) * np.array([0.003, 0.003, 0.03]) + rng.normal(size=3)
+    return q, t
+
+
+@pytest.mark.parametrize("n,K,precision", [(1, 5, 0), (2, 7, 0), (1000, 200, 0), (4096, 200, 1), (4096, 200, 0),
+                                           (1 << 18, 200, 0), (77777, 50, 1)])
+def test_megb_replay(n, K, precision):
+    q, t = cluster(n, n)
+    dt = np.float32 if precision == 0 else np.float64
+    q32, t32 = q.astype(dt), t.astype(dt)
+    with P.Purse(syn.purse_3d3d(8, 0)) as h:
+        res, far = megb(h.h, precision, K, q32, t32)
+    assert far.min() >= 0 and far.max() < n
+    q64, t64 = q32.astype(np.float64), t32.astype(np.float64)
+    C, D = check_rotation(q64, res, far[:K], precision)
+    c, d = check_translation(t64, res, far[K:], precision)
+    if n == 1:
+        assert res[7] <= 1e-12 and res[8] <= 1e-12
+    # containment and diameter bounds on a subsample
+    sub = np.random.default_rng(0).choice(n, min(n, 2000), replace=False)
+    dq = om.rotation_distances(res[:4], om.canonical(q64[sub]))
+    assert np.all(dq <= res[7] + 1e-12)
+    dmax = max(so3.dist_quat(om.canonical(q64[s])[None], om.canonical(q64[sub])).max() for s in sub[:200])
+    assert res[7] >= dmax / 2 - 1e-12
+
+
+def test_megb_one_ball_only():
+    q, t = cluster(500, 3)
+    with P.Purse(syn.purse_3d3d(8, 0)) as h:
+        res, far = megb(h.h, 0, 20, q.astype(np.float32), None)
+        assert res[8] == 0 and np.all(res[4:7] == 0) and res[7] > 0
+        res2, _ = megb(h.h, 0, 20, None, t.astype(np.float32))
+        assert res2[7] == 0 and res2[8] > 0
+
+
+def test_megb_closed_form_geodesic():
+    # rotations about one axis: the ball is the middle of the arc with radius half its length
+    rng = np.random.default_rng(1)
+    C0 = so3.quat_from_R(so3.exp_so3(rng.normal(size=3)))
+    u = rng.normal(size=3)
+    u /= np.linalg.norm(u)
+    ang = rng.uniform(-0.3, 0.5, 3000)
+    q = so3.quat_mul(so3.quat_exp(ang[:, None] * u), C0[None])
+    K = 400
+    with P.Purse(syn.purse_3d3d(8, 0)) as h:
+        res, _ = megb(h.h, 1, K, q, None)
+    half = 0.5 * (ang.max() - ang.min())
+    assert half * (1 - 1e-12) <= res[7] <= half * (1 + 1 / np.sqrt(K))
