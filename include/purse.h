@@ -129,6 +129,20 @@ purse_status megb_solve(purse_t h, int precision, int n_iters, const void* d_q, 
                         const void* d_t, int n_tr, double* d_result, int32_t* d_farthest,
                         purse_stream_t stream);
 
+/* megb_solve without any device allocation, for callers that must not allocate device memory
+ * once they are running: real-time perception loops that reserve all memory at start-up
+ * (cudaMalloc / cudaFree can synchronise the device and take unbounded time), and hosts whose
+ * device memory is owned by another allocator.  The paper has no counterpart; the computation
+ * and outputs are those of megb_solve, without a PURSE handle.
+ * Scratch: one 64 KiB array in the library's device memory, which every GPU that loads the
+ * library holds until the process exits.  Limits: n_iters <= 4096 (PURSE_ERR_ARG beyond).
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the one array and a call
+ * leaves its contents behind (it re-initialises what must start at zero), so calls whose
+ * work overlaps on the GPU (other streams, other host threads) race: serialise them. */
+purse_status megb_solve_noalloc(int precision, int n_iters, const void* d_q, int n_rot, const void* d_t, int n_tr,
+                                double* d_result, int32_t* d_farthest, purse_stream_t stream);
+
 /* The walks' random streams, exposed for verification: for streams w = w0 .. w0+n_streams-1
  * named (phase, j, i, w) under key = seed, writes their first n_words Philox4x32-10 words to
  * d_words (device, n_streams x n_words uint32) and, if d_lattice is not NULL, the first accepted

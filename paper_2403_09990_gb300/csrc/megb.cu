@@ -9,6 +9,7 @@
 // partials and takes the step in FP64.  A final pass computes the radius from
 // the farthest sample with an FP64 log map.  Ties go to the lowest index.
 #include <climits>
+#include <mutex>
 
 #include "dev.cuh"
 #include "internal.h"
@@ -212,4 +213,103 @@ cudaError_t launch_megb(purse_t h, int precision, int n_iters, const void* d_q, 
                                scratch, st);
 }
 
+// ---------------------------------------------------------------- allocation-free variant
+// megb_solve_noalloc runs the same kernels as megb_solve, but its scratch (ball state,
+// per-block partial maxima, farthest-sample sequence) lives in one file-scope device array
+// instead of handle-owned cudaMalloc memory.  Limits: at most kNoAllocMaxIters GGD
+// iterations; the grid is capped at kNoAllocMaxBlocks blocks.
+constexpr int kNoAllocMaxIters = 4096;
+constexpr int kNoAllocMaxBlocks = 512;
+constexpr size_t kNoAllocStateBytes = 256;
+constexpr size_t kNoAllocBytes = 65536;
+static_assert(sizeof(MegbState) <= kNoAllocStateBytes, "state slot too small");
+static_assert(kNoAllocStateBytes + 2 * kNoAllocMaxBlocks * sizeof(Part) + 2 * kNoAllocMaxIters * sizeof(int32_t) <=
+                  kNoAllocBytes,
+              "no-alloc scratch too small");
+
+// Every GPU that loads the library holds these 64 KiB until the process exits.
+static __device__ __align__(256) unsigned char g_megb_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+static int g_noalloc_sms[kNoAllocMaxDevices] = {};
+
+// Device address of the static scratch on the current device (looked up once per device).
+static cudaError_t noalloc_scratch(void** ptr, int* sms) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_megb_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+    g_noalloc_sms[dev] = n;
+  }
+  *ptr = g_noalloc_ptr[dev];
+  *sms = g_noalloc_sms[dev];
+  return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t launch_megb_noalloc_t(int sms, int n_iters, const T* q, int nq, const T* t, int nt, double* result,
+                                         int32_t* f_out, void* scratch, cudaStream_t st) {
+  MegbState* s = reinterpret_cast<MegbState*>(scratch);
+  Part* parts = reinterpret_cast<Part*>(reinterpret_cast<char*>(scratch) + kNoAllocStateBytes);
+  int32_t* f_int = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(parts) + 2 * kNoAllocMaxBlocks * sizeof(Part));
+  const long cap = 2L * sms < kNoAllocMaxBlocks ? 2L * sms : kNoAllocMaxBlocks;
+  megb_init<T><<<1, 32, 0, st>>>(q, nq, t, nt, s);  // also zeroes the completion counters
+  megb_zero_result<<<1, 32, 0, st>>>(result, nq == 0, nt == 0);
+  if (nq > 0) {
+    const long want = (nq + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
+    const int g = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+    for (int k = 1; k <= n_iters; ++k)
+      ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, k, f_int, f_out, result);
+    ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, 0, f_int, f_out, result);
+  }
+  if (nt > 0) {
+    const long want = (nt + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
+    const int g = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+    Part* parts_t = parts + kNoAllocMaxBlocks;
+    for (int k = 1; k <= n_iters; ++k)
+      ggd_step<T, 1><<<g, kMegbThreads, 0, st>>>(t, nt, s, parts_t, k, f_int + n_iters,
+                                                  f_out ? f_out + n_iters : nullptr, result);
+    ggd_step<T, 1><<<g, kMegbThreads, 0, st>>>(t, nt, s, parts_t, 0, f_int + n_iters, nullptr, result);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace purse
+
+extern "C" purse_status megb_solve_noalloc(int precision, int n_iters, const void* d_q, int n_rot, const void* d_t,
+                                           int n_tr, double* d_result, int32_t* d_farthest, purse_stream_t stream) {
+  using namespace purse;
+  if (precision != 0 && precision != 1) {
+    set_error("megb_solve_noalloc: precision must be 0 or 1");
+    return PURSE_ERR_ARG;
+  }
+  if (n_iters < 1 || n_iters > kNoAllocMaxIters) {
+    set_error("megb_solve_noalloc: n_iters must be in [1, 4096] (size of the static scratch)");
+    return PURSE_ERR_ARG;
+  }
+  if (n_rot < 0 || n_tr < 0 || (n_rot > 0 && !d_q) || (n_tr > 0 && !d_t) || !d_result) {
+    set_error("megb_solve_noalloc: negative sample count or NULL buffer");
+    return PURSE_ERR_ARG;
+  }
+  void* scratch = nullptr;
+  int sms = 0;
+  cudaError_t e = noalloc_scratch(&scratch, &sms);
+  if (e != cudaSuccess) return cuda_fail(e, "megb_solve_noalloc (static scratch address)");
+  cudaStream_t st = (cudaStream_t)stream;
+  e = precision == 0 ? launch_megb_noalloc_t<float>(sms, n_iters, (const float*)d_q, n_rot, (const float*)d_t, n_tr,
+                                                    d_result, d_farthest, scratch, st)
+                     : launch_megb_noalloc_t<double>(sms, n_iters, (const double*)d_q, n_rot, (const double*)d_t,
+                                                     n_tr, d_result, d_farthest, scratch, st);
+  return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "megb_solve_noalloc");
+}

@@ -51,6 +51,7 @@ _SIGS = {
                      _VP, _VP],
     "purse_last_evals": [_VP, ctypes.POINTER(ctypes.c_ulonglong), _VP],
     "megb_solve": [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP],
+    "megb_solve_noalloc": [ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP],
     "purse_rng_words": [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                         ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP],
     "purse_sync": [_VP, _VP],
@@ -146,6 +147,11 @@ def purse_last_evals(h, stream=None) -> int:
 def megb_solve(h, precision, n_iters, q, n_rot, t, n_tr, result, farthest=None, stream=None):
     _check(lib().megb_solve(h, precision, n_iters, _ptr(q), n_rot, _ptr(t), n_tr, _ptr(result), _ptr(farthest),
                             _stream(stream)), "megb_solve")
+
+
+def megb_solve_noalloc(precision, n_iters, q, n_rot, t, n_tr, result, farthest=None, stream=None):
+    _check(lib().megb_solve_noalloc(precision, n_iters, _ptr(q), n_rot, _ptr(t), n_tr, _ptr(result), _ptr(farthest),
+                                    _stream(stream)), "megb_solve_noalloc")
 
 
 def purse_rng_words(seed, phase, j, i, w0, n_streams, n_words, words, lattice=None, unit=0, stream=None):
