@@ -44,7 +44,7 @@ FP32_LANES_PER_SM = 128
 def workload_config():
     return {
         "workload": "2D-3D PURSE N=16 (pinhole 600/600/320/240, r_i~U[2,10] px, depth U[0.5,1.5] m); "
-                    "2^20 walks per sampler x 100 iterations (N_P=150, N_P*=10, N_T=15); "
+                    f"{N_WALKS} walks per sampler x {N_ITER} iterations (N_P=150, N_P*=10, N_T=15); "
                     "rotation + translation MEGB, 200 GGD iterations",
         "n_keypoints": N_KEYPOINTS, "walks_per_sampler": N_WALKS, "n_iter": N_ITER, "megb_iters": K_MEGB,
         "precision": "fp32 walk arithmetic, fp64 centre statistics and ball centres",
@@ -57,9 +57,9 @@ def make_purse(rank=0):
     return syn.purse_2d3d(N_KEYPOINTS, PURSE_SEED + rank)
 
 
-def closure_params(sampler, n_iter=N_ITER, precision=0):
+def closure_params(sampler, n_iter=None, precision=0):
     import paper_2403_09990_gb300.purse as P
-    return P.make_params(n_iter=n_iter, n_perturb=150, n_keep=10, n_steps=15, omega0=1.0, v0=2.0, gamma=0.5,
+    return P.make_params(n_iter=N_ITER if n_iter is None else n_iter, n_perturb=150, n_keep=10, n_steps=15, omega0=1.0, v0=2.0, gamma=0.5,
                          rot_perturb=0.2, trans_perturb=0.1, perturb_units=0, sampler=sampler, precision=precision)
 
 
@@ -131,9 +131,10 @@ def _oracle_chunk(args):
     return evals, dt, q, t
 
 
-def oracle_sample(walks_per_worker, workers, n_iter=N_ITER, rank=0):
+def oracle_sample(walks_per_worker, workers, n_iter=None, rank=0):
     """The oracle on a bounded sample of the workload: both samplers, then both balls."""
     import multiprocessing as mp
+    n_iter = N_ITER if n_iter is None else n_iter
     from oracle import megb as om
     ctx = mp.get_context("spawn")
     jobs = []
@@ -287,7 +288,7 @@ def run_gpu(args, rank, world):
     if rank == 0 and not args.no_cpu_baseline:
         ev_c, wall_c, walks_c = oracle_sample(args.cpu_walks, args.cpu_workers)
         out["cpu_baseline"] = {"value": ev_c / wall_c, "unit": UNIT, "cores": args.cpu_workers, "kind": "oracle",
-                               "sample": f"{walks_c} walks ({args.cpu_walks} per worker, both samplers, N_I=100) "
+                               "sample": f"{walks_c} walks ({args.cpu_walks} per worker, both samplers, N_I={N_ITER}) "
                                          f"+ both balls (200 GGD iterations); {wall_c:.1f} s"}
     hR.close()
     hT.close()
@@ -360,23 +361,27 @@ def run_reference(args, rank, world):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": dict(workload_config(), parallelism="host cores"),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": args.cpu_workers, "kind": "oracle",
-                            "sample": f"per step {walks} walks (both samplers, N_I=100) + both balls"},
+                            "sample": f"per step {walks} walks (both samplers, N_I={N_ITER}) + both balls"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
 def main():
+    global N_WALKS, N_ITER
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--cpu-walks", type=int, default=4, help="oracle walks per worker per sampler (cpu_baseline)")
+    ap.add_argument("--cpu-walks", type=int, default=48, help="oracle walks per worker per sampler (cpu_baseline)")
     ap.add_argument("--ref-walks", type=int, default=2, help="oracle walks per worker per sampler (reference arm)")
     ap.add_argument("--cpu-workers", type=int, default=min(16, cpu_cores()))
+    ap.add_argument("--walks", type=int, default=N_WALKS, help="walks per sampler (profiling of a smaller case)")
+    ap.add_argument("--iters", type=int, default=N_ITER, help="walk iterations (profiling of a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    N_WALKS, N_ITER = args.walks, args.iters
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus))
     if args.impl == "reference":
