@@ -14,7 +14,8 @@ Restates, in the paper's order and notation,
 Readings of the paper used here (each listed in the design doc):
 * update_rotation(R*, omega, dT) = Exp(dT omega) R*, translation unchanged;
   update_translation(t*, R_jk, v, dT) = t* + dT v (R_jk unused).
-* perturbation(t_p) is a point uniform in the ball of radius t_p * sigma_t,
+* perturbation(t_p) is a point uniform in the ball of radius t_p * sigma_t
+  (hat-box direction, radius whose cube is uniform; oracle.philox),
   perturbation(theta_p) is Exp of a vector uniform in the ball of radius
   theta_p * sigma_t / rho_a, where sigma_t is the PURSE translation scale
   (mean r_i for 3D-3D, mean r_i * t-bar_z / f for 2D-3D) and rho_a the RMS
@@ -28,11 +29,12 @@ Readings of the paper used here (each listed in the design doc):
   S = u1 u1^T + (rho_a / |t-bar|)(I - u1 u1^T) with u1 = t-bar/|t-bar| (the
   viewing ray, along which a 2D-3D PURSE is long).
 * Walk w starts from seed (w mod |S0|); its random draws are the Philox
-  streams of oracle.philox named by w.
+  streams of oracle.philox named by w; perturbations 2b and 2b + 1 of an
+  iteration come from one Philox block.
 
-Parity: pinned in tests/test_oracle_walk.py (unit-ball example of the
-appendix, octahedral PURSE with closed-form radii, Prop. 1, membership of
-every output sample).
+Parity: pinned in tests/test_oracle_walk.py (octahedral PURSE with
+closed-form radii and Prop. 1, membership of every output sample, the
+needle shape of a 2D-3D PURSE, seeds-versus-walks spread).
 """
 from __future__ import annotations
 
@@ -171,8 +173,7 @@ class Candidates:
 
 def rotation_walk_candidates(purse, R, t, omega, i, walk_ids, seed, params: Params, stats: Stats):
     """One iteration of Alg. 3 up to in_purse."""
-    j = np.arange(params.n_perturb)
-    delta, _ = philox.ball_points(seed, philox.PHASE_R_PERTURB, j[None, :], i, walk_ids[:, None])
+    delta = philox.hatbox_points(seed, philox.PHASE_R_PERTURB, i, walk_ids, params.n_perturb)
     tj = t[:, None, :] + stats.r_trans * delta                    # t* + perturbation(t_p)
     d = dist_to_boundary(purse, R[:, None], tj)                   # eq. 11
     J = top_k_indices(d, params.n_keep)
@@ -186,8 +187,7 @@ def rotation_walk_candidates(purse, R, t, omega, i, walk_ids, seed, params: Para
 
 def translation_walk_candidates(purse, R, t, v, i, walk_ids, seed, params: Params, stats: Stats):
     """One iteration of Alg. 5 up to in_purse."""
-    j = np.arange(params.n_perturb)
-    phi, _ = philox.ball_points(seed, philox.PHASE_T_PERTURB, j[None, :], i, walk_ids[:, None])
+    phi = philox.hatbox_points(seed, philox.PHASE_T_PERTURB, i, walk_ids, params.n_perturb)
     Rj = exp_so3(stats.r_rot * phi) @ R[:, None]                  # perturbation(theta_p) R*
     d = dist_to_boundary(purse, Rj, t[:, None])                   # eq. 11
     J = top_k_indices(d, params.n_keep)

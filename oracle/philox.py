@@ -11,14 +11,22 @@ Stream layout (the CUDA side implements the same definition on its own):
 a stream is named by (key, phase, j, i, w) and its word k is
     philox(ctr = (k >> 2, (phase << 24) | j, i, w), key = (lo32, hi32))[k & 3].
 phase: 1 translation perturbations of the rotation-boundary walk (Alg. 3),
-2 rotation perturbations of the translation-boundary walk (Alg. 5),
+2 rotation perturbations of the translation-boundary walk (Alg. 5) -- for
+these two, perturbations j = 2b and 2b + 1 of iteration i of walk w are the
+two points of block 0 of stream (phase, b, i, w) (see hatbox_points);
 3 the random unit vector of init_angular_velocity, 4 that of
 init_center_velocity, 5 one RANSAG trial (w = trial index; j = 0 gives
 the three constraint indices, j = 1, 2, 3 the three points drawn inside
 the chosen noise balls).
 A batched PURSE p uses key = seed + p (mod 2^64).
 
-Uniform ball points are drawn by integer rejection on a symmetric lattice so
+Perturbation points (phases 1, 2) use no rejection: point h of a block takes
+words 2h, 2h + 1 = (w0, w1); the direction follows Archimedes' hat-box theorem
+with z = ((w0 >> 16) + 1/2) / 2^15 - 1 and azimuth pi x, x = ((w0 & 0xFFFF) +
+1/2) / 2^15; the radius is (max of the three 10-bit fields of w1 + 1/2) / 2^10,
+whose cube is uniform, so the point is uniform in the unit ball.
+
+Other uniform ball points are drawn by integer rejection on a symmetric lattice so
 both sides take the same accept decisions: attempt a uses word a of the
 stream and X_c = 2 ((word >> 10c) & 1023) - 1023 for c = 0, 1, 2 (odd
 integers in [-1023, 1023]); it is accepted when sum X_c^2 <= 2^20 and the
@@ -126,6 +134,22 @@ def ball_points(seed: int, phase: int, j, i, w, unit: bool = False):
                 used[take] = a0 + a + 1
                 done |= take
     return pts, used
+
+
+def hatbox_points(seed: int, phase: int, i, w, n_points: int):
+    """Perturbation points j = 0..n_points-1 of iteration i of walks w: (..., n_points, 3)."""
+    w = np.asarray(w, dtype=np.uint64)
+    j = np.arange(n_points)
+    words = stream_words(seed, phase, (j >> 1).astype(np.uint64), i, w[..., None], 4)     # (..., n_points, 4)
+    h = (j & 1)[None, :] if w.ndim else (j & 1)
+    w0 = np.take_along_axis(words, np.broadcast_to(2 * h, words.shape[:-1])[..., None], -1)[..., 0].astype(np.int64)
+    w1 = np.take_along_axis(words, np.broadcast_to(2 * h + 1, words.shape[:-1])[..., None], -1)[..., 0].astype(np.int64)
+    z = ((w0 >> 16) + 0.5) / 32768.0 - 1.0
+    x = ((w0 & 0xFFFF) + 0.5) / 32768.0
+    k = np.maximum(np.maximum(w1 & 1023, (w1 >> 10) & 1023), (w1 >> 20) & 1023)
+    rho = (k + 0.5) / 1024.0
+    s = np.sqrt(1.0 - z * z)
+    return rho[..., None] * np.stack([s * np.cos(np.pi * x), s * np.sin(np.pi * x), z], axis=-1)
 
 
 def uniform_index(word, n):

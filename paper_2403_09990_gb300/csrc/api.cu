@@ -206,6 +206,10 @@ purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const
   a.n_iter = p->n_iter, a.n_perturb = p->n_perturb, a.n_keep = p->n_keep, a.n_steps = p->n_steps;
   a.omega0 = p->omega0, a.v0 = p->v0, a.gamma = p->gamma;
   a.key0 = (uint32_t)seed, a.key1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    a.rk[2 * r] = a.key0 + (uint32_t)r * 0x9E3779B9u;
+    a.rk[2 * r + 1] = a.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
   a.out_q = d_q, a.out_t = d_t;
   a.trace = d_trace;
   a.status = h->d_status;

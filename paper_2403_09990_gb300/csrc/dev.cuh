@@ -43,6 +43,37 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, ui
   return c;
 }
 
+// Philox4x32-10 with the ten round keys given (rk[2r], rk[2r+1]) = (k0 + r W0, k1 + r W1).
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk[2 * r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk[2 * r + 1],
+                   (uint32_t)p0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ void sin_cos_pi(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sin_cos_pi(double x, double* s, double* c) { sincospi(x, s, c); }
+
+// Perturbation point from two words (no rejection): hat-box direction with
+// z = ((w0 >> 16) + 1/2) 2^-15 - 1 and azimuth pi ((w0 & 0xFFFF) + 1/2) 2^-15, radius
+// (max of the three 10-bit fields of w1 + 1/2) 2^-10, whose cube is uniform; so the
+// point is uniform in the unit ball.  z, the azimuth fraction and the radius are exact.
+template <typename T>
+__device__ __forceinline__ void hatbox_point(uint32_t w0, uint32_t w1, T& x, T& y, T& z) {
+  const T zz = T((int)(w0 >> 16)) * T(1.0 / 32768) + T(0.5 / 32768 - 1.0);
+  const T az = T((int)(w0 & 0xFFFFu)) * T(1.0 / 32768) + T(0.5 / 32768);
+  const uint32_t k = max(max(w1 & 1023u, (w1 >> 10) & 1023u), (w1 >> 20) & 1023u);
+  const T rho = T((int)k) * T(1.0 / 1024) + T(0.5 / 1024);
+  T sp, cp;
+  sin_cos_pi(az, &sp, &cp);
+  const T s = rho * sqrt(T(1) - zz * zz);
+  x = s * cp, y = s * sp, z = rho * zz;
+}
+
 // Words of the stream named (phase, j, i, w) under key (k0, k1), in order.
 struct Stream {
   uint32_t k0, k1, c1, c2, c3, block;
@@ -264,6 +295,45 @@ __device__ __forceinline__ Q4<double> rotation_maximising_trace(const double* M)
   for (int k = 1; k < 4; ++k)
     if (N[k][k] > N[best][best]) best = k;
   return qnormalize(Q4<double>{V[0][best], V[1][best], V[2][best], V[3][best]});
+}
+
+// ---------------------------------------------------------------- paired arithmetic
+// Two independent lanes of arithmetic per thread: float2 maps to the paired FP32
+// instructions of sm_100+ (one issue slot for two FMAs), double2 to two scalar ops.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 rsq2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+__device__ __forceinline__ float2 min2(float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fminf(a.y, b.y)); }
+__device__ __forceinline__ float2 max2(float2 a, float2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 rsq2(double2 a) { return make_double2(rsqrt(a.x), rsqrt(a.y)); }
+__device__ __forceinline__ double2 min2(double2 a, double2 b) { return make_double2(fmin(a.x, b.x), fmin(a.y, b.y)); }
+__device__ __forceinline__ double2 max2(double2 a, double2 b) { return make_double2(fmax(a.x, b.x), fmax(a.y, b.y)); }
+
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+template <typename T>
+using P2 = typename Pair<T>::type;
+template <typename T>
+__device__ __forceinline__ P2<T> dup(T x) {
+  return P2<T>{x, x};
+}
+template <typename T>
+__device__ __forceinline__ P2<T> pr(T x, T y) {
+  return P2<T>{x, y};
 }
 
 // Float keys ordered like the values they encode (for warp max reductions).

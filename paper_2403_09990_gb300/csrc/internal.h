@@ -43,6 +43,7 @@ struct WalkArgs {
   int n_samples, n_iter, n_perturb, n_keep, n_steps;
   double omega0, v0, gamma;
   uint32_t key0, key1;
+  uint32_t rk[20];  // Philox round keys: (key0 + r W0, key1 + r W1), r = 0..9
   void* out_q;
   void* out_t;
   int16_t* trace;

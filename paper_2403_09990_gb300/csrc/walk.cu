@@ -2,22 +2,28 @@
 // sampler, Alg. 4/5 for the dS_t sampler), one warp per walk.
 //
 // Per iteration of a walk:
-//   1. tables: Y_i = R* Z_i (and the per-constraint constants of the
-//      perturbation phase) into the warp's shared-memory slab;
-//   2. perturbation + dist (eq. 11): lane l draws perturbations
-//      j = l + 32 s from Philox and evaluates d_j = min_i (r_i - |g_i|);
-//   3. top_k_indices: N_P* rounds of warp max (REDUX) over order-preserving
-//      keys, ties to the lower j;
+//   1. constraint order: the margins of the current pose are sorted across
+//      the warp (most nearly violated first) and the warp's tables
+//      (Y_i = R* Z_i, observations, perturbation-phase constants) are
+//      written in that order into its shared-memory slab;
+//   2. perturbation + dist (eq. 11): lane l owns the pairs of perturbations
+//      j = 2b, 2b + 1, b = l + 32 P, drawn from one Philox block each, and
+//      evaluates d_j = min_i (r_i - |g_i|) for both at once (paired FP32
+//      instructions), ceil(N_P / 64) pairs per lane;
+//   3. top_k_indices: each lane sorts its own keys once, then N_P* rounds of
+//      a warp max (REDUX) pop the best head; ties go to the lower j;
 //   4. step ladder: candidates (k, m) are laid out lane = m_local * N_P* + k
-//      over chunks of 32 / N_P* ladder rungs; in_purse is evaluated
-//      division-free; the first chunk with a feasible candidate ends the
-//      ladder, and __ffs of the ballot gives m0 (smallest m) then k0
-//      (best-ranked k), i.e. find_farthest;
+//      over chunks of 32 / N_P* rungs; in_purse is evaluated division-free
+//      two constraints at a time (paired FP32), four per group, and a chunk
+//      is left as soon
+//      as a warp vote shows that every candidate has violated one (in_purse
+//      is a conjunction, so the order and the early exit do not change it);
+//      the first chunk with a feasible candidate ends the ladder and __ffs
+//      of the ballot gives m0 (smallest m) then k0 (best-ranked k);
 //   5. update (R*, t*).
-// Factoring used on the hot loop (same values as the paper's per-pose
-// transform, fewer operations):
-//   dS_R, 2D-3D: K(R* Z_i + t* + delta_j) = Q_i + K delta_j,
-//                K(E_m R* Z_i + t_jk)     = W_mi + K t_jk
+// Factoring used on the perturbation phase (same values as the per-pose
+// transform of Alg. 3, fewer operations):
+//   dS_R, 2D-3D: K(R* Z_i + t* + delta_j) = Q_i + K delta_j
 //   dS_t, 2D-3D: K(R_p R* Z_i + t*)       = (K R_p) Y_i + K t*
 // and the same without K (minus b_i) for 3D-3D.
 #include <cfloat>
@@ -30,8 +36,6 @@ namespace purse {
 
 constexpr int kWalkWarps = 8;
 constexpr int kWalkThreads = kWalkWarps * 32;
-constexpr int kPertGroup = 4;  // perturbations per lane per pass
-constexpr int kPertPasses = 2; // N_P <= 32 * 4 * 2 = 256
 
 template <typename T>
 struct alignas(sizeof(T) * 4) T4 {
@@ -78,52 +82,191 @@ __device__ __forceinline__ T inf() {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Bytes of one warp's slab (must match the carving in the kernel).
-template <typename T>
-__host__ __device__ inline size_t walk_slab_bytes(int n, int n_perturb, int n_steps, int mc, int sampler) {
-  const size_t t4 = 4 * sizeof(T);
-  const size_t entries = 2 * (size_t)n + (sampler == 0 ? (size_t)mc * n : 0) + n_perturb + 4 * (size_t)n_steps;
-  return align_up(entries * t4 + 32 * sizeof(int), 128);
-}
-
 template <typename T>
 __host__ __device__ inline size_t walk_table_bytes(int n) {
   return align_up(8 * (size_t)n * sizeof(T), 128);
 }
 
-// Margin r - |g| of one 2D-3D constraint at P = K X (pixels), -inf behind the camera.
+template <typename K>
+__device__ __forceinline__ void cas_desc(K& a, K& b) {
+  const K hi = a > b ? a : b, lo = a > b ? b : a;
+  a = hi, b = lo;
+}
+// Sorting network for 8 keys, descending.
+template <typename K>
+__device__ __forceinline__ void sort8_desc(K (&k)[8]) {
+  cas_desc(k[0], k[1]); cas_desc(k[2], k[3]); cas_desc(k[4], k[5]); cas_desc(k[6], k[7]);
+  cas_desc(k[0], k[2]); cas_desc(k[1], k[3]); cas_desc(k[4], k[6]); cas_desc(k[5], k[7]);
+  cas_desc(k[1], k[2]); cas_desc(k[5], k[6]); cas_desc(k[0], k[4]); cas_desc(k[3], k[7]);
+  cas_desc(k[1], k[5]); cas_desc(k[2], k[6]);
+  cas_desc(k[1], k[4]); cas_desc(k[3], k[6]);
+  cas_desc(k[2], k[4]); cas_desc(k[3], k[5]);
+  cas_desc(k[3], k[4]);
+}
+
+// Per-warp view of the shared-memory slab (constraint order of the current iteration).
+//  D[r][0..7]  perturbation phase, constraint r broadcast to both halves of a pair:
+//              dS_R: (Q_x, Q_y, Q_z, r_i) with Q = K(R* Z + t*) or R* a + t* - b;
+//              dS_t: (Y_x, Y_y, Y_z, r_i) with Y = R* Z;
+//              then 2D-3D: (-u, -v), 3D-3D dS_t: (t* - b).
+//  L[q][0..7]  ladder, constraints 2q and 2q + 1 in the two halves of a pair:
+//              (Y_x, Y_y, Y_z), then 2D-3D: (-u, -v, -r^2), 3D-3D: (-b_x, -b_y, -b_z, -r^2).
+//  P[j]        perturbation j: translation offset (dS_R) or unit quaternion (dS_t)
+//  E[4m..]     ladder rung m: quaternion and rows of (K) E_m (dS_R) or s_m v (dS_t)
 template <typename T>
-__device__ __forceinline__ T margin2d(T Px, T Py, T Pz, T u, T v, T r) {
-  const T ex = Px - u * Pz;
-  const T ey = Py - v * Pz;
-  const T s2 = ex * ex + ey * ey;
-  const T q = fmax(s2 * (Pz * Pz), tiny<T>());
-  const T m = r - s2 * rsq(q);  // |e| / Pz
-  return Pz > T(0) ? m : -inf<T>();
+struct Slab {
+  P2<T>* D;
+  P2<T>* L;
+  T4<T>* P;
+  T4<T>* E;
+  typename KeyOf<T>::type* key;
+  int* J;
+};
+
+__host__ __device__ inline int ladder_pairs(int n) { return (n + 1) / 2; }
+
+template <typename T>
+__host__ __device__ inline size_t walk_slab_bytes2(int n, int n_perturb, int n_steps) {
+  const size_t p2 = 2 * sizeof(T), t4 = 4 * sizeof(T);
+  const size_t bytes = 8 * (size_t)n * p2 + 8 * (size_t)ladder_pairs(n) * p2 + (n_perturb + 4 * (size_t)n_steps) * t4 +
+                       (size_t)n_perturb * sizeof(typename KeyOf<T>::type) + 32 * sizeof(int);
+  return align_up(bytes, 128);
 }
 
 template <typename T>
-__device__ __forceinline__ T margin3d(T ex, T ey, T ez, T r) {
-  const T s2 = ex * ex + ey * ey + ez * ez;
-  return r - s2 * rsq(fmax(s2, tiny<T>()));
+__device__ __forceinline__ Slab<T> carve(unsigned char* base, int N, int NP, int NT) {
+  Slab<T> s;
+  s.D = reinterpret_cast<P2<T>*>(base);
+  s.L = s.D + 8 * N;
+  s.P = reinterpret_cast<T4<T>*>(s.L + 8 * ladder_pairs(N));
+  s.E = s.P + NP;
+  s.key = reinterpret_cast<typename KeyOf<T>::type*>(s.E + 4 * NT);
+  s.J = reinterpret_cast<int*>(s.key + NP);
+  return s;
+}
+
+// Perturbation phase over NPAIR pairs per lane, starting at pair pb: pair P of this lane holds
+// perturbations j = 2 b, 2 b + 1 with b = 32 P + lane, the two points of block 0 of stream
+// (phase, b, it, w).  Writes the keys of every valid j.
+template <typename T, int KIND, int SAMPLER, int NPAIR>
+__device__ __forceinline__ void dist_pass(const WalkArgs& a, int it, int w, const Slab<T>& sl, int N, int NP, int lane,
+                                          int pb, T r_pert, const V3<T>& t, T fx, T fy, T cx, T cy, T qzmin) {
+  using T2 = P2<T>;
+  T2 dmin[NPAIR], zmin[NPAIR];
+  T2 Dx[NPAIR], Dy[NPAIR], Dz[NPAIR];             // dS_R: translation offsets in P units
+  T2 A[SAMPLER == 1 ? NPAIR : 1][9];              // dS_t: (K) R_p per slot
+#pragma unroll
+  for (int p = 0; p < NPAIR; ++p) {
+    T dx[2], dy[2], dz[2];
+    M3<T> Ah[2];
+    const int b = 32 * (pb + p) + lane;
+    uint4 wd = make_uint4(0u, 0u, 0u, 0u);
+    if (2 * b < NP)
+      wd = philox4x32_10_rk(make_uint4(0u, ((SAMPLER == 0 ? kPhaseRPerturb : kPhaseTPerturb) << 24) | (uint32_t)b,
+                                       (uint32_t)it, (uint32_t)w),
+                            a.rk);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = 2 * b + h;
+      dx[h] = dy[h] = dz[h] = T(0);
+      Ah[h] = M3<T>{{T(1), T(0), T(0), T(0), T(1), T(0), T(0), T(0), T(1)}};
+      if (j < NP) {
+        T ux, uy, uz;
+        hatbox_point<T>(h ? wd.z : wd.x, h ? wd.w : wd.y, ux, uy, uz);
+        const V3<T> dl{r_pert * ux, r_pert * uy, r_pert * uz};
+        if constexpr (SAMPLER == 0) {
+          sl.P[j] = T4<T>{dl.x, dl.y, dl.z, T(0)};
+          if (KIND == 1) {
+            dx[h] = fx * dl.x + cx * dl.z, dy[h] = fy * dl.y + cy * dl.z, dz[h] = dl.z;
+          } else {
+            dx[h] = dl.x, dy[h] = dl.y, dz[h] = dl.z;
+          }
+        } else {
+          const Q4<T> pq = qexp(dl);
+          sl.P[j] = T4<T>{pq.w, pq.x, pq.y, pq.z};
+          M3<T> Rp = qmat(pq);
+          if (KIND == 1) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              Rp.m[c] = fx * Rp.m[c] + cx * Rp.m[6 + c];
+              Rp.m[3 + c] = fy * Rp.m[3 + c] + cy * Rp.m[6 + c];
+            }
+          }
+          Ah[h] = Rp;
+        }
+      }
+    }
+    Dx[p] = pr(dx[0], dx[1]), Dy[p] = pr(dy[0], dy[1]), Dz[p] = pr(dz[0], dz[1]);
+    if constexpr (SAMPLER == 1) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) A[p][c] = pr(Ah[0].m[c], Ah[1].m[c]);
+    }
+    dmin[p] = dup(inf<T>());
+    zmin[p] = dup(inf<T>());
+  }
+  const T2 neg1 = dup(T(-1)), tiny2 = dup(tiny<T>());
+  T2 c0x = dup(T(0)), c0y = c0x, c0z = c0x;
+  if (SAMPLER == 1 && KIND == 1) c0x = dup(fx * t.x + cx * t.z), c0y = dup(fy * t.y + cy * t.z), c0z = dup(t.z);
+  for (int i = 0; i < N; ++i) {
+    const T2* Di = sl.D + 8 * i;
+    const T2 d0 = Di[0], d1 = Di[1], d2 = Di[2], rr = Di[3];
+    T2 d4, d5, d6;
+    if (KIND == 1 || SAMPLER == 1) d4 = Di[4], d5 = Di[5];
+    if (KIND == 0 && SAMPLER == 1) d6 = Di[6];
+#pragma unroll
+    for (int p = 0; p < NPAIR; ++p) {
+      T2 Px, Py, Pz;
+      if constexpr (SAMPLER == 0) {
+        Px = add2(d0, Dx[p]), Py = add2(d1, Dy[p]), Pz = add2(d2, Dz[p]);
+      } else {
+        const T2 bx = KIND == 1 ? c0x : d4, by = KIND == 1 ? c0y : d5, bz = KIND == 1 ? c0z : d6;
+        Px = fma2(A[p][0], d0, fma2(A[p][1], d1, fma2(A[p][2], d2, bx)));
+        Py = fma2(A[p][3], d0, fma2(A[p][4], d1, fma2(A[p][5], d2, by)));
+        Pz = fma2(A[p][6], d0, fma2(A[p][7], d1, fma2(A[p][8], d2, bz)));
+      }
+      T2 s2, qq;
+      if (KIND == 1) {
+        const T2 ex = fma2(d4, Pz, Px), ey = fma2(d5, Pz, Py);
+        s2 = fma2(ey, ey, mul2(ex, ex));
+        qq = fma2(s2, mul2(Pz, Pz), tiny2);
+        if (SAMPLER == 1) zmin[p] = min2(zmin[p], Pz);
+      } else {
+        s2 = fma2(Pz, Pz, fma2(Py, Py, mul2(Px, Px)));
+        qq = add2(s2, tiny2);
+      }
+      const T2 m = fma2(mul2(s2, rsq2(qq)), neg1, rr);  // r - |e| (2D-3D: |e| / P_z)
+      dmin[p] = min2(dmin[p], m);
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < NPAIR; ++p) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = 2 * (32 * (pb + p) + lane) + h;
+      if (j < NP) {
+        T d = h ? dmin[p].y : dmin[p].x;
+        if (KIND == 1) {
+          // dS_R: P_z = Q_z,i + D_z,j and rounding is monotone, so min_i P_z = min_i Q_z,i + D_z,j
+          const T zm = SAMPLER == 0 ? qzmin + (h ? Dz[p].y : Dz[p].x) : (h ? zmin[p].y : zmin[p].x);
+          if (!(zm > T(0))) d = -inf<T>();
+        }
+        sl.key[j] = orderable(d);
+      }
+    }
+  }
 }
 
 template <typename T, int KIND, int SAMPLER>
-__global__ void __launch_bounds__(kWalkThreads) walk_kernel(const WalkArgs a, const int mc, const int slab_bytes) {
+__global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1) walk_kernel(const WalkArgs a, const int mc, const int slab_bytes) {
   using Key = typename KeyOf<T>::type;
+  using T2 = P2<T>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  const int N = a.n;
+  const int N = a.n, NQ = ladder_pairs(a.n);
   const int NP = a.n_perturb, K = a.n_keep, NT = a.n_steps;
-  const T4<T>* tab = reinterpret_cast<const T4<T>*>(smem + 128);  // rows [0,N): (a,r); [N,2N): (b or z, r^2)
+  const T4<T>* tab = reinterpret_cast<const T4<T>*>(smem + 128);  // rows [0,N): (a, r); [N,2N): (b or z, r^2)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* slab = smem + 128 + walk_table_bytes<T>(N) + (size_t)warp * slab_bytes;
-  T4<T>* Ytab = reinterpret_cast<T4<T>*>(slab);
-  T4<T>* Qtab = Ytab + N;
-  T4<T>* Wtab = Qtab + N;
-  T4<T>* Ptab = Wtab + (SAMPLER == 0 ? mc * N : 0);
-  T4<T>* Etab = Ptab + NP;
-  int* Jtab = reinterpret_cast<int*>(Etab + 4 * NT);
+  const Slab<T> sl = carve<T>(smem + 128 + walk_table_bytes<T>(N) + (size_t)warp * slab_bytes, N, NP, NT);
 
   // ---- a0: stage the constraint table with a 1-D TMA bulk copy.
   const uint32_t tbytes = 8u * N * sizeof(T);
@@ -140,165 +283,182 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const WalkArgs a, co
 
   const T fx = T(a.fx), fy = T(a.fy), cx = T(a.cx), cy = T(a.cy);
   const WalkStats* st = a.stats;
-  const T r_pert = T((SAMPLER == 0 ? st->r_trans : st->r_rot) / 1024.0);
+  const T r_pert = T(SAMPLER == 0 ? st->r_trans : st->r_rot);
   const int ncand = mc * K;
   const int cm = lane / K, ck = lane - (lane / K) * K;
+  const int npair = (NP + 63) / 64;
   unsigned long long evals = 0;
 
   for (int w = blockIdx.x * kWalkWarps + warp; w < a.n_samples; w += gridDim.x * kWalkWarps) {
-    // ---- a3: start pose and velocity (FP64), ladder table.
+    // ---- a3: start pose and velocity, ladder table of this walk.
     const double* sd = a.seed_data + (size_t)(w % a.s0) * kSeedStride;
     Q4<T> q{T(sd[0]), T(sd[1]), T(sd[2]), T(sd[3])};
     V3<T> t{T(sd[4]), T(sd[5]), T(sd[6])};
-    double vel[3];
+    V3<T> vel;
     {
       Stream s(a.key0, a.key1, SAMPLER == 0 ? kPhaseOmega : kPhaseV, 0u, 0u, (uint32_t)w);
       int X, Y, Z;
       lattice_draw<true>(s, X, Y, Z);
       const double nr = sqrt((double)(X * X + Y * Y + Z * Z));
-      const double ut[3] = {nr > 0 ? X / nr : 0.0, nr > 0 ? Y / nr : 0.0, nr > 0 ? Z / nr : 0.0};
+      const double ux = nr > 0 ? X / nr : 0.0, uy = nr > 0 ? Y / nr : 0.0, uz = nr > 0 ? Z / nr : 0.0;
       if (SAMPLER == 0) {
-        for (int c = 0; c < 3; ++c) vel[c] = a.omega0 * (sd[7 + c] + ut[c]);
+        vel = V3<T>{T(a.omega0 * (sd[7] + ux)), T(a.omega0 * (sd[8] + uy)), T(a.omega0 * (sd[9] + uz))};
       } else {
-        double d[3];
-        for (int c = 0; c < 3; ++c) d[c] = sd[10 + c] + ut[c];
-        for (int r = 0; r < 3; ++r)
-          vel[r] = a.v0 * (st->S[3 * r] * d[0] + st->S[3 * r + 1] * d[1] + st->S[3 * r + 2] * d[2]);
+        const double d0 = sd[10] + ux, d1 = sd[11] + uy, d2 = sd[12] + uz;
+        vel = V3<T>{T(a.v0 * (st->S[0] * d0 + st->S[1] * d1 + st->S[2] * d2)),
+                    T(a.v0 * (st->S[3] * d0 + st->S[4] * d1 + st->S[5] * d2)),
+                    T(a.v0 * (st->S[6] * d0 + st->S[7] * d1 + st->S[8] * d2))};
       }
     }
     for (int m = lane; m < NT; m += 32) {
-      const double sm = pow(a.gamma, (double)m);
+      T sm = T(1);
+      for (int k = 0; k < m; ++k) sm *= T(a.gamma);
       if (SAMPLER == 0) {
-        const Q4<double> e = qexp(V3<double>{sm * vel[0], sm * vel[1], sm * vel[2]});
-        const M3<double> E = qmat(e);
-        Etab[4 * m] = T4<T>{T(e.w), T(e.x), T(e.y), T(e.z)};
-        for (int r = 0; r < 3; ++r) Etab[4 * m + 1 + r] = T4<T>{T(E.m[3 * r]), T(E.m[3 * r + 1]), T(E.m[3 * r + 2]), T(0)};
+        const Q4<T> e = qexp(V3<T>{sm * vel.x, sm * vel.y, sm * vel.z});
+        M3<T> E = qmat(e);
+        if (KIND == 1) {
+          for (int c = 0; c < 3; ++c) {
+            E.m[c] = fx * E.m[c] + cx * E.m[6 + c];
+            E.m[3 + c] = fy * E.m[3 + c] + cy * E.m[6 + c];
+          }
+        }
+        sl.E[4 * m] = T4<T>{e.w, e.x, e.y, e.z};
+        for (int r = 0; r < 3; ++r) sl.E[4 * m + 1 + r] = T4<T>{E.m[3 * r], E.m[3 * r + 1], E.m[3 * r + 2], T(0)};
       } else {
-        Etab[4 * m] = T4<T>{T(sm * vel[0]), T(sm * vel[1]), T(sm * vel[2]), T(0)};
+        sl.E[4 * m] = T4<T>{sm * vel.x, sm * vel.y, sm * vel.z, T(0)};
       }
     }
     __syncwarp();
 
     for (int it = 0; it < a.n_iter; ++it) {
       const M3<T> R = qmat(q);
-      // ---- tables for this iteration
-      for (int i = lane; i < N; i += 32) {
+      // ---- constraint order: ascending margin of the current pose (N <= 32), then the tables
+      int perm = lane;
+      if (N <= 32) {
+        uint32_t kk = 0xFFFFFFFFu;
+        if (lane < N) {
+          const T4<T> mz = tab[lane], ob = tab[N + lane];
+          const V3<T> X = mul(R, V3<T>{mz.x, mz.y, mz.z}) + t;
+          float m;
+          if (KIND == 1) {
+            const T Pz = X.z, ex = fx * X.x + cx * X.z - ob.x * Pz, ey = fy * X.y + cy * X.z - ob.y * Pz;
+            m = Pz > T(0) ? (float)(mz.w * Pz * mz.w * Pz - ex * ex - ey * ey) : -INFINITY;
+          } else {
+            const T ex = X.x - ob.x, ey = X.y - ob.y, ez = X.z - ob.z;
+            m = (float)(ob.w - ex * ex - ey * ey - ez * ez);
+          }
+          kk = (orderable(m) & ~31u) | (uint32_t)lane;
+        }
+#pragma unroll
+        for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+          for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const uint32_t o = __shfl_xor_sync(kFullMask, kk, stride);
+            const bool up = ((lane & size) == 0);
+            const bool lower = (lane & stride) == 0;
+            const uint32_t mn = kk < o ? kk : o, mx = kk < o ? o : kk;
+            kk = (lower == up) ? mn : mx;
+          }
+        }
+        perm = (int)(kk & 31u);
+      }
+      T qzmin = inf<T>();
+      for (int r = lane; r < N; r += 32) {
+        const int i = N <= 32 ? perm : r;
         const T4<T> mz = tab[i], ob = tab[N + i];
         const V3<T> Y = mul(R, V3<T>{mz.x, mz.y, mz.z});
-        Ytab[i] = T4<T>{Y.x, Y.y, Y.z, T(0)};
+        T2* Dr = sl.D + 8 * r;
         if (SAMPLER == 0) {
           if (KIND == 1) {
             const V3<T> X = Y + t;
-            Qtab[i] = T4<T>{fx * X.x + cx * X.z, fy * X.y + cy * X.z, X.z, T(0)};
+            const T qz = X.z;
+            Dr[0] = dup(fx * X.x + cx * X.z), Dr[1] = dup(fy * X.y + cy * X.z), Dr[2] = dup(qz);
+            qzmin = fmin(qzmin, qz);
           } else {
-            Qtab[i] = T4<T>{Y.x + t.x - ob.x, Y.y + t.y - ob.y, Y.z + t.z - ob.z, T(0)};
+            Dr[0] = dup(Y.x + t.x - ob.x), Dr[1] = dup(Y.y + t.y - ob.y), Dr[2] = dup(Y.z + t.z - ob.z);
           }
-        } else if (KIND == 0) {
-          Qtab[i] = T4<T>{t.x - ob.x, t.y - ob.y, t.z - ob.z, T(0)};
+        } else {
+          Dr[0] = dup(Y.x), Dr[1] = dup(Y.y), Dr[2] = dup(Y.z);
         }
+        Dr[3] = dup(mz.w);
+        if (KIND == 1) {
+          Dr[4] = dup(-ob.x), Dr[5] = dup(-ob.y);
+        } else if (SAMPLER == 1) {
+          Dr[4] = dup(t.x - ob.x), Dr[5] = dup(t.y - ob.y), Dr[6] = dup(t.z - ob.z);
+        }
+        // ladder table: constraint r in half (r & 1) of pair r / 2
+        T* Lq = reinterpret_cast<T*>(sl.L + 8 * (r >> 1)) + (r & 1);
+        Lq[0] = Y.x, Lq[2] = Y.y, Lq[4] = Y.z;
+        if (KIND == 1) {
+          Lq[6] = -ob.x, Lq[8] = -ob.y, Lq[10] = -ob.w;
+        } else {
+          Lq[6] = -ob.x, Lq[8] = -ob.y, Lq[10] = -ob.z, Lq[12] = -ob.w;
+        }
+      }
+      if ((N & 1) && lane == 0) {  // odd N: the second half of the last pair is always satisfied
+        T* Lq = reinterpret_cast<T*>(sl.L + 8 * (N >> 1)) + 1;
+        Lq[0] = Lq[2] = Lq[4] = T(0);
+        Lq[6] = Lq[8] = T(0);
+        Lq[10] = T(-1e30);
+        if (KIND == 0) Lq[10] = T(0), Lq[12] = T(-1e30);
+      }
+      if (SAMPLER == 0 && KIND == 1) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) qzmin = fmin(qzmin, __shfl_xor_sync(kFullMask, qzmin, o));
       }
       __syncwarp();
 
       // ---- a4: perturbations and their distance to the boundary (eq. 11)
-      Key key[kPertGroup * kPertPasses];
-#pragma unroll
-      for (int p = 0; p < kPertPasses; ++p) {
-#pragma unroll
-        for (int g = 0; g < kPertGroup; ++g) key[p * kPertGroup + g] = 0;
-        if (p * 32 * kPertGroup >= NP) continue;
-        T dmin[kPertGroup];
-        bool valid[kPertGroup];
-        // dS_R: D = translation offset in P units; dS_t: A = rotation (K R_p for 2D-3D)
-        V3<T> D[kPertGroup];
-        M3<T> A[SAMPLER == 1 ? kPertGroup : 1];
-#pragma unroll
-        for (int g = 0; g < kPertGroup; ++g) {
-          const int j = p * 32 * kPertGroup + g * 32 + lane;
-          valid[g] = j < NP;
-          dmin[g] = inf<T>();
-          D[g] = V3<T>{T(0), T(0), T(0)};
-          if constexpr (SAMPLER == 1) A[g] = M3<T>{{T(1), T(0), T(0), T(0), T(1), T(0), T(0), T(0), T(1)}};
-          if (valid[g]) {
-            Stream s(a.key0, a.key1, SAMPLER == 0 ? kPhaseRPerturb : kPhaseTPerturb, (uint32_t)j, (uint32_t)it,
-                     (uint32_t)w);
-            int X, Y, Z;
-            lattice_draw<false>(s, X, Y, Z);
-            const V3<T> dl{r_pert * T(X), r_pert * T(Y), r_pert * T(Z)};
-            if constexpr (SAMPLER == 0) {
-              Ptab[j] = T4<T>{dl.x, dl.y, dl.z, T(0)};
-              D[g] = KIND == 1 ? V3<T>{fx * dl.x + cx * dl.z, fy * dl.y + cy * dl.z, dl.z} : dl;
-            } else {
-              const Q4<T> pq = qexp(dl);
-              Ptab[j] = T4<T>{pq.w, pq.x, pq.y, pq.z};
-              M3<T> Rp = qmat(pq);
-              if (KIND == 1) {
-                for (int c = 0; c < 3; ++c) {
-                  Rp.m[c] = fx * Rp.m[c] + cx * Rp.m[6 + c];
-                  Rp.m[3 + c] = fy * Rp.m[3 + c] + cy * Rp.m[6 + c];
-                }
-              }
-              A[g] = Rp;
-            }
-          }
+      if constexpr (SAMPLER == 0) {
+        if (npair == 4)
+          dist_pass<T, KIND, SAMPLER, 4>(a, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
+        else if (npair == 3)
+          dist_pass<T, KIND, SAMPLER, 3>(a, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
+        else if (npair == 2)
+          dist_pass<T, KIND, SAMPLER, 2>(a, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
+        else
+          dist_pass<T, KIND, SAMPLER, 1>(a, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
+      } else {
+        // dS_t keeps one rotation per perturbation in registers: two pairs at a time
+        for (int pb = 0; pb < npair; pb += 2) {
+          if (npair - pb >= 2)
+            dist_pass<T, KIND, SAMPLER, 2>(a, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
+          else
+            dist_pass<T, KIND, SAMPLER, 1>(a, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
         }
-        V3<T> Kt{T(0), T(0), T(0)};
-        if (SAMPLER == 1 && KIND == 1) Kt = V3<T>{fx * t.x + cx * t.z, fy * t.y + cy * t.z, t.z};
-        for (int i = 0; i < N; ++i) {
-          const T4<T> ob = tab[N + i];
-          const T r = tab[i].w;
-          if constexpr (SAMPLER == 0) {
-            const T4<T> Qi = Qtab[i];
-#pragma unroll
-            for (int g = 0; g < kPertGroup; ++g) {
-              const T Px = Qi.x + D[g].x, Py = Qi.y + D[g].y, Pz = Qi.z + D[g].z;
-              const T m = KIND == 1 ? margin2d(Px, Py, Pz, ob.x, ob.y, r) : margin3d(Px, Py, Pz, r);
-              dmin[g] = fmin(dmin[g], m);
-            }
-          } else {
-            const T4<T> Yi = Ytab[i];
-            const V3<T> c0 = KIND == 1 ? Kt : V3<T>{Qtab[i].x, Qtab[i].y, Qtab[i].z};
-#pragma unroll
-            for (int g = 0; g < kPertGroup; ++g) {
-              const M3<T>& M = A[g];
-              const T Px = M.m[0] * Yi.x + M.m[1] * Yi.y + M.m[2] * Yi.z + c0.x;
-              const T Py = M.m[3] * Yi.x + M.m[4] * Yi.y + M.m[5] * Yi.z + c0.y;
-              const T Pz = M.m[6] * Yi.x + M.m[7] * Yi.y + M.m[8] * Yi.z + c0.z;
-              const T m = KIND == 1 ? margin2d(Px, Py, Pz, ob.x, ob.y, r) : margin3d(Px, Py, Pz, r);
-              dmin[g] = fmin(dmin[g], m);
-            }
-          }
-        }
-#pragma unroll
-        for (int g = 0; g < kPertGroup; ++g)
-          key[p * kPertGroup + g] = valid[g] ? orderable(dmin[g]) : Key(0);
       }
       evals += (unsigned long long)NP * N;
+      __syncwarp();
 
-      // ---- a5: top_k_indices (ties to the lower j)
-      for (int r = 0; r < K; ++r) {
-        Key bk = 0;
-        int bs = -1;
+      // ---- a5: top_k_indices (ties to the lower j): per-lane sorted keys, warp max rounds
+      {
+        Key kk[8];
 #pragma unroll
-        for (int s = 0; s < kPertGroup * kPertPasses; ++s)
-          if (key[s] > bk) bk = key[s], bs = s;
-        const Key wmax = warp_max_key(bk);
-        const uint32_t myj = (bs >= 0 && bk == wmax) ? (uint32_t)(lane + 32 * bs) : 0xFFFFu;
-        const uint32_t jmin = __reduce_min_sync(kFullMask, myj);
-        if (myj == jmin) {
-#pragma unroll
-          for (int s = 0; s < kPertGroup * kPertPasses; ++s)
-            if (s == bs) key[s] = 0;
+        for (int s = 0; s < 8; ++s) {
+          const int j = lane + 32 * s;
+          kk[s] = j < NP ? ((sl.key[j] & ~Key(7)) | Key(7 - s)) : Key(0);
         }
-        if (lane == 0) Jtab[r] = (int)jmin;
+        sort8_desc(kk);
+        for (int r = 0; r < K; ++r) {
+          const Key mx = warp_max_key(kk[0]);
+          const unsigned bal = __ballot_sync(kFullMask, kk[0] == mx);
+          const int wl = __ffs(bal) - 1;
+          if (lane == wl) {
+#pragma unroll
+            for (int s = 0; s < 7; ++s) kk[s] = kk[s + 1];
+            kk[7] = Key(0);
+          }
+          if (lane == 0) sl.J[r] = wl + 32 * (7 - (int)(mx & Key(7)));
+        }
       }
       __syncwarp();
 
-      // ---- a6/a7: step ladder + in_purse, find_farthest
+      // ---- a6/a7: step ladder + in_purse with early exit, find_farthest
       int m0 = -1, k0 = -1;
       V3<T> base{T(0), T(0), T(0)};
-      M3<T> Ak;
+      M3<T> Ak;  // dS_t: (K) R_{j_k}
       if (lane < ncand) {
-        const T4<T> pj = Ptab[Jtab[ck]];
+        const T4<T> pj = sl.P[sl.J[ck]];
         if (SAMPLER == 0) {
           const V3<T> tk{t.x + pj.x, t.y + pj.y, t.z + pj.z};
           base = KIND == 1 ? V3<T>{fx * tk.x + cx * tk.z, fy * tk.y + cy * tk.z, tk.z} : tk;
@@ -313,65 +473,57 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const WalkArgs a, co
         }
       }
       for (int mb = 0; mb < NT; mb += mc) {
-        if (SAMPLER == 0) {
-          const int npair = mc * N;
-          for (int pi = lane; pi < npair; pi += 32) {
-            const int mi = pi / N, i = pi - mi * N, m = mb + mi;
-            if (m < NT) {
-              const T4<T> e0 = Etab[4 * m + 1], e1 = Etab[4 * m + 2], e2 = Etab[4 * m + 3];
-              const T4<T> Yi = Ytab[i];
-              const T X = e0.x * Yi.x + e0.y * Yi.y + e0.z * Yi.z;
-              const T Y = e1.x * Yi.x + e1.y * Yi.y + e1.z * Yi.z;
-              const T Z = e2.x * Yi.x + e2.y * Yi.y + e2.z * Yi.z;
-              if (KIND == 1) {
-                Wtab[pi] = T4<T>{fx * X + cx * Z, fy * Y + cy * Z, Z, T(0)};
-              } else {
-                const T4<T> ob = tab[N + i];
-                Wtab[pi] = T4<T>{X - ob.x, Y - ob.y, Z - ob.z, T(0)};
-              }
-            }
-          }
-          __syncwarp();
-        }
         const int m = mb + cm;
-        bool feas = false;
-        if (lane < ncand && m < NT) {
-          T cmax = -inf<T>(), zmin = inf<T>();
-          V3<T> bm = base;
-          if (SAMPLER == 1) {
-            const T4<T> sv = Etab[4 * m];
+        const bool active = lane < ncand && m < NT;
+        M3<T> M = M3<T>{{T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)}};
+        V3<T> bm = base;
+        if (active) {
+          if (SAMPLER == 0) {
+            const T4<T> e0 = sl.E[4 * m + 1], e1 = sl.E[4 * m + 2], e2 = sl.E[4 * m + 3];
+            M = M3<T>{{e0.x, e0.y, e0.z, e1.x, e1.y, e1.z, e2.x, e2.y, e2.z}};
+          } else {
+            M = Ak;
+            const T4<T> sv = sl.E[4 * m];
             const V3<T> Tm{t.x + sv.x, t.y + sv.y, t.z + sv.z};
             bm = KIND == 1 ? V3<T>{fx * Tm.x + cx * Tm.z, fy * Tm.y + cy * Tm.z, Tm.z} : Tm;
           }
-          for (int i = 0; i < N; ++i) {
-            const T4<T> ob = tab[N + i];
-            T Px, Py, Pz;
-            if (SAMPLER == 0) {
-              const T4<T> Wi = Wtab[cm * N + i];
-              Px = Wi.x + bm.x, Py = Wi.y + bm.y, Pz = Wi.z + bm.z;
-            } else {
-              const T4<T> Yi = Ytab[i];
-              Px = Ak.m[0] * Yi.x + Ak.m[1] * Yi.y + Ak.m[2] * Yi.z + bm.x;
-              Py = Ak.m[3] * Yi.x + Ak.m[4] * Yi.y + Ak.m[5] * Yi.z + bm.y;
-              Pz = Ak.m[6] * Yi.x + Ak.m[7] * Yi.y + Ak.m[8] * Yi.z + bm.z;
-              if (KIND == 0) Px -= ob.x, Py -= ob.y, Pz -= ob.z;
-            }
-            T c;
-            if (KIND == 1) {
-              const T ex = Px - ob.x * Pz, ey = Py - ob.y * Pz;
-              const T rz = tab[i].w * Pz;
-              c = ex * ex + ey * ey - rz * rz;
-              zmin = fmin(zmin, Pz);
-            } else {
-              c = Px * Px + Py * Py + Pz * Pz - ob.w;
-            }
-            cmax = fmax(cmax, c);
-          }
-          feas = cmax <= T(0) && (KIND == 0 || zmin > T(0));
         }
-        const unsigned bal = __ballot_sync(kFullMask, feas);
-        evals += (unsigned long long)N * K * (unsigned long long)min(mc, NT - mb);
-        __syncwarp();
+        T2 M2[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) M2[c] = dup(M.m[c]);
+        const T2 bx = dup(bm.x), by = dup(bm.y), bz = dup(bm.z);
+        T2 cmax = dup(-inf<T>()), zmin = dup(inf<T>());
+        bool alive = active;
+        const int nact = K * min(mc, NT - mb);
+        int done = 0;
+        for (int g0 = 0; g0 < NQ; g0 += 2) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int qi = g0 + u;
+            if (qi < NQ) {
+              const T2* Lq = sl.L + 8 * qi;
+              const T2 yx = Lq[0], yy = Lq[1], yz = Lq[2], o3 = Lq[3], o4 = Lq[4], o5 = Lq[5];
+              const T2 Px = fma2(M2[0], yx, fma2(M2[1], yy, fma2(M2[2], yz, bx)));
+              const T2 Py = fma2(M2[3], yx, fma2(M2[4], yy, fma2(M2[5], yz, by)));
+              const T2 Pz = fma2(M2[6], yx, fma2(M2[7], yy, fma2(M2[8], yz, bz)));
+              T2 c;
+              if (KIND == 1) {
+                const T2 ex = fma2(o3, Pz, Px), ey = fma2(o4, Pz, Py);
+                c = fma2(o5, mul2(Pz, Pz), fma2(ey, ey, mul2(ex, ex)));
+                zmin = min2(zmin, Pz);
+              } else {
+                const T2 ex = add2(Px, o3), ey = add2(Py, o4), ez = add2(Pz, o5);
+                c = add2(fma2(ez, ez, fma2(ey, ey, mul2(ex, ex))), Lq[6]);
+              }
+              cmax = max2(cmax, c);
+            }
+          }
+          done = min(N, 2 * (g0 + 2));
+          alive = alive && fmax(cmax.x, cmax.y) <= T(0) && (KIND == 0 || fmin(zmin.x, zmin.y) > T(0));
+          if (!__any_sync(kFullMask, alive)) break;
+        }
+        evals += (unsigned long long)nact * done;
+        const unsigned bal = __ballot_sync(kFullMask, alive);
         if (bal) {
           const int l = __ffs(bal) - 1;
           m0 = mb + l / K;
@@ -382,20 +534,20 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const WalkArgs a, co
 
       // ---- update (R*, t*)
       if (m0 >= 0) {
-        const T4<T> pj = Ptab[Jtab[k0]];
+        const T4<T> pj = sl.P[sl.J[k0]];
         if (SAMPLER == 0) {
-          const T4<T> e = Etab[4 * m0];
+          const T4<T> e = sl.E[4 * m0];
           q = qnormalize(qmul(Q4<T>{e.x, e.y, e.z, e.w}, q));
           t = V3<T>{t.x + pj.x, t.y + pj.y, t.z + pj.z};
         } else {
           q = qnormalize(qmul(Q4<T>{pj.x, pj.y, pj.z, pj.w}, q));
-          const T4<T> sv = Etab[4 * m0];
+          const T4<T> sv = sl.E[4 * m0];
           t = V3<T>{t.x + sv.x, t.y + sv.y, t.z + sv.z};
         }
       }
       if (a.trace != nullptr && lane == 0) {
         int16_t* tr = a.trace + ((size_t)w * a.n_iter + it) * (K + 2);
-        for (int r = 0; r < K; ++r) tr[r] = (int16_t)Jtab[r];
+        for (int r = 0; r < K; ++r) tr[r] = (int16_t)sl.J[r];
         tr[K] = (int16_t)m0;
         tr[K + 1] = (int16_t)k0;
       }
@@ -420,7 +572,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const WalkArgs a, co
 template <typename T, int KIND, int SAMPLER>
 static cudaError_t launch_walk_t(purse_t h, const purse_params* p, const WalkArgs& a, cudaStream_t st) {
   const int mc = p->n_keep >= 32 ? 1 : 32 / p->n_keep;
-  const size_t slab = walk_slab_bytes<T>(a.n, p->n_perturb, p->n_steps, mc, SAMPLER);
+  const size_t slab = walk_slab_bytes2<T>(a.n, p->n_perturb, p->n_steps);
   const size_t smem = 128 + walk_table_bytes<T>(a.n) + kWalkWarps * slab;
   auto kern = walk_kernel<T, KIND, SAMPLER>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

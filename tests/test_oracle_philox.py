@@ -81,3 +81,36 @@ def test_distinct_triple_uniform():
     assert len(cells) == 120
     chi2 = ((cells - 1000.0) ** 2 / 1000.0).sum()
     assert chi2 < 200  # 119 dof; p ~ 1e-5 at 200
+
+
+def test_hatbox_points_decode_the_stream_words():
+    seed, n_points = 77, 150
+    w = np.array([0, 5, 123456])
+    pts = philox.hatbox_points(seed, philox.PHASE_R_PERTURB, 3, w, n_points)
+    assert pts.shape == (3, n_points, 3)
+    for wi, ww in enumerate(w):
+        for j in (0, 1, 2, 77, 148, 149):
+            wd = [int(x) for x in philox.stream_words(seed, philox.PHASE_R_PERTURB, j >> 1, 3, ww, 4)]
+            w0, w1 = wd[2 * (j & 1)], wd[2 * (j & 1) + 1]
+            z = ((w0 >> 16) + 0.5) / 32768 - 1
+            x = ((w0 & 0xFFFF) + 0.5) / 32768
+            rho = (max(w1 & 1023, (w1 >> 10) & 1023, (w1 >> 20) & 1023) + 0.5) / 1024
+            s = np.sqrt(1 - z * z)
+            ref = rho * np.array([s * np.cos(np.pi * x), s * np.sin(np.pi * x), z])
+            assert np.allclose(pts[wi, j], ref, rtol=0, atol=1e-15)
+
+
+def test_hatbox_points_uniform_in_ball():
+    pts = philox.hatbox_points(3, philox.PHASE_T_PERTURB, 0, np.arange(2000), 150).reshape(-1, 3)
+    r = np.linalg.norm(pts, axis=1)
+    assert r.max() <= 1.0
+    # radius law of the uniform ball: P(|x| <= rho) = rho^3
+    for rho in (0.3, 0.5, 0.8, 0.95):
+        assert abs((r <= rho).mean() - rho ** 3) < 0.004
+    assert abs((r ** 2).mean() - 0.6) < 0.003
+    assert np.abs(pts.mean(0)).max() < 0.003
+    assert np.abs((pts ** 2).mean(0) - 0.2).max() < 0.003
+    # isotropy of the direction: octant frequencies
+    oct_ = (pts > 0).astype(int) @ np.array([1, 2, 4])
+    f = np.bincount(oct_, minlength=8) / len(pts)
+    assert np.abs(f - 0.125).max() < 0.003
