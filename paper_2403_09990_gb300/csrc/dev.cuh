@@ -68,9 +68,17 @@ __device__ __forceinline__ void hatbox_point(uint32_t w0, uint32_t w1, T& x, T& 
   const T az = T((int)(w0 & 0xFFFFu)) * T(1.0 / 32768) + T(0.5 / 32768);
   const uint32_t k = max(max(w1 & 1023u, (w1 >> 10) & 1023u), (w1 >> 20) & 1023u);
   const T rho = T((int)k) * T(1.0 / 1024) + T(0.5 / 1024);
-  T sp, cp;
-  sin_cos_pi(az, &sp, &cp);
-  const T s = rho * sqrt(T(1) - zz * zz);
+  T sp, cp, s;
+  const T c2 = T(1) - zz * zz;  // >= 2^-15
+  if constexpr (sizeof(T) == 4) {
+    // hardware sine/cosine and reciprocal square root: absolute errors ~1e-6 of a unit
+    // perturbation direction, far below what changes any walk decision
+    __sincosf(3.14159265358979f * az, &sp, &cp);
+    s = rho * c2 * rsqrtf(c2);
+  } else {
+    sin_cos_pi(az, &sp, &cp);
+    s = rho * sqrt(c2);
+  }
   x = s * cp, y = s * sp, z = rho * zz;
 }
 

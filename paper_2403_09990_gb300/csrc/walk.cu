@@ -207,6 +207,7 @@ __device__ __forceinline__ void dist_pass(const WalkArgs& a, int it, int w, cons
   const T2 neg1 = dup(T(-1)), tiny2 = dup(tiny<T>());
   T2 c0x = dup(T(0)), c0y = c0x, c0z = c0x;
   if (SAMPLER == 1 && KIND == 1) c0x = dup(fx * t.x + cx * t.z), c0y = dup(fy * t.y + cy * t.z), c0z = dup(t.z);
+#pragma unroll 2
   for (int i = 0; i < N; ++i) {
     const T2* Di = sl.D + 8 * i;
     const T2 d0 = Di[0], d1 = Di[1], d2 = Di[2], rr = Di[3];
@@ -332,7 +333,8 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1) walk_ker
 
     for (int it = 0; it < a.n_iter; ++it) {
       const M3<T> R = qmat(q);
-      // ---- constraint order: ascending margin of the current pose (N <= 32), then the tables
+      // ---- constraint order: ascending margin of the current pose (N <= 32; the order only decides how
+      //      soon the ladder's early exit triggers), then the tables
       int perm = lane;
       if (N <= 32) {
         uint32_t kk = 0xFFFFFFFFu;
