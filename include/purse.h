@@ -151,6 +151,53 @@ purse_status megb_solve_noalloc(int precision, int n_iters, const void* d_q, int
 purse_status purse_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t i, uint32_t w0, int n_streams,
                              int n_words, uint32_t* d_words, int32_t* d_lattice, int unit, purse_stream_t stream);
 
+/* ---- Batches: many PURSEs solved by one graph of three launches (centre statistics, one
+ * persistent walk launch over all (PURSE, sampler, walk) items, one block per ball).
+ * PURSE p has kind kinds[p] and constraints offsets[p] .. offsets[p+1]-1 (3..256 each) of
+ * model (host, x 3), obs (host, x 3; z ignored for 2D-3D) and radii (host, > 0); K (host,
+ * n_purses entries) holds the intrinsics of the 2D-3D PURSEs (others ignored; may be NULL if
+ * there are none).  3D-3D PURSEs use the dS_R samples for both balls; 2D-3D PURSEs the dS_R
+ * samples for the rotation ball and the dS_t samples for the translation ball. */
+typedef struct purse_batch_s* purse_batch_t;
+
+purse_status purse_batch_create(int n_purses, const int* kinds, const int* offsets, const double* model,
+                                const double* obs, const double* radii, const purse_intrinsics* K,
+                                purse_batch_t* out);
+
+purse_status purse_batch_destroy(purse_batch_t b);
+
+/* Alg. 1 for every PURSE of the batch, FP32 walks: n_samples walks per PURSE and sampler from the
+ * seed pose d_seeds[p] (device, n_purses x 12 doubles), the parameters p3d / p2d by kind (their
+ * sampler and precision fields must be 0), Philox key seed + p for PURSE p (so PURSE p gets the
+ * samples purse_sample would give with that key), then n_iters GGD iterations per ball.
+ * d_results: device, n_purses x 9 doubles as in megb_solve.  n_samples <= 12288.
+ * The launch sequence is captured into a CUDA graph on the first call and replayed while
+ * parameters, sizes and buffers stay the same (the seed may change). */
+purse_status purse_batch_solve(purse_batch_t b, const purse_params* p3d, const purse_params* p2d, uint64_t seed,
+                               const double* d_seeds, int n_samples, int n_iters, double* d_results,
+                               purse_stream_t stream);
+
+/* Autotuner: times the walk launch for work-queue chunks {1, 4, 16, 64} x {4, 8} warps per block
+ * on this batch with n_samples walks per PURSE, keeps the fastest for later solves and reports it
+ * (outputs may be NULL).  Synchronises the stream. */
+purse_status purse_batch_tune(purse_batch_t b, const purse_params* p3d, const purse_params* p2d, uint64_t seed,
+                              const double* d_seeds, int n_samples, int* best_chunk, int* best_warps,
+                              float* best_ms, purse_stream_t stream);
+
+/* Copy the farthest-sample sequences of the last solve to d_out (device, n_purses x 2 n_iters int32:
+ * rotation then translation sequence per PURSE).  PURSE_ERR_STATE before the first solve. */
+purse_status purse_batch_copy_farthest(purse_batch_t b, int32_t* d_out, purse_stream_t stream);
+
+/* Copy PURSE p's samples of the last solve (device, n_samples x 4 / x 3 floats each; any may be NULL):
+ * dS_R quaternions and translations, dS_t quaternions and translations (the dS_t buffers are
+ * unwritten for 3D-3D PURSEs). */
+purse_status purse_batch_copy_samples(purse_batch_t b, int p, float* d_q_rot, float* d_t_rot, float* d_q_tr,
+                                      float* d_t_tr, purse_stream_t stream);
+
+/* Synchronise the stream; *evals (host, may be NULL) receives the executed evaluations of the
+ * last batch walk launch; returns the batch's device status. */
+purse_status purse_batch_sync(purse_batch_t b, unsigned long long* evals, purse_stream_t stream);
+
 /* Synchronise the stream and return (and clear) the handle's device status. */
 purse_status purse_sync(purse_t h, purse_stream_t stream);
 

@@ -12,9 +12,12 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpurse.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["api.cu", "walk.cu", "stats.cu", "eval.cu", "megb.cu"]
+SOURCES = ["api.cu", "walk.cu", "stats.cu", "eval.cu", "megb.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", f"-I{INCLUDE}"]
+# The walk and ball kernels are instantiated in several launches (single PURSE, batch) that must draw and
+# decide identically: no implicit multiply-add contraction there, only the explicit fused ops.
+PER_FILE = {"walk.cu": ["-fmad=false"], "megb.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -39,7 +42,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [exe, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [exe, *ARCH, *FLAGS, *PER_FILE.get(src, []), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

@@ -44,7 +44,8 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, ui
 }
 
 // Philox4x32-10 with the ten round keys given (rk[2r], rk[2r+1]) = (k0 + r W0, k1 + r W1).
-__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk) {
+template <class RK>
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const RK& rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;

@@ -33,6 +33,38 @@ struct WalkStats {
 // t_0 - t-bar (0 when degenerate).  16 doubles.
 constexpr int kSeedStride = 16;
 
+// Per-PURSE description inside a batch (device array).
+struct BatchPurseInfo {
+  int kind, n, table_off, pad;  // table rows [table_off, table_off + 2 n) of the concatenated tables
+  double fx, fy, cx, cy;
+};
+
+// Perturbation parameters of the two kinds (index = kind) for the batched statistics.
+struct BatchStatParams {
+  double t_p[2], th_p[2];
+  int raw[2];
+};
+
+// Everything the batched walk kernel reads (kernel parameter).
+struct BatchArgs {
+  const BatchPurseInfo* info;
+  const float* table;  // FP32 tables, rows of 4 floats
+  const WalkStats* stats;
+  const double* seed_data;
+  int n_purses, n_samples, nmax;
+  int n_iter[2], n_perturb[2], n_keep[2], n_steps[2];
+  double omega0[2], v0[2], gamma[2];
+  const unsigned long long* seed;  // device scalar: PURSE p uses key seed + p
+  unsigned int* counter;           // work queue head
+  unsigned int total_items;        // 2 x n_purses x n_samples items (p, sampler, walk)
+  float* q_rot;                    // n_purses x n_samples x 4 (dS_R sampler)
+  float* t_rot;                    // n_purses x n_samples x 3
+  float* q_tr;                     // dS_t sampler
+  float* t_tr;
+  int* status;
+  unsigned long long* evals;
+};
+
 struct WalkArgs {
   const void* table;
   int n;
@@ -82,6 +114,12 @@ purse_status ensure_scratch(purse_t h, size_t bytes);
 cudaError_t launch_stats(purse_t h, const double* d_seeds, int s0, const purse_params* p, WalkStats* d_stats,
                          double* d_seed_data, cudaStream_t st);
 cudaError_t launch_walk(purse_t h, const purse_params* p, const WalkArgs& a, cudaStream_t st);
+cudaError_t launch_stats_batch(int n_purses, const BatchPurseInfo* info, const double* tab64, const double* seeds,
+                               const BatchStatParams& sp, WalkStats* out, double* seed_data, cudaStream_t st);
+size_t batch_walk_smem(int nmax, int n_perturb, int n_steps, int warps);
+cudaError_t launch_batch_walk(const BatchArgs& b, int chunk, int warps, int sm_count, cudaStream_t st);
+cudaError_t launch_megb_batch(const BatchArgs& b, int n_iters, double* d_results, int32_t* d_farthest,
+                              cudaStream_t st);
 cudaError_t launch_ransag(purse_t h, uint64_t seed, int trial0, int n_trials, double* d_pose, uint8_t* d_acc,
                           cudaStream_t st);
 cudaError_t launch_compact(const double* d_pose, const uint8_t* d_acc, int n_trials, double* d_seeds,

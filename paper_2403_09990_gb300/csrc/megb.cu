@@ -213,6 +213,118 @@ cudaError_t launch_megb(purse_t h, int precision, int n_iters, const void* d_q, 
                                scratch, st);
 }
 
+// ---------------------------------------------------------------- one block per ball
+// The same descent with the samples resident in shared memory and all K iterations inside
+// one block: per iteration a block argmax (ties to the lowest index) and the FP64 step by
+// thread 0.  Used for batches of PURSEs (one block per PURSE and ball).
+constexpr int kGgdBlockThreads = 512;
+
+template <typename T, int MODE>
+__device__ void ggd_block(const T* __restrict__ x, int n, int K, double* result, int32_t* f_out, T* xs) {
+  constexpr int D = MODE == 0 ? 4 : 3;
+  __shared__ double c[4];
+  __shared__ double wkey[kGgdBlockThreads / 32];
+  __shared__ int widx[kGgdBlockThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = tid; k < n * D; k += blockDim.x) xs[k] = x[k];
+  if (tid == 0) {
+    if (MODE == 0) {
+      const Q4<double> q0 = qnormalize(Q4<double>{(double)x[0], (double)x[1], (double)x[2], (double)x[3]});
+      c[0] = q0.w, c[1] = q0.x, c[2] = q0.y, c[3] = q0.z;
+    } else {
+      c[0] = x[0], c[1] = x[1], c[2] = x[2], c[3] = 0.0;
+    }
+  }
+  __syncthreads();
+  for (int k = 1; k <= K + 1; ++k) {  // k = K + 1: final pass for the radius
+    const T c0 = T(c[0]), c1 = T(c[1]), c2 = T(c[2]), c3 = T(c[3]);
+    double bk = -1.0;
+    int bi = INT_MAX;
+    for (int i = tid; i < n; i += blockDim.x) {
+      T key;
+      if (MODE == 0) {
+        key = rot_key(c0, c1, c2, c3, xs + 4 * i);
+      } else {
+        const T* pp = xs + 3 * i;
+        const T dx = pp[0] - c0, dy = pp[1] - c1, dz = pp[2] - c2;
+        key = dx * dx + dy * dy + dz * dz;
+      }
+      if ((double)key > bk) bk = (double)key, bi = i;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const double ok = __shfl_xor_sync(kFullMask, bk, o);
+      const int oi = __shfl_xor_sync(kFullMask, bi, o);
+      if (better(ok, oi, bk, bi)) bk = ok, bi = oi;
+    }
+    if (lane == 0) wkey[warp] = bk, widx[warp] = bi;
+    __syncthreads();
+    if (tid == 0) {
+      for (int w2 = 1; w2 < (int)(blockDim.x / 32); ++w2)
+        if (better(wkey[w2], widx[w2], bk, bi)) bk = wkey[w2], bi = widx[w2];
+      if (MODE == 0) {
+        const T* qs = x + 4 * (size_t)bi;
+        const Q4<double> cq{c[0], c[1], c[2], c[3]};
+        const Q4<double> qf = qnormalize(Q4<double>{(double)qs[0], (double)qs[1], (double)qs[2], (double)qs[3]});
+        Q4<double> d = qmul(Q4<double>{cq.w, -cq.x, -cq.y, -cq.z}, qf);
+        if (d.w < 0) d = Q4<double>{-d.w, -d.x, -d.y, -d.z};
+        const double sn = sqrt(d.x * d.x + d.y * d.y + d.z * d.z);
+        const double th = 2.0 * atan2(sn, d.w);
+        if (k <= K) {
+          Q4<double> step{1.0, 0.0, 0.0, 0.0};
+          if (sn > 0.0) {
+            const double h = 0.5 * th / k;
+            const double sh = sin(h) / sn;
+            step = Q4<double>{cos(h), sh * d.x, sh * d.y, sh * d.z};
+          }
+          const Q4<double> cn = qnormalize(qmul(cq, step));
+          c[0] = cn.w, c[1] = cn.x, c[2] = cn.y, c[3] = cn.z;
+        } else {
+          result[0] = cq.w, result[1] = cq.x, result[2] = cq.y, result[3] = cq.z;
+          result[7] = th;
+        }
+      } else {
+        const T* pp = x + 3 * (size_t)bi;
+        if (k <= K) {
+          for (int d = 0; d < 3; ++d) c[d] = c[d] + ((double)pp[d] - c[d]) / k;
+        } else {
+          const double dx = (double)pp[0] - c[0], dy = (double)pp[1] - c[1], dz = (double)pp[2] - c[2];
+          result[4] = c[0], result[5] = c[1], result[6] = c[2];
+          result[8] = sqrt(dx * dx + dy * dy + dz * dz);
+        }
+      }
+      if (k <= K && f_out) f_out[k - 1] = bi;
+    }
+    __syncthreads();
+  }
+}
+
+// Batch: block (p, ball) with ball 0 = rotation (dS_R samples), 1 = translation (3D-3D: dS_R
+// samples, 2D-3D: dS_t samples).  farthest: n_purses x 2K (rotation then translation sequence).
+__global__ void __launch_bounds__(kGgdBlockThreads)
+    ggd_batch_kernel(const __grid_constant__ BatchArgs b, int K, double* results, int32_t* farthest) {
+  extern __shared__ __align__(16) unsigned char ggd_smem[];
+  const int p = blockIdx.x >> 1, ball = blockIdx.x & 1;
+  const size_t off = (size_t)p * b.n_samples;
+  int32_t* f = farthest ? farthest + (size_t)p * 2 * K + ball * K : nullptr;
+  if (ball == 0) {
+    ggd_block<float, 0>(b.q_rot + 4 * off, b.n_samples, K, results + 9 * (size_t)p, f,
+                        reinterpret_cast<float*>(ggd_smem));
+  } else {
+    const float* t = (b.info[p].kind == 0 ? b.t_rot : b.t_tr) + 3 * off;
+    ggd_block<float, 1>(t, b.n_samples, K, results + 9 * (size_t)p, f, reinterpret_cast<float*>(ggd_smem));
+  }
+}
+
+cudaError_t launch_megb_batch(const BatchArgs& b, int n_iters, double* d_results, int32_t* d_farthest,
+                              cudaStream_t st) {
+  const size_t smem = (size_t)b.n_samples * 4 * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(ggd_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  ggd_batch_kernel<<<2 * b.n_purses, kGgdBlockThreads, smem, st>>>(b, n_iters, d_results, d_farthest);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- allocation-free variant
 // megb_solve_noalloc runs the same kernels as megb_solve, but its scratch (ball state,
 // per-block partial maxima, farthest-sample sequence) lives in one file-scope device array

@@ -23,12 +23,11 @@ __device__ void block_sum(double (&v)[NV], double* red) {
   __syncthreads();
 }
 
+// Centre statistics of one PURSE by one block of kStatsThreads threads.
 // tab: FP64 constraint table (rows (a_i, r_i), then (b_i or z_i, r_i^2)).
-__global__ void __launch_bounds__(kStatsThreads)
-    stats_kernel(const double* seeds, int s0, const double* tab, int n, int kind, double fx, double fy, double t_p,
-                 double th_p, int raw_units, WalkStats* out, double* seed_data) {
-  __shared__ double red[12 * kStatsThreads];
-  __shared__ WalkStats sh;
+__device__ void stats_block(const double* seeds, int s0, const double* tab, int n, int kind, double fx, double fy,
+                            double t_p, double th_p, int raw_units, WalkStats* out, double* seed_data, double* red,
+                            WalkStats& sh) {
   const int tid = threadIdx.x;
   // sums of seed rotations and translations
   double acc[12];
@@ -125,6 +124,33 @@ __global__ void __launch_bounds__(kStatsThreads)
     for (int c = 0; c < 3; ++c) o[10 + c] = has_d ? d[c] / dn : 0.0;
     for (int c = 13; c < kSeedStride; ++c) o[c] = 0.0;
   }
+}
+
+__global__ void __launch_bounds__(kStatsThreads)
+    stats_kernel(const double* seeds, int s0, const double* tab, int n, int kind, double fx, double fy, double t_p,
+                 double th_p, int raw_units, WalkStats* out, double* seed_data) {
+  __shared__ double red[12 * kStatsThreads];
+  __shared__ WalkStats sh;
+  stats_block(seeds, s0, tab, n, kind, fx, fy, t_p, th_p, raw_units, out, seed_data, red, sh);
+}
+
+// One block per PURSE of a batch; one seed pose per PURSE.
+__global__ void __launch_bounds__(kStatsThreads) stats_batch_kernel(const BatchPurseInfo* info, const double* tab64,
+                                                                    const double* seeds, BatchStatParams sp,
+                                                                    WalkStats* out, double* seed_data) {
+  __shared__ double red[12 * kStatsThreads];
+  __shared__ WalkStats sh;
+  const int p = blockIdx.x;
+  const BatchPurseInfo in = info[p];
+  stats_block(seeds + 12 * (size_t)p, 1, tab64 + 4 * (size_t)in.table_off, in.n, in.kind, in.fx, in.fy,
+              sp.t_p[in.kind], sp.th_p[in.kind], sp.raw[in.kind], out + p, seed_data + (size_t)p * kSeedStride, red,
+              sh);
+}
+
+cudaError_t launch_stats_batch(int n_purses, const BatchPurseInfo* info, const double* tab64, const double* seeds,
+                               const BatchStatParams& sp, WalkStats* out, double* seed_data, cudaStream_t st) {
+  stats_batch_kernel<<<n_purses, kStatsThreads, 0, st>>>(info, tab64, seeds, sp, out, seed_data);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_stats(purse_t h, const double* d_seeds, int s0, const purse_params* p, WalkStats* d_stats,

@@ -148,8 +148,8 @@ __device__ __forceinline__ Slab<T> carve(unsigned char* base, int N, int NP, int
 // Perturbation phase over NPAIR pairs per lane, starting at pair pb: pair P of this lane holds
 // perturbations j = 2 b, 2 b + 1 with b = 32 P + lane, the two points of block 0 of stream
 // (phase, b, it, w).  Writes the keys of every valid j.
-template <typename T, int KIND, int SAMPLER, int NPAIR>
-__device__ __forceinline__ void dist_pass(const WalkArgs& a, int it, int w, const Slab<T>& sl, int N, int NP, int lane,
+template <typename T, int KIND, int SAMPLER, int NPAIR, class RK>
+__device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Slab<T>& sl, int N, int NP, int lane,
                                           int pb, T r_pert, const V3<T>& t, T fx, T fy, T cx, T cy, T qzmin) {
   using T2 = P2<T>;
   T2 dmin[NPAIR], zmin[NPAIR];
@@ -164,7 +164,7 @@ __device__ __forceinline__ void dist_pass(const WalkArgs& a, int it, int w, cons
     if (2 * b < NP)
       wd = philox4x32_10_rk(make_uint4(0u, ((SAMPLER == 0 ? kPhaseRPerturb : kPhaseTPerturb) << 24) | (uint32_t)b,
                                        (uint32_t)it, (uint32_t)w),
-                            a.rk);
+                            rk);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int j = 2 * b + h;
@@ -257,17 +257,334 @@ __device__ __forceinline__ void dist_pass(const WalkArgs& a, int it, int w, cons
   }
 }
 
-template <typename T, int KIND, int SAMPLER>
-__global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1) walk_kernel(const WalkArgs a, const int mc, const int slab_bytes) {
+// Everything one walk needs about its PURSE and parameters (kept in registers).
+template <typename T>
+struct WalkCtx {
+  int N, NP, K, NT, mc, n_iter;
+  T fx, fy, cx, cy, r_pert;
+  double omega0, v0, gamma;
+  const WalkStats* st;
+  const double* seed_data;
+  int s0;
+  uint32_t key0, key1;
+  T* out_q;
+  T* out_t;
+  int16_t* trace;
+  int* status;
+};
+
+// Philox round keys from the kernel parameters (constant bank) or from memory.
+struct RkParam {
+  const WalkArgs& a;
+  __device__ __forceinline__ uint32_t operator[](int i) const { return a.rk[i]; }
+};
+struct RkPtr {
+  const uint32_t* p;
+  __device__ __forceinline__ uint32_t operator[](int i) const { return p[i]; }
+};
+
+// One walk of Alg. 3 (dS_R) or Alg. 5 (dS_t): N_I iterations from seed (w mod |S0|), then emit.
+// tab: the PURSE's constraint table in shared memory; sl: this warp's slab.
+template <typename T, int KIND, int SAMPLER, class RK>
+__device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int w, const T4<T>* tab,
+                                         const Slab<T>& sl, int lane, unsigned long long& evals) {
   using Key = typename KeyOf<T>::type;
   using T2 = P2<T>;
+  const int N = c.N, NQ = ladder_pairs(c.N);
+  const int NP = c.NP, K = c.K, NT = c.NT, mc = c.mc;
+  const T fx = c.fx, fy = c.fy, cx = c.cx, cy = c.cy, r_pert = c.r_pert;
+  const WalkStats* st = c.st;
+  const int ncand = mc * K;
+  const int cm = lane / K, ck = lane - (lane / K) * K;
+  const int npair = (NP + 63) / 64;
+  // ---- a3: start pose and velocity, ladder table of this walk.
+  const double* sd = c.seed_data + (size_t)(w % c.s0) * kSeedStride;
+  Q4<T> q{T(sd[0]), T(sd[1]), T(sd[2]), T(sd[3])};
+  V3<T> t{T(sd[4]), T(sd[5]), T(sd[6])};
+  V3<T> vel;
+  {
+    Stream s(c.key0, c.key1, SAMPLER == 0 ? kPhaseOmega : kPhaseV, 0u, 0u, (uint32_t)w);
+    int X, Y, Z;
+    lattice_draw<true>(s, X, Y, Z);
+    const double nr = sqrt((double)(X * X + Y * Y + Z * Z));
+    const double ux = nr > 0 ? X / nr : 0.0, uy = nr > 0 ? Y / nr : 0.0, uz = nr > 0 ? Z / nr : 0.0;
+    if (SAMPLER == 0) {
+      vel = V3<T>{T(c.omega0 * (sd[7] + ux)), T(c.omega0 * (sd[8] + uy)), T(c.omega0 * (sd[9] + uz))};
+    } else {
+      const double d0 = sd[10] + ux, d1 = sd[11] + uy, d2 = sd[12] + uz;
+      vel = V3<T>{T(c.v0 * (st->S[0] * d0 + st->S[1] * d1 + st->S[2] * d2)),
+                  T(c.v0 * (st->S[3] * d0 + st->S[4] * d1 + st->S[5] * d2)),
+                  T(c.v0 * (st->S[6] * d0 + st->S[7] * d1 + st->S[8] * d2))};
+    }
+  }
+  for (int m = lane; m < NT; m += 32) {
+    T sm = T(1);
+    for (int k = 0; k < m; ++k) sm *= T(c.gamma);
+    if (SAMPLER == 0) {
+      const Q4<T> e = qexp(V3<T>{sm * vel.x, sm * vel.y, sm * vel.z});
+      M3<T> E = qmat(e);
+      if (KIND == 1) {
+        for (int c = 0; c < 3; ++c) {
+          E.m[c] = fx * E.m[c] + cx * E.m[6 + c];
+          E.m[3 + c] = fy * E.m[3 + c] + cy * E.m[6 + c];
+        }
+      }
+      sl.E[4 * m] = T4<T>{e.w, e.x, e.y, e.z};
+      for (int r = 0; r < 3; ++r) sl.E[4 * m + 1 + r] = T4<T>{E.m[3 * r], E.m[3 * r + 1], E.m[3 * r + 2], T(0)};
+    } else {
+      sl.E[4 * m] = T4<T>{sm * vel.x, sm * vel.y, sm * vel.z, T(0)};
+    }
+  }
+  __syncwarp();
+
+  for (int it = 0; it < c.n_iter; ++it) {
+    const M3<T> R = qmat(q);
+    // ---- constraint order: ascending margin of the current pose (N <= 32; the order only decides how
+    //      soon the ladder's early exit triggers), then the tables
+    int perm = lane;
+    if (N <= 32) {
+      uint32_t kk = 0xFFFFFFFFu;
+      if (lane < N) {
+        const T4<T> mz = tab[lane], ob = tab[N + lane];
+        const V3<T> X = mul(R, V3<T>{mz.x, mz.y, mz.z}) + t;
+        float m;
+        if (KIND == 1) {
+          const T Pz = X.z, ex = fx * X.x + cx * X.z - ob.x * Pz, ey = fy * X.y + cy * X.z - ob.y * Pz;
+          m = Pz > T(0) ? (float)(mz.w * Pz * mz.w * Pz - ex * ex - ey * ey) : -INFINITY;
+        } else {
+          const T ex = X.x - ob.x, ey = X.y - ob.y, ez = X.z - ob.z;
+          m = (float)(ob.w - ex * ex - ey * ey - ez * ez);
+        }
+        kk = (orderable(m) & ~31u) | (uint32_t)lane;
+      }
+#pragma unroll
+      for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+          const uint32_t o = __shfl_xor_sync(kFullMask, kk, stride);
+          const bool up = ((lane & size) == 0);
+          const bool lower = (lane & stride) == 0;
+          const uint32_t mn = kk < o ? kk : o, mx = kk < o ? o : kk;
+          kk = (lower == up) ? mn : mx;
+        }
+      }
+      perm = (int)(kk & 31u);
+    }
+    T qzmin = inf<T>();
+    for (int r = lane; r < N; r += 32) {
+      const int i = N <= 32 ? perm : r;
+      const T4<T> mz = tab[i], ob = tab[N + i];
+      const V3<T> Y = mul(R, V3<T>{mz.x, mz.y, mz.z});
+      T2* Dr = sl.D + 8 * r;
+      if (SAMPLER == 0) {
+        if (KIND == 1) {
+          const V3<T> X = Y + t;
+          const T qz = X.z;
+          Dr[0] = dup(fx * X.x + cx * X.z), Dr[1] = dup(fy * X.y + cy * X.z), Dr[2] = dup(qz);
+          qzmin = fmin(qzmin, qz);
+        } else {
+          Dr[0] = dup(Y.x + t.x - ob.x), Dr[1] = dup(Y.y + t.y - ob.y), Dr[2] = dup(Y.z + t.z - ob.z);
+        }
+      } else {
+        Dr[0] = dup(Y.x), Dr[1] = dup(Y.y), Dr[2] = dup(Y.z);
+      }
+      Dr[3] = dup(mz.w);
+      if (KIND == 1) {
+        Dr[4] = dup(-ob.x), Dr[5] = dup(-ob.y);
+      } else if (SAMPLER == 1) {
+        Dr[4] = dup(t.x - ob.x), Dr[5] = dup(t.y - ob.y), Dr[6] = dup(t.z - ob.z);
+      }
+      // ladder table: constraint r in half (r & 1) of pair r / 2
+      T* Lq = reinterpret_cast<T*>(sl.L + 8 * (r >> 1)) + (r & 1);
+      Lq[0] = Y.x, Lq[2] = Y.y, Lq[4] = Y.z;
+      if (KIND == 1) {
+        Lq[6] = -ob.x, Lq[8] = -ob.y, Lq[10] = -ob.w;
+      } else {
+        Lq[6] = -ob.x, Lq[8] = -ob.y, Lq[10] = -ob.z, Lq[12] = -ob.w;
+      }
+    }
+    if ((N & 1) && lane == 0) {  // odd N: the second half of the last pair is always satisfied
+      T* Lq = reinterpret_cast<T*>(sl.L + 8 * (N >> 1)) + 1;
+      Lq[0] = Lq[2] = Lq[4] = T(0);
+      Lq[6] = Lq[8] = T(0);
+      Lq[10] = T(-1e30);
+      if (KIND == 0) Lq[10] = T(0), Lq[12] = T(-1e30);
+    }
+    if (SAMPLER == 0 && KIND == 1) {
+#pragma unroll
+      for (int o = 16; o; o >>= 1) qzmin = fmin(qzmin, __shfl_xor_sync(kFullMask, qzmin, o));
+    }
+    __syncwarp();
+
+    // ---- a4: perturbations and their distance to the boundary (eq. 11)
+    if constexpr (SAMPLER == 0) {
+      if (npair == 4)
+        dist_pass<T, KIND, SAMPLER, 4>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
+      else if (npair == 3)
+        dist_pass<T, KIND, SAMPLER, 3>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
+      else if (npair == 2)
+        dist_pass<T, KIND, SAMPLER, 2>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
+      else
+        dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
+    } else {
+      // dS_t keeps one rotation per perturbation in registers: two pairs at a time
+      for (int pb = 0; pb < npair; pb += 2) {
+        if (npair - pb >= 2)
+          dist_pass<T, KIND, SAMPLER, 2>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
+        else
+          dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
+      }
+    }
+    evals += (unsigned long long)NP * N;
+    __syncwarp();
+
+    // ---- a5: top_k_indices (ties to the lower j): per-lane sorted keys, warp max rounds
+    {
+      Key kk[8];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int j = lane + 32 * s;
+        kk[s] = j < NP ? ((sl.key[j] & ~Key(7)) | Key(7 - s)) : Key(0);
+      }
+      sort8_desc(kk);
+      for (int r = 0; r < K; ++r) {
+        const Key mx = warp_max_key(kk[0]);
+        const unsigned bal = __ballot_sync(kFullMask, kk[0] == mx);
+        const int wl = __ffs(bal) - 1;
+        if (lane == wl) {
+#pragma unroll
+          for (int s = 0; s < 7; ++s) kk[s] = kk[s + 1];
+          kk[7] = Key(0);
+        }
+        if (lane == 0) sl.J[r] = wl + 32 * (7 - (int)(mx & Key(7)));
+      }
+    }
+    __syncwarp();
+
+    // ---- a6/a7: step ladder + in_purse with early exit, find_farthest
+    int m0 = -1, k0 = -1;
+    V3<T> base{T(0), T(0), T(0)};
+    M3<T> Ak;  // dS_t: (K) R_{j_k}
+    if (lane < ncand) {
+      const T4<T> pj = sl.P[sl.J[ck]];
+      if (SAMPLER == 0) {
+        const V3<T> tk{t.x + pj.x, t.y + pj.y, t.z + pj.z};
+        base = KIND == 1 ? V3<T>{fx * tk.x + cx * tk.z, fy * tk.y + cy * tk.z, tk.z} : tk;
+      } else {
+        Ak = qmat(Q4<T>{pj.x, pj.y, pj.z, pj.w});
+        if (KIND == 1) {
+          for (int c = 0; c < 3; ++c) {
+            Ak.m[c] = fx * Ak.m[c] + cx * Ak.m[6 + c];
+            Ak.m[3 + c] = fy * Ak.m[3 + c] + cy * Ak.m[6 + c];
+          }
+        }
+      }
+    }
+    for (int mb = 0; mb < NT; mb += mc) {
+      const int m = mb + cm;
+      const bool active = lane < ncand && m < NT;
+      M3<T> M = M3<T>{{T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)}};
+      V3<T> bm = base;
+      if (active) {
+        if (SAMPLER == 0) {
+          const T4<T> e0 = sl.E[4 * m + 1], e1 = sl.E[4 * m + 2], e2 = sl.E[4 * m + 3];
+          M = M3<T>{{e0.x, e0.y, e0.z, e1.x, e1.y, e1.z, e2.x, e2.y, e2.z}};
+        } else {
+          M = Ak;
+          const T4<T> sv = sl.E[4 * m];
+          const V3<T> Tm{t.x + sv.x, t.y + sv.y, t.z + sv.z};
+          bm = KIND == 1 ? V3<T>{fx * Tm.x + cx * Tm.z, fy * Tm.y + cy * Tm.z, Tm.z} : Tm;
+        }
+      }
+      T2 M2[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) M2[c] = dup(M.m[c]);
+      const T2 bx = dup(bm.x), by = dup(bm.y), bz = dup(bm.z);
+      T2 cmax = dup(-inf<T>()), zmin = dup(inf<T>());
+      bool alive = active;
+      const int nact = K * min(mc, NT - mb);
+      int done = 0;
+      for (int g0 = 0; g0 < NQ; g0 += 2) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int qi = g0 + u;
+          if (qi < NQ) {
+            const T2* Lq = sl.L + 8 * qi;
+            const T2 yx = Lq[0], yy = Lq[1], yz = Lq[2], o3 = Lq[3], o4 = Lq[4], o5 = Lq[5];
+            const T2 Px = fma2(M2[0], yx, fma2(M2[1], yy, fma2(M2[2], yz, bx)));
+            const T2 Py = fma2(M2[3], yx, fma2(M2[4], yy, fma2(M2[5], yz, by)));
+            const T2 Pz = fma2(M2[6], yx, fma2(M2[7], yy, fma2(M2[8], yz, bz)));
+            T2 c;
+            if (KIND == 1) {
+              const T2 ex = fma2(o3, Pz, Px), ey = fma2(o4, Pz, Py);
+              c = fma2(o5, mul2(Pz, Pz), fma2(ey, ey, mul2(ex, ex)));
+              zmin = min2(zmin, Pz);
+            } else {
+              const T2 ex = add2(Px, o3), ey = add2(Py, o4), ez = add2(Pz, o5);
+              c = add2(fma2(ez, ez, fma2(ey, ey, mul2(ex, ex))), Lq[6]);
+            }
+            cmax = max2(cmax, c);
+          }
+        }
+        done = min(N, 2 * (g0 + 2));
+        alive = alive && fmax(cmax.x, cmax.y) <= T(0) && (KIND == 0 || fmin(zmin.x, zmin.y) > T(0));
+        if (!__any_sync(kFullMask, alive)) break;
+      }
+      evals += (unsigned long long)nact * done;
+      const unsigned bal = __ballot_sync(kFullMask, alive);
+      if (bal) {
+        const int l = __ffs(bal) - 1;
+        m0 = mb + l / K;
+        k0 = l - (l / K) * K;
+        break;
+      }
+    }
+
+    // ---- update (R*, t*)
+    if (m0 >= 0) {
+      const T4<T> pj = sl.P[sl.J[k0]];
+      if (SAMPLER == 0) {
+        const T4<T> e = sl.E[4 * m0];
+        q = qnormalize(qmul(Q4<T>{e.x, e.y, e.z, e.w}, q));
+        t = V3<T>{t.x + pj.x, t.y + pj.y, t.z + pj.z};
+      } else {
+        q = qnormalize(qmul(Q4<T>{pj.x, pj.y, pj.z, pj.w}, q));
+        const T4<T> sv = sl.E[4 * m0];
+        t = V3<T>{t.x + sv.x, t.y + sv.y, t.z + sv.z};
+      }
+    }
+    if (c.trace != nullptr && lane == 0) {
+      int16_t* tr = c.trace + ((size_t)w * c.n_iter + it) * (K + 2);
+      for (int r = 0; r < K; ++r) tr[r] = (int16_t)sl.J[r];
+      tr[K] = (int16_t)m0;
+      tr[K + 1] = (int16_t)k0;
+    }
+    __syncwarp();
+  }
+
+  // ---- a8: emit
+  if (lane == 0) {
+    T* oq = c.out_q + 4 * (size_t)w;
+    T* ot = c.out_t + 3 * (size_t)w;
+    oq[0] = q.w, oq[1] = q.x, oq[2] = q.y, oq[3] = q.z;
+    ot[0] = t.x, ot[1] = t.y, ot[2] = t.z;
+    if (!(isfinite(q.w) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(t.x) && isfinite(t.y) &&
+          isfinite(t.z)))
+      atomicOr(c.status, kDevErrNumeric);
+  }
+  __syncwarp();
+}
+
+template <typename T, int KIND, int SAMPLER>
+__global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
+    walk_kernel(const __grid_constant__ WalkArgs a, const int mc, const int slab_bytes) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  const int N = a.n, NQ = ladder_pairs(a.n);
-  const int NP = a.n_perturb, K = a.n_keep, NT = a.n_steps;
+  const int N = a.n;
   const T4<T>* tab = reinterpret_cast<const T4<T>*>(smem + 128);  // rows [0,N): (a, r); [N,2N): (b or z, r^2)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const Slab<T> sl = carve<T>(smem + 128 + walk_table_bytes<T>(N) + (size_t)warp * slab_bytes, N, NP, NT);
+  const Slab<T> sl = carve<T>(smem + 128 + walk_table_bytes<T>(N) + (size_t)warp * slab_bytes, N, a.n_perturb,
+                              a.n_steps);
 
   // ---- a0: stage the constraint table with a 1-D TMA bulk copy.
   const uint32_t tbytes = 8u * N * sizeof(T);
@@ -281,294 +598,110 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1) walk_ker
     if (threadIdx.x == 0) atomicOr(a.status, kDevErrTimeout);
     return;
   }
-
-  const T fx = T(a.fx), fy = T(a.fy), cx = T(a.cx), cy = T(a.cy);
-  const WalkStats* st = a.stats;
-  const T r_pert = T(SAMPLER == 0 ? st->r_trans : st->r_rot);
-  const int ncand = mc * K;
-  const int cm = lane / K, ck = lane - (lane / K) * K;
-  const int npair = (NP + 63) / 64;
+  WalkCtx<T> c;
+  c.N = N, c.NP = a.n_perturb, c.K = a.n_keep, c.NT = a.n_steps, c.mc = mc, c.n_iter = a.n_iter;
+  c.fx = T(a.fx), c.fy = T(a.fy), c.cx = T(a.cx), c.cy = T(a.cy);
+  c.r_pert = T(SAMPLER == 0 ? a.stats->r_trans : a.stats->r_rot);
+  c.omega0 = a.omega0, c.v0 = a.v0, c.gamma = a.gamma;
+  c.st = a.stats, c.seed_data = a.seed_data, c.s0 = a.s0;
+  c.key0 = a.key0, c.key1 = a.key1;
+  c.out_q = reinterpret_cast<T*>(a.out_q), c.out_t = reinterpret_cast<T*>(a.out_t);
+  c.trace = a.trace, c.status = a.status;
+  const RkParam rk{a};
   unsigned long long evals = 0;
-
-  for (int w = blockIdx.x * kWalkWarps + warp; w < a.n_samples; w += gridDim.x * kWalkWarps) {
-    // ---- a3: start pose and velocity, ladder table of this walk.
-    const double* sd = a.seed_data + (size_t)(w % a.s0) * kSeedStride;
-    Q4<T> q{T(sd[0]), T(sd[1]), T(sd[2]), T(sd[3])};
-    V3<T> t{T(sd[4]), T(sd[5]), T(sd[6])};
-    V3<T> vel;
-    {
-      Stream s(a.key0, a.key1, SAMPLER == 0 ? kPhaseOmega : kPhaseV, 0u, 0u, (uint32_t)w);
-      int X, Y, Z;
-      lattice_draw<true>(s, X, Y, Z);
-      const double nr = sqrt((double)(X * X + Y * Y + Z * Z));
-      const double ux = nr > 0 ? X / nr : 0.0, uy = nr > 0 ? Y / nr : 0.0, uz = nr > 0 ? Z / nr : 0.0;
-      if (SAMPLER == 0) {
-        vel = V3<T>{T(a.omega0 * (sd[7] + ux)), T(a.omega0 * (sd[8] + uy)), T(a.omega0 * (sd[9] + uz))};
-      } else {
-        const double d0 = sd[10] + ux, d1 = sd[11] + uy, d2 = sd[12] + uz;
-        vel = V3<T>{T(a.v0 * (st->S[0] * d0 + st->S[1] * d1 + st->S[2] * d2)),
-                    T(a.v0 * (st->S[3] * d0 + st->S[4] * d1 + st->S[5] * d2)),
-                    T(a.v0 * (st->S[6] * d0 + st->S[7] * d1 + st->S[8] * d2))};
-      }
-    }
-    for (int m = lane; m < NT; m += 32) {
-      T sm = T(1);
-      for (int k = 0; k < m; ++k) sm *= T(a.gamma);
-      if (SAMPLER == 0) {
-        const Q4<T> e = qexp(V3<T>{sm * vel.x, sm * vel.y, sm * vel.z});
-        M3<T> E = qmat(e);
-        if (KIND == 1) {
-          for (int c = 0; c < 3; ++c) {
-            E.m[c] = fx * E.m[c] + cx * E.m[6 + c];
-            E.m[3 + c] = fy * E.m[3 + c] + cy * E.m[6 + c];
-          }
-        }
-        sl.E[4 * m] = T4<T>{e.w, e.x, e.y, e.z};
-        for (int r = 0; r < 3; ++r) sl.E[4 * m + 1 + r] = T4<T>{E.m[3 * r], E.m[3 * r + 1], E.m[3 * r + 2], T(0)};
-      } else {
-        sl.E[4 * m] = T4<T>{sm * vel.x, sm * vel.y, sm * vel.z, T(0)};
-      }
-    }
-    __syncwarp();
-
-    for (int it = 0; it < a.n_iter; ++it) {
-      const M3<T> R = qmat(q);
-      // ---- constraint order: ascending margin of the current pose (N <= 32; the order only decides how
-      //      soon the ladder's early exit triggers), then the tables
-      int perm = lane;
-      if (N <= 32) {
-        uint32_t kk = 0xFFFFFFFFu;
-        if (lane < N) {
-          const T4<T> mz = tab[lane], ob = tab[N + lane];
-          const V3<T> X = mul(R, V3<T>{mz.x, mz.y, mz.z}) + t;
-          float m;
-          if (KIND == 1) {
-            const T Pz = X.z, ex = fx * X.x + cx * X.z - ob.x * Pz, ey = fy * X.y + cy * X.z - ob.y * Pz;
-            m = Pz > T(0) ? (float)(mz.w * Pz * mz.w * Pz - ex * ex - ey * ey) : -INFINITY;
-          } else {
-            const T ex = X.x - ob.x, ey = X.y - ob.y, ez = X.z - ob.z;
-            m = (float)(ob.w - ex * ex - ey * ey - ez * ez);
-          }
-          kk = (orderable(m) & ~31u) | (uint32_t)lane;
-        }
-#pragma unroll
-        for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-          for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            const uint32_t o = __shfl_xor_sync(kFullMask, kk, stride);
-            const bool up = ((lane & size) == 0);
-            const bool lower = (lane & stride) == 0;
-            const uint32_t mn = kk < o ? kk : o, mx = kk < o ? o : kk;
-            kk = (lower == up) ? mn : mx;
-          }
-        }
-        perm = (int)(kk & 31u);
-      }
-      T qzmin = inf<T>();
-      for (int r = lane; r < N; r += 32) {
-        const int i = N <= 32 ? perm : r;
-        const T4<T> mz = tab[i], ob = tab[N + i];
-        const V3<T> Y = mul(R, V3<T>{mz.x, mz.y, mz.z});
-        T2* Dr = sl.D + 8 * r;
-        if (SAMPLER == 0) {
-          if (KIND == 1) {
-            const V3<T> X = Y + t;
-            const T qz = X.z;
-            Dr[0] = dup(fx * X.x + cx * X.z), Dr[1] = dup(fy * X.y + cy * X.z), Dr[2] = dup(qz);
-            qzmin = fmin(qzmin, qz);
-          } else {
-            Dr[0] = dup(Y.x + t.x - ob.x), Dr[1] = dup(Y.y + t.y - ob.y), Dr[2] = dup(Y.z + t.z - ob.z);
-          }
-        } else {
-          Dr[0] = dup(Y.x), Dr[1] = dup(Y.y), Dr[2] = dup(Y.z);
-        }
-        Dr[3] = dup(mz.w);
-        if (KIND == 1) {
-          Dr[4] = dup(-ob.x), Dr[5] = dup(-ob.y);
-        } else if (SAMPLER == 1) {
-          Dr[4] = dup(t.x - ob.x), Dr[5] = dup(t.y - ob.y), Dr[6] = dup(t.z - ob.z);
-        }
-        // ladder table: constraint r in half (r & 1) of pair r / 2
-        T* Lq = reinterpret_cast<T*>(sl.L + 8 * (r >> 1)) + (r & 1);
-        Lq[0] = Y.x, Lq[2] = Y.y, Lq[4] = Y.z;
-        if (KIND == 1) {
-          Lq[6] = -ob.x, Lq[8] = -ob.y, Lq[10] = -ob.w;
-        } else {
-          Lq[6] = -ob.x, Lq[8] = -ob.y, Lq[10] = -ob.z, Lq[12] = -ob.w;
-        }
-      }
-      if ((N & 1) && lane == 0) {  // odd N: the second half of the last pair is always satisfied
-        T* Lq = reinterpret_cast<T*>(sl.L + 8 * (N >> 1)) + 1;
-        Lq[0] = Lq[2] = Lq[4] = T(0);
-        Lq[6] = Lq[8] = T(0);
-        Lq[10] = T(-1e30);
-        if (KIND == 0) Lq[10] = T(0), Lq[12] = T(-1e30);
-      }
-      if (SAMPLER == 0 && KIND == 1) {
-#pragma unroll
-        for (int o = 16; o; o >>= 1) qzmin = fmin(qzmin, __shfl_xor_sync(kFullMask, qzmin, o));
-      }
-      __syncwarp();
-
-      // ---- a4: perturbations and their distance to the boundary (eq. 11)
-      if constexpr (SAMPLER == 0) {
-        if (npair == 4)
-          dist_pass<T, KIND, SAMPLER, 4>(a, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
-        else if (npair == 3)
-          dist_pass<T, KIND, SAMPLER, 3>(a, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
-        else if (npair == 2)
-          dist_pass<T, KIND, SAMPLER, 2>(a, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
-        else
-          dist_pass<T, KIND, SAMPLER, 1>(a, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
-      } else {
-        // dS_t keeps one rotation per perturbation in registers: two pairs at a time
-        for (int pb = 0; pb < npair; pb += 2) {
-          if (npair - pb >= 2)
-            dist_pass<T, KIND, SAMPLER, 2>(a, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
-          else
-            dist_pass<T, KIND, SAMPLER, 1>(a, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
-        }
-      }
-      evals += (unsigned long long)NP * N;
-      __syncwarp();
-
-      // ---- a5: top_k_indices (ties to the lower j): per-lane sorted keys, warp max rounds
-      {
-        Key kk[8];
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          const int j = lane + 32 * s;
-          kk[s] = j < NP ? ((sl.key[j] & ~Key(7)) | Key(7 - s)) : Key(0);
-        }
-        sort8_desc(kk);
-        for (int r = 0; r < K; ++r) {
-          const Key mx = warp_max_key(kk[0]);
-          const unsigned bal = __ballot_sync(kFullMask, kk[0] == mx);
-          const int wl = __ffs(bal) - 1;
-          if (lane == wl) {
-#pragma unroll
-            for (int s = 0; s < 7; ++s) kk[s] = kk[s + 1];
-            kk[7] = Key(0);
-          }
-          if (lane == 0) sl.J[r] = wl + 32 * (7 - (int)(mx & Key(7)));
-        }
-      }
-      __syncwarp();
-
-      // ---- a6/a7: step ladder + in_purse with early exit, find_farthest
-      int m0 = -1, k0 = -1;
-      V3<T> base{T(0), T(0), T(0)};
-      M3<T> Ak;  // dS_t: (K) R_{j_k}
-      if (lane < ncand) {
-        const T4<T> pj = sl.P[sl.J[ck]];
-        if (SAMPLER == 0) {
-          const V3<T> tk{t.x + pj.x, t.y + pj.y, t.z + pj.z};
-          base = KIND == 1 ? V3<T>{fx * tk.x + cx * tk.z, fy * tk.y + cy * tk.z, tk.z} : tk;
-        } else {
-          Ak = qmat(Q4<T>{pj.x, pj.y, pj.z, pj.w});
-          if (KIND == 1) {
-            for (int c = 0; c < 3; ++c) {
-              Ak.m[c] = fx * Ak.m[c] + cx * Ak.m[6 + c];
-              Ak.m[3 + c] = fy * Ak.m[3 + c] + cy * Ak.m[6 + c];
-            }
-          }
-        }
-      }
-      for (int mb = 0; mb < NT; mb += mc) {
-        const int m = mb + cm;
-        const bool active = lane < ncand && m < NT;
-        M3<T> M = M3<T>{{T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)}};
-        V3<T> bm = base;
-        if (active) {
-          if (SAMPLER == 0) {
-            const T4<T> e0 = sl.E[4 * m + 1], e1 = sl.E[4 * m + 2], e2 = sl.E[4 * m + 3];
-            M = M3<T>{{e0.x, e0.y, e0.z, e1.x, e1.y, e1.z, e2.x, e2.y, e2.z}};
-          } else {
-            M = Ak;
-            const T4<T> sv = sl.E[4 * m];
-            const V3<T> Tm{t.x + sv.x, t.y + sv.y, t.z + sv.z};
-            bm = KIND == 1 ? V3<T>{fx * Tm.x + cx * Tm.z, fy * Tm.y + cy * Tm.z, Tm.z} : Tm;
-          }
-        }
-        T2 M2[9];
-#pragma unroll
-        for (int c = 0; c < 9; ++c) M2[c] = dup(M.m[c]);
-        const T2 bx = dup(bm.x), by = dup(bm.y), bz = dup(bm.z);
-        T2 cmax = dup(-inf<T>()), zmin = dup(inf<T>());
-        bool alive = active;
-        const int nact = K * min(mc, NT - mb);
-        int done = 0;
-        for (int g0 = 0; g0 < NQ; g0 += 2) {
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int qi = g0 + u;
-            if (qi < NQ) {
-              const T2* Lq = sl.L + 8 * qi;
-              const T2 yx = Lq[0], yy = Lq[1], yz = Lq[2], o3 = Lq[3], o4 = Lq[4], o5 = Lq[5];
-              const T2 Px = fma2(M2[0], yx, fma2(M2[1], yy, fma2(M2[2], yz, bx)));
-              const T2 Py = fma2(M2[3], yx, fma2(M2[4], yy, fma2(M2[5], yz, by)));
-              const T2 Pz = fma2(M2[6], yx, fma2(M2[7], yy, fma2(M2[8], yz, bz)));
-              T2 c;
-              if (KIND == 1) {
-                const T2 ex = fma2(o3, Pz, Px), ey = fma2(o4, Pz, Py);
-                c = fma2(o5, mul2(Pz, Pz), fma2(ey, ey, mul2(ex, ex)));
-                zmin = min2(zmin, Pz);
-              } else {
-                const T2 ex = add2(Px, o3), ey = add2(Py, o4), ez = add2(Pz, o5);
-                c = add2(fma2(ez, ez, fma2(ey, ey, mul2(ex, ex))), Lq[6]);
-              }
-              cmax = max2(cmax, c);
-            }
-          }
-          done = min(N, 2 * (g0 + 2));
-          alive = alive && fmax(cmax.x, cmax.y) <= T(0) && (KIND == 0 || fmin(zmin.x, zmin.y) > T(0));
-          if (!__any_sync(kFullMask, alive)) break;
-        }
-        evals += (unsigned long long)nact * done;
-        const unsigned bal = __ballot_sync(kFullMask, alive);
-        if (bal) {
-          const int l = __ffs(bal) - 1;
-          m0 = mb + l / K;
-          k0 = l - (l / K) * K;
-          break;
-        }
-      }
-
-      // ---- update (R*, t*)
-      if (m0 >= 0) {
-        const T4<T> pj = sl.P[sl.J[k0]];
-        if (SAMPLER == 0) {
-          const T4<T> e = sl.E[4 * m0];
-          q = qnormalize(qmul(Q4<T>{e.x, e.y, e.z, e.w}, q));
-          t = V3<T>{t.x + pj.x, t.y + pj.y, t.z + pj.z};
-        } else {
-          q = qnormalize(qmul(Q4<T>{pj.x, pj.y, pj.z, pj.w}, q));
-          const T4<T> sv = sl.E[4 * m0];
-          t = V3<T>{t.x + sv.x, t.y + sv.y, t.z + sv.z};
-        }
-      }
-      if (a.trace != nullptr && lane == 0) {
-        int16_t* tr = a.trace + ((size_t)w * a.n_iter + it) * (K + 2);
-        for (int r = 0; r < K; ++r) tr[r] = (int16_t)sl.J[r];
-        tr[K] = (int16_t)m0;
-        tr[K + 1] = (int16_t)k0;
-      }
-      __syncwarp();
-    }
-
-    // ---- a8: emit
-    if (lane == 0) {
-      T* oq = reinterpret_cast<T*>(a.out_q) + 4 * (size_t)w;
-      T* ot = reinterpret_cast<T*>(a.out_t) + 3 * (size_t)w;
-      oq[0] = q.w, oq[1] = q.x, oq[2] = q.y, oq[3] = q.z;
-      ot[0] = t.x, ot[1] = t.y, ot[2] = t.z;
-      if (!(isfinite(q.w) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(t.x) && isfinite(t.y) &&
-            isfinite(t.z)))
-        atomicOr(a.status, kDevErrNumeric);
-    }
-    __syncwarp();
-  }
+  for (int w = blockIdx.x * kWalkWarps + warp; w < a.n_samples; w += gridDim.x * kWalkWarps)
+    walk_one<T, KIND, SAMPLER>(c, rk, w, tab, sl, lane, evals);
   if (lane == 0 && evals) atomicAdd(a.evals, evals);
+}
+
+// ---------------------------------------------------------------- batched walks (one persistent launch)
+// Work item i = (PURSE p, sampler, walk w) with p = i / (2 S), sampler = (i / S) & 1, w = i mod S;
+// the dS_t items of 3D-3D PURSEs are skipped (their two balls use the dS_R samples).  Each warp
+// pops chunks of items from one atomic counter; the queue never waits, so the kernel ends when
+// the counter passes the last item.  A warp stages the constraint table and Philox round keys of
+// its current PURSE into its own shared-memory area when the PURSE changes.
+__host__ __device__ inline size_t batch_warp_bytes(int nmax, int n_perturb, int n_steps) {
+  return walk_table_bytes<float>(nmax) + 128 + walk_slab_bytes2<float>(nmax, n_perturb, n_steps);
+}
+
+size_t batch_walk_smem(int nmax, int n_perturb, int n_steps, int warps) {
+  return (size_t)warps * batch_warp_bytes(nmax, n_perturb, n_steps);
+}
+
+__global__ void __launch_bounds__(kWalkThreads, 2)
+    batch_walk_kernel(const __grid_constant__ BatchArgs b, const int chunk, const int np_max, const int nt_max) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* base = smem + (size_t)warp * batch_warp_bytes(b.nmax, np_max, nt_max);
+  T4<float>* tab = reinterpret_cast<T4<float>*>(base);
+  uint32_t* rkw = reinterpret_cast<uint32_t*>(base + walk_table_bytes<float>(b.nmax));
+  unsigned char* slab_base = base + walk_table_bytes<float>(b.nmax) + 128;
+  const unsigned S = (unsigned)b.n_samples;
+  const unsigned long long seed = *b.seed;
+  unsigned long long evals = 0;
+  int cur = -1;
+  WalkCtx<float> c;
+  Slab<float> sl;
+  const RkPtr rk{rkw};
+  for (;;) {
+    unsigned head = 0;
+    if (lane == 0) head = atomicAdd(b.counter, (unsigned)chunk);
+    head = __shfl_sync(kFullMask, head, 0);
+    if (head >= b.total_items) break;
+    const unsigned end = min(head + (unsigned)chunk, b.total_items);
+    for (unsigned item = head; item < end; ++item) {
+      const int p = (int)(item / (2 * S));
+      const int smp = (int)((item / S) & 1u);
+      const int w = (int)(item % S);
+      const BatchPurseInfo in = b.info[p];
+      if (in.kind == 0 && smp == 1) continue;
+      if (p != cur) {
+        __syncwarp();
+        const T4<float>* src = reinterpret_cast<const T4<float>*>(b.table) + in.table_off;
+        for (int r = lane; r < 2 * in.n; r += 32) tab[r] = src[r];
+        const unsigned long long key = seed + (unsigned long long)p;
+        if (lane < 10) {
+          rkw[2 * lane] = (uint32_t)key + (uint32_t)lane * 0x9E3779B9u;
+          rkw[2 * lane + 1] = (uint32_t)(key >> 32) + (uint32_t)lane * 0xBB67AE85u;
+        }
+        const int kd = in.kind;
+        c.N = in.n, c.NP = b.n_perturb[kd], c.K = b.n_keep[kd], c.NT = b.n_steps[kd], c.n_iter = b.n_iter[kd];
+        c.mc = c.K >= 32 ? 1 : 32 / c.K;
+        c.fx = float(in.fx), c.fy = float(in.fy), c.cx = float(in.cx), c.cy = float(in.cy);
+        c.omega0 = b.omega0[kd], c.v0 = b.v0[kd], c.gamma = b.gamma[kd];
+        c.st = b.stats + p, c.seed_data = b.seed_data + (size_t)p * kSeedStride, c.s0 = 1;
+        c.key0 = (uint32_t)key, c.key1 = (uint32_t)(key >> 32);
+        c.trace = nullptr, c.status = b.status;
+        sl = carve<float>(slab_base, c.N, c.NP, c.NT);
+        cur = p;
+        __syncwarp();
+      }
+      c.r_pert = float(smp == 0 ? c.st->r_trans : c.st->r_rot);
+      const size_t off = (size_t)p * S;
+      c.out_q = (smp == 0 ? b.q_rot : b.q_tr) + 4 * off;
+      c.out_t = (smp == 0 ? b.t_rot : b.t_tr) + 3 * off;
+      if (in.kind == 0)
+        walk_one<float, 0, 0>(c, rk, w, tab, sl, lane, evals);
+      else if (smp == 0)
+        walk_one<float, 1, 0>(c, rk, w, tab, sl, lane, evals);
+      else
+        walk_one<float, 1, 1>(c, rk, w, tab, sl, lane, evals);
+    }
+  }
+  if (lane == 0 && evals) atomicAdd(b.evals, evals);
+}
+
+cudaError_t launch_batch_walk(const BatchArgs& b, int chunk, int warps, int sm_count, cudaStream_t st) {
+  const int np_max = max(b.n_perturb[0], b.n_perturb[1]), nt_max = max(b.n_steps[0], b.n_steps[1]);
+  const size_t smem = batch_walk_smem(b.nmax, np_max, nt_max, warps);
+  cudaError_t e = cudaFuncSetAttribute(batch_walk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_walk_kernel, 32 * warps, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  batch_walk_kernel<<<per_sm * sm_count, 32 * warps, smem, st>>>(b, chunk, np_max, nt_max);
+  return cudaGetLastError();
 }
 
 template <typename T, int KIND, int SAMPLER>

@@ -55,6 +55,16 @@ _SIGS = {
     "purse_rng_words": [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                         ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP],
     "purse_sync": [_VP, _VP],
+    "purse_batch_create": [ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)],
+    "purse_batch_destroy": [_VP],
+    "purse_batch_solve": [_VP, ctypes.POINTER(purse_params), ctypes.POINTER(purse_params), ctypes.c_uint64, _VP,
+                          ctypes.c_int, ctypes.c_int, _VP, _VP],
+    "purse_batch_tune": [_VP, ctypes.POINTER(purse_params), ctypes.POINTER(purse_params), ctypes.c_uint64, _VP,
+                         ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                         ctypes.POINTER(ctypes.c_float), _VP],
+    "purse_batch_copy_farthest": [_VP, _VP, _VP],
+    "purse_batch_copy_samples": [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP],
+    "purse_batch_sync": [_VP, ctypes.POINTER(ctypes.c_ulonglong), _VP],
     "purse_last_error": [],
     "purse_version": [],
 }
@@ -161,6 +171,60 @@ def purse_rng_words(seed, phase, j, i, w0, n_streams, n_words, words, lattice=No
 
 def purse_sync(h, stream=None):
     _check(lib().purse_sync(h, _stream(stream)), "purse_sync")
+
+
+def purse_batch_create(purses) -> int:
+    """Batch handle from a list of synthetic.Purse-like objects."""
+    import numpy as np
+    kinds = np.array([int(p.kind) for p in purses], dtype=np.int32)
+    offsets = np.zeros(len(purses) + 1, dtype=np.int32)
+    offsets[1:] = np.cumsum([p.radii.shape[0] for p in purses])
+    model = np.ascontiguousarray(np.concatenate([p.model for p in purses]), dtype=np.float64)
+    obs = np.ascontiguousarray(np.concatenate(
+        [p.obs if p.obs.shape[1] == 3 else np.concatenate([p.obs, np.zeros((p.obs.shape[0], 1))], 1) for p in purses]),
+        dtype=np.float64)
+    radii = np.ascontiguousarray(np.concatenate([p.radii for p in purses]), dtype=np.float64)
+    Ks = (purse_intrinsics * len(purses))()
+    for i, p in enumerate(purses):
+        if p.K is not None:
+            Ks[i] = purse_intrinsics(*p.K)
+    h = _VP()
+    _check(lib().purse_batch_create(len(purses), kinds.ctypes.data, offsets.ctypes.data, model.ctypes.data,
+                                    obs.ctypes.data, radii.ctypes.data, ctypes.cast(Ks, _VP), ctypes.byref(h)),
+           "purse_batch_create")
+    return h.value
+
+
+def purse_batch_destroy(b):
+    _check(lib().purse_batch_destroy(b), "purse_batch_destroy")
+
+
+def purse_batch_solve(b, p3d: purse_params, p2d: purse_params, seed, seeds, n_samples, n_iters, results, stream=None):
+    _check(lib().purse_batch_solve(b, ctypes.byref(p3d), ctypes.byref(p2d), seed, _ptr(seeds), n_samples, n_iters,
+                                   _ptr(results), _stream(stream)), "purse_batch_solve")
+
+
+def purse_batch_tune(b, p3d, p2d, seed, seeds, n_samples, stream=None):
+    c, w, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_float(0)
+    _check(lib().purse_batch_tune(b, ctypes.byref(p3d), ctypes.byref(p2d), seed, _ptr(seeds), n_samples,
+                                  ctypes.byref(c), ctypes.byref(w), ctypes.byref(ms), _stream(stream)),
+           "purse_batch_tune")
+    return c.value, w.value, ms.value
+
+
+def purse_batch_copy_farthest(b, out, stream=None):
+    _check(lib().purse_batch_copy_farthest(b, _ptr(out), _stream(stream)), "purse_batch_copy_farthest")
+
+
+def purse_batch_copy_samples(b, p, q_rot=None, t_rot=None, q_tr=None, t_tr=None, stream=None):
+    _check(lib().purse_batch_copy_samples(b, p, _ptr(q_rot), _ptr(t_rot), _ptr(q_tr), _ptr(t_tr), _stream(stream)),
+           "purse_batch_copy_samples")
+
+
+def purse_batch_sync(b, stream=None) -> int:
+    v = ctypes.c_ulonglong(0)
+    _check(lib().purse_batch_sync(b, ctypes.byref(v), _stream(stream)), "purse_batch_sync")
+    return v.value
 
 
 def version() -> str:
