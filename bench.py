@@ -296,6 +296,8 @@ def run_gpu(args, rank, world):
     }
     if rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(args, p, dev)
+    if not args.no_batch:
+        out["batch"] = run_batch(args, dev)
     if rank == 0 and not args.no_cpu_baseline:
         ev_c, wall_c, walks_c = oracle_sample(args.cpu_walks, args.cpu_workers)
         out["cpu_baseline"] = {"value": ev_c / wall_c, "unit": UNIT, "cores": args.cpu_workers, "kind": "oracle",
@@ -308,6 +310,52 @@ def run_gpu(args, rank, world):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def run_batch(args, dev):
+    """Batched workload: 4096 PURSEs (fair-coin kind, N ~ U{4..64}), 4096 samples each, FP32, both balls
+    with 200 GGD iterations; one CUDA graph (statistics, persistent walk launch, one block per ball)
+    after the autotuner picked the walk launch shape."""
+    import torch
+    import paper_2403_09990_gb300.purse as P
+    from paper_2403_09990_gb300 import synthetic as syn
+    n_purses, S, K = args.batch_purses, args.batch_samples, K_MEGB
+    purses = syn.purse_batch(n_purses, seed=7)
+    seeds = torch.as_tensor(syn.seed_array(purses), dtype=torch.float64, device=dev)
+    res = torch.empty((n_purses, 9), dtype=torch.float64, device=dev)
+    p3 = P.make_params(n_iter=5, n_perturb=150, n_keep=10, n_steps=15, omega0=0.5, v0=0.0, gamma=0.5,
+                       rot_perturb=0.0, trans_perturb=0.1)
+    p2 = P.make_params(n_iter=5, n_perturb=150, n_keep=10, n_steps=15, omega0=1.0, v0=2.0, gamma=0.5,
+                       rot_perturb=0.2, trans_perturb=0.1)
+    b = P.purse_batch_create(purses)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    try:
+        chunk, warps, _ = P.purse_batch_tune(b, p3, p2, 1, seeds, min(S, 1024), stream)
+        for w in range(args.batch_warmup):
+            P.purse_batch_solve(b, p3, p2, 10 + w, seeds, S, K, res, stream)
+        P.purse_batch_sync(b, stream)
+        tot, ev_total = 0.0, 0
+        for st in range(args.batch_steps):
+            flush.fill_(st & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.purse_batch_solve(b, p3, p2, 100 + st, seeds, S, K, res, stream)
+            e1.record(stream)
+            ev_total += P.purse_batch_sync(b, stream)
+            tot += e0.elapsed_time(e1)
+    finally:
+        P.purse_batch_destroy(b)
+    kinds = np.array([p.kind for p in purses])
+    ns = np.array([p.n for p in purses])
+    alg = float(((1 + kinds) * S * 5 * (150 + 10 * 15) * ns).sum())
+    ms = tot / args.batch_steps
+    return {"workload": f"{n_purses} PURSEs (3D-3D / 2D-3D by a fair coin, N ~ U{{4..64}}), {S} samples each, "
+                        f"presets of Section V (N_I = 5), both balls with {K} GGD iterations, FP32",
+            "purses_per_s": n_purses / (ms / 1e3), "ms_per_solve": ms, "steps": args.batch_steps,
+            "evals_per_s": alg / (ms / 1e3), "evals_executed_per_s": ev_total / args.batch_steps / (ms / 1e3),
+            "launch": {"graph": "statistics + persistent walk kernel + one block per ball", "chunk": chunk,
+                       "warps_per_block": warps}}
 
 
 def run_e2e(args, p, dev):
@@ -391,6 +439,11 @@ def main():
     ap.add_argument("--walks", type=int, default=N_WALKS, help="walks per sampler (profiling of a smaller case)")
     ap.add_argument("--iters", type=int, default=N_ITER, help="walk iterations (profiling of a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-PURSE measurement")
+    ap.add_argument("--batch-purses", type=int, default=4096)
+    ap.add_argument("--batch-samples", type=int, default=4096)
+    ap.add_argument("--batch-steps", type=int, default=2)
+    ap.add_argument("--batch-warmup", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     N_WALKS, N_ITER = args.walks, args.iters
