@@ -107,9 +107,17 @@ purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds,
  * (phase, j, i, w) is output lane k & 3 of counter (k >> 2, phase << 24 | j, i, w); phase 1/2 are
  * the perturbations j of iteration i of walk w in the dS_R / dS_t sampler, 3/4 the random unit
  * vector of the initial angular / centre velocity.  A ball point takes one word per attempt:
- * X_c = 2 ((word >> 10c) & 1023) - 1023, accepted if |X|^2 <= 2^20, point X / 1024. */
+ * X_c = 2 ((word >> 10c) & 1023) - 1023, accepted if |X|^2 <= 2^20, point X / 1024.
+ * d_snap (device, may be NULL): snap every final sample to the PURSE boundary along its walk's
+ * last-move ray (rotation ray Exp(tau omega) R* for the dS_R sampler, translation ray t* + tau v for
+ * dS_t; the paper has no snap -- it makes the balls differentiable): tau_hi = the smallest ladder
+ * value gamma^m leaving S, bisection of [0, tau_hi] (24 steps FP32, 52 FP64) keeping the feasible
+ * end, which replaces the sample in d_q / d_t.  Record per walk, 12 values in the sample precision:
+ * j* (the active constraint, -1 if no ladder pose left S), ray kind (0 rotation, 1 translation),
+ * ray direction (3), h'(tau*) = d|g_j*|/d tau, d|g_j*|/d y_j* (3; 2 used for 2D-3D), 3 unused.
+ * Pass the records to megb_backward. */
 purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const double* d_seeds,
-                          int s0, int n_samples, void* d_q, void* d_t, int16_t* d_trace,
+                          int s0, int n_samples, void* d_q, void* d_t, int16_t* d_trace, void* d_snap,
                           purse_stream_t stream);
 
 /* Number of (pose, constraint) evaluations the last purse_sample on this handle executed
@@ -128,6 +136,33 @@ purse_status purse_last_evals(purse_t h, unsigned long long* evals, purse_stream
 purse_status megb_solve(purse_t h, int precision, int n_iters, const void* d_q, int n_rot,
                         const void* d_t, int n_tr, double* d_result, int32_t* d_farthest,
                         purse_stream_t stream);
+
+/* Reverse-mode derivative of the balls of megb_solve with respect to the PURSE observations y_i
+ * and radii r_i (the paper has no adjoint; the samples come from the discrete walks of Alg. 3/5,
+ * so they are differentiated through the boundary snap of purse_sample's d_snap records).
+ * Loss L = g . (C (4), c (3), D-hat, d-hat) with g = d_grad_result (device, 9 doubles).
+ * Rotations are perturbed on the left, R -> Exp(delta) R.  The descent of Section II is
+ * reversed with the SO(3) Jacobians (step k: A_k = (1/k) C_k J_r(phi_k / k) J_l(phi_k)^-1 C_{k-1}^T,
+ * phi_k = Log(C_{k-1}^T R_{f_k}); iterates recomputed from d_farthest, not stored); the radius
+ * uses dD = (C_K u)^T (delta_f* - eps_K), u the unit axis of C_K^T R_f*, f* the farthest sample
+ * from the final centre (found again here with megb_solve's final pass); the translation ball
+ * is an affine combination of its farthest samples.  A sample gradient v then moves the
+ * sample's snapped ray parameter: d tau* = (d r_j* - dh/dy . d y_j*) / h'(tau*) with
+ * tau-gradient v . direction, accumulated onto constraint j* of the sample's record.
+ * Inputs: exactly the arguments given to megb_solve (precision, n_iters, d_q, n_rot, d_t, n_tr,
+ * its d_result and d_farthest, unchanged since), plus the snap records of the rotation samples
+ * (d_snap_rot, n_rot x 12) and of the translation samples (d_snap_tr, n_tr x 12), in the sample
+ * precision.  A record whose ray does not move its ball's coordinate (a rotation ray in the
+ * translation ball) or with j* = -1 contributes nothing.
+ * Outputs (device, overwritten): d_grad_obs n x 3 (3D-3D, metres) or n x 2 (2D-3D, pixels)
+ * doubles, d_grad_radii n doubles.  One thread runs the reverse sweep in FP64.  A record whose
+ * j* is out of range or whose h' is 0 is skipped and flags PURSE_ERR_NUMERIC at the next
+ * purse_sync.  Uses handle-owned scratch ((n_iters + 1) x 32 bytes beyond megb_solve's). */
+purse_status megb_backward(purse_t h, int precision, int n_iters, const void* d_q,
+                           const void* d_snap_rot, int n_rot, const void* d_t, const void* d_snap_tr,
+                           int n_tr, const int32_t* d_farthest, const double* d_result,
+                           const double* d_grad_result, double* d_grad_obs, double* d_grad_radii,
+                           purse_stream_t stream);
 
 /* megb_solve without any device allocation, for callers that must not allocate device memory
  * once they are running: real-time perception loops that reserve all memory at start-up

@@ -165,7 +165,8 @@ purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds,
 }
 
 purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const double* d_seeds, int s0,
-                          int n_samples, void* d_q, void* d_t, int16_t* d_trace, purse_stream_t stream) {
+                          int n_samples, void* d_q, void* d_t, int16_t* d_trace, void* d_snap,
+                          purse_stream_t stream) {
   if (!h || !p) return arg_error("purse_sample: NULL handle or params");
   if (p->n_iter < 0) return arg_error("purse_sample: n_iter < 0");
   if (p->n_perturb < 1 || p->n_perturb > 256) return arg_error("purse_sample: n_perturb must be in [1, 256]");
@@ -212,6 +213,7 @@ purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const
   }
   a.out_q = d_q, a.out_t = d_t;
   a.trace = d_trace;
+  a.out_snap = d_snap;
   a.status = h->d_status;
   a.evals = h->d_evals;
   e = launch_walk(h, p, a, st);
@@ -250,6 +252,26 @@ purse_status megb_solve(purse_t h, int precision, int n_iters, const void* d_q, 
   h->megb_q = d_q, h->megb_t = d_t;
   h->megb_nrot = n_rot, h->megb_ntr = n_tr;
   return PURSE_OK;
+}
+
+purse_status megb_backward(purse_t h, int precision, int n_iters, const void* d_q, const void* d_snap_rot, int n_rot,
+                           const void* d_t, const void* d_snap_tr, int n_tr, const int32_t* d_farthest,
+                           const double* d_result, const double* d_grad_result, double* d_grad_obs,
+                           double* d_grad_radii, purse_stream_t stream) {
+  if (!h) return arg_error("megb_backward: NULL handle");
+  if (precision != 0 && precision != 1) return arg_error("megb_backward: precision must be 0 or 1");
+  if (n_iters < 1 || n_iters > (1 << 20)) return arg_error("megb_backward: n_iters must be in [1, 2^20]");
+  if (n_rot < 0 || n_tr < 0) return arg_error("megb_backward: negative sample count");
+  if ((n_rot > 0 && (!d_q || !d_snap_rot)) || (n_tr > 0 && (!d_t || !d_snap_tr)))
+    return arg_error("megb_backward: NULL samples or snap records");
+  if (!d_farthest || !d_result || !d_grad_result || !d_grad_obs || !d_grad_radii)
+    return arg_error("megb_backward: NULL buffer");
+  purse_status s = ensure_scratch(h, megb_backward_scratch_bytes(n_iters, h->sm_count));
+  if (s != PURSE_OK) return s;
+  cudaError_t e = launch_megb_backward(h, precision, n_iters, d_q, d_snap_rot, n_rot, d_t, d_snap_tr, n_tr, d_farthest,
+                                       d_result, d_grad_result, d_grad_obs, d_grad_radii, h->d_scratch,
+                                       (cudaStream_t)stream);
+  return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "megb_backward");
 }
 
 purse_status purse_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t i, uint32_t w0, int n_streams,

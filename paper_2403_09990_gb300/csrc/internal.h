@@ -33,6 +33,9 @@ struct WalkStats {
 // t_0 - t-bar (0 when degenerate).  16 doubles.
 constexpr int kSeedStride = 16;
 
+// Values per walk in the boundary-snap record (see purse_sample).
+constexpr int kSnapStride = 12;
+
 // Per-PURSE description inside a batch (device array).
 struct BatchPurseInfo {
   int kind, n, table_off, pad;  // table rows [table_off, table_off + 2 n) of the concatenated tables
@@ -79,6 +82,7 @@ struct WalkArgs {
   void* out_q;
   void* out_t;
   int16_t* trace;
+  void* out_snap;
   int* status;
   unsigned long long* evals;  // executed (pose, constraint) evaluations
 };
@@ -131,5 +135,10 @@ cudaError_t launch_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t
 size_t megb_scratch_bytes(int n_iters, int sm_count);
 cudaError_t launch_megb(purse_t h, int precision, int n_iters, const void* d_q, int n_rot, const void* d_t,
                         int n_tr, double* d_result, int32_t* d_farthest, void* scratch, cudaStream_t st);
+size_t megb_backward_scratch_bytes(int n_iters, int sm_count);
+cudaError_t launch_megb_backward(purse_t h, int precision, int n_iters, const void* d_q, const void* d_snap_rot,
+                                 int n_rot, const void* d_t, const void* d_snap_tr, int n_tr,
+                                 const int32_t* d_farthest, const double* d_result, const double* d_grad_result,
+                                 double* d_grad_obs, double* d_grad_radii, void* scratch, cudaStream_t st);
 
 }  // namespace purse

@@ -22,7 +22,7 @@ struct MegbState {
   double C[4];
   double c[4];
   unsigned int counter[2];
-  unsigned int pad[2];
+  int fstar[2];  // farthest sample from the final centre (rotation, translation)
 };
 
 struct Part {
@@ -64,6 +64,31 @@ __device__ __forceinline__ T rot_key(T cw, T cx, T cy, T cz, const T* qs) {
   const T vy = cw * qy - qw * cy - (cz * qx - cx * qz);
   const T vz = cw * qz - qw * cz - (cx * qy - cy * qx);
   return vx * vx + vy * vy + vz * vz;
+}
+
+// Relative rotation d = C* (x) q_f on the short path (w >= 0), its sine norm and angle.
+struct RelRot {
+  Q4<double> d;
+  double sn, th;
+};
+__device__ __forceinline__ RelRot rel_rot(const Q4<double>& c, const Q4<double>& qf) {
+  RelRot r;
+  r.d = qmul(Q4<double>{c.w, -c.x, -c.y, -c.z}, qf);
+  if (r.d.w < 0) r.d = Q4<double>{-r.d.w, -r.d.x, -r.d.y, -r.d.z};
+  r.sn = sqrt(r.d.x * r.d.x + r.d.y * r.d.y + r.d.z * r.d.z);
+  r.th = 2.0 * atan2(r.sn, r.d.w);
+  return r;
+}
+
+// GGD step k on SO(3): SLERP(C, q_f, 1/k) = C Exp(Log(C^T R_f) / k).
+__device__ __forceinline__ Q4<double> slerp_step(const Q4<double>& c, const RelRot& r, int k) {
+  Q4<double> step{1.0, 0.0, 0.0, 0.0};
+  if (r.sn > 0.0) {
+    const double h = 0.5 * r.th / k;
+    const double sh = sin(h) / r.sn;
+    step = Q4<double>{cos(h), sh * r.d.x, sh * r.d.y, sh * r.d.z};
+  }
+  return qnormalize(qmul(c, step));
 }
 
 // MODE 0: rotation ball, MODE 1: translation ball.  k >= 1: GGD step k; k == 0: final radius.
@@ -137,22 +162,13 @@ __global__ void __launch_bounds__(kMegbThreads)
     const T* qs = x + 4 * (size_t)bi;
     const Q4<double> c{s->C[0], s->C[1], s->C[2], s->C[3]};
     const Q4<double> qf = qnormalize(Q4<double>{(double)qs[0], (double)qs[1], (double)qs[2], (double)qs[3]});
-    Q4<double> d = qmul(Q4<double>{c.w, -c.x, -c.y, -c.z}, qf);
-    if (d.w < 0) d = Q4<double>{-d.w, -d.x, -d.y, -d.z};
-    const double sn = sqrt(d.x * d.x + d.y * d.y + d.z * d.z);
-    const double th = 2.0 * atan2(sn, d.w);
+    const RelRot r = rel_rot(c, qf);
     if (k > 0) {
-      Q4<double> step{1.0, 0.0, 0.0, 0.0};
-      if (sn > 0.0) {
-        const double h = 0.5 * th / k;
-        const double sh = sin(h) / sn;
-        step = Q4<double>{cos(h), sh * d.x, sh * d.y, sh * d.z};
-      }
-      const Q4<double> cn = qnormalize(qmul(c, step));
+      const Q4<double> cn = slerp_step(c, r, k);
       s->C[0] = cn.w, s->C[1] = cn.x, s->C[2] = cn.y, s->C[3] = cn.z;
     } else {
       result[0] = c.w, result[1] = c.x, result[2] = c.y, result[3] = c.z;
-      result[7] = th;
+      result[7] = r.th;
     }
   } else {
     const T* p = x + 3 * (size_t)bi;
@@ -167,6 +183,8 @@ __global__ void __launch_bounds__(kMegbThreads)
   if (k > 0) {
     f_int[k - 1] = bi;
     if (f_out) f_out[k - 1] = bi;
+  } else {
+    s->fstar[MODE] = bi;
   }
 }
 
@@ -211,6 +229,179 @@ cudaError_t launch_megb(purse_t h, int precision, int n_iters, const void* d_q, 
                                 scratch, st);
   return launch_megb_t<double>(h, n_iters, (const double*)d_q, n_rot, (const double*)d_t, n_tr, d_result, d_farthest,
                                scratch, st);
+}
+
+// ---------------------------------------------------------------- adjoint
+// Reverse-mode derivative of the balls through the boundary snap.  Rotations are perturbed on
+// the left, R -> Exp(delta) R.  GGD step k linearises to eps_k = (I - A_k) eps_{k-1} + A_k delta_{f_k}
+// with A_k = (1/k) C_k J_r(phi_k / k) J_l(phi_k)^-1 C_{k-1}^T, phi_k = Log(C_{k-1}^T R_{f_k}); the radius
+// D = |Log(C_K^T R_f*)| gives dD = (C_K u)^T (delta_f* - eps_K) (u the unit axis; Section II and the
+// appendix on geodesic gradient descent give the gradient of the squared distance along it).
+// Translation: c_K is an affine combination of the farthest samples (Badoiu-Clarkson).  Each sample
+// gradient g then moves its snapped sample along its ray: d tau* = (dr_j* - dh/dy . dy_j*) / h'.
+
+// J_l(phi) y (inverse = false) or J_l(phi)^-1 y (inverse = true); J_l(phi)^T = J_l(-phi).
+__device__ __forceinline__ V3<double> jl_apply(const V3<double>& phi, const V3<double>& y, bool inverse) {
+  const double th2 = dot(phi, phi), th = sqrt(th2);
+  const V3<double> py = cross(phi, y), ppy = cross(phi, py);
+  double a, b;
+  if (th < 1e-3) {
+    a = inverse ? -0.5 : 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+    b = inverse ? 1.0 / 12.0 + th2 / 720.0 + th2 * th2 / 30240.0 : 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+  } else if (inverse) {
+    a = -0.5;
+    b = 1.0 / th2 - 1.0 / (2.0 * th * tan(0.5 * th));
+  } else {
+    const double sh = sin(0.5 * th);
+    a = 2.0 * sh * sh / th2;
+    b = (th - sin(th)) / (th2 * th);
+  }
+  return V3<double>{y.x + a * py.x + b * ppy.x, y.y + a * py.y + b * ppy.y, y.z + a * py.z + b * ppy.z};
+}
+
+__device__ __forceinline__ V3<double> mul_t(const M3<double>& R, const V3<double>& a) {
+  return V3<double>{R.m[0] * a.x + R.m[3] * a.y + R.m[6] * a.z, R.m[1] * a.x + R.m[4] * a.y + R.m[7] * a.z,
+                    R.m[2] * a.x + R.m[5] * a.y + R.m[8] * a.z};
+}
+
+template <typename T>
+__device__ __forceinline__ Q4<double> load_q(const T* q, int i) {
+  const T* p = q + 4 * (size_t)i;
+  return qnormalize(Q4<double>{(double)p[0], (double)p[1], (double)p[2], (double)p[3]});
+}
+
+// Scatter a sample gradient v (left tangent for rotation-ball samples, R^3 for translation-ball
+// samples) through the sample's snap record.  Records whose ray does not move this ball's
+// coordinate (ray kind != ball) or that were not snapped (j* < 0) take nothing.
+template <typename T>
+__device__ __forceinline__ void snap_scatter(const T* rec, int ball, V3<double> v, int n, int dim,
+                                             double* gy, double* gr, int* status) {
+  const double jd = (double)rec[0];
+  if (!(jd >= 0.0) || (int)rec[1] != ball) return;
+  const int j = (int)jd;
+  const double hp = (double)rec[5];
+  if (j >= n || !(hp != 0.0)) {
+    atomicOr(status, kDevErrNumeric);
+    return;
+  }
+  const double gt = (v.x * (double)rec[2] + v.y * (double)rec[3] + v.z * (double)rec[4]) / hp;
+  gr[j] += gt;
+  for (int c = 0; c < dim; ++c) gy[(size_t)dim * j + c] -= gt * (double)rec[6 + c];
+}
+
+// One thread walks both balls backwards (serial in k, FP64); the block zeroes the outputs first.
+template <typename T>
+__global__ void megb_adjoint_kernel(const T* q, const T* snap_r, int nq, const T* t, const T* snap_t, int nt, int K,
+                                    const int32_t* f, const MegbState* s, const double* result, const double* g,
+                                    Q4<double>* Cs, int n, int dim, double* gy, double* gr, int* status) {
+  for (int i = threadIdx.x; i < n * dim; i += blockDim.x) gy[i] = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) gr[i] = 0.0;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  if (nq > 0) {
+    // recompute the iterates C_0..C_K from the stored farthest sequence
+    Cs[0] = load_q(q, 0);
+    for (int k = 1; k <= K; ++k) Cs[k] = slerp_step(Cs[k - 1], rel_rot(Cs[k - 1], load_q(q, f[k - 1])), k);
+    const Q4<double> CK = Cs[K];
+    const M3<double> RK = qmat(CK);
+    // dL/d eps_K from the centre-quaternion gradient: g_C = (w g_v - g_w v + v x g_v) / 2
+    const V3<double> vq{CK.x, CK.y, CK.z}, gv{g[1], g[2], g[3]};
+    const V3<double> cv = cross(vq, gv);
+    V3<double> lam{0.5 * (CK.w * gv.x - g[0] * vq.x + cv.x), 0.5 * (CK.w * gv.y - g[0] * vq.y + cv.y),
+                   0.5 * (CK.w * gv.z - g[0] * vq.z + cv.z)};
+    const int fs = s->fstar[0];
+    const RelRot r = rel_rot(CK, load_q(q, fs));
+    if (r.sn > 0.0 && g[7] != 0.0) {
+      const V3<double> w = mul(RK, V3<double>{r.d.x / r.sn, r.d.y / r.sn, r.d.z / r.sn});
+      snap_scatter(snap_r + (size_t)kSnapStride * fs, 0, g[7] * w, n, dim, gy, gr, status);
+      lam = lam - g[7] * w;
+    }
+    for (int k = K; k >= 1; --k) {
+      const RelRot rk = rel_rot(Cs[k - 1], load_q(q, f[k - 1]));
+      V3<double> phi{0.0, 0.0, 0.0};
+      if (rk.sn > 0.0) phi = (rk.th / rk.sn) * V3<double>{rk.d.x, rk.d.y, rk.d.z};
+      // A_k^T lam = (1/k) C_{k-1} J_l(-phi)^-1 J_l(phi/k) C_k^T lam
+      V3<double> y = mul_t(qmat(Cs[k]), lam);
+      y = jl_apply((1.0 / k) * phi, y, false);
+      y = jl_apply(-1.0 * phi, y, true);
+      const V3<double> v = (1.0 / k) * mul(qmat(Cs[k - 1]), y);
+      snap_scatter(snap_r + (size_t)kSnapStride * f[k - 1], 0, v, n, dim, gy, gr, status);
+      lam = lam - v;
+    }
+    snap_scatter(snap_r, 0, lam, n, dim, gy, gr, status);
+  }
+  if (nt > 0) {
+    const int fs = s->fstar[1];
+    const T* tf = t + 3 * (size_t)fs;
+    const V3<double> e{(double)tf[0] - result[4], (double)tf[1] - result[5], (double)tf[2] - result[6]};
+    const double dn = sqrt(dot(e, e));
+    V3<double> mu{g[4], g[5], g[6]};
+    if (dn > 0.0 && g[8] != 0.0) {
+      const V3<double> u = (g[8] / dn) * e;
+      snap_scatter(snap_t + (size_t)kSnapStride * fs, 1, u, n, dim, gy, gr, status);
+      mu = mu - u;
+    }
+    for (int k = K; k >= 1; --k) {
+      snap_scatter(snap_t + (size_t)kSnapStride * f[K + k - 1], 1, (1.0 / k) * mu, n, dim, gy, gr, status);
+      mu = (1.0 - 1.0 / k) * mu;
+    }
+    snap_scatter(snap_t, 1, mu, n, dim, gy, gr, status);
+  }
+}
+
+__global__ void megb_state_from_result(const double* result, MegbState* s) {
+  if (threadIdx.x != 0) return;
+  for (int i = 0; i < 4; ++i) s->C[i] = result[i];
+  for (int i = 0; i < 3; ++i) s->c[i] = result[4 + i];
+  s->c[3] = 0.0;
+  s->counter[0] = s->counter[1] = 0;
+  s->fstar[0] = s->fstar[1] = 0;
+}
+
+size_t megb_backward_scratch_bytes(int n_iters, int sm_count) {
+  return megb_scratch_bytes(n_iters, sm_count) + 16 * sizeof(double) + ((size_t)n_iters + 1) * sizeof(Q4<double>);
+}
+
+template <typename T>
+static cudaError_t launch_megb_backward_t(purse_t h, int K, const T* q, const T* snap_r, int nq, const T* t,
+                                          const T* snap_t, int nt, const int32_t* f, const double* result,
+                                          const double* g, double* gy, double* gr, void* scratch, cudaStream_t st) {
+  MegbState* s = reinterpret_cast<MegbState*>(scratch);
+  Part* parts = reinterpret_cast<Part*>(reinterpret_cast<char*>(scratch) + sizeof(MegbState));
+  const long cap = (long)megb_blocks_cap(h->sm_count);
+  int32_t* f_int = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(parts) + 2 * cap * sizeof(Part));
+  char* tail = reinterpret_cast<char*>(scratch) + megb_scratch_bytes(K, h->sm_count);
+  double* dummy = reinterpret_cast<double*>(tail);
+  Q4<double>* Cs = reinterpret_cast<Q4<double>*>(tail + 16 * sizeof(double));
+  megb_state_from_result<<<1, 32, 0, st>>>(result, s);
+  // farthest sample from the final centres, by the forward's own final pass
+  if (nq > 0) {
+    const long want = (nq + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
+    const int gsz = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+    ggd_step<T, 0><<<gsz, kMegbThreads, 0, st>>>(q, nq, s, parts, 0, f_int, nullptr, dummy);
+  }
+  if (nt > 0) {
+    const long want = (nt + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
+    const int gsz = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+    ggd_step<T, 1><<<gsz, kMegbThreads, 0, st>>>(t, nt, s, parts + cap, 0, f_int, nullptr, dummy);
+  }
+  const int dim = h->kind == PURSE_2D3D ? 2 : 3;
+  megb_adjoint_kernel<T><<<1, 256, 0, st>>>(q, snap_r, nq, t, snap_t, nt, K, f, s, result, g, Cs, h->n, dim, gy, gr,
+                                            h->d_status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_megb_backward(purse_t h, int precision, int n_iters, const void* d_q, const void* d_snap_rot,
+                                 int n_rot, const void* d_t, const void* d_snap_tr, int n_tr,
+                                 const int32_t* d_farthest, const double* d_result, const double* d_grad_result,
+                                 double* d_grad_obs, double* d_grad_radii, void* scratch, cudaStream_t st) {
+  if (precision == 0)
+    return launch_megb_backward_t<float>(h, n_iters, (const float*)d_q, (const float*)d_snap_rot, n_rot,
+                                         (const float*)d_t, (const float*)d_snap_tr, n_tr, d_farthest, d_result,
+                                         d_grad_result, d_grad_obs, d_grad_radii, scratch, st);
+  return launch_megb_backward_t<double>(h, n_iters, (const double*)d_q, (const double*)d_snap_rot, n_rot,
+                                        (const double*)d_t, (const double*)d_snap_tr, n_tr, d_farthest, d_result,
+                                        d_grad_result, d_grad_obs, d_grad_radii, scratch, st);
 }
 
 // ---------------------------------------------------------------- one block per ball
@@ -266,22 +457,13 @@ __device__ void ggd_block(const T* __restrict__ x, int n, int K, double* result,
         const T* qs = x + 4 * (size_t)bi;
         const Q4<double> cq{c[0], c[1], c[2], c[3]};
         const Q4<double> qf = qnormalize(Q4<double>{(double)qs[0], (double)qs[1], (double)qs[2], (double)qs[3]});
-        Q4<double> d = qmul(Q4<double>{cq.w, -cq.x, -cq.y, -cq.z}, qf);
-        if (d.w < 0) d = Q4<double>{-d.w, -d.x, -d.y, -d.z};
-        const double sn = sqrt(d.x * d.x + d.y * d.y + d.z * d.z);
-        const double th = 2.0 * atan2(sn, d.w);
+        const RelRot r = rel_rot(cq, qf);
         if (k <= K) {
-          Q4<double> step{1.0, 0.0, 0.0, 0.0};
-          if (sn > 0.0) {
-            const double h = 0.5 * th / k;
-            const double sh = sin(h) / sn;
-            step = Q4<double>{cos(h), sh * d.x, sh * d.y, sh * d.z};
-          }
-          const Q4<double> cn = qnormalize(qmul(cq, step));
+          const Q4<double> cn = slerp_step(cq, r, k);
           c[0] = cn.w, c[1] = cn.x, c[2] = cn.y, c[3] = cn.z;
         } else {
           result[0] = cq.w, result[1] = cq.x, result[2] = cq.y, result[3] = cq.z;
-          result[7] = th;
+          result[7] = r.th;
         }
       } else {
         const T* pp = x + 3 * (size_t)bi;

@@ -270,6 +270,7 @@ struct WalkCtx {
   T* out_q;
   T* out_t;
   int16_t* trace;
+  T* out_snap;  // NULL: no snap; else kSnapStride values per walk
   int* status;
 };
 
@@ -282,6 +283,130 @@ struct RkPtr {
   const uint32_t* p;
   __device__ __forceinline__ uint32_t operator[](int i) const { return p[i]; }
 };
+
+// Pose on the walk's last-move ray: rotation ray (Exp(tau d) R*, t*) for dS_R, translation ray
+// (R*, t* + tau d) for dS_t.
+template <typename T, int SAMPLER>
+__device__ __forceinline__ void ray_pose(const Q4<T>& q, const V3<T>& t, const V3<T>& d, T tau, Q4<T>& qo, V3<T>& to) {
+  if (SAMPLER == 0) {
+    qo = qnormalize(qmul(qexp(V3<T>{tau * d.x, tau * d.y, tau * d.z}), q));
+    to = t;
+  } else {
+    qo = q;
+    to = V3<T>{t.x + tau * d.x, t.y + tau * d.y, t.z + tau * d.z};
+  }
+}
+
+// in_purse of one pose, constraints spread over the lanes (warp-uniform result).
+template <typename T, int KIND>
+__device__ __forceinline__ bool pose_in_purse(const T4<T>* tab, int N, const M3<T>& R, const V3<T>& t, T fx, T fy,
+                                              T cx, T cy, int lane) {
+  bool ok = true;
+  for (int i = lane; i < N; i += 32) {
+    const T4<T> mz = tab[i], ob = tab[N + i];
+    const V3<T> X = mul(R, V3<T>{mz.x, mz.y, mz.z}) + t;
+    if (KIND == 1) {
+      const T Pz = X.z, ex = fx * X.x + cx * X.z - ob.x * Pz, ey = fy * X.y + cy * X.z - ob.y * Pz;
+      const T rz = mz.w * Pz;
+      ok = ok && Pz > T(0) && ex * ex + ey * ey - rz * rz <= T(0);
+    } else {
+      const T ex = X.x - ob.x, ey = X.y - ob.y, ez = X.z - ob.z;
+      ok = ok && ex * ex + ey * ey + ez * ez - ob.w <= T(0);
+    }
+  }
+  return __all_sync(kFullMask, ok);
+}
+
+// Boundary snap along the last-move ray (used to differentiate the balls): tau_hi = the
+// smallest ladder value whose pose leaves S, bisection of [0, tau_hi] keeping the feasible end,
+// j* = the constraint of smallest margin there.  Record (kSnapStride values): j* (-1: nothing
+// left S along the ladder, pose unchanged), ray kind (0 rotation, 1 translation), direction (3),
+// h'(tau*) = d|g_j*|/d tau, d|g_j*|/d y_j* (3; 2 used for 2D-3D).
+template <typename T, int KIND, int SAMPLER>
+__device__ __forceinline__ void snap_walk(const WalkCtx<T>& c, const T4<T>* tab, const V3<T>& dir, Q4<T>& q,
+                                          V3<T>& t, int w, int lane) {
+  const int N = c.N;
+  const T fx = c.fx, fy = c.fy, cx = c.cx, cy = c.cy;
+  T hi = T(-1);
+  for (int m = c.NT - 1; m >= 0 && hi < T(0); --m) {
+    T sm = T(1);
+    for (int k = 0; k < m; ++k) sm *= T(c.gamma);
+    Q4<T> qx;
+    V3<T> tx;
+    ray_pose<T, SAMPLER>(q, t, dir, sm, qx, tx);
+    if (!pose_in_purse<T, KIND>(tab, N, qmat(qx), tx, fx, fy, cx, cy, lane)) hi = sm;
+  }
+  T* rec = c.out_snap + (size_t)kSnapStride * w;
+  if (hi < T(0)) {
+    if (lane == 0) {
+      rec[0] = T(-1), rec[1] = T(SAMPLER);
+      for (int k = 2; k < kSnapStride; ++k) rec[k] = T(0);
+    }
+    return;
+  }
+  T lo = T(0);
+  const int nb = sizeof(T) == 4 ? 24 : 52;
+  for (int b = 0; b < nb; ++b) {
+    const T mid = T(0.5) * (lo + hi);
+    Q4<T> qx;
+    V3<T> tx;
+    ray_pose<T, SAMPLER>(q, t, dir, mid, qx, tx);
+    if (pose_in_purse<T, KIND>(tab, N, qmat(qx), tx, fx, fy, cx, cy, lane))
+      lo = mid;
+    else
+      hi = mid;
+  }
+  Q4<T> qs;
+  V3<T> ts;
+  ray_pose<T, SAMPLER>(q, t, dir, lo, qs, ts);
+  q = qs, t = ts;
+  const M3<T> R = qmat(qs);
+  // active constraint: smallest margin r_i - |g_i| (ties to the lower index)
+  unsigned long long best = ~0ull;
+  for (int i = lane; i < N; i += 32) {
+    const T4<T> mz = tab[i], ob = tab[N + i];
+    const V3<T> X = mul(R, V3<T>{mz.x, mz.y, mz.z}) + ts;
+    T m;
+    if (KIND == 1) {
+      const T u = (fx * X.x + cx * X.z) / X.z, v = (fy * X.y + cy * X.z) / X.z;
+      m = mz.w - sqrt((ob.x - u) * (ob.x - u) + (ob.y - v) * (ob.y - v));
+    } else {
+      const V3<T> e = X - V3<T>{ob.x, ob.y, ob.z};
+      m = mz.w - sqrt(dot(e, e));
+    }
+    const unsigned long long key = ((unsigned long long)orderable((float)m) << 32) | (unsigned)i;
+    best = key < best ? key : best;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(kFullMask, best, o);
+    best = v < best ? v : best;
+  }
+  if (lane != 0) return;
+  const int j = (int)(best & 0xFFFFFFFFull);
+  const T4<T> mz = tab[j], ob = tab[N + j];
+  const V3<T> RA = mul(R, V3<T>{mz.x, mz.y, mz.z});
+  const V3<T> X = RA + ts;
+  V3<T> wv, dy;  // d|g|/d(translation of the keypoint), d|g|/d y
+  if (KIND == 1) {
+    const T Px = fx * X.x + cx * X.z, Py = fy * X.y + cy * X.z, Pz = X.z;
+    const T e0 = Px / Pz - ob.x, e1 = Py / Pz - ob.y;
+    const T nrm = sqrt(e0 * e0 + e1 * e1);
+    const T n0 = e0 / nrm, n1 = e1 / nrm;
+    const V3<T> jn{n0 / Pz, n1 / Pz, -(Px * n0 + Py * n1) / (Pz * Pz)};
+    wv = V3<T>{fx * jn.x, fy * jn.y, cx * jn.x + cy * jn.y + jn.z};
+    dy = V3<T>{-n0, -n1, T(0)};
+  } else {
+    const V3<T> e = X - V3<T>{ob.x, ob.y, ob.z};
+    const T nrm = sqrt(dot(e, e));
+    wv = (T(1) / nrm) * e;
+    dy = (T(-1) / nrm) * e;
+  }
+  const T dh = SAMPLER == 0 ? dot(cross(RA, wv), dir) : dot(wv, dir);
+  rec[0] = T(j), rec[1] = T(SAMPLER), rec[2] = dir.x, rec[3] = dir.y, rec[4] = dir.z, rec[5] = dh;
+  rec[6] = dy.x, rec[7] = dy.y, rec[8] = dy.z;
+  for (int k = 9; k < kSnapStride; ++k) rec[k] = T(0);
+}
 
 // One walk of Alg. 3 (dS_R) or Alg. 5 (dS_t): N_I iterations from seed (w mod |S0|), then emit.
 // tab: the PURSE's constraint table in shared memory; sl: this warp's slab.
@@ -562,7 +687,8 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
     __syncwarp();
   }
 
-  // ---- a8: emit
+  // ---- optional boundary snap (for the adjoint), then a8: emit
+  if (c.out_snap) snap_walk<T, KIND, SAMPLER>(c, tab, vel, q, t, w, lane);
   if (lane == 0) {
     T* oq = c.out_q + 4 * (size_t)w;
     T* ot = c.out_t + 3 * (size_t)w;
@@ -607,6 +733,7 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
   c.key0 = a.key0, c.key1 = a.key1;
   c.out_q = reinterpret_cast<T*>(a.out_q), c.out_t = reinterpret_cast<T*>(a.out_t);
   c.trace = a.trace, c.status = a.status;
+  c.out_snap = reinterpret_cast<T*>(a.out_snap);
   const RkParam rk{a};
   unsigned long long evals = 0;
   for (int w = blockIdx.x * kWalkWarps + warp; w < a.n_samples; w += gridDim.x * kWalkWarps)
@@ -671,7 +798,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2)
         c.omega0 = b.omega0[kd], c.v0 = b.v0[kd], c.gamma = b.gamma[kd];
         c.st = b.stats + p, c.seed_data = b.seed_data + (size_t)p * kSeedStride, c.s0 = 1;
         c.key0 = (uint32_t)key, c.key1 = (uint32_t)(key >> 32);
-        c.trace = nullptr, c.status = b.status;
+        c.trace = nullptr, c.out_snap = nullptr, c.status = b.status;
         sl = carve<float>(slab_base, c.N, c.NP, c.NT);
         cur = p;
         __syncwarp();

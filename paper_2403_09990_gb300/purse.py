@@ -48,9 +48,11 @@ _SIGS = {
     "purse_eval": [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP, _VP],
     "purse_ransag": [_VP, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int), _VP],
     "purse_sample": [_VP, ctypes.POINTER(purse_params), ctypes.c_uint64, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP,
-                     _VP, _VP],
+                     _VP, _VP, _VP],
     "purse_last_evals": [_VP, ctypes.POINTER(ctypes.c_ulonglong), _VP],
     "megb_solve": [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP],
+    "megb_backward": [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP, _VP,
+                      _VP, _VP, _VP, _VP],
     "megb_solve_noalloc": [ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP],
     "purse_rng_words": [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                         ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP],
@@ -143,9 +145,9 @@ def purse_ransag(h, seed, n_trials, max_seeds, seeds, stream=None) -> int:
     return n.value
 
 
-def purse_sample(h, params: purse_params, seed, seeds, s0, n_samples, q, t, trace=None, stream=None):
+def purse_sample(h, params: purse_params, seed, seeds, s0, n_samples, q, t, trace=None, stream=None, snap=None):
     _check(lib().purse_sample(h, ctypes.byref(params), seed, _ptr(seeds), s0, n_samples, _ptr(q), _ptr(t),
-                              _ptr(trace), _stream(stream)), "purse_sample")
+                              _ptr(trace), _ptr(snap), _stream(stream)), "purse_sample")
 
 
 def purse_last_evals(h, stream=None) -> int:
@@ -157,6 +159,13 @@ def purse_last_evals(h, stream=None) -> int:
 def megb_solve(h, precision, n_iters, q, n_rot, t, n_tr, result, farthest=None, stream=None):
     _check(lib().megb_solve(h, precision, n_iters, _ptr(q), n_rot, _ptr(t), n_tr, _ptr(result), _ptr(farthest),
                             _stream(stream)), "megb_solve")
+
+
+def megb_backward(h, precision, n_iters, q, snap_rot, n_rot, t, snap_tr, n_tr, farthest, result, grad_result,
+                  grad_obs, grad_radii, stream=None):
+    _check(lib().megb_backward(h, precision, n_iters, _ptr(q), _ptr(snap_rot), n_rot, _ptr(t), _ptr(snap_tr), n_tr,
+                               _ptr(farthest), _ptr(result), _ptr(grad_result), _ptr(grad_obs), _ptr(grad_radii),
+                               _stream(stream)), "megb_backward")
 
 
 def megb_solve_noalloc(precision, n_iters, q, n_rot, t, n_tr, result, farthest=None, stream=None):

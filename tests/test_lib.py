@@ -59,7 +59,7 @@ def test_argument_validation_without_gpu():
     assert L.purse_create(1, 3, m3.ctypes.data, m3.ctypes.data, r3.ctypes.data, None, ctypes.byref(h)) == 1
     # NULL handles are rejected before any CUDA call
     prm = P.make_params()
-    assert L.purse_sample(None, ctypes.byref(prm), 0, None, 1, 1, None, None, None, None) == 1
+    assert L.purse_sample(None, ctypes.byref(prm), 0, None, 1, 1, None, None, None, None, None) == 1
     assert L.megb_solve(None, 0, 10, None, 0, None, 0, None, None, None) == 1
     assert L.purse_sync(None, None) == 1
     assert L.purse_destroy(None) == 0
