@@ -104,10 +104,15 @@ purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds,
  * NULL) receives per walk and iteration n_keep + 2 int16: the top-k perturbation indices in
  * rank order, then m0 and k0 (0-based; -1 when no candidate was feasible).
  * Random draws: Philox4x32-10, key = (low, high 32 bits of seed); word k of the stream named
- * (phase, j, i, w) is output lane k & 3 of counter (k >> 2, phase << 24 | j, i, w); phase 1/2 are
- * the perturbations j of iteration i of walk w in the dS_R / dS_t sampler, 3/4 the random unit
- * vector of the initial angular / centre velocity.  A ball point takes one word per attempt:
- * X_c = 2 ((word >> 10c) & 1023) - 1023, accepted if |X|^2 <= 2^20, point X / 1024.
+ * (phase, j, i, w) is output lane k & 3 of counter (k >> 2, phase << 24 | j, i, w).  Phase 1/2:
+ * the perturbations of iteration i of walk w in the dS_R / dS_t sampler; perturbations 2b and
+ * 2b + 1 are the two points of words 0-1 and 2-3 of stream (phase, b, i, w), a point of words
+ * (w0, w1) being rho (sqrt(1 - z^2) cos a, sqrt(1 - z^2) sin a, z) in the unit ball with
+ * z = ((w0 >> 16) + 1/2) / 2^15 - 1, a = pi ((w0 & 0xFFFF) + 1/2) / 2^15 and
+ * rho = (max of the three 10-bit fields of w1 + 1/2) / 1024 (no rejection), scaled by the
+ * perturbation radius.  Phase 3/4: the random unit vector of the initial angular / centre
+ * velocity, one word per attempt: X_c = 2 ((word >> 10c) & 1023) - 1023, accepted if
+ * 2^14 <= |X|^2 <= 2^20, normalised.
  * d_snap (device, may be NULL): snap every final sample to the PURSE boundary along its walk's
  * last-move ray (rotation ray Exp(tau omega) R* for the dS_R sampler, translation ray t* + tau v for
  * dS_t; the paper has no snap -- it makes the balls differentiable): tau_hi = the smallest ladder
