@@ -298,6 +298,8 @@ def run_gpu(args, rank, world):
         out["e2e"] = run_e2e(args, p, dev)
     if not args.no_batch:
         out["batch"] = run_batch(args, dev)
+    if not args.no_grad:
+        out["grad"] = run_grad(args, dev)
     if rank == 0 and not args.no_cpu_baseline:
         ev_c, wall_c, walks_c = oracle_sample(args.cpu_walks, args.cpu_workers)
         out["cpu_baseline"] = {"value": ev_c / wall_c, "unit": UNIT, "cores": args.cpu_workers, "kind": "oracle",
@@ -350,12 +352,109 @@ def run_batch(args, dev):
     ns = np.array([p.n for p in purses])
     alg = float(((1 + kinds) * S * 5 * (150 + 10 * 15) * ns).sum())
     ms = tot / args.batch_steps
+    per_instance = run_per_instance(args, purses[:args.per_instance_purses], p3, p2, S, K, dev)
     return {"workload": f"{n_purses} PURSEs (3D-3D / 2D-3D by a fair coin, N ~ U{{4..64}}), {S} samples each, "
                         f"presets of Section V (N_I = 5), both balls with {K} GGD iterations, FP32",
             "purses_per_s": n_purses / (ms / 1e3), "ms_per_solve": ms, "steps": args.batch_steps,
             "evals_per_s": alg / (ms / 1e3), "evals_executed_per_s": ev_total / args.batch_steps / (ms / 1e3),
             "launch": {"graph": "statistics + persistent walk kernel + one block per ball", "chunk": chunk,
-                       "warps_per_block": warps}}
+                       "warps_per_block": warps},
+            "per_instance": per_instance,
+            "speedup_vs_per_instance": (n_purses / (ms / 1e3)) / per_instance["purses_per_s"]}
+
+
+def run_per_instance(args, purses, p3, p2, S, K, dev):
+    """The plain per-instance GPU path on the same GPU: the batch's first PURSEs solved one call sequence
+    per PURSE (purse_create, purse_sample per sampler, megb_solve, result read back), as a caller without
+    the batch API would."""
+    import torch
+    import paper_2403_09990_gb300.purse as P
+    stream = torch.cuda.current_stream()
+    q1 = torch.empty((S, 4), dtype=torch.float32, device=dev)
+    t1 = torch.empty((S, 3), dtype=torch.float32, device=dev)
+    q2 = torch.empty((S, 4), dtype=torch.float32, device=dev)
+    t2 = torch.empty((S, 3), dtype=torch.float32, device=dev)
+    res = torch.empty(9, dtype=torch.float64, device=dev)
+    out = torch.empty(9, dtype=torch.float64)
+
+    def one(pu, seed):
+        with P.Purse(pu) as h:
+            sd = torch.as_tensor(pu.seed_pose()[None], dtype=torch.float64, device=dev)
+            prm = p3 if pu.kind == 0 else p2
+            P.purse_sample(h.h, P.purse_params.from_buffer_copy(prm), seed, sd, 1, S, q1, t1, None, stream)
+            if pu.kind == 1:
+                p_t = P.purse_params.from_buffer_copy(prm)
+                p_t.sampler = 1
+                P.purse_sample(h.h, p_t, seed, sd, 1, S, q2, t2, None, stream)
+            P.megb_solve(h.h, 0, K, q1, S, t2 if pu.kind == 1 else t1, S, res, None, stream)
+            out.copy_(res)
+            P.purse_sync(h.h, stream)
+
+    for pu in purses[:2]:
+        one(pu, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, pu in enumerate(purses):
+        one(pu, 100 + i)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return {"purses": len(purses), "purses_per_s": len(purses) / wall, "ms_per_purse": 1e3 * wall / len(purses),
+            "path": "per PURSE: purse_create + purse_sample (dS_R; dS_t for 2D-3D) + megb_solve + result D2H, "
+                    "the batch's first PURSEs, wall clock"}
+
+
+def run_grad(args, dev):
+    """Differentiation workload: 1024 3D-3D PURSEs (N = 32, r_i ~ U[0.005, 0.02] m), 4096 samples per PURSE
+    and sampler with boundary snap (dS_R walks for the rotation ball, dS_t walks with v0 = 0.02 m for the
+    translation ball), both balls with 200 GGD iterations, then the adjoint of both radii with respect to
+    every y_i and r_i (purse_batch_backward)."""
+    import torch
+    import paper_2403_09990_gb300.purse as P
+    from paper_2403_09990_gb300 import synthetic as syn
+    n_purses, S, K = args.grad_purses, 4096, K_MEGB
+    purses = [syn.purse_3d3d(32, seed=5000 + i) for i in range(n_purses)]
+    seeds = torch.as_tensor(syn.seed_array(purses), dtype=torch.float64, device=dev)
+    res = torch.empty((n_purses, 9), dtype=torch.float64, device=dev)
+    g = torch.zeros((n_purses, 9), dtype=torch.float64, device=dev)
+    g[:, 7] = 1.0
+    g[:, 8] = 1.0
+    total = sum(pu.n for pu in purses)
+    gy = torch.empty((total, 3), dtype=torch.float64, device=dev)
+    gr = torch.empty(total, dtype=torch.float64, device=dev)
+    p3 = P.make_params(n_iter=5, n_perturb=150, n_keep=10, n_steps=15, omega0=0.5, v0=0.02, gamma=0.5,
+                       rot_perturb=0.025, trans_perturb=0.00125, perturb_units=1)
+    p2 = P.make_params(n_iter=5)
+    b = P.purse_batch_create(purses)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    try:
+        P.purse_batch_set_grad(b, 1)
+        P.purse_batch_tune(b, p3, p2, 1, seeds, 1024, stream)
+        P.purse_batch_solve(b, p3, p2, 3, seeds, S, K, res, stream)
+        P.purse_batch_backward(b, res, g, gy, gr, stream)
+        P.purse_batch_sync(b, stream)
+        fw = bw = 0.0
+        for st in range(args.batch_steps):
+            flush.fill_(st & 0xFF)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            P.purse_batch_solve(b, p3, p2, 200 + st, seeds, S, K, res, stream)
+            e[1].record(stream)
+            P.purse_batch_backward(b, res, g, gy, gr, stream)
+            e[2].record(stream)
+            P.purse_batch_sync(b, stream)
+            fw += e[0].elapsed_time(e[1])
+            bw += e[1].elapsed_time(e[2])
+        nz = float((gr != 0).double().mean())
+    finally:
+        P.purse_batch_destroy(b)
+    fw /= args.batch_steps
+    bw /= args.batch_steps
+    return {"workload": f"{n_purses} 3D-3D PURSEs, N=32, {S} samples per PURSE and sampler with boundary snap, "
+                        f"both balls ({K} GGD iterations), adjoint of D-hat + d-hat w.r.t. every y_i and r_i, FP32 "
+                        "walks, FP64 adjoint",
+            "ms_forward": fw, "ms_backward": bw, "purses_per_s": n_purses / ((fw + bw) / 1e3),
+            "backward_purses_per_s": n_purses / (bw / 1e3), "frac_radii_with_gradient": nz}
 
 
 def run_e2e(args, p, dev):
@@ -445,6 +544,10 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--batch-warmup", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-grad", action="store_true", help="skip the batched differentiation measurement")
+    ap.add_argument("--grad-purses", type=int, default=1024)
+    ap.add_argument("--per-instance-purses", type=int, default=256,
+                    help="PURSEs of the batch solved one by one for the per-instance comparison")
     args = ap.parse_args()
     N_WALKS, N_ITER = args.walks, args.iters
     rank = int(os.environ.get("RANK", 0))

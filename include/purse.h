@@ -196,8 +196,10 @@ purse_status purse_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t
  * PURSE p has kind kinds[p] and constraints offsets[p] .. offsets[p+1]-1 (3..256 each) of
  * model (host, x 3), obs (host, x 3; z ignored for 2D-3D) and radii (host, > 0); K (host,
  * n_purses entries) holds the intrinsics of the 2D-3D PURSEs (others ignored; may be NULL if
- * there are none).  3D-3D PURSEs use the dS_R samples for both balls; 2D-3D PURSEs the dS_R
- * samples for the rotation ball and the dS_t samples for the translation ball. */
+ * there are none).  2D-3D PURSEs use the dS_R samples for the rotation ball and the dS_t samples
+ * for the translation ball.  3D-3D PURSEs use the dS_R samples for both balls when p3d->v0 = 0 (the
+ * dS_t walks would not move); with p3d->v0 > 0 their dS_t walks run too and feed the translation
+ * ball, as for 2D-3D. */
 typedef struct purse_batch_s* purse_batch_t;
 
 purse_status purse_batch_create(int n_purses, const int* kinds, const int* offsets, const double* model,
@@ -230,9 +232,30 @@ purse_status purse_batch_copy_farthest(purse_batch_t b, int32_t* d_out, purse_st
 
 /* Copy PURSE p's samples of the last solve (device, n_samples x 4 / x 3 floats each; any may be NULL):
  * dS_R quaternions and translations, dS_t quaternions and translations (the dS_t buffers are
- * unwritten for 3D-3D PURSEs). */
+ * unwritten for 3D-3D PURSEs solved with p3d->v0 = 0). */
 purse_status purse_batch_copy_samples(purse_batch_t b, int p, float* d_q_rot, float* d_t_rot, float* d_q_tr,
                                       float* d_t_tr, purse_stream_t stream);
+
+/* Differentiation of batched solves (enable = 1) or not (0, the default).  While enabled, every
+ * purse_batch_solve also snaps the final samples to the boundary (as purse_sample's d_snap) and
+ * keeps the snap records and the farthest samples of the final centres in batch-owned memory
+ * (2 x n_purses x n_samples x 12 floats), for purse_batch_backward.  The paper has no adjoint;
+ * see megb_backward.  Changing the flag re-captures the graph at the next solve. */
+purse_status purse_batch_set_grad(purse_batch_t b, int enable);
+
+/* Copy PURSE p's snap records of the last solve (device, n_samples x 12 floats each; either may be
+ * NULL): dS_R walks, dS_t walks.  PURSE_ERR_STATE unless the last solve had gradients enabled. */
+purse_status purse_batch_copy_snap(purse_batch_t b, int p, float* d_snap_rot, float* d_snap_tr,
+                                   purse_stream_t stream);
+
+/* megb_backward for every PURSE of the last solve (which must have had gradients enabled):
+ * d_results the solve's results (device, n_purses x 9, unchanged since), d_grad_results dL/d
+ * results (device, n_purses x 9); writes d_grad_obs (device, total keypoints x 3 doubles in the
+ * CSR order of purse_batch_create; the third column is 0 for 2D-3D) and d_grad_radii (device,
+ * total keypoints doubles).  One block per PURSE, the two sweeps on two warps, FP64; identical
+ * to megb_backward on the PURSE's samples.  PURSE_ERR_STATE without such a solve. */
+purse_status purse_batch_backward(purse_batch_t b, const double* d_results, const double* d_grad_results,
+                                  double* d_grad_obs, double* d_grad_radii, purse_stream_t stream);
 
 /* Synchronise the stream; *evals (host, may be NULL) receives the executed evaluations of the
  * last batch walk launch; returns the batch's device status. */

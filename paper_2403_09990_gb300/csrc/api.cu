@@ -266,7 +266,7 @@ purse_status megb_backward(purse_t h, int precision, int n_iters, const void* d_
     return arg_error("megb_backward: NULL samples or snap records");
   if (!d_farthest || !d_result || !d_grad_result || !d_grad_obs || !d_grad_radii)
     return arg_error("megb_backward: NULL buffer");
-  purse_status s = ensure_scratch(h, megb_backward_scratch_bytes(n_iters, h->sm_count));
+  purse_status s = ensure_scratch(h, megb_backward_scratch_bytes(n_iters, h->sm_count, h->n));
   if (s != PURSE_OK) return s;
   cudaError_t e = launch_megb_backward(h, precision, n_iters, d_q, d_snap_rot, n_rot, d_t, d_snap_tr, n_tr, d_farthest,
                                        d_result, d_grad_result, d_grad_obs, d_grad_radii, h->d_scratch,

@@ -27,6 +27,16 @@ struct purse_batch_s {
   int last_iters = 0;          // GGD iterations of the last solve
   int32_t* d_far = nullptr;
   size_t far_cap = 0;
+  // differentiation: snap records of both samplers, farthest samples of the final centres,
+  // scratch for the recomputed rotation iterates
+  int grad = 0;
+  float* d_snap = nullptr;
+  size_t snap_cap = 0;
+  int32_t* d_fstar = nullptr;
+  void* d_cs = nullptr;
+  size_t cs_cap = 0;
+  int last_grad = 0;  // the last solve wrote snap records
+  int last_tr3d = 0;
   // launch shape of the walk kernel (autotuned)
   int chunk = 8, warps = 8;
   // captured graph and what it was captured for
@@ -75,6 +85,10 @@ static BatchArgs make_args(purse_batch_t b, const purse_params* p3, const purse_
   a.t_rot = a.q_rot + 4 * S;
   a.q_tr = a.t_rot + 3 * S;
   a.t_tr = a.q_tr + 4 * S;
+  a.snap_rot = b->grad ? b->d_snap : nullptr;
+  a.snap_tr = b->grad ? b->d_snap + (size_t)kSnapStride * S : nullptr;
+  a.fstar = b->grad ? b->d_fstar : nullptr;
+  a.tr3d = p3->v0 > 0.0 ? 1 : 0;
   a.status = b->d_status;
   a.evals = b->d_evals;
   return a;
@@ -97,6 +111,18 @@ static purse_status ensure_batch_buffers(purse_batch_t b, int n_samples, int n_i
     cudaError_t e = cudaMalloc(&b->d_far, (size_t)b->n_purses * 2 * n_iters * sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "purse_batch_solve (traces)");
     b->far_cap = n_iters;
+  }
+  if (b->grad && (size_t)n_samples > b->snap_cap) {
+    if (b->d_snap) cudaFree(b->d_snap);
+    b->d_snap = nullptr;
+    b->snap_cap = 0;
+    cudaError_t e = cudaMalloc(&b->d_snap, 2 * (size_t)b->n_purses * n_samples * kSnapStride * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e, "purse_batch_solve (snap records)");
+    b->snap_cap = n_samples;
+  }
+  if (b->grad && !b->d_fstar) {
+    cudaError_t e = cudaMalloc(&b->d_fstar, 2 * (size_t)b->n_purses * sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "purse_batch_solve (farthest samples)");
   }
   return PURSE_OK;
 }
@@ -205,6 +231,9 @@ purse_status purse_batch_destroy(purse_batch_t b) {
   cudaFree(b->d_counter);
   cudaFree(b->d_samples);
   cudaFree(b->d_far);
+  cudaFree(b->d_snap);
+  cudaFree(b->d_fstar);
+  cudaFree(b->d_cs);
   delete b;
   return PURSE_OK;
 }
@@ -231,6 +260,8 @@ purse_status purse_batch_solve(purse_batch_t b, const purse_params* p3d, const p
   b->host_seed = seed;
   b->last_samples = n_samples;
   b->last_iters = n_iters;
+  b->last_grad = b->grad;
+  b->last_tr3d = p3d->v0 > 0.0 ? 1 : 0;
   cudaError_t e = cudaMemcpyAsync(b->d_seed, &b->host_seed, sizeof(unsigned long long), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "purse_batch_solve (seed)");
   // the graph is captured once per (parameters, sizes, buffers, launch shape) and replayed
@@ -239,7 +270,7 @@ purse_status purse_batch_solve(purse_batch_t b, const purse_params* p3d, const p
   memcpy(key.data() + sizeof(purse_params), p2d, sizeof(purse_params));
   char* kp = key.data() + 2 * sizeof(purse_params);
   const void* ptrs[2] = {d_seeds, d_results};
-  const int ints[4] = {n_samples, n_iters, b->chunk, b->warps};
+  const int ints[5] = {n_samples, n_iters, b->chunk, b->warps, b->grad};
   memcpy(kp, ptrs, sizeof(ptrs));
   memcpy(kp + sizeof(ptrs), ints, sizeof(ints));
   if (!b->exec || key != b->graph_key) {
@@ -343,6 +374,69 @@ purse_status purse_batch_copy_samples(purse_batch_t b, int p, float* d_q_rot, fl
     if (dst[k])
       e = cudaMemcpyAsync(dst[k], src[k], width[k] * n * sizeof(float), cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
   return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_batch_copy_samples");
+}
+
+purse_status purse_batch_set_grad(purse_batch_t b, int enable) {
+  if (!b) return barg("purse_batch_set_grad: NULL batch");
+  if (enable != 0 && enable != 1) return barg("purse_batch_set_grad: enable must be 0 or 1");
+  if (b->grad != enable) {
+    b->grad = enable;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return PURSE_OK;
+}
+
+purse_status purse_batch_copy_snap(purse_batch_t b, int p, float* d_snap_rot, float* d_snap_tr, purse_stream_t stream) {
+  if (!b) return barg("purse_batch_copy_snap: NULL batch");
+  if (p < 0 || p >= b->n_purses) return barg("purse_batch_copy_snap: PURSE index out of range");
+  if (!b->last_grad) return (set_error("purse_batch_copy_snap: no solve with gradients enabled yet"), PURSE_ERR_STATE);
+  const size_t S = (size_t)b->n_purses * b->last_samples, n = (size_t)b->last_samples, o = (size_t)p * n;
+  const float* src[2] = {b->d_snap + kSnapStride * o, b->d_snap + kSnapStride * (S + o)};
+  float* dst[2] = {d_snap_rot, d_snap_tr};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+    if (dst[k])
+      e = cudaMemcpyAsync(dst[k], src[k], kSnapStride * n * sizeof(float), cudaMemcpyDeviceToDevice,
+                          (cudaStream_t)stream);
+  return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_batch_copy_snap");
+}
+
+purse_status purse_batch_backward(purse_batch_t b, const double* d_results, const double* d_grad_results,
+                                  double* d_grad_obs, double* d_grad_radii, purse_stream_t stream) {
+  if (!b) return barg("purse_batch_backward: NULL batch");
+  if (!d_results || !d_grad_results || !d_grad_obs || !d_grad_radii) return barg("purse_batch_backward: NULL buffer");
+  if (!b->last_grad || b->last_iters == 0)
+    return (set_error("purse_batch_backward: no solve with gradients enabled yet"), PURSE_ERR_STATE);
+  const int K = b->last_iters;
+  const size_t need = (size_t)b->n_purses * (K + 1) * 4 * sizeof(double);
+  if (need > b->cs_cap) {
+    if (b->d_cs) cudaFree(b->d_cs);
+    b->d_cs = nullptr;
+    b->cs_cap = 0;
+    cudaError_t e = cudaMalloc(&b->d_cs, need);
+    if (e != cudaSuccess) return cuda_fail(e, "purse_batch_backward (scratch)");
+    b->cs_cap = need;
+  }
+  BatchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.info = b->d_info;
+  a.n_purses = b->n_purses;
+  a.n_samples = b->last_samples;
+  a.nmax = b->nmax;
+  const size_t S = (size_t)b->n_purses * b->last_samples;
+  a.q_rot = b->d_samples;
+  a.t_rot = a.q_rot + 4 * S;
+  a.q_tr = a.t_rot + 3 * S;
+  a.t_tr = a.q_tr + 4 * S;
+  a.snap_rot = b->d_snap;
+  a.snap_tr = b->d_snap + (size_t)kSnapStride * S;
+  a.fstar = b->d_fstar;
+  a.tr3d = b->last_tr3d;
+  a.status = b->d_status;
+  cudaError_t e = launch_batch_backward(a, K, b->d_far, d_results, d_grad_results, b->d_cs, d_grad_obs, d_grad_radii,
+                                        (cudaStream_t)stream);
+  return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_batch_backward");
 }
 
 purse_status purse_batch_sync(purse_batch_t b, unsigned long long* evals, purse_stream_t stream) {

@@ -64,6 +64,10 @@ struct BatchArgs {
   float* t_rot;                    // n_purses x n_samples x 3
   float* q_tr;                     // dS_t sampler
   float* t_tr;
+  float* snap_rot;  // NULL or n_purses x n_samples x kSnapStride snap records (dS_R walks)
+  float* snap_tr;   // same for the dS_t walks
+  int32_t* fstar;   // NULL or n_purses x 2: farthest sample from each final centre
+  int tr3d;         // 3D-3D: run the dS_t walks and take the translation ball from them (v0 > 0)
   int* status;
   unsigned long long* evals;
 };
@@ -135,7 +139,10 @@ cudaError_t launch_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t
 size_t megb_scratch_bytes(int n_iters, int sm_count);
 cudaError_t launch_megb(purse_t h, int precision, int n_iters, const void* d_q, int n_rot, const void* d_t,
                         int n_tr, double* d_result, int32_t* d_farthest, void* scratch, cudaStream_t st);
-size_t megb_backward_scratch_bytes(int n_iters, int sm_count);
+size_t megb_backward_scratch_bytes(int n_iters, int sm_count, int n);
+cudaError_t launch_batch_backward(const BatchArgs& b, int n_iters, const int32_t* d_far, const double* d_results,
+                                  const double* d_grad_results, void* d_cs, double* d_grad_obs, double* d_grad_radii,
+                                  cudaStream_t st);
 cudaError_t launch_megb_backward(purse_t h, int precision, int n_iters, const void* d_q, const void* d_snap_rot,
                                  int n_rot, const void* d_t, const void* d_snap_tr, int n_tr,
                                  const int32_t* d_farthest, const double* d_result, const double* d_grad_result,

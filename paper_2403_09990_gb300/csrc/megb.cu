@@ -289,64 +289,87 @@ __device__ __forceinline__ void snap_scatter(const T* rec, int ball, V3<double> 
   for (int c = 0; c < dim; ++c) gy[(size_t)dim * j + c] -= gt * (double)rec[6 + c];
 }
 
-// One thread walks both balls backwards (serial in k, FP64); the block zeroes the outputs first.
+// Reverse sweep of the rotation ball (one thread, FP64), accumulating into gy / gr.
+// q: samples; snap: their records; f: the K farthest indices; fs: farthest from C_K;
+// g: dL/d(result) (9); Cs: K + 1 quaternions of scratch.
 template <typename T>
-__global__ void megb_adjoint_kernel(const T* q, const T* snap_r, int nq, const T* t, const T* snap_t, int nt, int K,
-                                    const int32_t* f, const MegbState* s, const double* result, const double* g,
-                                    Q4<double>* Cs, int n, int dim, double* gy, double* gr, int* status) {
-  for (int i = threadIdx.x; i < n * dim; i += blockDim.x) gy[i] = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) gr[i] = 0.0;
+__device__ void adjoint_rotation(const T* q, const T* snap, int K, const int32_t* f, int fs, const double* g,
+                                 Q4<double>* Cs, int n, int dim, double* gy, double* gr, int* status) {
+  // recompute the iterates C_0..C_K from the stored farthest sequence
+  Cs[0] = load_q(q, 0);
+  for (int k = 1; k <= K; ++k) Cs[k] = slerp_step(Cs[k - 1], rel_rot(Cs[k - 1], load_q(q, f[k - 1])), k);
+  const Q4<double> CK = Cs[K];
+  const M3<double> RK = qmat(CK);
+  // dL/d eps_K from the centre-quaternion gradient: g_C = (w g_v - g_w v + v x g_v) / 2
+  const V3<double> vq{CK.x, CK.y, CK.z}, gv{g[1], g[2], g[3]};
+  const V3<double> cv = cross(vq, gv);
+  V3<double> lam{0.5 * (CK.w * gv.x - g[0] * vq.x + cv.x), 0.5 * (CK.w * gv.y - g[0] * vq.y + cv.y),
+                 0.5 * (CK.w * gv.z - g[0] * vq.z + cv.z)};
+  const RelRot r = rel_rot(CK, load_q(q, fs));
+  if (r.sn > 0.0 && g[7] != 0.0) {
+    const V3<double> w = mul(RK, V3<double>{r.d.x / r.sn, r.d.y / r.sn, r.d.z / r.sn});
+    snap_scatter(snap + (size_t)kSnapStride * fs, 0, g[7] * w, n, dim, gy, gr, status);
+    lam = lam - g[7] * w;
+  }
+  for (int k = K; k >= 1; --k) {
+    const RelRot rk = rel_rot(Cs[k - 1], load_q(q, f[k - 1]));
+    V3<double> phi{0.0, 0.0, 0.0};
+    if (rk.sn > 0.0) phi = (rk.th / rk.sn) * V3<double>{rk.d.x, rk.d.y, rk.d.z};
+    // A_k^T lam = (1/k) C_{k-1} J_l(-phi)^-1 J_l(phi/k) C_k^T lam
+    V3<double> y = mul_t(qmat(Cs[k]), lam);
+    y = jl_apply((1.0 / k) * phi, y, false);
+    y = jl_apply(-1.0 * phi, y, true);
+    const V3<double> v = (1.0 / k) * mul(qmat(Cs[k - 1]), y);
+    snap_scatter(snap + (size_t)kSnapStride * f[k - 1], 0, v, n, dim, gy, gr, status);
+    lam = lam - v;
+  }
+  snap_scatter(snap, 0, lam, n, dim, gy, gr, status);
+}
+
+// Reverse sweep of the translation ball; c: the final centre c_K (3 doubles).
+template <typename T>
+__device__ void adjoint_translation(const T* t, const T* snap, int K, const int32_t* f, int fs, const double* c,
+                                    const double* g, int n, int dim, double* gy, double* gr, int* status) {
+  const T* tf = t + 3 * (size_t)fs;
+  const V3<double> e{(double)tf[0] - c[0], (double)tf[1] - c[1], (double)tf[2] - c[2]};
+  const double dn = sqrt(dot(e, e));
+  V3<double> mu{g[4], g[5], g[6]};
+  if (dn > 0.0 && g[8] != 0.0) {
+    const V3<double> u = (g[8] / dn) * e;
+    snap_scatter(snap + (size_t)kSnapStride * fs, 1, u, n, dim, gy, gr, status);
+    mu = mu - u;
+  }
+  for (int k = K; k >= 1; --k) {
+    snap_scatter(snap + (size_t)kSnapStride * f[k - 1], 1, (1.0 / k) * mu, n, dim, gy, gr, status);
+    mu = (1.0 - 1.0 / k) * mu;
+  }
+  snap_scatter(snap, 1, mu, n, dim, gy, gr, status);
+}
+
+// Both sweeps in parallel (warp 0: rotation into acc, warp 1: translation into acc + n (dim + 1)),
+// then gy = rotation part + translation part, gr likewise.  acc: 2 n (dim + 1) zeroed here.
+template <typename T>
+__device__ void adjoint_both(const T* q, const T* snap_r, int nq, const T* t, const T* snap_t, int nt, int K,
+                             const int32_t* f, const int* fstar, const double* result, const double* g,
+                             Q4<double>* Cs, int n, int dim, double* acc, double* gy, double* gr, int* status) {
+  const int m = n * (dim + 1);
+  for (int i = threadIdx.x; i < 2 * m; i += blockDim.x) acc[i] = 0.0;
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  if (nq > 0) {
-    // recompute the iterates C_0..C_K from the stored farthest sequence
-    Cs[0] = load_q(q, 0);
-    for (int k = 1; k <= K; ++k) Cs[k] = slerp_step(Cs[k - 1], rel_rot(Cs[k - 1], load_q(q, f[k - 1])), k);
-    const Q4<double> CK = Cs[K];
-    const M3<double> RK = qmat(CK);
-    // dL/d eps_K from the centre-quaternion gradient: g_C = (w g_v - g_w v + v x g_v) / 2
-    const V3<double> vq{CK.x, CK.y, CK.z}, gv{g[1], g[2], g[3]};
-    const V3<double> cv = cross(vq, gv);
-    V3<double> lam{0.5 * (CK.w * gv.x - g[0] * vq.x + cv.x), 0.5 * (CK.w * gv.y - g[0] * vq.y + cv.y),
-                   0.5 * (CK.w * gv.z - g[0] * vq.z + cv.z)};
-    const int fs = s->fstar[0];
-    const RelRot r = rel_rot(CK, load_q(q, fs));
-    if (r.sn > 0.0 && g[7] != 0.0) {
-      const V3<double> w = mul(RK, V3<double>{r.d.x / r.sn, r.d.y / r.sn, r.d.z / r.sn});
-      snap_scatter(snap_r + (size_t)kSnapStride * fs, 0, g[7] * w, n, dim, gy, gr, status);
-      lam = lam - g[7] * w;
-    }
-    for (int k = K; k >= 1; --k) {
-      const RelRot rk = rel_rot(Cs[k - 1], load_q(q, f[k - 1]));
-      V3<double> phi{0.0, 0.0, 0.0};
-      if (rk.sn > 0.0) phi = (rk.th / rk.sn) * V3<double>{rk.d.x, rk.d.y, rk.d.z};
-      // A_k^T lam = (1/k) C_{k-1} J_l(-phi)^-1 J_l(phi/k) C_k^T lam
-      V3<double> y = mul_t(qmat(Cs[k]), lam);
-      y = jl_apply((1.0 / k) * phi, y, false);
-      y = jl_apply(-1.0 * phi, y, true);
-      const V3<double> v = (1.0 / k) * mul(qmat(Cs[k - 1]), y);
-      snap_scatter(snap_r + (size_t)kSnapStride * f[k - 1], 0, v, n, dim, gy, gr, status);
-      lam = lam - v;
-    }
-    snap_scatter(snap_r, 0, lam, n, dim, gy, gr, status);
-  }
-  if (nt > 0) {
-    const int fs = s->fstar[1];
-    const T* tf = t + 3 * (size_t)fs;
-    const V3<double> e{(double)tf[0] - result[4], (double)tf[1] - result[5], (double)tf[2] - result[6]};
-    const double dn = sqrt(dot(e, e));
-    V3<double> mu{g[4], g[5], g[6]};
-    if (dn > 0.0 && g[8] != 0.0) {
-      const V3<double> u = (g[8] / dn) * e;
-      snap_scatter(snap_t + (size_t)kSnapStride * fs, 1, u, n, dim, gy, gr, status);
-      mu = mu - u;
-    }
-    for (int k = K; k >= 1; --k) {
-      snap_scatter(snap_t + (size_t)kSnapStride * f[K + k - 1], 1, (1.0 / k) * mu, n, dim, gy, gr, status);
-      mu = (1.0 - 1.0 / k) * mu;
-    }
-    snap_scatter(snap_t, 1, mu, n, dim, gy, gr, status);
-  }
+  if (threadIdx.x == 0 && nq > 0)
+    adjoint_rotation(q, snap_r, K, f, fstar[0], g, Cs, n, dim, acc, acc + n * dim, status);
+  if (threadIdx.x == 32 && nt > 0)
+    adjoint_translation(t, snap_t, K, f + K, fstar[1], result + 4, g, n, dim, acc + m, acc + m + n * dim, status);
+  __syncthreads();
+  for (int i = threadIdx.x; i < n * dim; i += blockDim.x) gy[i] = acc[i] + acc[m + i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) gr[i] = acc[n * dim + i] + acc[m + n * dim + i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(64)
+    megb_adjoint_kernel(const T* q, const T* snap_r, int nq, const T* t, const T* snap_t, int nt, int K,
+                        const int32_t* f, const MegbState* s, const double* result, const double* g, Q4<double>* Cs,
+                        double* acc, int n, int dim, double* gy, double* gr, int* status) {
+  adjoint_both(q, snap_r, nq, t, snap_t, nt, K, f, s->fstar, result, g, Cs, n, dim, acc, gy, gr, status);
 }
 
 __global__ void megb_state_from_result(const double* result, MegbState* s) {
@@ -358,8 +381,9 @@ __global__ void megb_state_from_result(const double* result, MegbState* s) {
   s->fstar[0] = s->fstar[1] = 0;
 }
 
-size_t megb_backward_scratch_bytes(int n_iters, int sm_count) {
-  return megb_scratch_bytes(n_iters, sm_count) + 16 * sizeof(double) + ((size_t)n_iters + 1) * sizeof(Q4<double>);
+size_t megb_backward_scratch_bytes(int n_iters, int sm_count, int n) {
+  return megb_scratch_bytes(n_iters, sm_count) + 16 * sizeof(double) + ((size_t)n_iters + 1) * sizeof(Q4<double>) +
+         8 * (size_t)n * sizeof(double);
 }
 
 template <typename T>
@@ -373,6 +397,7 @@ static cudaError_t launch_megb_backward_t(purse_t h, int K, const T* q, const T*
   char* tail = reinterpret_cast<char*>(scratch) + megb_scratch_bytes(K, h->sm_count);
   double* dummy = reinterpret_cast<double*>(tail);
   Q4<double>* Cs = reinterpret_cast<Q4<double>*>(tail + 16 * sizeof(double));
+  double* acc = reinterpret_cast<double*>(Cs + K + 1);
   megb_state_from_result<<<1, 32, 0, st>>>(result, s);
   // farthest sample from the final centres, by the forward's own final pass
   if (nq > 0) {
@@ -386,8 +411,8 @@ static cudaError_t launch_megb_backward_t(purse_t h, int K, const T* q, const T*
     ggd_step<T, 1><<<gsz, kMegbThreads, 0, st>>>(t, nt, s, parts + cap, 0, f_int, nullptr, dummy);
   }
   const int dim = h->kind == PURSE_2D3D ? 2 : 3;
-  megb_adjoint_kernel<T><<<1, 256, 0, st>>>(q, snap_r, nq, t, snap_t, nt, K, f, s, result, g, Cs, h->n, dim, gy, gr,
-                                            h->d_status);
+  megb_adjoint_kernel<T><<<1, 64, 0, st>>>(q, snap_r, nq, t, snap_t, nt, K, f, s, result, g, Cs, acc, h->n, dim, gy,
+                                           gr, h->d_status);
   return cudaGetLastError();
 }
 
@@ -411,7 +436,7 @@ cudaError_t launch_megb_backward(purse_t h, int precision, int n_iters, const vo
 constexpr int kGgdBlockThreads = 512;
 
 template <typename T, int MODE>
-__device__ void ggd_block(const T* __restrict__ x, int n, int K, double* result, int32_t* f_out, T* xs) {
+__device__ void ggd_block(const T* __restrict__ x, int n, int K, double* result, int32_t* f_out, int32_t* fstar, T* xs) {
   constexpr int D = MODE == 0 ? 4 : 3;
   __shared__ double c[4];
   __shared__ double wkey[kGgdBlockThreads / 32];
@@ -476,6 +501,7 @@ __device__ void ggd_block(const T* __restrict__ x, int n, int K, double* result,
         }
       }
       if (k <= K && f_out) f_out[k - 1] = bi;
+      if (k > K && fstar) *fstar = bi;
     }
     __syncthreads();
   }
@@ -489,12 +515,13 @@ __global__ void __launch_bounds__(kGgdBlockThreads)
   const int p = blockIdx.x >> 1, ball = blockIdx.x & 1;
   const size_t off = (size_t)p * b.n_samples;
   int32_t* f = farthest ? farthest + (size_t)p * 2 * K + ball * K : nullptr;
+  int32_t* fs = b.fstar ? b.fstar + 2 * (size_t)p + ball : nullptr;
   if (ball == 0) {
-    ggd_block<float, 0>(b.q_rot + 4 * off, b.n_samples, K, results + 9 * (size_t)p, f,
+    ggd_block<float, 0>(b.q_rot + 4 * off, b.n_samples, K, results + 9 * (size_t)p, f, fs,
                         reinterpret_cast<float*>(ggd_smem));
   } else {
-    const float* t = (b.info[p].kind == 0 ? b.t_rot : b.t_tr) + 3 * off;
-    ggd_block<float, 1>(t, b.n_samples, K, results + 9 * (size_t)p, f, reinterpret_cast<float*>(ggd_smem));
+    const float* t = (b.info[p].kind == 0 && !b.tr3d ? b.t_rot : b.t_tr) + 3 * off;
+    ggd_block<float, 1>(t, b.n_samples, K, results + 9 * (size_t)p, f, fs, reinterpret_cast<float*>(ggd_smem));
   }
 }
 
@@ -504,6 +531,47 @@ cudaError_t launch_megb_batch(const BatchArgs& b, int n_iters, double* d_results
   cudaError_t e = cudaFuncSetAttribute(ggd_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   ggd_batch_kernel<<<2 * b.n_purses, kGgdBlockThreads, smem, st>>>(b, n_iters, d_results, d_farthest);
+  return cudaGetLastError();
+}
+
+// Batched adjoint: block p runs both sweeps of PURSE p (warp 0 rotation, warp 1 translation)
+// with the accumulators in shared memory, and writes its rows of the CSR gradients
+// (grad_obs rows x 3, the third column 0 for 2D-3D; grad_radii rows).
+__global__ void __launch_bounds__(64)
+    batch_adjoint_kernel(const __grid_constant__ BatchArgs b, int K, const int32_t* far, const double* results,
+                         const double* g, Q4<double>* cs, double* gy, double* gr) {
+  extern __shared__ __align__(16) unsigned char adj_smem[];
+  const int p = blockIdx.x;
+  const BatchPurseInfo in = b.info[p];
+  const int n = in.n, dim = in.kind == 1 ? 2 : 3;
+  const size_t off = (size_t)p * b.n_samples;
+  double* acc = reinterpret_cast<double*>(adj_smem);
+  double* ly = acc + 2 * n * (dim + 1);  // local gradient rows before the CSR write
+  double* lr = ly + n * dim;
+  const bool tr = in.kind == 1 || b.tr3d;
+  const float* t = (tr ? b.t_tr : b.t_rot) + 3 * off;
+  const float* snap_t = (tr ? b.snap_tr : b.snap_rot) + (size_t)kSnapStride * off;
+  adjoint_both<float>(b.q_rot + 4 * off, b.snap_rot + (size_t)kSnapStride * off, b.n_samples, t, snap_t, b.n_samples,
+                      K, far + (size_t)p * 2 * K, b.fstar + 2 * (size_t)p, results + 9 * (size_t)p,
+                      g + 9 * (size_t)p, cs + (size_t)p * (K + 1), n, dim, acc, ly, lr, b.status);
+  __syncthreads();
+  const int o = in.table_off / 2;  // first keypoint of PURSE p (tables hold 2 rows per keypoint)
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    gy[3 * (size_t)(o + i)] = ly[dim * i];
+    gy[3 * (size_t)(o + i) + 1] = ly[dim * i + 1];
+    gy[3 * (size_t)(o + i) + 2] = dim == 3 ? ly[dim * i + 2] : 0.0;
+    gr[o + i] = lr[i];
+  }
+}
+
+cudaError_t launch_batch_backward(const BatchArgs& b, int n_iters, const int32_t* d_far, const double* d_results,
+                                  const double* d_grad_results, void* d_cs, double* d_grad_obs, double* d_grad_radii,
+                                  cudaStream_t st) {
+  const size_t smem = (size_t)b.nmax * (2 * 4 + 4) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(batch_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  batch_adjoint_kernel<<<b.n_purses, 64, smem, st>>>(b, n_iters, d_far, d_results, d_grad_results,
+                                                       reinterpret_cast<Q4<double>*>(d_cs), d_grad_obs, d_grad_radii);
   return cudaGetLastError();
 }
 

@@ -755,6 +755,9 @@ size_t batch_walk_smem(int nmax, int n_perturb, int n_steps, int warps) {
   return (size_t)warps * batch_warp_bytes(nmax, n_perturb, n_steps);
 }
 
+// TR3D: the 3D-3D dS_t walks run too (b.tr3d); a separate instantiation so that batches without
+// them keep the smaller kernel.
+template <bool TR3D>
 __global__ void __launch_bounds__(kWalkThreads, 2)
     batch_walk_kernel(const __grid_constant__ BatchArgs b, const int chunk, const int np_max, const int nt_max) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -781,7 +784,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2)
       const int smp = (int)((item / S) & 1u);
       const int w = (int)(item % S);
       const BatchPurseInfo in = b.info[p];
-      if (in.kind == 0 && smp == 1) continue;
+      if (in.kind == 0 && smp == 1 && !TR3D) continue;
       if (p != cur) {
         __syncwarp();
         const T4<float>* src = reinterpret_cast<const T4<float>*>(b.table) + in.table_off;
@@ -798,7 +801,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2)
         c.omega0 = b.omega0[kd], c.v0 = b.v0[kd], c.gamma = b.gamma[kd];
         c.st = b.stats + p, c.seed_data = b.seed_data + (size_t)p * kSeedStride, c.s0 = 1;
         c.key0 = (uint32_t)key, c.key1 = (uint32_t)(key >> 32);
-        c.trace = nullptr, c.out_snap = nullptr, c.status = b.status;
+        c.trace = nullptr, c.status = b.status;
         sl = carve<float>(slab_base, c.N, c.NP, c.NT);
         cur = p;
         __syncwarp();
@@ -807,8 +810,13 @@ __global__ void __launch_bounds__(kWalkThreads, 2)
       const size_t off = (size_t)p * S;
       c.out_q = (smp == 0 ? b.q_rot : b.q_tr) + 4 * off;
       c.out_t = (smp == 0 ? b.t_rot : b.t_tr) + 3 * off;
-      if (in.kind == 0)
+      float* snap = smp == 0 ? b.snap_rot : b.snap_tr;
+      c.out_snap = snap ? snap + (size_t)kSnapStride * off : nullptr;
+      if (in.kind == 0 && smp == 0)
         walk_one<float, 0, 0>(c, rk, w, tab, sl, lane, evals);
+      else if (in.kind == 0) {
+        if constexpr (TR3D) walk_one<float, 0, 1>(c, rk, w, tab, sl, lane, evals);
+      }
       else if (smp == 0)
         walk_one<float, 1, 0>(c, rk, w, tab, sl, lane, evals);
       else
@@ -818,17 +826,24 @@ __global__ void __launch_bounds__(kWalkThreads, 2)
   if (lane == 0 && evals) atomicAdd(b.evals, evals);
 }
 
-cudaError_t launch_batch_walk(const BatchArgs& b, int chunk, int warps, int sm_count, cudaStream_t st) {
+template <bool TR3D>
+static cudaError_t launch_batch_walk_t(const BatchArgs& b, int chunk, int warps, int sm_count, cudaStream_t st) {
   const int np_max = max(b.n_perturb[0], b.n_perturb[1]), nt_max = max(b.n_steps[0], b.n_steps[1]);
   const size_t smem = batch_walk_smem(b.nmax, np_max, nt_max, warps);
-  cudaError_t e = cudaFuncSetAttribute(batch_walk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = batch_walk_kernel<TR3D>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_walk_kernel, 32 * warps, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  batch_walk_kernel<<<per_sm * sm_count, 32 * warps, smem, st>>>(b, chunk, np_max, nt_max);
+  kern<<<per_sm * sm_count, 32 * warps, smem, st>>>(b, chunk, np_max, nt_max);
   return cudaGetLastError();
+}
+
+cudaError_t launch_batch_walk(const BatchArgs& b, int chunk, int warps, int sm_count, cudaStream_t st) {
+  return b.tr3d ? launch_batch_walk_t<true>(b, chunk, warps, sm_count, st)
+                : launch_batch_walk_t<false>(b, chunk, warps, sm_count, st);
 }
 
 template <typename T, int KIND, int SAMPLER>

@@ -66,6 +66,9 @@ _SIGS = {
                          ctypes.POINTER(ctypes.c_float), _VP],
     "purse_batch_copy_farthest": [_VP, _VP, _VP],
     "purse_batch_copy_samples": [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP],
+    "purse_batch_set_grad": [_VP, ctypes.c_int],
+    "purse_batch_copy_snap": [_VP, ctypes.c_int, _VP, _VP, _VP],
+    "purse_batch_backward": [_VP, _VP, _VP, _VP, _VP, _VP],
     "purse_batch_sync": [_VP, ctypes.POINTER(ctypes.c_ulonglong), _VP],
     "purse_last_error": [],
     "purse_version": [],
@@ -228,6 +231,19 @@ def purse_batch_copy_farthest(b, out, stream=None):
 def purse_batch_copy_samples(b, p, q_rot=None, t_rot=None, q_tr=None, t_tr=None, stream=None):
     _check(lib().purse_batch_copy_samples(b, p, _ptr(q_rot), _ptr(t_rot), _ptr(q_tr), _ptr(t_tr), _stream(stream)),
            "purse_batch_copy_samples")
+
+
+def purse_batch_set_grad(b, enable):
+    _check(lib().purse_batch_set_grad(b, int(enable)), "purse_batch_set_grad")
+
+
+def purse_batch_copy_snap(b, p, snap_rot=None, snap_tr=None, stream=None):
+    _check(lib().purse_batch_copy_snap(b, p, _ptr(snap_rot), _ptr(snap_tr), _stream(stream)), "purse_batch_copy_snap")
+
+
+def purse_batch_backward(b, results, grad_results, grad_obs, grad_radii, stream=None):
+    _check(lib().purse_batch_backward(b, _ptr(results), _ptr(grad_results), _ptr(grad_obs), _ptr(grad_radii),
+                                      _stream(stream)), "purse_batch_backward")
 
 
 def purse_batch_sync(b, stream=None) -> int:
