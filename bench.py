@@ -314,6 +314,78 @@ def run_gpu(args, rank, world):
         print(json.dumps(out))
 
 
+def run_sweep(args):
+    """Precision / scale sweep of the single-PURSE path (2D-3D, presets of Section V with N_I = 5, ground-truth
+    seeds, both balls with 200 GGD iterations): FP32 against FP64 walks and balls for N in {8, 32, 128, 256}
+    and 2^16..2^20 samples per sampler, then FP32 alone up to 2^26 samples at N = 16, where the ball kernels
+    stream the samples from HBM.  One JSON line per point."""
+    import torch
+    import paper_2403_09990_gb300.purse as P
+    from paper_2403_09990_gb300 import synthetic as syn
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    K = K_MEGB
+
+    def solve(p, S, precision, reps):
+        dt = torch.float32 if precision == 0 else torch.float64
+        h = P.Purse(p)
+        sd = torch.as_tensor(p.seed_pose()[None], dtype=torch.float64, device=dev)
+        qR = torch.empty((S, 4), dtype=dt, device=dev)
+        tR = torch.empty((S, 3), dtype=dt, device=dev)
+        qT = torch.empty((S, 4), dtype=dt, device=dev)
+        tT = torch.empty((S, 3), dtype=dt, device=dev)
+        res = torch.empty(9, dtype=torch.float64, device=dev)
+        pr = P.make_params(n_iter=5, precision=precision, sampler=0)
+        pt = P.make_params(n_iter=5, precision=precision, sampler=1)
+        times = []
+        evals = 0
+        for r in range(reps + 1):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            P.purse_sample(h.h, pr, 9, sd, 1, S, qR, tR, None, stream)
+            P.purse_sample(h.h, pt, 9, sd, 1, S, qT, tT, None, stream)
+            e[1].record(stream)
+            P.megb_solve(h.h, precision, K, qR, S, tT, S, res, None, stream)
+            e[2].record(stream)
+            P.purse_sync(h.h, stream)
+            if r > 0:  # the first pass warms up
+                times.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])))
+        h.close()
+        walk_ms = statistics.median(t[0] for t in times)
+        megb_ms = statistics.median(t[1] for t in times)
+        return res.cpu().numpy(), walk_ms, megb_ms
+
+    def angle(a, b):
+        d = abs(float(np.dot(a, b)))
+        return 2.0 * float(np.arccos(min(1.0, d)))
+
+    for n in ((8, 32, 128, 256) if "precision" in args.sweep_parts else ()):
+        p = syn.purse_2d3d(n, 0)
+        for lg in (16, 18, 20):
+            S = 1 << lg
+            r32, w32, m32 = solve(p, S, 0, 2)
+            r64, w64, m64 = solve(p, S, 1, 1)
+            alg = 2 * S * 5 * (N_PERTURB + N_KEEP * N_STEPS) * n
+            print(json.dumps({"sweep": "precision", "n_keypoints": n, "samples_per_sampler": S,
+                              "fp32": {"walk_ms": w32, "megb_ms": m32, "evals_per_s": alg / (w32 / 1e3)},
+                              "fp64": {"walk_ms": w64, "megb_ms": m64},
+                              "err_vs_fp64": {"D_rel": abs(r32[7] - r64[7]) / r64[7],
+                                              "d_rel": abs(r32[8] - r64[8]) / r64[8],
+                                              "C_rad": angle(r32[:4], r64[:4]),
+                                              "c_m": float(np.linalg.norm(r32[4:7] - r64[4:7]))}}), flush=True)
+    p = syn.purse_2d3d(N_KEYPOINTS, 0)
+    for lg in ((22, 24, 26) if "scale" in args.sweep_parts else ()):
+        S = 1 << lg
+        r32, w32, m32 = solve(p, S, 0, 1)
+        ball_bytes = (16 + 12) * S * (K + 1)
+        print(json.dumps({"sweep": "scale", "n_keypoints": N_KEYPOINTS, "samples_per_sampler": S,
+                          "walk_ms": w32, "megb_ms": m32, "samples_per_s": 2 * S / ((w32 + m32) / 1e3),
+                          "megb_gbs": ball_bytes / (m32 / 1e3) / 1e9,
+                          "megb_bytes_note": "16 B per rotation sample + 12 B per translation sample, per GGD "
+                                             "iteration and the final pass", "D": r32[7], "d": r32[8]}), flush=True)
+
+
 def run_batch(args, dev):
     """Batched workload: 4096 PURSEs (fair-coin kind, N ~ U{4..64}), 4096 samples each, FP32, both balls
     with 200 GGD iterations; one CUDA graph (statistics, persistent walk launch, one block per ball)
@@ -545,6 +617,8 @@ def main():
     ap.add_argument("--batch-warmup", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad", action="store_true", help="skip the batched differentiation measurement")
+    ap.add_argument("--sweep", action="store_true", help="precision / scale sweep instead of the bench step")
+    ap.add_argument("--sweep-parts", default="precision,scale", help="which parts of the sweep to run")
     ap.add_argument("--grad-purses", type=int, default=1024)
     ap.add_argument("--per-instance-purses", type=int, default=256,
                     help="PURSEs of the batch solved one by one for the per-instance comparison")
@@ -554,6 +628,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", args.gpus))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_gpu(args, rank, world)
 

@@ -31,7 +31,7 @@ struct Part {
   int pad;
 };
 
-__host__ __device__ inline size_t megb_blocks_cap(int sm_count) { return 2 * (size_t)sm_count; }
+__host__ __device__ inline size_t megb_blocks_cap(int sm_count) { return 4 * (size_t)sm_count; }
 
 size_t megb_scratch_bytes(int n_iters, int sm_count) {
   return sizeof(MegbState) + 2 * megb_blocks_cap(sm_count) * sizeof(Part) + 2 * (size_t)n_iters * sizeof(int32_t) + 256;
@@ -91,6 +91,29 @@ __device__ __forceinline__ Q4<double> slerp_step(const Q4<double>& c, const RelR
   return qnormalize(qmul(c, step));
 }
 
+// Key of sample i: squared sine of half the angle to the centre (rotation) or squared distance.
+template <typename T, int MODE>
+__device__ __forceinline__ T sample_key(const T* __restrict__ x, int i, bool vec, T c0, T c1, T c2, T c3) {
+  if (MODE == 0) {
+    if (vec) {
+      T qv[4];
+      if constexpr (sizeof(T) == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(x) + i);
+        qv[0] = v.x, qv[1] = v.y, qv[2] = v.z, qv[3] = v.w;
+      } else {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(x) + 2 * (size_t)i);
+        const double2 b = __ldg(reinterpret_cast<const double2*>(x) + 2 * (size_t)i + 1);
+        qv[0] = a.x, qv[1] = a.y, qv[2] = b.x, qv[3] = b.y;
+      }
+      return rot_key(c0, c1, c2, c3, qv);
+    }
+    return rot_key(c0, c1, c2, c3, x + 4 * (size_t)i);
+  }
+  const T* p = x + 3 * (size_t)i;
+  const T dx = __ldg(p) - c0, dy = __ldg(p + 1) - c1, dz = __ldg(p + 2) - c2;
+  return dx * dx + dy * dy + dz * dz;
+}
+
 // MODE 0: rotation ball, MODE 1: translation ball.  k >= 1: GGD step k; k == 0: final radius.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kMegbThreads)
@@ -106,20 +129,66 @@ __global__ void __launch_bounds__(kMegbThreads)
   } else {
     c0 = T(s->c[0]), c1 = T(s->c[1]), c2 = T(s->c[2]), c3 = T(0);
   }
-  double bk = -1.0;
+  // per-thread maximum in the key precision (the conversion to FP64 is exact and keeps the order)
+  T bkt = T(-1);
   int bi = INT_MAX;
   const int stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + tid; i < n; i += stride) {
-    T key;
-    if (MODE == 0) {
-      key = rot_key(c0, c1, c2, c3, x + 4 * (size_t)i);
-    } else {
-      const T* p = x + 3 * (size_t)i;
-      const T dx = p[0] - c0, dy = p[1] - c1, dz = p[2] - c2;
-      key = dx * dx + dy * dy + dz * dz;
+  // Four samples in flight per thread (indices ascending, so the strict > keeps the lowest index
+  // among equal keys); quaternions are read as 16-byte vectors when the array allows it.
+  const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+  int i = blockIdx.x * blockDim.x + tid;
+  const bool grouped = MODE == 1 && sizeof(T) == 4 && vec;
+  if (grouped) {
+    // FP32 translations: groups of four samples = three 16-byte vectors per thread, two groups in
+    // flight; the n mod 4 tail is read by the first threads after all groups (indices stay ascending).
+    const int ng = n >> 2;
+    int gi = i;
+    for (; (long)gi + stride < (long)ng; gi += 2 * stride) {
+      float4 v[6];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) v[3 * u + r] = __ldg(reinterpret_cast<const float4*>(x) + 3 * (size_t)(gi + u * stride) + r);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const float f[12] = {v[3 * u].x, v[3 * u].y, v[3 * u].z, v[3 * u].w, v[3 * u + 1].x, v[3 * u + 1].y,
+                             v[3 * u + 1].z, v[3 * u + 1].w, v[3 * u + 2].x, v[3 * u + 2].y, v[3 * u + 2].z,
+                             v[3 * u + 2].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const T dx = f[3 * e] - c0, dy = f[3 * e + 1] - c1, dz = f[3 * e + 2] - c2;
+          const T key = dx * dx + dy * dy + dz * dz;
+          if (key > bkt) bkt = key, bi = 4 * (gi + u * stride) + e;
+        }
+      }
     }
-    if ((double)key > bk) bk = (double)key, bi = i;
+    for (; gi < ng; gi += stride) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(x) + 3 * (size_t)gi);
+      const float4 b = __ldg(reinterpret_cast<const float4*>(x) + 3 * (size_t)gi + 1);
+      const float4 c = __ldg(reinterpret_cast<const float4*>(x) + 3 * (size_t)gi + 2);
+      const float f[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const T dx = f[3 * e] - c0, dy = f[3 * e + 1] - c1, dz = f[3 * e + 2] - c2;
+        const T key = dx * dx + dy * dy + dz * dz;
+        if (key > bkt) bkt = key, bi = 4 * gi + e;
+      }
+    }
+    i = 4 * ng + i;  // tail
   }
+  for (; !grouped && (long)i + 3L * stride < (long)n; i += 4 * stride) {
+    T key[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) key[u] = sample_key<T, MODE>(x, i + u * stride, vec, c0, c1, c2, c3);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (key[u] > bkt) bkt = key[u], bi = i + u * stride;
+  }
+  for (; i < n; i += stride) {
+    const T key = sample_key<T, MODE>(x, i, vec, c0, c1, c2, c3);
+    if (key > bkt) bkt = key, bi = i;
+  }
+  double bk = (double)bkt;
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     const double ok = __shfl_xor_sync(kFullMask, bk, o);
@@ -454,7 +523,7 @@ __device__ void ggd_block(const T* __restrict__ x, int n, int K, double* result,
   __syncthreads();
   for (int k = 1; k <= K + 1; ++k) {  // k = K + 1: final pass for the radius
     const T c0 = T(c[0]), c1 = T(c[1]), c2 = T(c[2]), c3 = T(c[3]);
-    double bk = -1.0;
+    T bkt = T(-1);
     int bi = INT_MAX;
     for (int i = tid; i < n; i += blockDim.x) {
       T key;
@@ -465,8 +534,9 @@ __device__ void ggd_block(const T* __restrict__ x, int n, int K, double* result,
         const T dx = pp[0] - c0, dy = pp[1] - c1, dz = pp[2] - c2;
         key = dx * dx + dy * dy + dz * dz;
       }
-      if ((double)key > bk) bk = (double)key, bi = i;
+      if (key > bkt) bkt = key, bi = i;
     }
+    double bk = (double)bkt;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       const double ok = __shfl_xor_sync(kFullMask, bk, o);

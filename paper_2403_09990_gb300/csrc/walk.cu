@@ -36,6 +36,7 @@ namespace purse {
 
 constexpr int kWalkWarps = 8;
 constexpr int kWalkThreads = kWalkWarps * 32;
+constexpr size_t kMaxSmemPerBlock = 227 * 1024;
 
 template <typename T>
 struct alignas(sizeof(T) * 4) T4 {
@@ -736,7 +737,8 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
   c.out_snap = reinterpret_cast<T*>(a.out_snap);
   const RkParam rk{a};
   unsigned long long evals = 0;
-  for (int w = blockIdx.x * kWalkWarps + warp; w < a.n_samples; w += gridDim.x * kWalkWarps)
+  const int nw = blockDim.x >> 5;  // warps per block (fewer than kWalkWarps for large tables)
+  for (int w = blockIdx.x * nw + warp; w < a.n_samples; w += gridDim.x * nw)
     walk_one<T, KIND, SAMPLER>(c, rk, w, tab, sl, lane, evals);
   if (lane == 0 && evals) atomicAdd(a.evals, evals);
 }
@@ -850,18 +852,22 @@ template <typename T, int KIND, int SAMPLER>
 static cudaError_t launch_walk_t(purse_t h, const purse_params* p, const WalkArgs& a, cudaStream_t st) {
   const int mc = p->n_keep >= 32 ? 1 : 32 / p->n_keep;
   const size_t slab = walk_slab_bytes2<T>(a.n, p->n_perturb, p->n_steps);
-  const size_t smem = 128 + walk_table_bytes<T>(a.n) + kWalkWarps * slab;
+  // as many warps per block (up to kWalkWarps) as the shared memory holds slabs for
+  int warps = kWalkWarps;
+  while (warps > 1 && 128 + walk_table_bytes<T>(a.n) + warps * slab > kMaxSmemPerBlock) --warps;
+  const size_t smem = 128 + walk_table_bytes<T>(a.n) + warps * slab;
+  if (smem > kMaxSmemPerBlock) return cudaErrorInvalidConfiguration;
   auto kern = walk_kernel<T, KIND, SAMPLER>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const long need = (a.n_samples + kWalkWarps - 1) / kWalkWarps;
+  const long need = (a.n_samples + warps - 1) / warps;
   const long cap = (long)per_sm * h->sm_count;
   const int grid = (int)(need < cap ? need : cap);
-  kern<<<grid, kWalkThreads, smem, st>>>(a, mc, (int)slab);
+  kern<<<grid, 32 * warps, smem, st>>>(a, mc, (int)slab);
   return cudaGetLastError();
 }
 

@@ -103,3 +103,22 @@ def test_megb_closed_form_geodesic():
         res, _ = megb(h.h, 1, K, q, None)
     half = 0.5 * (ang.max() - ang.min())
     assert half * (1 - 1e-12) <= res[7] <= half * (1 + 1 / np.sqrt(K))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rotation_ball_with_radius_near_pi(precision):
+    """Samples up to 3.1 rad from a centre in every direction: the keys sin^2(theta/2) flatten near pi
+    (FP32 resolves about 3e-6 rad there) and the final angle comes from the FP64 log map."""
+    rng = np.random.default_rng(11)
+    n, K = 20000, 100
+    C0 = so3.quat_from_R(so3.exp_so3(rng.normal(size=3)))
+    u = rng.normal(size=(n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    th = 3.1 * rng.random(n) ** (1 / 3)
+    q = so3.quat_mul(so3.quat_exp(u * th[:, None]), C0[None])
+    if precision == 0:
+        q = q.astype(np.float32).astype(np.float64)  # the samples the FP32 kernels see
+    with P.Purse(syn.purse_3d3d(8, 0)) as h:
+        res, f = megb(h.h, precision, K, q, None)
+    _, D = check_rotation(q, res, f[:K], precision)
+    assert D > 3.0

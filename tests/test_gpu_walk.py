@@ -46,16 +46,20 @@ CASES = {
     "3d3d-R-fp32-keep32-np256-nt32-raw": dict(kind=0, sampler=0, precision=0,
                                               prm=dict(n_keep=32, n_perturb=256, n_steps=32, perturb_units=1,
                                                        trans_perturb=0.002), seeds="ransag"),
+    # large constraint tables: fewer warps per block fit the shared memory (N > 32 keeps table order)
+    "2d3d-R-fp64-n256": dict(kind=1, sampler=0, precision=1, prm=dict(n_iter=3), seeds="gt", n=256),
+    "2d3d-t-fp32-n128": dict(kind=1, sampler=1, precision=0, prm=dict(n_iter=3), seeds="gt", n=128),
+    "3d3d-R-fp32-n64": dict(kind=0, sampler=0, precision=0, prm=dict(n_iter=3), seeds="gt", n=64),
 }
 
 
 def make_case(c):
     if c["kind"] == 0:
-        p = syn.purse_3d3d(8, 0)
+        p = syn.purse_3d3d(c.get("n", 8), 0)
         prm = closure.preset_3d3d(**c["prm"])
-        seeds = seeds_3d3d(p, 32)
+        seeds = p.seed_pose()[None] if c["seeds"] == "gt" else seeds_3d3d(p, 32)
     else:
-        p = syn.purse_2d3d(16, 0)
+        p = syn.purse_2d3d(c.get("n", 16), 0)
         prm = closure.preset_2d3d(**c["prm"])
         seeds = p.seed_pose()[None] if c["seeds"] == "gt" else seeds_2d3d_multi(p, 8)
     return p, prm, seeds
