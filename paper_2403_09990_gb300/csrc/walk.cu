@@ -147,12 +147,17 @@ __device__ __forceinline__ Slab<T> carve(unsigned char* base, int N, int NP, int
 }
 
 // Perturbation phase over NPAIR pairs per lane, starting at pair pb: pair P of this lane holds
-// perturbations j = 2 b, 2 b + 1 with b = 32 P + lane, the two points of block 0 of stream
-// (phase, b, it, w).  Writes the keys of every valid j.
+// perturbations j = 2 b, 2 b + 1 with b = 32 (pb + P) + (lane >> sh), the two points of block 0 of
+// stream (phase, b, it, w).  sh > 0 (the ragged last pass, NPAIR = 1): the 2^sh lanes of a pair
+// split its constraints (i = sub, sub + 2^sh, ...) and combine their minima by shuffles -- the
+// minimum is exact, so the keys are those of one lane taking every constraint.  Writes the keys of
+// every valid j.
 template <typename T, int KIND, int SAMPLER, int NPAIR, class RK>
 __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Slab<T>& sl, int N, int NP, int lane,
-                                          int pb, T r_pert, const V3<T>& t, T fx, T fy, T cx, T cy, T qzmin) {
+                                          int pb, T r_pert, const V3<T>& t, T fx, T fy, T cx, T cy, T qzmin,
+                                          int sh = 0) {
   using T2 = P2<T>;
+  const int pl = lane >> sh, sub = lane & ((1 << sh) - 1), S = 1 << sh;
   T2 dmin[NPAIR], zmin[NPAIR];
   T2 Dx[NPAIR], Dy[NPAIR], Dz[NPAIR];             // dS_R: translation offsets in P units
   T2 A[SAMPLER == 1 ? NPAIR : 1][9];              // dS_t: (K) R_p per slot
@@ -160,7 +165,7 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
   for (int p = 0; p < NPAIR; ++p) {
     T dx[2], dy[2], dz[2];
     M3<T> Ah[2];
-    const int b = 32 * (pb + p) + lane;
+    const int b = 32 * (pb + p) + pl;
     uint4 wd = make_uint4(0u, 0u, 0u, 0u);
     if (2 * b < NP)
       wd = philox4x32_10_rk(make_uint4(0u, ((SAMPLER == 0 ? kPhaseRPerturb : kPhaseTPerturb) << 24) | (uint32_t)b,
@@ -209,7 +214,7 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
   T2 c0x = dup(T(0)), c0y = c0x, c0z = c0x;
   if (SAMPLER == 1 && KIND == 1) c0x = dup(fx * t.x + cx * t.z), c0y = dup(fy * t.y + cy * t.z), c0z = dup(t.z);
 #pragma unroll 2
-  for (int i = 0; i < N; ++i) {
+  for (int i = sub; i < N; i += S) {
     const T2* Di = sl.D + 8 * i;
     const T2 d0 = Di[0], d1 = Di[1], d2 = Di[2], rr = Di[3];
     T2 d4, d5, d6;
@@ -240,12 +245,20 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
       dmin[p] = min2(dmin[p], m);
     }
   }
+  for (int o = 1; o < S; o <<= 1) {
+#pragma unroll
+    for (int p = 0; p < NPAIR; ++p) {
+      dmin[p] = min2(dmin[p], pr(__shfl_xor_sync(kFullMask, dmin[p].x, o), __shfl_xor_sync(kFullMask, dmin[p].y, o)));
+      if (SAMPLER == 1 && KIND == 1)
+        zmin[p] = min2(zmin[p], pr(__shfl_xor_sync(kFullMask, zmin[p].x, o), __shfl_xor_sync(kFullMask, zmin[p].y, o)));
+    }
+  }
 #pragma unroll
   for (int p = 0; p < NPAIR; ++p) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int j = 2 * (32 * (pb + p) + lane) + h;
-      if (j < NP) {
+      const int j = 2 * (32 * (pb + p) + pl) + h;
+      if (j < NP && sub == 0) {
         T d = h ? dmin[p].y : dmin[p].x;
         if (KIND == 1) {
           // dS_R: P_z = Q_z,i + D_z,j and rounding is monotone, so min_i P_z = min_i Q_z,i + D_z,j
@@ -422,7 +435,9 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
   const WalkStats* st = c.st;
   const int ncand = mc * K;
   const int cm = lane / K, ck = lane - (lane / K) * K;
-  const int npair = (NP + 63) / 64;
+  // perturbation pairs: nfull passes of 32, then qtail pairs with 2^tsh lanes each
+  const int npairs = (NP + 1) / 2, nfull = npairs / 32, qtail = npairs % 32;
+  const int tsh = qtail == 0 ? 0 : qtail <= 1 ? 5 : qtail <= 2 ? 4 : qtail <= 4 ? 3 : qtail <= 8 ? 2 : qtail <= 16 ? 1 : 0;
   // ---- a3: start pose and velocity, ladder table of this walk.
   const double* sd = c.seed_data + (size_t)(w % c.s0) * kSeedStride;
   Q4<T> q{T(sd[0]), T(sd[1]), T(sd[2]), T(sd[3])};
@@ -542,25 +557,27 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
     }
     __syncwarp();
 
-    // ---- a4: perturbations and their distance to the boundary (eq. 11)
+    // ---- a4: perturbations and their distance to the boundary (eq. 11): full passes of 32 pairs
+    //      (dS_R: all at once; dS_t keeps one rotation per perturbation in registers: two pairs at
+    //      a time), then the ragged remainder of q pairs with 32 / q lanes (a power of two) per pair
     if constexpr (SAMPLER == 0) {
-      if (npair == 4)
+      if (nfull == 4)
         dist_pass<T, KIND, SAMPLER, 4>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
-      else if (npair == 3)
+      else if (nfull == 3)
         dist_pass<T, KIND, SAMPLER, 3>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
-      else if (npair == 2)
+      else if (nfull == 2)
         dist_pass<T, KIND, SAMPLER, 2>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
-      else
+      else if (nfull == 1)
         dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
     } else {
-      // dS_t keeps one rotation per perturbation in registers: two pairs at a time
-      for (int pb = 0; pb < npair; pb += 2) {
-        if (npair - pb >= 2)
+      for (int pb = 0; pb < nfull; pb += 2) {
+        if (nfull - pb >= 2)
           dist_pass<T, KIND, SAMPLER, 2>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
         else
           dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
       }
     }
+    if (qtail) dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, nfull, r_pert, t, fx, fy, cx, cy, qzmin, tsh);
     evals += (unsigned long long)NP * N;
     __syncwarp();
 
