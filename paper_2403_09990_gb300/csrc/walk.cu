@@ -241,7 +241,11 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
         s2 = fma2(Pz, Pz, fma2(Py, Py, mul2(Px, Px)));
         qq = add2(s2, tiny2);
       }
-      const T2 m = fma2(mul2(s2, rsq2(qq)), neg1, rr);  // r - |e| (2D-3D: |e| / P_z)
+      T2 m;  // r - |e| (2D-3D: |e| / P_z)
+      if constexpr (SAMPLER == 0)
+        m = fma2(pr(-s2.x, -s2.y), rsq2(qq), rr);
+      else
+        m = fma2(mul2(s2, rsq2(qq)), neg1, rr);
       dmin[p] = min2(dmin[p], m);
     }
   }
@@ -268,6 +272,41 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
         sl.key[j] = orderable(d);
       }
     }
+  }
+}
+
+// in_purse of one ladder chunk (one candidate per lane): constraint pairs in groups of two, a warp
+// vote after each group leaves the chunk once every candidate has violated a constraint.  Z: track
+// the cheirality minimum (2D-3D; off when the caller has bounded P_z away from 0).
+template <typename T, int KIND, bool Z>
+__device__ __forceinline__ void ladder_scan(const P2<T>* L, int NQ, int N, const P2<T> (&M2)[9], P2<T> bx, P2<T> by,
+                                            P2<T> bz, P2<T>& cmax, P2<T>& zmin, bool& alive, int& done) {
+  using T2 = P2<T>;
+  for (int g0 = 0; g0 < NQ; g0 += 2) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int qi = g0 + u;
+      if (qi < NQ) {
+        const T2* Lq = L + 8 * qi;
+        const T2 yx = Lq[0], yy = Lq[1], yz = Lq[2], o3 = Lq[3], o4 = Lq[4], o5 = Lq[5];
+        const T2 Px = fma2(M2[0], yx, fma2(M2[1], yy, fma2(M2[2], yz, bx)));
+        const T2 Py = fma2(M2[3], yx, fma2(M2[4], yy, fma2(M2[5], yz, by)));
+        const T2 Pz = fma2(M2[6], yx, fma2(M2[7], yy, fma2(M2[8], yz, bz)));
+        T2 c;
+        if (KIND == 1) {
+          const T2 ex = fma2(o3, Pz, Px), ey = fma2(o4, Pz, Py);
+          c = fma2(o5, mul2(Pz, Pz), fma2(ey, ey, mul2(ex, ex)));
+          if (Z) zmin = min2(zmin, Pz);
+        } else {
+          const T2 ex = add2(Px, o3), ey = add2(Py, o4), ez = add2(Pz, o5);
+          c = add2(fma2(ez, ez, fma2(ey, ey, mul2(ex, ex))), Lq[6]);
+        }
+        cmax = max2(cmax, c);
+      }
+    }
+    done = min(N, 2 * (g0 + 2));
+    alive = alive && fmax(cmax.x, cmax.y) <= T(0) && (KIND == 0 || !Z || fmin(zmin.x, zmin.y) > T(0));
+    if (!__any_sync(kFullMask, alive)) break;
   }
 }
 
@@ -458,6 +497,15 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
                   T(c.v0 * (st->S[6] * d0 + st->S[7] * d1 + st->S[8] * d2))};
     }
   }
+  T rho_max = T(0);  // largest keypoint radius |Z_i| (cheirality bound of the dS_R ladder)
+  if constexpr (SAMPLER == 0 && KIND == 1) {
+    for (int i = lane; i < N; i += 32) {
+      const T4<T> mz = tab[i];
+      rho_max = fmax(rho_max, sqrt(mz.x * mz.x + mz.y * mz.y + mz.z * mz.z));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) rho_max = fmax(rho_max, __shfl_xor_sync(kFullMask, rho_max, o));
+  }
   for (int m = lane; m < NT; m += 32) {
     T sm = T(1);
     for (int k = 0; k < m; ++k) sm *= T(c.gamma);
@@ -478,7 +526,12 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
   }
   __syncwarp();
 
+  // The order and the tables depend on (R*, t*) only: an iteration after one that kept the pose
+  // reuses them (and qzmin).
+  bool moved = true;
+  T qzmin = inf<T>();
   for (int it = 0; it < c.n_iter; ++it) {
+   if (moved) {
     const M3<T> R = qmat(q);
     // ---- constraint order: ascending margin of the current pose (N <= 32; the order only decides how
     //      soon the ladder's early exit triggers), then the tables
@@ -511,7 +564,7 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
       }
       perm = (int)(kk & 31u);
     }
-    T qzmin = inf<T>();
+    qzmin = inf<T>();
     for (int r = lane; r < N; r += 32) {
       const int i = N <= 32 ? perm : r;
       const T4<T> mz = tab[i], ob = tab[N + i];
@@ -556,6 +609,7 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
       for (int o = 16; o; o >>= 1) qzmin = fmin(qzmin, __shfl_xor_sync(kFullMask, qzmin, o));
     }
     __syncwarp();
+   }
 
     // ---- a4: perturbations and their distance to the boundary (eq. 11): full passes of 32 pairs
     //      (dS_R: all at once; dS_t keeps one rotation per perturbation in registers: two pairs at
@@ -569,6 +623,7 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
         dist_pass<T, KIND, SAMPLER, 2>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
       else if (nfull == 1)
         dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
+      if (qtail) dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, nfull, r_pert, t, fx, fy, cx, cy, qzmin, tsh);
     } else {
       for (int pb = 0; pb < nfull; pb += 2) {
         if (nfull - pb >= 2)
@@ -576,8 +631,8 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
         else
           dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
       }
+      if (qtail) dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, nfull, r_pert, t, fx, fy, cx, cy, qzmin, tsh);
     }
-    if (qtail) dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, nfull, r_pert, t, fx, fy, cx, cy, qzmin, tsh);
     evals += (unsigned long long)NP * N;
     __syncwarp();
 
@@ -647,32 +702,14 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
       bool alive = active;
       const int nact = K * min(mc, NT - mb);
       int done = 0;
-      for (int g0 = 0; g0 < NQ; g0 += 2) {
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int qi = g0 + u;
-          if (qi < NQ) {
-            const T2* Lq = sl.L + 8 * qi;
-            const T2 yx = Lq[0], yy = Lq[1], yz = Lq[2], o3 = Lq[3], o4 = Lq[4], o5 = Lq[5];
-            const T2 Px = fma2(M2[0], yx, fma2(M2[1], yy, fma2(M2[2], yz, bx)));
-            const T2 Py = fma2(M2[3], yx, fma2(M2[4], yy, fma2(M2[5], yz, by)));
-            const T2 Pz = fma2(M2[6], yx, fma2(M2[7], yy, fma2(M2[8], yz, bz)));
-            T2 c;
-            if (KIND == 1) {
-              const T2 ex = fma2(o3, Pz, Px), ey = fma2(o4, Pz, Py);
-              c = fma2(o5, mul2(Pz, Pz), fma2(ey, ey, mul2(ex, ex)));
-              zmin = min2(zmin, Pz);
-            } else {
-              const T2 ex = add2(Px, o3), ey = add2(Py, o4), ez = add2(Pz, o5);
-              c = add2(fma2(ez, ez, fma2(ey, ey, mul2(ex, ex))), Lq[6]);
-            }
-            cmax = max2(cmax, c);
-          }
-        }
-        done = min(N, 2 * (g0 + 2));
-        alive = alive && fmax(cmax.x, cmax.y) <= T(0) && (KIND == 0 || fmin(zmin.x, zmin.y) > T(0));
-        if (!__any_sync(kFullMask, alive)) break;
-      }
+      // 2D-3D: P_z >= (candidate translation)_z - max |Z_i| (the rotation rows are unit vectors);
+      // when that bound is positive for every candidate of the chunk, cheirality is not tracked
+      const bool zsafe = KIND == 1 && SAMPLER == 0 &&
+                         __all_sync(kFullMask, !active || bm.z - rho_max > T(1e-3) * (fabs(bm.z) + rho_max));
+      if (zsafe)
+        ladder_scan<T, KIND, false>(sl.L, NQ, N, M2, bx, by, bz, cmax, zmin, alive, done);
+      else
+        ladder_scan<T, KIND, true>(sl.L, NQ, N, M2, bx, by, bz, cmax, zmin, alive, done);
       evals += (unsigned long long)nact * done;
       const unsigned bal = __ballot_sync(kFullMask, alive);
       if (bal) {
@@ -684,6 +721,7 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
     }
 
     // ---- update (R*, t*)
+    moved = m0 >= 0;
     if (m0 >= 0) {
       const T4<T> pj = sl.P[sl.J[k0]];
       if (SAMPLER == 0) {
