@@ -213,7 +213,8 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
   const T2 neg1 = dup(T(-1)), tiny2 = dup(tiny<T>());
   T2 c0x = dup(T(0)), c0y = c0x, c0z = c0x;
   if (SAMPLER == 1 && KIND == 1) c0x = dup(fx * t.x + cx * t.z), c0y = dup(fy * t.y + cy * t.z), c0z = dup(t.z);
-#pragma unroll 2
+  constexpr int kUnroll = SAMPLER == 0 ? 2 : 1;  // measured: dS_t runs faster with the smaller loop
+#pragma unroll kUnroll
   for (int i = sub; i < N; i += S) {
     const T2* Di = sl.D + 8 * i;
     const T2 d0 = Di[0], d1 = Di[1], d2 = Di[2], rr = Di[3];
@@ -272,6 +273,38 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
         sl.key[j] = orderable(d);
       }
     }
+  }
+}
+
+// top_k_indices of Alg. 3/5 (ties to the lower j): lane l holds keys j = l + 32 s, s < NS (the low
+// three bits of a key encode 7 - s), sorts them, and K rounds of a warp maximum pop the best head;
+// the winners' indices go to sl.J in rank order.
+template <typename Key, int NS, typename T>
+__device__ __forceinline__ void top_k(const Slab<T>& sl, int NP, int K, int lane) {
+  Key kk[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int j = lane + 32 * s;
+    kk[s] = j < NP ? ((sl.key[j] & ~Key(7)) | Key(7 - s)) : Key(0);
+  }
+  if constexpr (NS == 8) {
+    sort8_desc(kk);
+  } else {
+#pragma unroll
+    for (int a = 0; a < NS - 1; ++a)
+#pragma unroll
+      for (int b = 0; b < NS - 1 - a; ++b) cas_desc(kk[b], kk[b + 1]);
+  }
+  for (int r = 0; r < K; ++r) {
+    const Key mx = warp_max_key(kk[0]);
+    const unsigned bal = __ballot_sync(kFullMask, kk[0] == mx);
+    const int wl = __ffs(bal) - 1;
+    if (lane == wl) {
+#pragma unroll
+      for (int s = 0; s < NS - 1; ++s) kk[s] = kk[s + 1];
+      kk[NS - 1] = Key(0);
+    }
+    if (lane == 0) sl.J[r] = wl + 32 * (7 - (int)(mx & Key(7)));
   }
 }
 
@@ -637,26 +670,10 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
     __syncwarp();
 
     // ---- a5: top_k_indices (ties to the lower j): per-lane sorted keys, warp max rounds
-    {
-      Key kk[8];
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const int j = lane + 32 * s;
-        kk[s] = j < NP ? ((sl.key[j] & ~Key(7)) | Key(7 - s)) : Key(0);
-      }
-      sort8_desc(kk);
-      for (int r = 0; r < K; ++r) {
-        const Key mx = warp_max_key(kk[0]);
-        const unsigned bal = __ballot_sync(kFullMask, kk[0] == mx);
-        const int wl = __ffs(bal) - 1;
-        if (lane == wl) {
-#pragma unroll
-          for (int s = 0; s < 7; ++s) kk[s] = kk[s + 1];
-          kk[7] = Key(0);
-        }
-        if (lane == 0) sl.J[r] = wl + 32 * (7 - (int)(mx & Key(7)));
-      }
-    }
+    if (NP <= 160)
+      top_k<Key, 5>(sl, NP, K, lane);
+    else
+      top_k<Key, 8>(sl, NP, K, lane);
     __syncwarp();
 
     // ---- a6/a7: step ladder + in_purse with early exit, find_farthest
