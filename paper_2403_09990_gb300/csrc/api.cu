@@ -1,5 +1,6 @@
 // C ABI of libpurse (declared in include/purse.h): argument validation,
 // handle lifetime, handle-owned scratch, the device status word.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -90,6 +91,9 @@ purse_status purse_create(int kind, int n, const double* model, const double* ob
   purse_s* h = new purse_s();
   h->kind = kind;
   h->n = n;
+  for (int i = 0; i < n; ++i)
+    h->rho_max = std::max(h->rho_max, std::sqrt(model[3 * i] * model[3 * i] + model[3 * i + 1] * model[3 * i + 1] +
+                                                model[3 * i + 2] * model[3 * i + 2]));
   h->K = Kc;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -200,6 +204,7 @@ purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const
   a.table = p->precision == 0 ? (const void*)h->tables.f32 : (const void*)h->tables.f64;
   a.n = h->n;
   a.fx = h->K.fx, a.fy = h->K.fy, a.cx = h->K.cx, a.cy = h->K.cy;
+  a.rho_max = h->rho_max;
   a.seed_data = d_seed_data;
   a.s0 = s0;
   a.stats = d_stats;

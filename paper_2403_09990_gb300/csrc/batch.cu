@@ -2,6 +2,7 @@
 // all (PURSE, sampler, walk) items, and one block per ball -- three kernels captured once into a
 // CUDA graph and replayed.  The walk launch shape (work-queue chunk, warps per block) is chosen
 // by purse_batch_tune, which times the candidates on the caller's batch.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -181,6 +182,11 @@ purse_status purse_batch_create(int n_purses, const int* kinds, const int* offse
     info[p].kind = kinds[p], info[p].n = n, info[p].table_off = 2 * o, info[p].pad = 0;
     info[p].fx = kinds[p] ? K[p].fx : 0.0, info[p].fy = kinds[p] ? K[p].fy : 0.0;
     info[p].cx = kinds[p] ? K[p].cx : 0.0, info[p].cy = kinds[p] ? K[p].cy : 0.0;
+    info[p].rho_max = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double* m = model + 3 * (size_t)(o + i);
+      info[p].rho_max = std::max(info[p].rho_max, std::sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]));
+    }
     for (int i = 0; i < n; ++i) {
       double* a = &t64[4 * (2 * (size_t)o + i)];
       double* bb = &t64[4 * (2 * (size_t)o + n + i)];

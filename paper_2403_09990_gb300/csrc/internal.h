@@ -40,6 +40,7 @@ constexpr int kSnapStride = 12;
 struct BatchPurseInfo {
   int kind, n, table_off, pad;  // table rows [table_off, table_off + 2 n) of the concatenated tables
   double fx, fy, cx, cy;
+  double rho_max;  // largest model-point radius max_i |a_i| (or |Z_i|)
 };
 
 // Perturbation parameters of the two kinds (index = kind) for the batched statistics.
@@ -76,6 +77,7 @@ struct WalkArgs {
   const void* table;
   int n;
   double fx, fy, cx, cy;
+  double rho_max;  // largest model-point radius max_i |Z_i|
   const double* seed_data;  // s0 x kSeedStride
   int s0;
   const WalkStats* stats;
@@ -96,6 +98,7 @@ struct WalkArgs {
 struct purse_s {
   int kind = 0;
   int n = 0;
+  double rho_max = 0;  // largest model-point radius
   purse_intrinsics K{0, 0, 0, 0};
   purse::purse_tables tables;
   int* d_status = nullptr;

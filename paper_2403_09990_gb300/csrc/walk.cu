@@ -152,7 +152,9 @@ __device__ __forceinline__ Slab<T> carve(unsigned char* base, int N, int NP, int
 // split its constraints (i = sub, sub + 2^sh, ...) and combine their minima by shuffles -- the
 // minimum is exact, so the keys are those of one lane taking every constraint.  Writes the keys of
 // every valid j.
-template <typename T, int KIND, int SAMPLER, int NPAIR, class RK>
+// ZCHK = false (dS_t, 2D-3D): the caller has bounded P_z away from 0 for every constraint and
+// perturbation, so the cheirality minimum is not tracked.
+template <typename T, int KIND, int SAMPLER, int NPAIR, bool ZCHK = true, class RK>
 __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Slab<T>& sl, int N, int NP, int lane,
                                           int pb, T r_pert, const V3<T>& t, T fx, T fy, T cx, T cy, T qzmin,
                                           int sh = 0) {
@@ -237,7 +239,7 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
         const T2 ex = fma2(d4, Pz, Px), ey = fma2(d5, Pz, Py);
         s2 = fma2(ey, ey, mul2(ex, ex));
         qq = fma2(s2, mul2(Pz, Pz), tiny2);
-        if (SAMPLER == 1) zmin[p] = min2(zmin[p], Pz);
+        if (SAMPLER == 1 && ZCHK) zmin[p] = min2(zmin[p], Pz);
       } else {
         s2 = fma2(Pz, Pz, fma2(Py, Py, mul2(Px, Px)));
         qq = add2(s2, tiny2);
@@ -254,7 +256,7 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
       dmin[p] = min2(dmin[p], pr(__shfl_xor_sync(kFullMask, dmin[p].x, o), __shfl_xor_sync(kFullMask, dmin[p].y, o)));
-      if (SAMPLER == 1 && KIND == 1)
+      if (SAMPLER == 1 && KIND == 1 && ZCHK)
         zmin[p] = min2(zmin[p], pr(__shfl_xor_sync(kFullMask, zmin[p].x, o), __shfl_xor_sync(kFullMask, zmin[p].y, o)));
     }
   }
@@ -267,7 +269,7 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
         T d = h ? dmin[p].y : dmin[p].x;
         if (KIND == 1) {
           // dS_R: P_z = Q_z,i + D_z,j and rounding is monotone, so min_i P_z = min_i Q_z,i + D_z,j
-          const T zm = SAMPLER == 0 ? qzmin + (h ? Dz[p].y : Dz[p].x) : (h ? zmin[p].y : zmin[p].x);
+          const T zm = SAMPLER == 0 ? qzmin + (h ? Dz[p].y : Dz[p].x) : ZCHK ? (h ? zmin[p].y : zmin[p].x) : T(1);
           if (!(zm > T(0))) d = -inf<T>();
         }
         sl.key[j] = orderable(d);
@@ -348,6 +350,7 @@ template <typename T>
 struct WalkCtx {
   int N, NP, K, NT, mc, n_iter;
   T fx, fy, cx, cy, r_pert;
+  T rho_max;  // largest model-point radius (bounds P_z from below for the cheirality test)
   double omega0, v0, gamma;
   const WalkStats* st;
   const double* seed_data;
@@ -530,15 +533,7 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
                   T(c.v0 * (st->S[6] * d0 + st->S[7] * d1 + st->S[8] * d2))};
     }
   }
-  T rho_max = T(0);  // largest keypoint radius |Z_i| (cheirality bound of the dS_R ladder)
-  if constexpr (SAMPLER == 0 && KIND == 1) {
-    for (int i = lane; i < N; i += 32) {
-      const T4<T> mz = tab[i];
-      rho_max = fmax(rho_max, sqrt(mz.x * mz.x + mz.y * mz.y + mz.z * mz.z));
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) rho_max = fmax(rho_max, __shfl_xor_sync(kFullMask, rho_max, o));
-  }
+  const T rho_max = c.rho_max;
   for (int m = lane; m < NT; m += 32) {
     T sm = T(1);
     for (int k = 0; k < m; ++k) sm *= T(c.gamma);
@@ -658,13 +653,25 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
         dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
       if (qtail) dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, nfull, r_pert, t, fx, fy, cx, cy, qzmin, tsh);
     } else {
-      for (int pb = 0; pb < nfull; pb += 2) {
-        if (nfull - pb >= 2)
-          dist_pass<T, KIND, SAMPLER, 2>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
-        else
-          dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
+      // P_z = (R Z_i)_z + t*_z >= t*_z - max |Z_i| (rotations keep |Z_i|); the margin covers rounding
+      if (KIND == 1 && t.z - rho_max > T(1e-3) * (fabs(t.z) + rho_max)) {
+        for (int pb = 0; pb < nfull; pb += 2) {
+          if (nfull - pb >= 2)
+            dist_pass<T, KIND, SAMPLER, 2, false>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
+          else
+            dist_pass<T, KIND, SAMPLER, 1, false>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
+        }
+        if (qtail)
+          dist_pass<T, KIND, SAMPLER, 1, false>(rk, it, w, sl, N, NP, lane, nfull, r_pert, t, fx, fy, cx, cy, qzmin, tsh);
+      } else {
+        for (int pb = 0; pb < nfull; pb += 2) {
+          if (nfull - pb >= 2)
+            dist_pass<T, KIND, SAMPLER, 2>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
+          else
+            dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
+        }
+        if (qtail) dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, nfull, r_pert, t, fx, fy, cx, cy, qzmin, tsh);
       }
-      if (qtail) dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, nfull, r_pert, t, fx, fy, cx, cy, qzmin, tsh);
     }
     evals += (unsigned long long)NP * N;
     __syncwarp();
@@ -721,6 +728,7 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
       int done = 0;
       // 2D-3D: P_z >= (candidate translation)_z - max |Z_i| (the rotation rows are unit vectors);
       // when that bound is positive for every candidate of the chunk, cheirality is not tracked
+      // (dS_R only: the dS_t kernel measured slower with the second ladder instantiation)
       const bool zsafe = KIND == 1 && SAMPLER == 0 &&
                          __all_sync(kFullMask, !active || bm.z - rho_max > T(1e-3) * (fabs(bm.z) + rho_max));
       if (zsafe)
@@ -800,6 +808,7 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
   WalkCtx<T> c;
   c.N = N, c.NP = a.n_perturb, c.K = a.n_keep, c.NT = a.n_steps, c.mc = mc, c.n_iter = a.n_iter;
   c.fx = T(a.fx), c.fy = T(a.fy), c.cx = T(a.cx), c.cy = T(a.cy);
+  c.rho_max = T(a.rho_max);
   c.r_pert = T(SAMPLER == 0 ? a.stats->r_trans : a.stats->r_rot);
   c.omega0 = a.omega0, c.v0 = a.v0, c.gamma = a.gamma;
   c.st = a.stats, c.seed_data = a.seed_data, c.s0 = a.s0;
@@ -872,6 +881,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2)
         c.N = in.n, c.NP = b.n_perturb[kd], c.K = b.n_keep[kd], c.NT = b.n_steps[kd], c.n_iter = b.n_iter[kd];
         c.mc = c.K >= 32 ? 1 : 32 / c.K;
         c.fx = float(in.fx), c.fy = float(in.fy), c.cx = float(in.cx), c.cy = float(in.cy);
+        c.rho_max = float(in.rho_max);
         c.omega0 = b.omega0[kd], c.v0 = b.v0[kd], c.gamma = b.gamma[kd];
         c.st = b.stats + p, c.seed_data = b.seed_data + (size_t)p * kSeedStride, c.s0 = 1;
         c.key0 = (uint32_t)key, c.key1 = (uint32_t)(key >> 32);
