@@ -90,6 +90,18 @@ purse_status purse_destroy(purse_t h);
 purse_status purse_eval(purse_t h, int precision, const void* d_poses, int n_poses,
                         void* d_margin, int32_t* d_active, void* d_grad, purse_stream_t stream);
 
+/* dist(R, t, dS) of eq. 11 -- min_i (r_i - |g_i|), -inf when a 2D-3D keypoint is behind the
+ * camera -- for n_poses FP32 poses d_poses (n_poses x 12: R row-major, then t; 16-byte aligned),
+ * written to d_dist (n_poses floats).  The pose transform of all constraints is one dense
+ * contraction [poses x 16] . [16 x 3n] of the pose row (R, t, 1, 0, 0, 0) with a constraint
+ * matrix (3D-3D: the residual R a_i + t - b_i; 2D-3D: P_x - u_i P_z, P_y - v_i P_z, P_z of
+ * P = K (R Z_i + t)).  mode 0: FP32 on the CUDA cores (the per-pose formula of eq. 2/3);
+ * mode 1: tensor cores (tcgen05, TF32) with both operands split into TF32 hi + lo and three
+ * passes hi.hi + hi.lo + lo.hi accumulated in FP32 (about 2^-21 relative per product);
+ * mode 2: one TF32 pass (about 2^-11).  Asynchronous on the stream. */
+purse_status purse_dist(purse_t h, int mode, const float* d_poses, long long n_poses, float* d_dist,
+                        purse_stream_t stream);
+
 /* Step I for 3D-3D (Section IV, RANSAG): trials tau = 0..n_trials-1 each fit a pose to three
  * distinct constraints with one point drawn inside each noise ball (Arun's least-squares
  * rotation) and accept it if it lies in the PURSE.  The first max_seeds accepted poses in
@@ -124,6 +136,20 @@ purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds,
 purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const double* d_seeds,
                           int s0, int n_samples, void* d_q, void* d_t, int16_t* d_trace, void* d_snap,
                           purse_stream_t stream);
+
+/* Step II by the plain per-operation samplers (Alg. 3 / Alg. 5 in the paper's parallel form):
+ * the same walks, draws, decisions, outputs and trace as purse_sample (no snap), computed by one
+ * kernel per tensor operation of the listing (perturbation, dist of eq. 11, top_k_indices,
+ * update_rotation / update_translation, in_purse, find_farthest) with every intermediate tensor
+ * -- perturbed poses (W, N_P, 12), distances (W, N_P), kept indices (W, N_P*), ladder
+ * candidates (W, N_T, N_P*, 12), in_purse flags (W, N_T, N_P*) -- in device memory, and every
+ * constraint of every pose evaluated.  It is the per-instance comparator of the fused walk
+ * kernel.  Arguments as for purse_sample.  The intermediates of up to about 2 GB of walks at a
+ * time live in handle-owned scratch (grown with cudaMalloc; PURSE_ERR_NOMEM).
+ * purse_last_evals afterwards returns n_samples N_I (N_P + N_T N_P*) n. */
+purse_status purse_sample_plain(purse_t h, const purse_params* p, uint64_t seed, const double* d_seeds,
+                                int s0, int n_samples, void* d_q, void* d_t, int16_t* d_trace,
+                                purse_stream_t stream);
 
 /* Number of (pose, constraint) evaluations the last purse_sample on this handle executed
  * (perturbation distances of eq. 11 plus in_purse checks of the step ladder up to m0).

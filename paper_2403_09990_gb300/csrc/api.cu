@@ -134,6 +134,18 @@ purse_status purse_eval(purse_t h, int precision, const void* d_poses, int n_pos
   return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_eval");
 }
 
+purse_status purse_dist(purse_t h, int mode, const float* d_poses, long long n_poses, float* d_dist,
+                        purse_stream_t stream) {
+  if (!h) return arg_error("purse_dist: NULL handle");
+  if (mode < 0 || mode > 2) return arg_error("purse_dist: mode must be 0 (FP32), 1 (split TF32) or 2 (TF32)");
+  if (n_poses < 0) return arg_error("purse_dist: n_poses < 0");
+  if (n_poses > 0 && (!d_poses || !d_dist)) return arg_error("purse_dist: NULL buffer");
+  if ((reinterpret_cast<uintptr_t>(d_poses) & 15) != 0) return arg_error("purse_dist: d_poses must be 16-byte aligned");
+  cudaError_t e = mode == 0 ? launch_plain_dist(h, d_poses, (long)n_poses, d_dist, (cudaStream_t)stream)
+                            : launch_tc_dist(h, mode == 1 ? 3 : 1, d_poses, (long)n_poses, d_dist, (cudaStream_t)stream);
+  return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_dist");
+}
+
 purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds, double* d_seeds, int* n_seeds,
                           purse_stream_t stream) {
   if (!h) return arg_error("purse_ransag: NULL handle");
@@ -227,6 +239,43 @@ purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const
     return PURSE_ERR_ARG;
   }
   return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_sample (walk)");
+}
+
+purse_status purse_sample_plain(purse_t h, const purse_params* p, uint64_t seed, const double* d_seeds, int s0,
+                                int n_samples, void* d_q, void* d_t, int16_t* d_trace, purse_stream_t stream) {
+  if (!h || !p) return arg_error("purse_sample_plain: NULL handle or params");
+  if (p->n_iter < 0) return arg_error("purse_sample_plain: n_iter < 0");
+  if (p->n_perturb < 1 || p->n_perturb > 256) return arg_error("purse_sample_plain: n_perturb must be in [1, 256]");
+  if (p->n_keep < 1 || p->n_keep > 32 || p->n_keep > p->n_perturb)
+    return arg_error("purse_sample_plain: n_keep must be in [1, min(32, n_perturb)]");
+  if (p->n_steps < 1 || p->n_steps > 32) return arg_error("purse_sample_plain: n_steps must be in [1, 32]");
+  if (!(p->gamma > 0 && p->gamma <= 1)) return arg_error("purse_sample_plain: gamma must be in (0, 1]");
+  if (!std::isfinite(p->omega0) || !std::isfinite(p->v0) || !std::isfinite(p->rot_perturb) ||
+      !std::isfinite(p->trans_perturb) || p->rot_perturb < 0 || p->trans_perturb < 0)
+    return arg_error("purse_sample_plain: speeds and perturbation scales must be finite (scales >= 0)");
+  if (p->sampler != 0 && p->sampler != 1) return arg_error("purse_sample_plain: sampler must be 0 or 1");
+  if (p->precision != 0 && p->precision != 1) return arg_error("purse_sample_plain: precision must be 0 or 1");
+  if (p->perturb_units != 0 && p->perturb_units != 1)
+    return arg_error("purse_sample_plain: perturb_units must be 0 or 1");
+  if (s0 < 1 || !d_seeds) return arg_error("purse_sample_plain: need at least one seed pose");
+  if (n_samples < 0) return arg_error("purse_sample_plain: n_samples < 0");
+  if (n_samples > 0 && (!d_q || !d_t)) return arg_error("purse_sample_plain: NULL output");
+  cudaStream_t st = (cudaStream_t)stream;
+  int chunk = 1;
+  const size_t stats_bytes = align256(sizeof(WalkStats));
+  const size_t seed_bytes = align256((size_t)s0 * kSeedStride * sizeof(double));
+  const size_t work_bytes = plain_scratch_bytes(p, n_samples, &chunk);
+  purse_status s = ensure_scratch(h, stats_bytes + seed_bytes + work_bytes);
+  if (s != PURSE_OK) return s;
+  WalkStats* d_stats = reinterpret_cast<WalkStats*>(h->d_scratch);
+  double* d_seed_data = reinterpret_cast<double*>(reinterpret_cast<char*>(h->d_scratch) + stats_bytes);
+  void* work = reinterpret_cast<char*>(h->d_scratch) + stats_bytes + seed_bytes;
+  cudaError_t e = cudaMemsetAsync(h->d_evals, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = launch_stats(h, d_seeds, s0, p, d_stats, d_seed_data, st);
+  if (e != cudaSuccess) return cuda_fail(e, "purse_sample_plain (stats)");
+  if (n_samples == 0) return PURSE_OK;
+  e = launch_plain(h, p, d_stats, d_seed_data, s0, seed, n_samples, d_q, d_t, d_trace, work, work_bytes, chunk, st);
+  return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_sample_plain");
 }
 
 purse_status purse_last_evals(purse_t h, unsigned long long* evals, purse_stream_t stream) {

@@ -135,6 +135,12 @@ cudaError_t launch_ransag(purse_t h, uint64_t seed, int trial0, int n_trials, do
                           cudaStream_t st);
 cudaError_t launch_compact(const double* d_pose, const uint8_t* d_acc, int n_trials, double* d_seeds,
                            int* d_count, int max_seeds, cudaStream_t st);
+size_t plain_scratch_bytes(const purse_params* p, int n_samples, int* chunk);
+cudaError_t launch_plain(purse_t h, const purse_params* p, const WalkStats* d_stats, const double* d_seed_data, int s0,
+                         uint64_t seed, int n_samples, void* d_q, void* d_t, int16_t* d_trace, void* scratch,
+                         size_t scratch_bytes, int chunk, cudaStream_t st);
+cudaError_t launch_plain_dist(purse_t h, const float* d_poses, long n_poses, float* d_dist, cudaStream_t st);
+cudaError_t launch_tc_dist(purse_t h, int passes, const float* d_poses, long n_poses, float* d_dist, cudaStream_t st);
 cudaError_t launch_eval(purse_t h, int precision, const void* d_poses, int n_poses, void* d_margin,
                         int32_t* d_active, void* d_grad, cudaStream_t st);
 cudaError_t launch_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t i, uint32_t w0, int n_streams,

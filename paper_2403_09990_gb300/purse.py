@@ -46,9 +46,12 @@ _SIGS = {
     "purse_create": [ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)],
     "purse_destroy": [_VP],
     "purse_eval": [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP, _VP],
+    "purse_dist": [_VP, ctypes.c_int, _VP, ctypes.c_longlong, _VP, _VP],
     "purse_ransag": [_VP, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int), _VP],
     "purse_sample": [_VP, ctypes.POINTER(purse_params), ctypes.c_uint64, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP,
                      _VP, _VP, _VP],
+    "purse_sample_plain": [_VP, ctypes.POINTER(purse_params), ctypes.c_uint64, _VP, ctypes.c_int, ctypes.c_int, _VP,
+                           _VP, _VP, _VP],
     "purse_last_evals": [_VP, ctypes.POINTER(ctypes.c_ulonglong), _VP],
     "megb_solve": [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP],
     "megb_backward": [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP, _VP,
@@ -141,6 +144,10 @@ def purse_eval(h, precision, poses, n_poses, margin=None, active=None, grad=None
                             _stream(stream)), "purse_eval")
 
 
+def purse_dist(h, mode, poses, n_poses, dist, stream=None):
+    _check(lib().purse_dist(h, mode, _ptr(poses), n_poses, _ptr(dist), _stream(stream)), "purse_dist")
+
+
 def purse_ransag(h, seed, n_trials, max_seeds, seeds, stream=None) -> int:
     n = ctypes.c_int(0)
     _check(lib().purse_ransag(h, seed, n_trials, max_seeds, _ptr(seeds), ctypes.byref(n), _stream(stream)),
@@ -151,6 +158,11 @@ def purse_ransag(h, seed, n_trials, max_seeds, seeds, stream=None) -> int:
 def purse_sample(h, params: purse_params, seed, seeds, s0, n_samples, q, t, trace=None, stream=None, snap=None):
     _check(lib().purse_sample(h, ctypes.byref(params), seed, _ptr(seeds), s0, n_samples, _ptr(q), _ptr(t),
                               _ptr(trace), _ptr(snap), _stream(stream)), "purse_sample")
+
+
+def purse_sample_plain(h, params: purse_params, seed, seeds, s0, n_samples, q, t, trace=None, stream=None):
+    _check(lib().purse_sample_plain(h, ctypes.byref(params), seed, _ptr(seeds), s0, n_samples, _ptr(q), _ptr(t),
+                                    _ptr(trace), _stream(stream)), "purse_sample_plain")
 
 
 def purse_last_evals(h, stream=None) -> int:
