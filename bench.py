@@ -294,6 +294,8 @@ def run_gpu(args, rank, world):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": ck, "wall_s_timed": wall,
     }
+    if not args.no_plain:
+        out["plain_gpu"] = run_plain(args, p, dev, seeds, value / world, t_step)
     if rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(args, p, dev)
     if not args.no_batch:
@@ -312,6 +314,42 @@ def run_gpu(args, rank, world):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def run_plain(args, p, dev, seeds, fused_value, fused_step_s):
+    """The same step through the plain per-operation samplers (Alg. 3/5 in the paper's tensor form: one
+    kernel per operation, intermediates in HBM, every constraint of every pose evaluated), then the same
+    two balls; CUDA events around each step, L2 flushed in between."""
+    import torch
+    import paper_2403_09990_gb300.purse as P
+    stream = torch.cuda.current_stream()
+    h = P.Purse(p)
+    qR = torch.empty((N_WALKS, 4), dtype=torch.float32, device=dev)
+    tR = torch.empty((N_WALKS, 3), dtype=torch.float32, device=dev)
+    qT = torch.empty((N_WALKS, 4), dtype=torch.float32, device=dev)
+    tT = torch.empty((N_WALKS, 3), dtype=torch.float32, device=dev)
+    res = torch.empty(9, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    pR, pT = closure_params(0), closure_params(1)
+    times = []
+    for s in range(1 + args.plain_steps):
+        flush.fill_(s & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.purse_sample_plain(h.h, pR, 1000 + s, seeds, 1, N_WALKS, qR, tR, None, stream)
+        P.purse_sample_plain(h.h, pT, 1000 + s, seeds, 1, N_WALKS, qT, tT, None, stream)
+        P.megb_solve(h.h, 0, K_MEGB, qR, N_WALKS, tT, N_WALKS, res, None, stream)
+        e1.record(stream)
+        P.purse_sync(h.h, stream)
+        if s > 0:  # the first step warms up
+            times.append(e0.elapsed_time(e1))
+    h.close()
+    ms = statistics.median(times)
+    evals_alg = 2 * N_WALKS * N_ITER * (N_PERTURB + N_KEEP * N_STEPS) * p.n
+    return {"ms_per_step": ms, "value": evals_alg / (ms / 1e3), "unit": UNIT, "steps": len(times),
+            "megb_solves_per_s": 1e3 / ms, "fused_speedup": (ms / 1e3) / fused_step_s,
+            "path": "purse_sample_plain per sampler (perturbation, eq. 11 dist, top_k_indices, ladder candidates, "
+                    "in_purse, find_farthest: one kernel each per iteration, intermediates in HBM) + megb_solve"}
 
 
 def run_sweep(args):
@@ -374,6 +412,9 @@ def run_sweep(args):
                                               "d_rel": abs(r32[8] - r64[8]) / r64[8],
                                               "C_rad": angle(r32[:4], r64[:4]),
                                               "c_m": float(np.linalg.norm(r32[4:7] - r64[4:7]))}}), flush=True)
+    for kind in ((1, 0) if "dist" in args.sweep_parts else ()):
+        for n in (8, 16, 32, 64, 128, 256):
+            print(json.dumps(sweep_dist(P, syn, dev, stream, kind, n)), flush=True)
     p = syn.purse_2d3d(N_KEYPOINTS, 0)
     for lg in ((22, 24, 26) if "scale" in args.sweep_parts else ()):
         S = 1 << lg
@@ -384,6 +425,56 @@ def run_sweep(args):
                           "megb_gbs": ball_bytes / (m32 / 1e3) / 1e9,
                           "megb_bytes_note": "16 B per rotation sample + 12 B per translation sample, per GGD "
                                              "iteration and the final pass", "D": r32[7], "d": r32[8]}), flush=True)
+
+
+def sweep_dist(P, syn, dev, stream, kind, n, n_poses=1 << 24):
+    """eq. 11 distance of 2^24 materialised FP32 poses around the ground truth of one PURSE (rotations
+    of about 0.02 rad, translations of a few noise radii) by the FP32 CUDA-core kernel, the tcgen05
+    split-TF32 contraction and one TF32 pass; errors against the FP64 margins of the same poses
+    (purse_eval in FP64); CUDA-event times with L2 flushed in between."""
+    import torch
+    p = syn.purse_3d3d(n, 0) if kind == 0 else syn.purse_2d3d(n, 0)
+    rng = np.random.default_rng(n)
+    m = 1 << 16
+    phi = rng.normal(size=(m, 3)) * 0.02
+    th = np.linalg.norm(phi, axis=1, keepdims=True)
+    k = phi / th
+    K = np.zeros((m, 3, 3))
+    K[:, 0, 1], K[:, 0, 2], K[:, 1, 2] = -k[:, 2], k[:, 1], -k[:, 0]
+    K = K - K.transpose(0, 2, 1)
+    s_, c_ = np.sin(th)[..., None], np.cos(th)[..., None]
+    R = (np.eye(3) + s_ * K + (1 - c_) * (K @ K)) @ p.R_gt
+    t = p.t_gt + rng.normal(size=(m, 3)) * (3 * p.radii.mean() if kind == 0 else 0.01)
+    base = np.concatenate([R.reshape(m, 9), t], axis=1).astype(np.float32)
+    poses = torch.as_tensor(base, device=dev).repeat(n_poses // m, 1).contiguous()
+    out = torch.empty(n_poses, dtype=torch.float32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    res = {"sweep": "dist", "kind": "3D-3D" if kind == 0 else "2D-3D", "n_keypoints": n, "poses": n_poses}
+    with P.Purse(p) as h:
+        m64 = torch.empty((m, n), dtype=torch.float64, device=dev)
+        P.purse_eval(h.h, 1, poses[:m].double().contiguous(), m, m64, None, None, stream)
+        ref = m64.min(dim=1).values
+        scale = float(ref.abs().max())
+        for mode, name in ((0, "fp32"), (1, "split_tf32"), (2, "tf32")):
+            for _ in range(2):
+                P.purse_dist(h.h, mode, poses, n_poses, out, stream)
+            ts = []
+            for r in range(5):
+                flush.fill_(r)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                P.purse_dist(h.h, mode, poses, n_poses, out, stream)
+                e1.record(stream)
+                P.purse_sync(h.h, stream)
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            d = out[:m].double()
+            fin = torch.isfinite(ref)
+            err = float((d[fin] - ref[fin]).abs().max())
+            res[name] = {"ms": ms, "poses_per_s": n_poses / (ms / 1e3), "evals_per_s": n_poses * n / (ms / 1e3),
+                         "hbm_gbs": n_poses * 52 / (ms / 1e3) / 1e9, "max_abs_err": err,
+                         "max_rel_err": err / scale}
+    return res
 
 
 def run_batch(args, dev):
@@ -425,6 +516,7 @@ def run_batch(args, dev):
     alg = float(((1 + kinds) * S * 5 * (150 + 10 * 15) * ns).sum())
     ms = tot / args.batch_steps
     per_instance = run_per_instance(args, purses[:args.per_instance_purses], p3, p2, S, K, dev)
+    per_plain = run_per_instance(args, purses[:args.per_instance_purses], p3, p2, S, K, dev, plain=True)
     return {"workload": f"{n_purses} PURSEs (3D-3D / 2D-3D by a fair coin, N ~ U{{4..64}}), {S} samples each, "
                         f"presets of Section V (N_I = 5), both balls with {K} GGD iterations, FP32",
             "purses_per_s": n_purses / (ms / 1e3), "ms_per_solve": ms, "steps": args.batch_steps,
@@ -432,13 +524,16 @@ def run_batch(args, dev):
             "launch": {"graph": "statistics + persistent walk kernel + one block per ball", "chunk": chunk,
                        "warps_per_block": warps},
             "per_instance": per_instance,
-            "speedup_vs_per_instance": (n_purses / (ms / 1e3)) / per_instance["purses_per_s"]}
+            "speedup_vs_per_instance": (n_purses / (ms / 1e3)) / per_instance["purses_per_s"],
+            "per_instance_plain": per_plain,
+            "speedup_vs_per_instance_plain": (n_purses / (ms / 1e3)) / per_plain["purses_per_s"]}
 
 
-def run_per_instance(args, purses, p3, p2, S, K, dev):
-    """The plain per-instance GPU path on the same GPU: the batch's first PURSEs solved one call sequence
-    per PURSE (purse_create, purse_sample per sampler, megb_solve, result read back), as a caller without
-    the batch API would."""
+def run_per_instance(args, purses, p3, p2, S, K, dev, plain=False):
+    """Per-instance GPU paths on the same GPU: the batch's first PURSEs solved one call sequence per PURSE
+    (purse_create, a sampler call per sampler, megb_solve, result read back), as a caller without the batch
+    API would; the sampler is the fused walk kernel (purse_sample) or, with plain=True, the plain
+    per-operation samplers (purse_sample_plain, Alg. 3/5 in the paper's tensor form)."""
     import torch
     import paper_2403_09990_gb300.purse as P
     stream = torch.cuda.current_stream()
@@ -453,11 +548,17 @@ def run_per_instance(args, purses, p3, p2, S, K, dev):
         with P.Purse(pu) as h:
             sd = torch.as_tensor(pu.seed_pose()[None], dtype=torch.float64, device=dev)
             prm = p3 if pu.kind == 0 else p2
-            P.purse_sample(h.h, P.purse_params.from_buffer_copy(prm), seed, sd, 1, S, q1, t1, None, stream)
+            if plain:
+                P.purse_sample_plain(h.h, P.purse_params.from_buffer_copy(prm), seed, sd, 1, S, q1, t1, None, stream)
+            else:
+                P.purse_sample(h.h, P.purse_params.from_buffer_copy(prm), seed, sd, 1, S, q1, t1, None, stream)
             if pu.kind == 1:
                 p_t = P.purse_params.from_buffer_copy(prm)
                 p_t.sampler = 1
-                P.purse_sample(h.h, p_t, seed, sd, 1, S, q2, t2, None, stream)
+                if plain:
+                    P.purse_sample_plain(h.h, p_t, seed, sd, 1, S, q2, t2, None, stream)
+                else:
+                    P.purse_sample(h.h, p_t, seed, sd, 1, S, q2, t2, None, stream)
             P.megb_solve(h.h, 0, K, q1, S, t2 if pu.kind == 1 else t1, S, res, None, stream)
             out.copy_(res)
             P.purse_sync(h.h, stream)
@@ -471,8 +572,8 @@ def run_per_instance(args, purses, p3, p2, S, K, dev):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     return {"purses": len(purses), "purses_per_s": len(purses) / wall, "ms_per_purse": 1e3 * wall / len(purses),
-            "path": "per PURSE: purse_create + purse_sample (dS_R; dS_t for 2D-3D) + megb_solve + result D2H, "
-                    "the batch's first PURSEs, wall clock"}
+            "path": f"per PURSE: purse_create + {'purse_sample_plain' if plain else 'purse_sample'} (dS_R; dS_t for "
+                    "2D-3D) + megb_solve + result D2H, the batch's first PURSEs, wall clock"}
 
 
 def run_grad(args, dev):
@@ -616,9 +717,11 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--batch-warmup", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain per-operation comparator")
+    ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-grad", action="store_true", help="skip the batched differentiation measurement")
     ap.add_argument("--sweep", action="store_true", help="precision / scale sweep instead of the bench step")
-    ap.add_argument("--sweep-parts", default="precision,scale", help="which parts of the sweep to run")
+    ap.add_argument("--sweep-parts", default="precision,scale,dist", help="which parts of the sweep to run")
     ap.add_argument("--grad-purses", type=int, default=1024)
     ap.add_argument("--per-instance-purses", type=int, default=256,
                     help="PURSEs of the batch solved one by one for the per-instance comparison")
