@@ -210,6 +210,43 @@ __host__ __device__ __forceinline__ M3<T> qmat(Q4<T> q) {
 __device__ __forceinline__ void sin_cos(float x, float* s, float* c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sin_cos(double x, double* s, double* c) { sincos(x, s, c); }
 
+// sin and cos of a small angle: for |x| <= 1/4 the Taylor series through x^7 and x^8 (the first
+// omitted terms, x^9/9! and x^10/10!, are below 1.1e-11 there), else the library sincos.
+template <typename T>
+__device__ __forceinline__ void sincos_small(T x, T& s, T& c) {
+  if (fabs(x) <= T(0.25)) {
+    const T x2 = x * x;
+    s = x * fma(-x2, fma(-x2, fma(-x2, T(1.0 / 5040), T(1.0 / 120)), T(1.0 / 6)), T(1));
+    c = fma(-x2, fma(-x2, fma(-x2, fma(-x2, T(1.0 / 40320), T(1.0 / 720)), T(1.0 / 24)), T(0.5)), T(1));
+  } else {
+    sin_cos(x, &s, &c);
+  }
+}
+
+// Exp(r u) as a unit quaternion for the perturbation point u of hatbox_point(w0, w1): u is rho
+// times the unit direction (sqrt(1 - z^2) cos a, sqrt(1 - z^2) sin a, z), so the rotation angle
+// is r rho and the axis that direction -- no norm and no division are formed.
+template <typename T>
+__device__ __forceinline__ Q4<T> hatbox_quat(uint32_t w0, uint32_t w1, T r) {
+  const T zz = T((int)(w0 >> 16)) * T(1.0 / 32768) + T(0.5 / 32768 - 1.0);
+  const T az = T((int)(w0 & 0xFFFFu)) * T(1.0 / 32768) + T(0.5 / 32768);
+  const uint32_t k = max(max(w1 & 1023u, (w1 >> 10) & 1023u), (w1 >> 20) & 1023u);
+  const T rho = T((int)k) * T(1.0 / 1024) + T(0.5 / 1024);
+  const T c2 = T(1) - zz * zz;  // >= 2^-15
+  T sp, cp, sq;
+  if constexpr (sizeof(T) == 4) {
+    __sincosf(3.14159265358979f * az, &sp, &cp);
+    sq = c2 * rsqrtf(c2);
+  } else {
+    sin_cos_pi(az, &sp, &cp);
+    sq = sqrt(c2);
+  }
+  T sh, ch;
+  sincos_small(T(0.5) * r * rho, sh, ch);
+  const T f = sh * sq;
+  return Q4<T>{ch, f * cp, f * sp, sh * zz};
+}
+
 // Unit quaternion of the rotation vector v (Exp of so(3), Rodrigues).
 template <typename T>
 __device__ __forceinline__ Q4<T> qexp(V3<T> v) {

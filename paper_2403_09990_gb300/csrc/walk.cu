@@ -179,10 +179,10 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
       dx[h] = dy[h] = dz[h] = T(0);
       Ah[h] = M3<T>{{T(1), T(0), T(0), T(0), T(1), T(0), T(0), T(0), T(1)}};
       if (j < NP) {
-        T ux, uy, uz;
-        hatbox_point<T>(h ? wd.z : wd.x, h ? wd.w : wd.y, ux, uy, uz);
-        const V3<T> dl{r_pert * ux, r_pert * uy, r_pert * uz};
         if constexpr (SAMPLER == 0) {
+          T ux, uy, uz;
+          hatbox_point<T>(h ? wd.z : wd.x, h ? wd.w : wd.y, ux, uy, uz);
+          const V3<T> dl{r_pert * ux, r_pert * uy, r_pert * uz};
           sl.P[j] = T4<T>{dl.x, dl.y, dl.z, T(0)};
           if (KIND == 1) {
             dx[h] = fx * dl.x + cx * dl.z, dy[h] = fy * dl.y + cy * dl.z, dz[h] = dl.z;
@@ -190,7 +190,7 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
             dx[h] = dl.x, dy[h] = dl.y, dz[h] = dl.z;
           }
         } else {
-          const Q4<T> pq = qexp(dl);
+          const Q4<T> pq = hatbox_quat<T>(h ? wd.z : wd.x, h ? wd.w : wd.y, r_pert);
           sl.P[j] = T4<T>{pq.w, pq.x, pq.y, pq.z};
           M3<T> Rp = qmat(pq);
           if (KIND == 1) {
