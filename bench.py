@@ -412,8 +412,10 @@ def run_sweep(args):
                                               "d_rel": abs(r32[8] - r64[8]) / r64[8],
                                               "C_rad": angle(r32[:4], r64[:4]),
                                               "c_m": float(np.linalg.norm(r32[4:7] - r64[4:7]))}}), flush=True)
-    for kind in ((1, 0) if "dist" in args.sweep_parts else ()):
-        for n in (8, 16, 32, 64, 128, 256):
+    kinds = (1, 0) if args.dist_kind is None else (args.dist_kind,)
+    ns = (8, 16, 32, 64, 128, 256) if args.dist_n is None else (args.dist_n,)
+    for kind in (kinds if "dist" in args.sweep_parts else ()):
+        for n in ns:
             print(json.dumps(sweep_dist(P, syn, dev, stream, kind, n)), flush=True)
     p = syn.purse_2d3d(N_KEYPOINTS, 0)
     for lg in ((22, 24, 26) if "scale" in args.sweep_parts else ()):
@@ -722,6 +724,8 @@ def main():
     ap.add_argument("--no-grad", action="store_true", help="skip the batched differentiation measurement")
     ap.add_argument("--sweep", action="store_true", help="precision / scale sweep instead of the bench step")
     ap.add_argument("--sweep-parts", default="precision,scale,dist", help="which parts of the sweep to run")
+    ap.add_argument("--dist-kind", type=int, default=None, help="dist sweep: one PURSE kind (0 3D-3D, 1 2D-3D)")
+    ap.add_argument("--dist-n", type=int, default=None, help="dist sweep: one keypoint count")
     ap.add_argument("--grad-purses", type=int, default=1024)
     ap.add_argument("--per-instance-purses", type=int, default=256,
                     help="PURSEs of the batch solved one by one for the per-instance comparison")

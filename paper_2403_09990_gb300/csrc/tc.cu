@@ -14,11 +14,14 @@
 // one TF32 pass (2^-11).  B is split from the FP64 constraint table.
 //
 // Mapping: one CTA of 128 threads per tile of 128 poses (persistent over tiles), M = 128
-// rows in TMEM lanes, constraints in rounds of up to 80 (N <= 240 columns per MMA).  Shared
-// memory holds A (hi, lo) and B (hi, lo) in the K-major no-swizzle canonical layout: core
-// matrices of 8 rows x 16 bytes, the four core matrices of a row group along K contiguous
-// (LBO = 128 B), row groups 512 B apart (SBO).  One thread issues the MMAs and commits them
-// to an mbarrier; all four warps read their 32 TMEM lanes back with tcgen05.ld.
+// rows in TMEM lanes, constraints in rounds of up to 32 (N <= 96 columns per MMA, 128 TMEM
+// columns at most, so four CTAs fit an SM).  The raw 6 KB pose tiles stream through a ring of
+// four shared-memory stages filled by 1-D bulk copies (cp.async.bulk, one mbarrier per
+// stage); the threads split a landed tile into A (hi, lo).  Shared memory holds A and B in
+// the K-major no-swizzle canonical layout: core matrices of 8 rows x 16 bytes, the four core
+// matrices of a row group along K contiguous (LBO = 128 B), row groups 512 B apart (SBO).
+// One thread issues the MMAs and commits them to an mbarrier; all four warps read their 32
+// TMEM lanes back with tcgen05.ld.
 #include <algorithm>
 #include <cfloat>
 
@@ -28,8 +31,10 @@
 namespace purse {
 
 constexpr int kTcThreads = 128;
-constexpr int kTcRoundMax = 80;         // constraints per MMA round (N = 240)
+constexpr int kTcRoundMax = 32;          // constraints per MMA round (N = 96, 128 TMEM columns)
+constexpr int kTcStages = 4;             // raw pose tiles in flight per CTA
 constexpr uint32_t kTcTileBytes = 8192;  // 128 rows x 16 fp32
+constexpr uint32_t kTcRawBytes = 6144;   // 128 poses x 48 B
 
 __device__ __forceinline__ float rna_tf32(float x) {
   uint32_t r;
@@ -108,22 +113,25 @@ __device__ double tc_coef(int kind, const double* tab, int n, double fx, double 
 }
 
 template <int KIND, int PASSES>
-__global__ void __launch_bounds__(kTcThreads, 7)
+__global__ void __launch_bounds__(kTcThreads, 4)
     tc_dist_kernel(const double* __restrict__ tab, const float* __restrict__ tab32, int n, double fx, double fy,
                    double cx, double cy, const float* __restrict__ poses, long n_poses, float* __restrict__ dist,
                    uint32_t tmem_cols, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  // layout: [A_hi 8 KB][A_lo 8 KB][B_hi 64 B per column][B_lo][radii][mbarrier, TMEM address]
+  // layout: [raw pose tiles, kTcStages x 6 KB][A_hi 8 KB][A_lo 8 KB][B_hi 64 B per column][B_lo][radii]
+  //         [mbarriers: MMA completion, one per raw stage][TMEM address]
   const int n_pad = (n + 15) & ~15;
   const int cols = 3 * n_pad;
-  unsigned char* a_hi = smem;
-  unsigned char* a_lo = smem + kTcTileBytes;
-  unsigned char* b_hi = smem + 2 * kTcTileBytes;
+  unsigned char* raw = smem;
+  unsigned char* a_hi = smem + kTcStages * kTcRawBytes;
+  unsigned char* a_lo = a_hi + kTcTileBytes;
+  unsigned char* b_hi = a_lo + kTcTileBytes;
   unsigned char* b_lo = b_hi + 64 * (size_t)cols;
   float* r_s = reinterpret_cast<float*>(b_lo + 64 * (size_t)cols);
   uint64_t* bar = reinterpret_cast<uint64_t*>(r_s + n_pad);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint64_t* full = bar + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + kTcStages);
+  const int tid = threadIdx.x, warp = tid >> 5;
 
   // ---- operands that stay: B (hi, lo), radii, the constant column k = 12..15 of A
   for (int e = tid; e < cols * 16; e += kTcThreads) {
@@ -141,7 +149,10 @@ __global__ void __launch_bounds__(kTcThreads, 7)
     *reinterpret_cast<float4*>(a_hi + kmaj_off(row, 12)) = make_float4(1.f, 0.f, 0.f, 0.f);
     *reinterpret_cast<float4*>(a_lo + kmaj_off(row, 12)) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  if (tid == 0) mbar_init(bar, 1);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    for (int s = 0; s < kTcStages; ++s) mbar_init(full + s, 1);
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
                  "r"(tmem_cols)
@@ -157,28 +168,41 @@ __global__ void __launch_bounds__(kTcThreads, 7)
   uint32_t phase = 0;
   bool failed = false;
 
+  // ---- raw pose tiles: tile k of this CTA (global tile blockIdx.x + k gridDim.x, 48 B per pose,
+  //      one 1-D bulk copy) lands in stage k mod kTcStages; thread 0 keeps kTcStages tiles in flight
   const long n_tiles = (n_poses + 127) / 128;
-  // the tile's 384 float4 (48 B per pose): thread tid loads q = tid + 128 j, the next tile's
-  // loads are issued before the current tile's MMAs and epilogue
-  float4 xa[3];
-  auto load_tile = [&](long tile) {
-    const float4* src = reinterpret_cast<const float4*>(poses + 12 * (tile * 128));
-    const long avail4 = (n_poses - tile * 128) * 3;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int q = tid + kTcThreads * j;
-      xa[j] = (tile < n_tiles && q < avail4) ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+  long issued = 0;  // thread 0: bulk copies issued so far
+  auto issue = [&](long k) {
+    const long tile = blockIdx.x + k * (long)gridDim.x;
+    if (tile >= n_tiles) return;
+    const int s = (int)(k % kTcStages);
+    const long rows = n_poses - tile * 128 < 128 ? n_poses - tile * 128 : 128;
+    const uint32_t bytes = (uint32_t)(rows * 48);
+    mbar_arrive_expect_tx(full + s, bytes);
+    bulk_copy_g2s(raw + (size_t)s * kTcRawBytes, poses + 12 * (tile * 128), bytes, full + s);
+    issued = k + 1;
   };
-  load_tile(blockIdx.x);
-  for (long tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+  if (tid == 0)
+    for (int k = 0; k < kTcStages; ++k) issue(k);
+  long k = 0;
+  for (;; ++k) {
+    const long tile = blockIdx.x + k * (long)gridDim.x;
+    if (tile >= n_tiles) break;
+    const int st = (int)(k % kTcStages);
+    const bool okf = mbar_wait_bounded(full + st, (uint32_t)((k / kTcStages) & 1), 1 << 24);
+    if (__syncthreads_or(!okf)) {
+      failed = true;
+      break;
+    }
     const long row0 = tile * 128;
+    const long avail4 = (n_poses - row0) * 3;
+    const float4* src = reinterpret_cast<const float4*>(raw + (size_t)st * kTcRawBytes);
     // ---- A split into hi and lo (K-major core matrices)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const int q = tid + kTcThreads * j;
       const int row = q / 3, kb = q - 3 * row;
-      const float4 x = xa[j];
+      const float4 x = q < avail4 ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 h = make_float4(rna_tf32(x.x), rna_tf32(x.y), rna_tf32(x.z), rna_tf32(x.w));
       *reinterpret_cast<float4*>(a_hi + kmaj_off(row, 4 * kb)) = h;
       if (PASSES == 3)
@@ -187,7 +211,7 @@ __global__ void __launch_bounds__(kTcThreads, 7)
     }
     fence_async_smem();
     __syncthreads();
-    load_tile(tile + gridDim.x);
+    if (tid == 0) issue(k + kTcStages);  // every thread has read stage st: refill it
     float best = INFINITY;
     for (int c0 = 0; c0 < n_pad && !failed; c0 += kTcRoundMax) {
       const int nr = min(kTcRoundMax, n_pad - c0);  // constraints of this round (a multiple of 16)
@@ -224,7 +248,7 @@ __global__ void __launch_bounds__(kTcThreads, 7)
         tc_wait_ld();
         float v[48];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = v0[k], v[16 + k] = v1[k], v[32 + k] = v2[k];
+        for (int u = 0; u < 16; ++u) v[u] = v0[u], v[16 + u] = v1[u], v[32 + u] = v2[u];
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
           const int i = c0 + g + u;
@@ -246,12 +270,18 @@ __global__ void __launch_bounds__(kTcThreads, 7)
       tc_fence_before();
       __syncthreads();  // every warp has read TMEM before the next round overwrites it
     }
+    if (failed) break;
     const long row = row0 + tid;
-    if (!failed && row < n_poses) dist[row] = best;
+    if (row < n_poses) dist[row] = best;
   }
   if (failed) {
-    if (tid == 0) atomicOr(status, kDevErrTimeout);
-    // let the MMAs still in flight finish (bounded) before the accumulator is released
+    if (tid == 0) {
+      atomicOr(status, kDevErrTimeout);
+      // the bulk copies still in flight land before the shared memory is released (bounded)
+      for (long kk = k; kk < issued; ++kk)
+        mbar_wait_bounded(full + (int)(kk % kTcStages), (uint32_t)((kk / kTcStages) & 1), 1 << 24);
+    }
+    // and the MMAs still in flight finish before the accumulator is released (bounded)
     mbar_wait_bounded(bar, phase ^ 1u, 1 << 24);
   }
   tc_fence_before();
@@ -262,7 +292,8 @@ __global__ void __launch_bounds__(kTcThreads, 7)
 
 size_t tc_dist_smem(int n) {
   const int n_pad = (n + 15) & ~15;
-  return 2 * kTcTileBytes + 2 * 64 * (size_t)(3 * n_pad) + 4 * (size_t)n_pad + 64;
+  return kTcStages * kTcRawBytes + 2 * kTcTileBytes + 2 * 64 * (size_t)(3 * n_pad) + 4 * (size_t)n_pad +
+         8 * (1 + kTcStages) + 16;
 }
 
 cudaError_t launch_tc_dist(purse_t h, int passes, const float* d_poses, long n_poses, float* d_dist, cudaStream_t st) {
