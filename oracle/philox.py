@@ -17,7 +17,7 @@ two points of block 0 of stream (phase, b, i, w) (see hatbox_points);
 3 the random unit vector of init_angular_velocity, 4 that of
 init_center_velocity, 5 one RANSAG trial (w = trial index; j = 0 gives
 the three constraint indices, j = 1, 2, 3 the three points drawn inside
-the chosen noise balls).
+the chosen noise balls -- disks of pixels for 2D-3D, see disk_points).
 A batched PURSE p uses key = seed + p (mod 2^64).
 
 Perturbation points (phases 1, 2) use no rejection: point h of a block takes
@@ -131,6 +131,31 @@ def ball_points(seed: int, phase: int, j, i, w, unit: bool = False):
                 else:
                     val = Xa / 1024.0
                 pts[take] = val[take]
+                used[take] = a0 + a + 1
+                done |= take
+    return pts, used
+
+
+def disk_points(seed: int, phase: int, j, i, w):
+    """First accepted attempt of each stream in the unit disk: attempt a uses word a,
+    X = 2 (word & 1023) - 1023, Y = 2 ((word >> 10) & 1023) - 1023, accepted when
+    X^2 + Y^2 <= 2^20; the point is (X, Y) / 1024 (zero after MAX_ATTEMPTS rejections).
+
+    Returns (points float64 (..., 2), words_used int64 (...))."""
+    shape = np.broadcast_shapes(np.shape(j), np.shape(i), np.shape(w))
+    pts = np.zeros(shape + (2,))
+    used = np.full(shape, MAX_ATTEMPTS, dtype=np.int64)
+    done = np.zeros(shape, dtype=bool)
+    chunk = 8
+    for a0 in range(0, MAX_ATTEMPTS, chunk):
+        if done.all():
+            break
+        X = lattice_point(stream_words(seed, phase, j, i, w, chunk, start=a0))[..., :2]   # (..., chunk, 2)
+        ok = (X * X).sum(axis=-1) <= BALL_R2
+        for a in range(chunk):
+            take = ok[..., a] & ~done
+            if take.any():
+                pts[take] = (X[..., a, :].astype(np.float64) / 1024.0)[take]
                 used[take] = a0 + a + 1
                 done |= take
     return pts, used
