@@ -44,6 +44,11 @@ PURSE_SEED = 0
 FLOPS_DIST, FLOPS_INPURSE = 28, 24
 N_PERTURB, N_KEEP, N_STEPS = 150, 10, 15
 SM_COUNT_NOMINAL = 152
+# DRAM bytes (read + write) per launch of each walk kernel on this workload, from one ncu capture of the
+# full-size bench step: ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+# -k regex:walk_kernel -s 6 -c 2 python bench.py --steps 1 --warmup 3 --no-e2e --no-batch --no-cpu-baseline
+# --no-plain --no-grad (one pass).  Taken on the current kernels; a kernel change needs a new capture.
+WALK_DRAM_BYTES = {"R": None, "t": None}
 FP32_LANES_PER_SM = 128
 
 
@@ -289,7 +294,7 @@ def run_gpu(args, rank, world):
         "roofline": {"bound": "alu", "kernel": f"walk_kernel<float, 2D-3D, dS_{kern}>", "achieved": achieved,
                      "flops_per_eval": {"dist": FLOPS_DIST, "in_purse": FLOPS_INPURSE},
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                     "traffic": None,
+                     "traffic": WALK_DRAM_BYTES[kern], "traffic_unit": "bytes per launch",
                      "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz (max SM clock)"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": ck, "wall_s_timed": wall,

@@ -382,6 +382,69 @@ __device__ __forceinline__ P2<T> pr(T x, T y) {
   return P2<T>{x, y};
 }
 
+// The two perturbation quaternions of one Philox block -- points (words x, y) and (words z, w) of
+// hatbox_quat -- with the floating-point work on paired lanes (.x the first point, .y the second).
+template <typename T>
+__device__ __forceinline__ void hatbox_quat2(uint4 wd, T r, P2<T>& qw, P2<T>& qx, P2<T>& qy, P2<T>& qz) {
+  using T2 = P2<T>;
+  const T zz0 = T((int)(wd.x >> 16)) * T(1.0 / 32768) + T(0.5 / 32768 - 1.0);
+  const T zz1 = T((int)(wd.z >> 16)) * T(1.0 / 32768) + T(0.5 / 32768 - 1.0);
+  const T az0 = T((int)(wd.x & 0xFFFFu)) * T(1.0 / 32768) + T(0.5 / 32768);
+  const T az1 = T((int)(wd.z & 0xFFFFu)) * T(1.0 / 32768) + T(0.5 / 32768);
+  const uint32_t k0 = max(max(wd.y & 1023u, (wd.y >> 10) & 1023u), (wd.y >> 20) & 1023u);
+  const uint32_t k1 = max(max(wd.w & 1023u, (wd.w >> 10) & 1023u), (wd.w >> 20) & 1023u);
+  const T2 rho = fma2(pr(T((int)k0), T((int)k1)), dup(T(1.0 / 1024)), dup(T(0.5 / 1024)));
+  const T2 zz = pr(zz0, zz1);
+  const T2 c2 = fma2(pr(-zz0, -zz1), zz, dup(T(1)));  // >= 2^-15
+  T sp0, cp0, sp1, cp1;
+  T2 sq;
+  if constexpr (sizeof(T) == 4) {
+    __sincosf(3.14159265358979f * az0, &sp0, &cp0);
+    __sincosf(3.14159265358979f * az1, &sp1, &cp1);
+    sq = mul2(c2, rsq2(c2));
+  } else {
+    sin_cos_pi(az0, &sp0, &cp0);
+    sin_cos_pi(az1, &sp1, &cp1);
+    sq = pr(sqrt(c2.x), sqrt(c2.y));
+  }
+  const T2 x = mul2(dup(T(0.5) * r), rho);  // half angles
+  T2 sh, ch;
+  if (fabs(x.x) <= T(0.25) && fabs(x.y) <= T(0.25)) {  // Taylor series as in sincos_small
+    const T2 n2 = mul2(pr(-x.x, -x.y), x);
+    sh = mul2(x, fma2(n2, fma2(n2, fma2(n2, dup(T(1.0 / 5040)), dup(T(1.0 / 120))), dup(T(1.0 / 6))), dup(T(1))));
+    ch = fma2(n2, fma2(n2, fma2(n2, fma2(n2, dup(T(1.0 / 40320)), dup(T(1.0 / 720))), dup(T(1.0 / 24))),
+                       dup(T(0.5))),
+              dup(T(1)));
+  } else {
+    sincos_small(x.x, sh.x, ch.x);
+    sincos_small(x.y, sh.y, ch.y);
+  }
+  const T2 f = mul2(sh, sq);
+  qw = ch;
+  qx = mul2(f, pr(cp0, cp1));
+  qy = mul2(f, pr(sp0, sp1));
+  qz = mul2(sh, zz);
+}
+
+// Rotation matrices (row-major) of two unit quaternions on paired lanes.
+template <typename T>
+__device__ __forceinline__ void qmat2(P2<T> w, P2<T> x, P2<T> y, P2<T> z, P2<T> (&m)[9]) {
+  using T2 = P2<T>;
+  const T2 two = dup(T(2)), m2 = dup(T(-2)), one = dup(T(1));
+  const T2 xx = mul2(x, x), yy = mul2(y, y), zq = mul2(z, z);
+  const T2 xy = mul2(x, y), xz = mul2(x, z), yz = mul2(y, z);
+  const T2 nw = pr(-w.x, -w.y);
+  m[0] = fma2(m2, add2(yy, zq), one);
+  m[1] = mul2(two, fma2(nw, z, xy));
+  m[2] = mul2(two, fma2(w, y, xz));
+  m[3] = mul2(two, fma2(w, z, xy));
+  m[4] = fma2(m2, add2(xx, zq), one);
+  m[5] = mul2(two, fma2(nw, x, yz));
+  m[6] = mul2(two, fma2(nw, y, xz));
+  m[7] = mul2(two, fma2(w, x, yz));
+  m[8] = fma2(m2, add2(xx, yy), one);
+}
+
 // Float keys ordered like the values they encode (for warp max reductions).
 __device__ __forceinline__ uint32_t orderable(float f) {
   const uint32_t u = __float_as_uint(f);

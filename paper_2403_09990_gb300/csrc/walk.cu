@@ -166,49 +166,48 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
 #pragma unroll
   for (int p = 0; p < NPAIR; ++p) {
     T dx[2], dy[2], dz[2];
-    M3<T> Ah[2];
     const int b = 32 * (pb + p) + pl;
     uint4 wd = make_uint4(0u, 0u, 0u, 0u);
     if (2 * b < NP)
       wd = philox4x32_10_rk(make_uint4(0u, ((SAMPLER == 0 ? kPhaseRPerturb : kPhaseTPerturb) << 24) | (uint32_t)b,
                                        (uint32_t)it, (uint32_t)w),
                             rk);
+    if constexpr (SAMPLER == 1) {
+      // both rotations of the block at once on paired lanes: (K) R_p for the constraint loop
+      T2 qw, qx, qy, qz;
+      hatbox_quat2<T>(wd, r_pert, qw, qx, qy, qz);
+      qmat2<T>(qw, qx, qy, qz, A[p]);
+      if (KIND == 1) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+        for (int c = 0; c < 3; ++c) {
+          A[p][c] = fma2(dup(fx), A[p][c], mul2(dup(cx), A[p][6 + c]));
+          A[p][3 + c] = fma2(dup(fy), A[p][3 + c], mul2(dup(cy), A[p][6 + c]));
+        }
+      }
+      if (2 * b < NP) sl.P[2 * b] = T4<T>{qw.x, qx.x, qy.x, qz.x};
+      if (2 * b + 1 < NP) sl.P[2 * b + 1] = T4<T>{qw.y, qx.y, qy.y, qz.y};
+      Dx[p] = Dy[p] = Dz[p] = dup(T(0));
+      dmin[p] = dup(inf<T>());
+      zmin[p] = dup(inf<T>());
+      continue;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {  // dS_R: the translation offsets K delta_j
       const int j = 2 * b + h;
       dx[h] = dy[h] = dz[h] = T(0);
-      Ah[h] = M3<T>{{T(1), T(0), T(0), T(0), T(1), T(0), T(0), T(0), T(1)}};
       if (j < NP) {
-        if constexpr (SAMPLER == 0) {
-          T ux, uy, uz;
-          hatbox_point<T>(h ? wd.z : wd.x, h ? wd.w : wd.y, ux, uy, uz);
-          const V3<T> dl{r_pert * ux, r_pert * uy, r_pert * uz};
-          sl.P[j] = T4<T>{dl.x, dl.y, dl.z, T(0)};
-          if (KIND == 1) {
-            dx[h] = fx * dl.x + cx * dl.z, dy[h] = fy * dl.y + cy * dl.z, dz[h] = dl.z;
-          } else {
-            dx[h] = dl.x, dy[h] = dl.y, dz[h] = dl.z;
-          }
+        T ux, uy, uz;
+        hatbox_point<T>(h ? wd.z : wd.x, h ? wd.w : wd.y, ux, uy, uz);
+        const V3<T> dl{r_pert * ux, r_pert * uy, r_pert * uz};
+        sl.P[j] = T4<T>{dl.x, dl.y, dl.z, T(0)};
+        if (KIND == 1) {
+          dx[h] = fx * dl.x + cx * dl.z, dy[h] = fy * dl.y + cy * dl.z, dz[h] = dl.z;
         } else {
-          const Q4<T> pq = hatbox_quat<T>(h ? wd.z : wd.x, h ? wd.w : wd.y, r_pert);
-          sl.P[j] = T4<T>{pq.w, pq.x, pq.y, pq.z};
-          M3<T> Rp = qmat(pq);
-          if (KIND == 1) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              Rp.m[c] = fx * Rp.m[c] + cx * Rp.m[6 + c];
-              Rp.m[3 + c] = fy * Rp.m[3 + c] + cy * Rp.m[6 + c];
-            }
-          }
-          Ah[h] = Rp;
+          dx[h] = dl.x, dy[h] = dl.y, dz[h] = dl.z;
         }
       }
     }
     Dx[p] = pr(dx[0], dx[1]), Dy[p] = pr(dy[0], dy[1]), Dz[p] = pr(dz[0], dz[1]);
-    if constexpr (SAMPLER == 1) {
-#pragma unroll
-      for (int c = 0; c < 9; ++c) A[p][c] = pr(Ah[0].m[c], Ah[1].m[c]);
-    }
     dmin[p] = dup(inf<T>());
     zmin[p] = dup(inf<T>());
   }
