@@ -102,11 +102,16 @@ purse_status purse_eval(purse_t h, int precision, const void* d_poses, int n_pos
 purse_status purse_dist(purse_t h, int mode, const float* d_poses, long long n_poses, float* d_dist,
                         purse_stream_t stream);
 
-/* Step I for 3D-3D (Section IV, RANSAG): trials tau = 0..n_trials-1 each fit a pose to three
- * distinct constraints with one point drawn inside each noise ball (Arun's least-squares
- * rotation) and accept it if it lies in the PURSE.  The first max_seeds accepted poses in
- * trial order are written to d_seeds (device, max_seeds x 12 doubles); *n_seeds (host)
- * receives their count.  Synchronises the stream.  PURSE_ERR_EMPTY if none. */
+/* Step I (Section IV, RANSAG), FP64: trials tau = 0..n_trials-1 each pick three distinct
+ * constraints (multiply-shift of words 0-2 of Philox stream (5, 0, 0, tau)) and draw one point
+ * inside each noise region (stream (5, c, 0, tau), c = 1..3: lattice rejection in the ball for
+ * 3D-3D, in the disk of pixels for 2D-3D -- see purse_sample for the word layout).
+ * 3D-3D (Example 2): one pose fitted to the three pairs (least-squares rotation, Arun/Horn).
+ * 2D-3D (Example 1): the poses of the perspective-three-point problem on the three pixels (up to
+ * four; Grunert's quartic in the depth ratio, candidates in ascending order of its real roots).
+ * A candidate is accepted if it lies in the PURSE.  The first max_seeds accepted poses in
+ * (trial, candidate) order are written to d_seeds (device, max_seeds x 12 doubles); *n_seeds
+ * (host) receives their count.  Synchronises the stream.  PURSE_ERR_EMPTY if none. */
 purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds,
                           double* d_seeds, int* n_seeds, purse_stream_t stream);
 

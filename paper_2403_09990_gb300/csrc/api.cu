@@ -149,13 +149,13 @@ purse_status purse_dist(purse_t h, int mode, const float* d_poses, long long n_p
 purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds, double* d_seeds, int* n_seeds,
                           purse_stream_t stream) {
   if (!h) return arg_error("purse_ransag: NULL handle");
-  if (h->kind != PURSE_3D3D) return arg_error("purse_ransag: RANSAG is implemented for 3D-3D PURSEs");
   if (n_trials < 1 || max_seeds < 1) return arg_error("purse_ransag: n_trials and max_seeds must be >= 1");
   if (!d_seeds || !n_seeds) return arg_error("purse_ransag: NULL output");
   cudaStream_t st = (cudaStream_t)stream;
   const int chunk = 1 << 16;
-  const size_t pose_bytes = align256((size_t)chunk * 12 * sizeof(double));
-  const size_t acc_bytes = align256(chunk);
+  const int slots = h->kind == PURSE_3D3D ? 1 : 4;  // candidate poses per trial (P3P: up to four)
+  const size_t pose_bytes = align256((size_t)chunk * slots * 12 * sizeof(double));
+  const size_t acc_bytes = align256((size_t)chunk * slots);
   purse_status s = ensure_scratch(h, pose_bytes + acc_bytes + 256);
   if (s != PURSE_OK) return s;
   double* d_pose = reinterpret_cast<double*>(h->d_scratch);
@@ -165,8 +165,9 @@ purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds,
   int count = 0;
   for (int t0 = 0; t0 < n_trials && e == cudaSuccess; t0 += chunk) {
     const int nt = n_trials - t0 < chunk ? n_trials - t0 : chunk;
-    e = launch_ransag(h, seed, t0, nt, d_pose, d_acc, st);
-    if (e == cudaSuccess) e = launch_compact(d_pose, d_acc, nt, d_seeds, d_count, max_seeds, st);
+    e = h->kind == PURSE_3D3D ? launch_ransag(h, seed, t0, nt, d_pose, d_acc, st)
+                              : launch_ransag_p3p(h, seed, t0, nt, d_pose, d_acc, st);
+    if (e == cudaSuccess) e = launch_compact(d_pose, d_acc, nt * slots, d_seeds, d_count, max_seeds, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&count, d_count, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (count >= max_seeds) break;

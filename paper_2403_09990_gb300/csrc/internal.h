@@ -133,6 +133,8 @@ cudaError_t launch_megb_batch(const BatchArgs& b, int n_iters, double* d_results
                               cudaStream_t st);
 cudaError_t launch_ransag(purse_t h, uint64_t seed, int trial0, int n_trials, double* d_pose, uint8_t* d_acc,
                           cudaStream_t st);
+cudaError_t launch_ransag_p3p(purse_t h, uint64_t seed, int trial0, int n_trials, double* d_pose, uint8_t* d_acc,
+                              cudaStream_t st);
 cudaError_t launch_compact(const double* d_pose, const uint8_t* d_acc, int n_trials, double* d_seeds,
                            int* d_count, int max_seeds, cudaStream_t st);
 size_t plain_scratch_bytes(const purse_params* p, int n_samples, int* chunk);

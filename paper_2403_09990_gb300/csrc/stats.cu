@@ -234,6 +234,239 @@ cudaError_t launch_ransag(purse_t h, uint64_t seed, int trial0, int n_trials, do
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- RANSAG (2D-3D, P3P)
+// First accepted 2-D lattice point of the stream: X = 2 (word & 1023) - 1023,
+// Y = 2 ((word >> 10) & 1023) - 1023, accepted when X^2 + Y^2 <= 2^20 (zero after kMaxAttempts).
+__device__ __forceinline__ void disk_draw(Stream& s, int& x, int& y) {
+  for (int a = 0; a < kMaxAttempts; ++a) {
+    const uint32_t wd = s.next();
+    const int X = 2 * (int)(wd & 1023u) - 1023;
+    const int Y = 2 * (int)((wd >> 10) & 1023u) - 1023;
+    if (X * X + Y * Y <= (1 << 20)) {
+      x = X, y = Y;
+      return;
+    }
+  }
+  x = y = 0;
+}
+
+__device__ __forceinline__ double horner(const double* c, int deg, double x) {
+  double v = c[deg];
+  for (int k = deg - 1; k >= 0; --k) v = fma(v, x, c[k]);
+  return v;
+}
+
+// Real roots of c3 x^3 + c2 x^2 + c1 x + c0 (c3 != 0), Cardano's formula for one real root and
+// the trigonometric form for three, each polished by two Newton steps; ascending.
+__device__ int cubic_real_roots(double c3, double c2, double c1, double c0, double (&r)[3]) {
+  const double a = c2 / c3, b = c1 / c3, c = c0 / c3;
+  const double p = b - a * a / 3.0, q = 2.0 * a * a * a / 27.0 - a * b / 3.0 + c;
+  const double disc = q * q / 4.0 + p * p * p / 27.0;
+  int m;
+  if (disc > 0.0 || p == 0.0) {
+    const double sd = sqrt(fmax(disc, 0.0));
+    r[0] = cbrt(-q / 2.0 + sd) + cbrt(-q / 2.0 - sd) - a / 3.0;
+    m = 1;
+  } else {
+    const double s = 2.0 * sqrt(-p / 3.0);
+    const double arg = fmin(1.0, fmax(-1.0, (3.0 * q) / (p * s)));
+    const double phi = acos(arg) / 3.0;
+    for (int k = 0; k < 3; ++k) r[k] = s * cos(phi - 2.0943951023931957 * k) - a / 3.0;
+    m = 3;
+  }
+  const double cc[4] = {c0, c1, c2, c3}, dc[3] = {c1, 2.0 * c2, 3.0 * c3};
+  for (int k = 0; k < m; ++k)
+    for (int it = 0; it < 2; ++it) {
+      const double d = horner(dc, 2, r[k]);
+      if (d != 0.0) r[k] -= horner(cc, 3, r[k]) / d;
+    }
+  for (int i = 1; i < m; ++i)
+    for (int j = i; j > 0 && r[j] < r[j - 1]; --j) {
+      const double t = r[j];
+      r[j] = r[j - 1], r[j - 1] = t;
+    }
+  return m;
+}
+
+// Real roots of the quartic A (increasing powers, A[4] != 0), ascending: the critical points (roots
+// of the derivative) split [-B, B] (B = 1 + max |A_k / A_4|, Cauchy's bound) into intervals where A is
+// monotone; each interval with a sign change holds one root, found by Newton steps safeguarded by
+// bisection to full precision.  A double root without a sign change is not reported.
+__device__ int quartic_real_roots(const double (&A)[5], double (&out)[4]) {
+  double B = 0.0;
+  for (int k = 0; k < 4; ++k) B = fmax(B, fabs(A[k] / A[4]));
+  B += 1.0;
+  double cr[3];
+  const int m = cubic_real_roots(4.0 * A[4], 3.0 * A[3], 2.0 * A[2], A[1], cr);
+  double x[5];
+  int nx = 0;
+  x[nx++] = -B;
+  for (int k = 0; k < m; ++k)
+    if (cr[k] > -B && cr[k] < B) x[nx++] = cr[k];
+  x[nx++] = B;
+  const double dA[4] = {A[1], 2.0 * A[2], 3.0 * A[3], 4.0 * A[4]};
+  int nr = 0;
+  for (int k = 0; k + 1 < nx; ++k) {
+    double lo = x[k], hi = x[k + 1];
+    double flo = horner(A, 4, lo), fhi = horner(A, 4, hi);
+    if (flo == 0.0) {
+      if (nr == 0 || out[nr - 1] != lo) out[nr++] = lo;
+      continue;
+    }
+    if (fhi == 0.0 || (flo < 0.0) == (fhi < 0.0)) continue;  // the right end is the next interval's left end
+    if (flo > 0.0) {  // orient: A(lo) < 0 < A(hi)
+      const double t = lo;
+      lo = hi, hi = t;
+    }
+    double v = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {
+      const double fv = horner(A, 4, v);
+      if (fv == 0.0) break;
+      if (fv < 0.0) lo = v; else hi = v;
+      const double d = horner(dA, 3, v);
+      double vn = d != 0.0 ? v - fv / d : 0.5 * (lo + hi);
+      const double a0 = fmin(lo, hi), a1 = fmax(lo, hi);
+      if (!(vn > a0 && vn < a1)) vn = 0.5 * (lo + hi);
+      const bool done = fabs(vn - v) <= 1e-16 * fmax(1.0, fabs(v));
+      v = vn;
+      if (done) break;
+    }
+    out[nr++] = v;
+  }
+  return nr;
+}
+
+// One RANSAG trial of Step I for 2D-3D: three distinct constraints (index words as for 3D-3D), one
+// pixel uniform in each noise disk, bearings f_i = K^-1 (z_i, 1) / |.|, and P3P by Grunert's
+// elimination: the law of cosines on the triangle sides a = |P_2 - P_3|, b = |P_1 - P_3|,
+// c = |P_1 - P_2| with s_2 = u s_1, s_3 = v s_1 gives the quartic
+//   N(v)^2 - 2 cos(g) N(v) D(v) + (1 - (c^2 / b^2) Q(v)) D(v)^2 = 0,
+//   Q = 1 + v^2 - 2 v cos(b'), N = k Q + v^2 - 1, k = (c^2 - a^2) / b^2, D = 2 (v cos(a') - cos(g))
+// (a', b', g: the angles between bearings 2-3, 1-3, 1-2).  Per real root v (ascending):
+// s_1 = b / sqrt(Q(v)); u from u^2 - 2 cos(g) u + 1 - (c^2 / b^2) Q(v) = 0, each root kept when
+// u^2 + v^2 - 2 u v cos(a') = (a^2 / b^2) Q(v) holds to 1e-8 relative and every depth is positive;
+// the pose maps P_i onto s_i f_i (Horn's fit).  Candidate slot k of the trial holds the k-th pose
+// and acc = 1 when it lies in the PURSE (eq. 2/5, FP64).  Up to four slots per trial.
+__global__ void __launch_bounds__(128)
+    ransag_p3p_kernel(const double* tab, int n, double fx, double fy, double cx, double cy, uint32_t k0, uint32_t k1,
+                      int trial0, int n_trials, double* pose, uint8_t* acc) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= n_trials) return;
+  const uint32_t tau = (uint32_t)(trial0 + tid);
+  Stream s(k0, k1, kPhaseRansag, 0u, 0u, tau);
+  const uint32_t w0 = s.next(), w1 = s.next(), w2 = s.next();
+  uint32_t i1 = uniform_index(w0, n);
+  uint32_t i2 = uniform_index(w1, n - 1);
+  i2 += (i2 >= i1);
+  uint32_t i3 = uniform_index(w2, n - 2);
+  const uint32_t lo = min(i1, i2), hi = max(i1, i2);
+  i3 += (i3 >= lo);
+  i3 += (i3 >= hi);
+  const uint32_t idx[3] = {i1, i2, i3};
+  double P[3][3], f[3][3];
+  for (int c = 0; c < 3; ++c) {
+    Stream sc(k0, k1, kPhaseRansag, (uint32_t)(c + 1), 0u, tau);
+    int X, Y;
+    disk_draw(sc, X, Y);
+    const double* ai = tab + 4 * idx[c];
+    const double* bi = tab + 4 * (n + idx[c]);
+    const double r = ai[3];
+    P[c][0] = ai[0], P[c][1] = ai[1], P[c][2] = ai[2];
+    const double zx = bi[0] + r * (X / 1024.0), zy = bi[1] + r * (Y / 1024.0);
+    const double rx = (zx - cx) / fx, ry = (zy - cy) / fy;
+    const double nr = sqrt(rx * rx + ry * ry + 1.0);
+    f[c][0] = rx / nr, f[c][1] = ry / nr, f[c][2] = 1.0 / nr;
+  }
+  auto d2 = [&](int i, int j) {
+    double v = 0.0;
+    for (int k = 0; k < 3; ++k) v += (P[i][k] - P[j][k]) * (P[i][k] - P[j][k]);
+    return v;
+  };
+  auto dotf = [&](int i, int j) { return f[i][0] * f[j][0] + f[i][1] * f[j][1] + f[i][2] * f[j][2]; };
+  const double a2 = d2(1, 2), b2 = d2(0, 2), c2 = d2(0, 1), b = sqrt(b2);
+  const double ca = dotf(1, 2), cb = dotf(0, 2), cg = dotf(0, 1);
+  const double k = (c2 - a2) / b2;
+  const double Q[3] = {1.0, -2.0 * cb, 1.0};
+  const double N[3] = {k - 1.0, -2.0 * k * cb, k + 1.0};
+  const double D[2] = {-2.0 * cg, 2.0 * ca};
+  const double Rq[3] = {1.0 - (c2 / b2) * Q[0], -(c2 / b2) * Q[1], -(c2 / b2) * Q[2]};
+  double A[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) A[i + j] += N[i] * N[j];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 2; ++j) A[i + j] -= 2.0 * cg * N[i] * D[j];
+  double DD[3] = {D[0] * D[0], 2.0 * D[0] * D[1], D[1] * D[1]};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) A[i + j] += Rq[i] * DD[j];
+  double roots[4];
+  const int nroots = A[4] != 0.0 ? quartic_real_roots(A, roots) : 0;
+  int slot = 0;
+  double* o = pose + 48 * (size_t)tid;
+  uint8_t* ac = acc + 4 * (size_t)tid;
+  for (int q = 0; q < nroots && slot < 4; ++q) {
+    const double v = roots[q];
+    const double Qv = horner(Q, 2, v);
+    if (!(Qv > 0.0)) continue;
+    const double disc = cg * cg - 1.0 + (c2 / b2) * Qv;
+    if (disc < -1e-12) continue;
+    const double r = sqrt(fmax(disc, 0.0));
+    for (int h = 0; h < (r > 0.0 ? 2 : 1) && slot < 4; ++h) {
+      const double u = h == 0 ? cg - r : cg + r;
+      if (fabs(u * u + v * v - 2.0 * u * v * ca - (a2 / b2) * Qv) > 1e-8 * (1.0 + u * u + v * v)) continue;
+      const double s1 = b / sqrt(Qv);
+      const double sd[3] = {s1, u * s1, v * s1};
+      if (!(sd[0] > 0.0 && sd[1] > 0.0 && sd[2] > 0.0)) continue;
+      double B3[3][3], pbar[3], xbar[3];
+      for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d) B3[c][d] = sd[c] * f[c][d];
+      for (int d = 0; d < 3; ++d) {
+        pbar[d] = (P[0][d] + P[1][d] + P[2][d]) / 3.0;
+        xbar[d] = (B3[0][d] + B3[1][d] + B3[2][d]) / 3.0;
+      }
+      double M[9];  // sum (x - xbar)(p - pbar)^T
+      for (int rr = 0; rr < 3; ++rr)
+        for (int cc = 0; cc < 3; ++cc) {
+          double acc_m = 0.0;
+          for (int kk = 0; kk < 3; ++kk) acc_m += (B3[kk][rr] - xbar[rr]) * (P[kk][cc] - pbar[cc]);
+          M[3 * rr + cc] = acc_m;
+        }
+      const M3<double> R = qmat(rotation_maximising_trace(M));
+      double t[3];
+      for (int rr = 0; rr < 3; ++rr)
+        t[rr] = xbar[rr] - (R.m[3 * rr] * pbar[0] + R.m[3 * rr + 1] * pbar[1] + R.m[3 * rr + 2] * pbar[2]);
+      bool ok = true;
+      for (int i = 0; i < n && ok; ++i) {
+        const double* ai = tab + 4 * i;
+        const double* bi = tab + 4 * (n + i);
+        const double X0 = R.m[0] * ai[0] + R.m[1] * ai[1] + R.m[2] * ai[2] + t[0];
+        const double X1 = R.m[3] * ai[0] + R.m[4] * ai[1] + R.m[5] * ai[2] + t[1];
+        const double X2 = R.m[6] * ai[0] + R.m[7] * ai[1] + R.m[8] * ai[2] + t[2];
+        if (!(X2 > 0.0)) {
+          ok = false;
+        } else {
+          const double gu = bi[0] - (fx * X0 / X2 + cx), gv = bi[1] - (fy * X1 / X2 + cy);
+          ok = ai[3] - sqrt(gu * gu + gv * gv) >= 0.0;
+        }
+      }
+      double* os = o + 12 * slot;
+      for (int kk = 0; kk < 9; ++kk) os[kk] = R.m[kk];
+      for (int rr = 0; rr < 3; ++rr) os[9 + rr] = t[rr];
+      ac[slot] = ok ? 1 : 0;
+      ++slot;
+    }
+  }
+  for (; slot < 4; ++slot) ac[slot] = 0;
+}
+
+cudaError_t launch_ransag_p3p(purse_t h, uint64_t seed, int trial0, int n_trials, double* d_pose, uint8_t* d_acc,
+                              cudaStream_t st) {
+  const int threads = 128;
+  ransag_p3p_kernel<<<(n_trials + threads - 1) / threads, threads, 0, st>>>(
+      h->tables.f64, h->n, h->K.fx, h->K.fy, h->K.cx, h->K.cy, (uint32_t)seed, (uint32_t)(seed >> 32), trial0,
+      n_trials, d_pose, d_acc);
+  return cudaGetLastError();
+}
+
 // In-order compaction of accepted trials: appends to d_seeds after *d_count entries.
 __global__ void __launch_bounds__(1024)
     compact_kernel(const double* pose, const uint8_t* acc, int n_trials, double* seeds, int* count, int max_seeds) {
