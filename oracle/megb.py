@@ -10,8 +10,13 @@
   of Section II.
 * megb_translation: the Euclidean version (Badoiu-Clarkson,
   c_k = c_{k-1} + (t_far - c_{k-1}) / k).
-* welzl_meb / meb_bruteforce: exact minimum enclosing ball in R^d (Step III
-  uses Gaertner's exact miniball; here it is a pin only).
+* welzl_meb / meb_bruteforce: exact minimum enclosing ball in R^d.
+* meb_exact_translation / meb_exact_rotation: Step III as the paper states it
+  (Section IV, Step III): the exact minimum enclosing ball of the translation
+  samples in R^3, and of the rotation samples embedded as unit quaternions in
+  R^4 (signs aligned to a reference rotation, the quaternion of each rotation
+  on the reference's side), its centre projected back to the unit sphere and
+  the radius taken as the largest geodesic distance from that centre.
 Ties in the farthest point go to the lowest sample index.
 
 Parity: pinned in tests/test_oracle_megb.py (rectangle corners, points on one
@@ -132,3 +137,20 @@ def welzl_meb(P):
 
     order = list(np.random.default_rng(0).permutation(P.shape[0]))
     return mtf(order, [])
+
+
+def meb_exact_translation(ts):
+    """(centre, radius) of the exact minimum enclosing ball of the translations in R^3."""
+    ts = np.asarray(ts, dtype=np.float64)
+    c, _ = welzl_meb(ts)
+    return c, float(np.linalg.norm(ts - c, axis=1).max())
+
+
+def meb_exact_rotation(qs, ref):
+    """(centre quaternion with w >= 0, geodesic radius) from the exact minimum enclosing ball of the
+    unit quaternions in R^4, each taken with the sign that puts it on the side of ``ref``."""
+    qs = np.asarray(qs, dtype=np.float64)
+    s = np.where(qs @ np.asarray(ref, dtype=np.float64) < 0, -1.0, 1.0)
+    c4, _ = welzl_meb(qs * s[:, None])
+    C = canonical(c4)
+    return C, float(rotation_distances(C, qs).max())

@@ -109,3 +109,52 @@ def test_replay_reproduces_free_run():
     ts = rng.normal(size=(100, 3))
     c, d, g = megb.megb_translation(ts, 50)
     assert np.allclose(megb.megb_translation_replay(ts, g)[-1], c, atol=1e-15)
+
+
+def test_exact_translation_ball_closed_forms_and_jung():
+    # rectangle corners: the circumcircle; random clouds: brute force, diam/2 <= r <= diam sqrt(3/8)
+    w, h = 2.0, 0.5
+    P = np.array([[0, 0, 0], [w, 0, 0], [0, h, 0], [w, h, 0]], float) - 1.0
+    c, r = megb.meb_exact_translation(P)
+    assert np.allclose(c, [w / 2 - 1, h / 2 - 1, -1]) and abs(r - 0.5 * np.hypot(w, h)) < 1e-12
+    for _ in range(5):
+        P = rng.normal(size=(10, 3)) * np.array([0.01, 0.03, 0.02])
+        c, r = megb.meb_exact_translation(P)
+        c2, r2 = megb.meb_bruteforce(P)
+        assert abs(r - r2) < 1e-12 and np.allclose(c, c2, atol=1e-10)
+        diam = max(np.linalg.norm(P - p, axis=1).max() for p in P)
+        assert diam / 2 - 1e-15 <= r <= diam * np.sqrt(3 / 8) + 1e-15
+
+
+def test_exact_rotation_ball_closed_forms():
+    C0 = so3.quat_from_R(so3.exp_so3(rng.normal(size=3)))
+    # six rotations Exp(+-theta e_k) C0 plus interior ones: centre C0, radius theta (by symmetry)
+    theta = 0.3
+    axes = np.concatenate([np.eye(3), -np.eye(3)])
+    qs = so3.quat_mul(so3.quat_exp(theta * axes), C0[None])
+    qs = np.concatenate([qs, so3.quat_mul(so3.quat_exp(rng.normal(size=(40, 3)) * 0.02), C0[None])])
+    C, D = megb.meb_exact_rotation(qs, qs[0])
+    assert so3.dist_quat(C, C0) < 1e-10 and abs(D - theta) < 1e-10
+    # samples along one geodesic: the middle of the arc, half its length
+    u = rng.normal(size=3)
+    u /= np.linalg.norm(u)
+    ang = rng.uniform(-0.5, 0.8, 200)
+    qs = so3.quat_mul(so3.quat_exp(ang[:, None] * u), C0[None])
+    C, D = megb.meb_exact_rotation(qs, qs[0])
+    mid, half = 0.5 * (ang.max() + ang.min()), 0.5 * (ang.max() - ang.min())
+    assert so3.dist_quat(C, so3.quat_mul(so3.quat_exp(mid * u), C0)) < 1e-9 and abs(D - half) < 1e-10
+
+
+def test_exact_rotation_ball_sign_and_left_invariance():
+    C0 = so3.quat_from_R(so3.exp_so3(rng.normal(size=3)))
+    qs = so3.quat_mul(so3.quat_exp(rng.normal(size=(300, 3)) * np.array([0.03, 0.05, 0.1])), C0[None])
+    C, D = megb.meb_exact_rotation(qs, qs[0])
+    flip = qs * np.where(rng.random(len(qs)) < 0.5, -1.0, 1.0)[:, None]
+    C2, D2 = megb.meb_exact_rotation(flip, qs[5])
+    assert so3.dist_quat(C, C2) < 1e-12 and abs(D - D2) < 1e-12
+    G = so3.quat_from_R(so3.exp_so3(rng.normal(size=3)))
+    C3, D3 = megb.meb_exact_rotation(so3.quat_mul(G[None], qs), G)
+    assert so3.dist_quat(C3, so3.quat_mul(G, C)) < 1e-10 and abs(D3 - D) < 1e-12
+    # never worse than the geodesic-descent ball by more than its (1 + 1/sqrt K) bound
+    Cg, Dg, _ = megb.megb_rotation(qs, 400)
+    assert D <= Dg * (1 + 1e-9) and Dg <= D * (1 + 1 / np.sqrt(400))
