@@ -299,6 +299,7 @@ def run_gpu(args, rank, world):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": ck, "wall_s_timed": wall,
     }
+    out["megb_exact"] = run_exact(hR, qR, tT, res, dev)
     if not args.no_plain:
         out["plain_gpu"] = run_plain(args, p, dev, seeds, value / world, t_step)
     if rank == 0 and not args.no_e2e:
@@ -319,6 +320,31 @@ def run_gpu(args, rank, world):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def run_exact(h, qR, tT, res, dev):
+    """Step III exactly (the miniball of the last step's samples: translations in R^3, rotations as
+    quaternions in R^4 on the side of the descent centre) beside the geodesic-descent balls of the step;
+    CUDA events around the call (it reads a flag from the device every eight passes)."""
+    import torch
+    import paper_2403_09990_gb300.purse as P
+    stream = torch.cuda.current_stream()
+    ggd = res.clone()
+    out = torch.empty(9, dtype=torch.float64, device=dev)
+    times = []
+    for r in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.megb_solve_exact(h.h, 0, qR, N_WALKS, tT, N_WALKS, out, ggd[:4].contiguous(), stream)
+        e1.record(stream)
+        P.purse_sync(h.h, stream)
+        if r:
+            times.append(e0.elapsed_time(e1))
+    g, x = ggd.cpu().numpy(), out.cpu().numpy()
+    return {"ms": statistics.median(times), "D_exact": float(x[7]), "d_exact": float(x[8]),
+            "D_descent": float(g[7]), "d_descent": float(g[8]),
+            "descent_over_exact": {"D": float(g[7] / x[7]), "d": float(g[8] / x[8])},
+            "samples": N_WALKS, "K_descent": K_MEGB}
 
 
 def run_plain(args, p, dev, seeds, fused_value, fused_step_s):

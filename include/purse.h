@@ -200,6 +200,22 @@ purse_status megb_backward(purse_t h, int precision, int n_iters, const void* d_
                            const double* d_grad_result, double* d_grad_obs, double* d_grad_radii,
                            purse_stream_t stream);
 
+/* Step III exactly as the paper states it (Section IV, Step III, the miniball of the samples):
+ * the exact minimum enclosing ball of the n_tr translations d_t (n_tr x 3) in R^3, and of the
+ * n_rot rotations d_q (n_rot x 4, unit quaternions) embedded in R^4 -- each quaternion taken on
+ * the side of the reference rotation d_ref (device, 4 doubles; NULL: the first rotation sample)
+ * -- whose centre is projected back to the unit sphere.  Output d_result (device, 9 doubles,
+ * the layout of megb_solve): centre quaternion (w >= 0), centre translation, the largest
+ * geodesic distance D from that rotation centre and the largest distance d from the
+ * translation centre (0 for an empty set).  Method: a candidate set grown by the farthest
+ * sample outside the exact ball of the candidates (FP64 passes over all samples, Welzl's
+ * recursion on the candidates) until no sample lies outside (relative 1e-12); at most 96
+ * candidates, beyond which the ball of the candidates is returned and PURSE_ERR_NUMERIC is
+ * flagged for the next purse_sync.  Synchronises the stream (it reads a flag every eight
+ * passes).  Uses handle-owned scratch. */
+purse_status megb_solve_exact(purse_t h, int precision, const void* d_q, int n_rot, const void* d_t,
+                              int n_tr, const double* d_ref, double* d_result, purse_stream_t stream);
+
 /* megb_solve without any device allocation, for callers that must not allocate device memory
  * once they are running: real-time perception loops that reserve all memory at start-up
  * (cudaMalloc / cudaFree can synchronise the device and take unbounded time), and hosts whose

@@ -309,6 +309,19 @@ purse_status megb_solve(purse_t h, int precision, int n_iters, const void* d_q, 
   return PURSE_OK;
 }
 
+purse_status megb_solve_exact(purse_t h, int precision, const void* d_q, int n_rot, const void* d_t, int n_tr,
+                              const double* d_ref, double* d_result, purse_stream_t stream) {
+  if (!h) return arg_error("megb_solve_exact: NULL handle");
+  if (precision != 0 && precision != 1) return arg_error("megb_solve_exact: precision must be 0 or 1");
+  if (n_rot < 0 || n_tr < 0) return arg_error("megb_solve_exact: negative sample count");
+  if ((n_rot > 0 && !d_q) || (n_tr > 0 && !d_t) || !d_result) return arg_error("megb_solve_exact: NULL buffer");
+  purse_status s = ensure_scratch(h, exact_scratch_bytes(h->sm_count));
+  if (s != PURSE_OK) return s;
+  cudaError_t e = launch_megb_exact(h, precision, d_q, n_rot, d_t, n_tr, d_ref, d_result, h->d_scratch,
+                                    (cudaStream_t)stream);
+  return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "megb_solve_exact");
+}
+
 purse_status megb_backward(purse_t h, int precision, int n_iters, const void* d_q, const void* d_snap_rot, int n_rot,
                            const void* d_t, const void* d_snap_tr, int n_tr, const int32_t* d_farthest,
                            const double* d_result, const double* d_grad_result, double* d_grad_obs,

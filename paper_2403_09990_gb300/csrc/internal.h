@@ -150,6 +150,9 @@ cudaError_t launch_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t
 size_t megb_scratch_bytes(int n_iters, int sm_count);
 cudaError_t launch_megb(purse_t h, int precision, int n_iters, const void* d_q, int n_rot, const void* d_t,
                         int n_tr, double* d_result, int32_t* d_farthest, void* scratch, cudaStream_t st);
+size_t exact_scratch_bytes(int sm_count);
+cudaError_t launch_megb_exact(purse_t h, int precision, const void* d_q, long n_rot, const void* d_t, long n_tr,
+                              const double* d_ref, double* d_result, void* scratch, cudaStream_t st);
 size_t megb_backward_scratch_bytes(int n_iters, int sm_count, int n);
 cudaError_t launch_batch_backward(const BatchArgs& b, int n_iters, const int32_t* d_far, const double* d_results,
                                   const double* d_grad_results, void* d_cs, double* d_grad_obs, double* d_grad_radii,

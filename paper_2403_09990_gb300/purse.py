@@ -56,6 +56,7 @@ _SIGS = {
     "megb_solve": [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP],
     "megb_backward": [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP, _VP,
                       _VP, _VP, _VP, _VP],
+    "megb_solve_exact": [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP],
     "megb_solve_noalloc": [ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP],
     "purse_rng_words": [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                         ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP],
@@ -181,6 +182,11 @@ def megb_backward(h, precision, n_iters, q, snap_rot, n_rot, t, snap_tr, n_tr, f
     _check(lib().megb_backward(h, precision, n_iters, _ptr(q), _ptr(snap_rot), n_rot, _ptr(t), _ptr(snap_tr), n_tr,
                                _ptr(farthest), _ptr(result), _ptr(grad_result), _ptr(grad_obs), _ptr(grad_radii),
                                _stream(stream)), "megb_backward")
+
+
+def megb_solve_exact(h, precision, q, n_rot, t, n_tr, result, ref=None, stream=None):
+    _check(lib().megb_solve_exact(h, precision, _ptr(q), n_rot, _ptr(t), n_tr, _ptr(ref), _ptr(result),
+                                  _stream(stream)), "megb_solve_exact")
 
 
 def megb_solve_noalloc(precision, n_iters, q, n_rot, t, n_tr, result, farthest=None, stream=None):
