@@ -18,8 +18,11 @@ Readings of the paper used here (each listed in the design doc):
   (hat-box direction, radius whose cube is uniform; oracle.philox),
   perturbation(theta_p) is Exp of a vector uniform in the ball of radius
   theta_p * sigma_t / rho_a, where sigma_t is the PURSE translation scale
-  (mean r_i for 3D-3D, mean r_i * t-bar_z / f for 2D-3D) and rho_a the RMS
-  spread of the model points; ``perturb_units = 1`` uses t_p, theta_p raw.
+  (mean r_i for 3D-3D, mean r_i * t-bar_z / f for 2D-3D, mean beta_i^t for
+  pose regression) and rho_a the RMS spread of the model points (pose
+  regression: sigma_t sqrt(2) / mean beta_i^R, so that the rotation radius is
+  theta_p times the angle scale of the rotation balls); ``perturb_units = 1``
+  uses t_p, theta_p raw.
 * Ties in top_k_indices go to the lower index; k0 is the best-ranked
   feasible k at m0; when nothing is feasible the walk keeps its pose.
 * u = 0 when the angle of R_0 R-bar^T is <= 1e-9 rad, the direction term of
@@ -43,7 +46,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import philox
-from .purse import KIND_2D3D, KIND_3D3D, dist_to_boundary, in_purse
+from .purse import KIND_2D3D, KIND_3D3D, KIND_REG, dist_to_boundary, in_purse
 from .so3 import exp_so3, log_so3, proj_so3, quat_from_R
 
 
@@ -81,6 +84,16 @@ def preset_3d3d(**kw) -> Params:
     return p
 
 
+def preset_reg(**kw) -> Params:
+    """LM (pose regression) setting of Section V-C: N_W = 20, N_I = 5, N_T = 10, no rotation
+    perturbation, no centre velocity."""
+    p = Params(n_walk=20, n_iter=5, n_perturb=150, n_keep=10, n_steps=10, omega0=0.5, v0=0.0,
+               gamma=0.5, rot_perturb=0.0, trans_perturb=0.1)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
 def unpack_seeds(seeds):
     seeds = np.asarray(seeds, dtype=np.float64).reshape(-1, 12)
     return seeds[:, :9].reshape(-1, 3, 3), seeds[:, 9:]
@@ -103,7 +116,14 @@ def center_stats(purse, seeds, params: Params) -> Stats:
     tbar = t0.mean(axis=0)
     a = purse.model
     rho_a = float(np.sqrt(((a - a.mean(axis=0)) ** 2).sum(axis=1).mean()))
-    if purse.kind == KIND_3D3D:
+    if purse.kind == KIND_REG:
+        # translation scale mean beta^t; rotation scale mean beta^R / sqrt(2), the angle of a
+        # Frobenius distance (|R - R'|_F = 2 sqrt(2) sin(theta / 2) ~ sqrt(2) theta); written through
+        # rho_a so that r_rot = theta_p sigma_t / rho_a is that angle scale times theta_p
+        sigma_t = float(purse.radii.mean())
+        rho_a = float(sigma_t * np.sqrt(2.0) / purse.radii_rot.mean())
+        S = np.eye(3)
+    elif purse.kind == KIND_3D3D:
         sigma_t = float(purse.radii.mean())
         S = np.eye(3)
     else:

@@ -7,6 +7,10 @@
 * PURSE (eq. 5) with Lambda_i = I, beta_i = r_i: all |g_i| <= r_i.
 * margins r_i - |g_i| (-inf behind the camera) and dist(R, t, dS) =
   min_i margins (eq. 11).
+* pose regression (Example 3, eq. PURSEreg): per hypothesis (R_i, t_i) two
+  constraints, |vec(R) - vec(R_i)| <= beta_i^R (Frobenius) and
+  |t - t_i| <= beta_i^t; the margins are the N rotation margins followed by
+  the N translation margins.
 * SE(3) gradient of h_i = |g_i| under the world-frame left perturbation
   R <- Exp(phi) R, t <- t + rho, returned as d h_i / d(phi, rho) (6 values).
 Pinned in tests/test_oracle_purse.py against a direct scalar restatement of
@@ -18,6 +22,7 @@ import numpy as np
 
 KIND_3D3D = 0
 KIND_2D3D = 1
+KIND_REG = 2
 
 
 def transform(model, R, t):
@@ -43,7 +48,18 @@ def residual_norms(purse, R, t):
 
 
 def margins(purse, R, t):
-    """r_i - |g_i|, -inf for keypoints behind the camera."""
+    """r_i - |g_i|, -inf for keypoints behind the camera; for a regression PURSE the 2N margins
+    beta_i^R - |R - R_i|_F, then beta_i^t - |t - t_i|."""
+    if purse.kind == KIND_REG:
+        R = np.asarray(R, dtype=np.float64)
+        t = np.asarray(t, dtype=np.float64)
+        dR = np.sqrt(((R[..., None, :, :] - purse.rot_hyp) ** 2).sum(axis=(-2, -1)))
+        dt = np.linalg.norm(t[..., None, :] - purse.obs, axis=-1)
+        mR, mt = purse.radii_rot - dR, purse.radii - dt
+        lead = np.broadcast_shapes(mR.shape[:-1], mt.shape[:-1])
+        mR = np.broadcast_to(mR, lead + mR.shape[-1:])
+        mt = np.broadcast_to(mt, lead + mt.shape[-1:])
+        return np.concatenate([mR, mt], axis=-1)
     h, front = residual_norms(purse, R, t)
     return np.where(front, purse.radii - h, -np.inf)
 

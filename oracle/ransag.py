@@ -10,9 +10,16 @@ most ``max_seeds`` of them, from ``n_trials`` trials.
 Random draws: trial tau uses the Philox streams (phase 5, j, 0, tau) of
 oracle.philox; j = 0 gives the index triple, j = 1..3 the ball points.
 
+Step I for pose regression (Example 3, the convex-combination sampler):
+trial tau draws weights uniform on the simplex, w_i = e_i / sum_j e_j with
+e_i = -log u_i and u_i = ((word_i >> 8) + 1/2) 2^-24 from words 0..N-1 of
+stream (5, 0, 0, tau), and forms the pose t = sum w_i t_i,
+R = proj_SO3(sum w_i R_i); it is kept if it lies in the PURSE.
+
 Parity: pinned in tests/test_oracle_ransag.py (exact recovery of a
 noise-free pose, least-squares optimality of the fitted rotation, every
-accepted seed inside the PURSE).
+accepted seed inside the PURSE) and tests/test_oracle_reg.py (simplex
+weights, seeds inside the regression PURSE).
 """
 from __future__ import annotations
 
@@ -20,6 +27,7 @@ import numpy as np
 
 from . import philox
 from .purse import in_purse
+from .so3 import proj_so3
 
 
 def arun(A, B):
@@ -59,6 +67,38 @@ def ransag_3d3d(purse, seed: int, n_trials: int, max_seeds: int, chunk: int = 1 
     for start in range(0, n_trials, chunk):
         tau = np.arange(start, min(n_trials, start + chunk))
         R, t, ok, _ = ransag_trials(purse, seed, tau)
+        for n in np.nonzero(ok)[0]:
+            if len(seeds) == max_seeds:
+                break
+            seeds.append(np.concatenate([R[n].reshape(9), t[n]]))
+            acc.append(int(tau[n]))
+        if len(seeds) == max_seeds:
+            break
+    return np.array(seeds).reshape(-1, 12), np.array(acc, dtype=np.int64)
+
+
+def simplex_weights(seed: int, trials, n: int):
+    """Weights (T, n) uniform on the simplex for the trials (Dirichlet(1, ..., 1) by -log u)."""
+    words = philox.stream_words(seed, philox.PHASE_RANSAG, 0, 0, np.asarray(trials, np.int64), n)
+    u = ((words >> np.uint64(8)).astype(np.float64) + 0.5) * 2.0 ** -24
+    e = -np.log(u)
+    return e / e.sum(axis=-1, keepdims=True)
+
+
+def convex_trials(purse, seed: int, trials):
+    """Candidate pose and acceptance of each trial of the convex-combination sampler."""
+    w = simplex_weights(seed, trials, purse.n)
+    t = w @ purse.obs
+    R = proj_so3(np.einsum('tn,nij->tij', w, purse.rot_hyp))
+    return R, t, in_purse(purse, R, t)
+
+
+def convex_seeds(purse, seed: int, n_trials: int, max_seeds: int, chunk: int = 1 << 14):
+    """S0 of a regression PURSE as an (n, 12) array and the accepted trial indices."""
+    seeds, acc = [], []
+    for start in range(0, n_trials, chunk):
+        tau = np.arange(start, min(n_trials, start + chunk))
+        R, t, ok = convex_trials(purse, seed, tau)
         for n in np.nonzero(ok)[0]:
             if len(seeds) == max_seeds:
                 break

@@ -21,6 +21,16 @@ instances stand in for them with the sizes of the published settings:
   estimation, Example 1).
 * ``purse_octahedron`` -- noise-free 3D-3D instance with model points at
   L * (+-e_x, +-e_y, +-e_z) and equal radii; its ball radii have a closed form.
+* ``purse_reg`` -- pose-regression PURSE (Example 3): ten pose hypotheses
+  (R_i, t_i) scattered around a ground-truth pose (rotation noise of about
+  0.03 rad, translation noise of about 0.01 m, the LM setting's ten hypotheses)
+  with radii beta_i^R (Frobenius distance of rotation matrices) and beta_i^t
+  (metres) each exceeding the hypothesis' distance to the ground truth by a
+  random slack, so the ground truth lies in the PURSE.
+* ``purse_reg_nested`` -- a regression PURSE whose first hypothesis is the
+  ground truth with the smallest balls, each contained in every other
+  hypothesis' ball: the PURSE is then that pair of balls and its geodesic balls
+  are known in closed form.
 
 All randomness comes from ``numpy.random.default_rng(seed)``.
 """
@@ -32,19 +42,22 @@ import numpy as np
 
 KIND_3D3D = 0
 KIND_2D3D = 1
+KIND_REG = 2
 
 
 @dataclass
 class Purse:
     """One PURSE instance (eq. 5 with Lambda_i = I and beta_i = r_i)."""
 
-    kind: int                      # KIND_3D3D or KIND_2D3D
-    model: np.ndarray              # (N, 3) a_i (3D-3D) or Z_i (2D-3D), float64
-    obs: np.ndarray                # (N, 3) b_i or (N, 2) pixel z_i, float64
-    radii: np.ndarray              # (N,) r_i > 0, float64
-    K: tuple | None = None         # (fx, fy, cx, cy) for 2D-3D, None for 3D-3D
+    kind: int                      # KIND_3D3D, KIND_2D3D or KIND_REG
+    model: np.ndarray              # (N, 3) a_i (3D-3D) or Z_i (2D-3D); zeros for KIND_REG
+    obs: np.ndarray                # (N, 3) b_i, (N, 2) pixel z_i, or (N, 3) hypotheses t_i (KIND_REG)
+    radii: np.ndarray              # (N,) r_i > 0 (KIND_REG: beta_i^t)
+    K: tuple | None = None         # (fx, fy, cx, cy) for 2D-3D, None otherwise
     R_gt: np.ndarray = field(default_factory=lambda: np.eye(3))
     t_gt: np.ndarray = field(default_factory=lambda: np.zeros(3))
+    rot_hyp: np.ndarray | None = None    # (N, 3, 3) hypotheses R_i (KIND_REG)
+    radii_rot: np.ndarray | None = None  # (N,) beta_i^R, Frobenius distance (KIND_REG)
 
     @property
     def n(self) -> int:
@@ -115,6 +128,41 @@ def purse_octahedron(L: float = 0.1, r: float = 0.01, seed: int = 0) -> Purse:
     t = rng.uniform(-0.5, 0.5, 3)
     b = a @ R.T + t
     return Purse(KIND_3D3D, a, b, np.full(6, r), None, R, t)
+
+
+def _rotation_exp(v: np.ndarray) -> np.ndarray:
+    """Rotation matrices exp([v]x) of rotation vectors v (..., 3) (Rodrigues' formula)."""
+    v = np.asarray(v, dtype=np.float64)
+    th = np.linalg.norm(v, axis=-1)[..., None, None]
+    k = v / np.where(th[..., 0] > 0, th[..., 0], 1.0)
+    Kx = np.zeros(v.shape[:-1] + (3, 3))
+    Kx[..., 0, 1], Kx[..., 0, 2], Kx[..., 1, 2] = -k[..., 2], k[..., 1], -k[..., 0]
+    Kx = Kx - np.swapaxes(Kx, -1, -2)
+    return np.eye(3) + np.sin(th) * Kx + (1.0 - np.cos(th)) * (Kx @ Kx)
+
+
+def purse_reg(n: int = 10, seed: int = 0, rot_sigma: float = 0.03, t_sigma: float = 0.01,
+              slack_rot: tuple = (0.01, 0.04), slack_t: tuple = (0.003, 0.012)) -> Purse:
+    rng = np.random.default_rng(seed)
+    R = _random_rotation(rng)
+    t = rng.uniform(-0.3, 0.3, 3) + np.array([0.0, 0.0, 1.0])
+    Ri = _rotation_exp(rng.normal(size=(n, 3)) * rot_sigma) @ R
+    ti = t + rng.normal(size=(n, 3)) * t_sigma
+    bR = np.linalg.norm((Ri - R).reshape(n, 9), axis=1) + rng.uniform(*slack_rot, n)
+    bt = np.linalg.norm(ti - t, axis=1) + rng.uniform(*slack_t, n)
+    return Purse(KIND_REG, np.zeros((n, 3)), ti, bt, None, R, t, Ri, bR)
+
+
+def purse_reg_nested(n: int = 10, seed: int = 0, beta_rot: float = 0.04, beta_t: float = 0.006) -> Purse:
+    """Hypothesis 0 = ground truth with radii (beta_rot, beta_t); every other hypothesis' radii exceed
+    its distance to hypothesis 0 plus those radii, so its balls contain hypothesis 0's."""
+    p = purse_reg(n, seed)
+    Ri, ti = p.rot_hyp.copy(), p.obs.copy()
+    Ri[0], ti[0] = p.R_gt, p.t_gt
+    bR = np.linalg.norm((Ri - Ri[0]).reshape(n, 9), axis=1) + beta_rot + 0.01
+    bt = np.linalg.norm(ti - ti[0], axis=1) + beta_t + 0.002
+    bR[0], bt[0] = beta_rot, beta_t
+    return Purse(KIND_REG, np.zeros((n, 3)), ti, bt, None, p.R_gt, p.t_gt, Ri, bR)
 
 
 def purse_batch(n_purses: int = 4096, seed: int = 0, n_lo: int = 4, n_hi: int = 64) -> list[Purse]:
