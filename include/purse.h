@@ -39,7 +39,7 @@ extern "C" {
 typedef struct purse_s* purse_t;
 typedef void* purse_stream_t;
 
-typedef enum { PURSE_3D3D = 0, PURSE_2D3D = 1 } purse_kind;
+typedef enum { PURSE_3D3D = 0, PURSE_2D3D = 1, PURSE_REG = 2 } purse_kind;
 
 typedef enum {
   PURSE_OK = 0,
@@ -78,6 +78,16 @@ typedef struct {
 purse_status purse_create(int kind, int n, const double* model, const double* obs,
                           const double* radii, const purse_intrinsics* K, purse_t* out);
 
+/* Create a handle of a pose-regression PURSE (Example 3, eq. PURSEreg): n pose hypotheses
+ * (R_i, t_i), host n x 12 (R_i row-major, then t_i; each R_i a rotation to 1e-6), and radii
+ * beta_rot (host n, the Frobenius distance |vec(R) - vec(R_i)| allowed) and beta_t (host n,
+ * metres), each > 0; n in [1, 256].  The PURSE is every (R, t) within both radii of every
+ * hypothesis.  Sampled by purse_sample_plain (the fused purse_sample serves 3D-3D and 2D-3D);
+ * purse_ransag draws its seeds by convex combinations of the hypotheses; purse_dist takes mode 0;
+ * megb_solve and megb_solve_exact take its samples like any other.  Allocates device memory. */
+purse_status purse_create_regression(int n, const double* hyp, const double* beta_rot,
+                                     const double* beta_t, purse_t* out);
+
 purse_status purse_destroy(purse_t h);
 
 /* Constraint evaluation (eq. 2/3, eq. 11).  d_poses: n_poses x 12 poses (R row-major,
@@ -109,6 +119,9 @@ purse_status purse_dist(purse_t h, int mode, const float* d_poses, long long n_p
  * 3D-3D (Example 2): one pose fitted to the three pairs (least-squares rotation, Arun/Horn).
  * 2D-3D (Example 1): the poses of the perspective-three-point problem on the three pixels (up to
  * four; Grunert's quartic in the depth ratio, candidates in ascending order of its real roots).
+ * Pose regression (Example 3): one pose per trial, the convex combination of all hypotheses with
+ * weights uniform on the simplex (w_i = e_i / sum e, e_i = -log u_i, u_i = ((word_i >> 8) + 1/2)
+ * 2^-24 from words 0..n-1 of stream (5, 0, 0, tau)): t = sum w_i t_i, R = proj_SO3(sum w_i R_i).
  * A candidate is accepted if it lies in the PURSE.  The first max_seeds accepted poses in
  * (trial, candidate) order are written to d_seeds (device, max_seeds x 12 doubles); *n_seeds
  * (host) receives their count.  Synchronises the stream.  PURSE_ERR_EMPTY if none. */

@@ -80,20 +80,32 @@ purse_status purse_create(int kind, int n, const double* model, const double* ob
       return arg_error("purse_create: intrinsics must be finite with fx, fy > 0");
   }
   std::vector<double> t64(8 * (size_t)n);
-  std::vector<float> t32(8 * (size_t)n);
   for (int i = 0; i < n; ++i) {
     double* a = &t64[4 * i];
     double* b = &t64[4 * (n + i)];
     a[0] = model[3 * i], a[1] = model[3 * i + 1], a[2] = model[3 * i + 2], a[3] = radii[i];
     b[0] = obs[od * i], b[1] = obs[od * i + 1], b[2] = od == 3 ? obs[od * i + 2] : 0.0, b[3] = radii[i] * radii[i];
   }
+  double rho_max = 0.0;
+  for (int i = 0; i < n; ++i)
+    rho_max = std::max(rho_max, std::sqrt(model[3 * i] * model[3 * i] + model[3 * i + 1] * model[3 * i + 1] +
+                                          model[3 * i + 2] * model[3 * i + 2]));
+  return make_handle(kind, n, t64, Kc, rho_max, out);
+}
+
+}  // extern "C"
+
+namespace purse {
+
+// A handle owning device copies (FP64 and FP32) of the constraint table t64.
+purse_status make_handle(int kind, int n, const std::vector<double>& t64, const purse_intrinsics& Kc, double rho_max,
+                         purse_t* out) {
+  std::vector<float> t32(t64.size());
   for (size_t k = 0; k < t64.size(); ++k) t32[k] = (float)t64[k];
   purse_s* h = new purse_s();
   h->kind = kind;
   h->n = n;
-  for (int i = 0; i < n; ++i)
-    h->rho_max = std::max(h->rho_max, std::sqrt(model[3 * i] * model[3 * i] + model[3 * i + 1] * model[3 * i + 1] +
-                                                model[3 * i + 2] * model[3 * i + 2]));
+  h->rho_max = rho_max;
   h->K = Kc;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -114,6 +126,46 @@ purse_status purse_create(int kind, int n, const double* model, const double* ob
   return PURSE_OK;
 }
 
+}  // namespace purse
+
+extern "C" {
+
+purse_status purse_create_regression(int n, const double* hyp, const double* beta_rot, const double* beta_t,
+                                     purse_t* out) {
+  if (!out) return arg_error("purse_create_regression: out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > 256) return arg_error("purse_create_regression: n must be in [1, 256]");
+  if (!hyp || !beta_rot || !beta_t) return arg_error("purse_create_regression: NULL input array");
+  if (!finite_all(hyp, 12 * (size_t)n) || !finite_all(beta_rot, n) || !finite_all(beta_t, n))
+    return arg_error("purse_create_regression: non-finite input");
+  for (int i = 0; i < n; ++i) {
+    if (!(beta_rot[i] > 0) || !(beta_t[i] > 0)) return arg_error("purse_create_regression: radii must be > 0");
+    const double* R = hyp + 12 * (size_t)i;
+    double err = 0.0;  // |R R^T - I| and det R - 1
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        const double d = R[3 * r] * R[3 * c] + R[3 * r + 1] * R[3 * c + 1] + R[3 * r + 2] * R[3 * c + 2];
+        err = std::max(err, std::fabs(d - (r == c ? 1.0 : 0.0)));
+      }
+    const double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                       R[2] * (R[3] * R[7] - R[4] * R[6]);
+    if (err > 1e-6 || std::fabs(det - 1.0) > 1e-6)
+      return arg_error("purse_create_regression: a hypothesis rotation is not a rotation matrix");
+  }
+  // rows [0, n): (t_i, beta_i^t); rows [n, 4n): the rows of R_i, beta_i^R in the first, 0 in the others
+  std::vector<double> t64(16 * (size_t)n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    const double* H = hyp + 12 * (size_t)i;
+    double* a = &t64[4 * (size_t)i];
+    a[0] = H[9], a[1] = H[10], a[2] = H[11], a[3] = beta_t[i];
+    for (int r = 0; r < 3; ++r) {
+      double* row = &t64[4 * ((size_t)(1 + r) * n + i)];
+      row[0] = H[3 * r], row[1] = H[3 * r + 1], row[2] = H[3 * r + 2], row[3] = r == 0 ? beta_rot[i] : 0.0;
+    }
+  }
+  return make_handle(PURSE_REG, n, t64, purse_intrinsics{0, 0, 0, 0}, 0.0, out);
+}
+
 purse_status purse_destroy(purse_t h) {
   if (!h) return PURSE_OK;
   if (h->tables.f64) cudaFree(h->tables.f64);
@@ -130,6 +182,7 @@ purse_status purse_eval(purse_t h, int precision, const void* d_poses, int n_pos
   if (precision != 0 && precision != 1) return arg_error("purse_eval: precision must be 0 or 1");
   if (n_poses < 0) return arg_error("purse_eval: n_poses < 0");
   if (n_poses > 0 && !d_poses) return arg_error("purse_eval: NULL poses");
+  if (h->kind == PURSE_REG) return arg_error("purse_eval: not available for regression PURSEs (use purse_dist)");
   cudaError_t e = launch_eval(h, precision, d_poses, n_poses, d_margin, d_active, d_grad, (cudaStream_t)stream);
   return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_eval");
 }
@@ -141,6 +194,7 @@ purse_status purse_dist(purse_t h, int mode, const float* d_poses, long long n_p
   if (n_poses < 0) return arg_error("purse_dist: n_poses < 0");
   if (n_poses > 0 && (!d_poses || !d_dist)) return arg_error("purse_dist: NULL buffer");
   if ((reinterpret_cast<uintptr_t>(d_poses) & 15) != 0) return arg_error("purse_dist: d_poses must be 16-byte aligned");
+  if (mode != 0 && h->kind == PURSE_REG) return arg_error("purse_dist: regression PURSEs take mode 0");
   cudaError_t e = mode == 0 ? launch_plain_dist(h, d_poses, (long)n_poses, d_dist, (cudaStream_t)stream)
                             : launch_tc_dist(h, mode == 1 ? 3 : 1, d_poses, (long)n_poses, d_dist, (cudaStream_t)stream);
   return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_dist");
@@ -153,7 +207,7 @@ purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds,
   if (!d_seeds || !n_seeds) return arg_error("purse_ransag: NULL output");
   cudaStream_t st = (cudaStream_t)stream;
   const int chunk = 1 << 16;
-  const int slots = h->kind == PURSE_3D3D ? 1 : 4;  // candidate poses per trial (P3P: up to four)
+  const int slots = h->kind == PURSE_2D3D ? 4 : 1;  // candidate poses per trial (P3P: up to four)
   const size_t pose_bytes = align256((size_t)chunk * slots * 12 * sizeof(double));
   const size_t acc_bytes = align256((size_t)chunk * slots);
   purse_status s = ensure_scratch(h, pose_bytes + acc_bytes + 256);
@@ -165,8 +219,9 @@ purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds,
   int count = 0;
   for (int t0 = 0; t0 < n_trials && e == cudaSuccess; t0 += chunk) {
     const int nt = n_trials - t0 < chunk ? n_trials - t0 : chunk;
-    e = h->kind == PURSE_3D3D ? launch_ransag(h, seed, t0, nt, d_pose, d_acc, st)
-                              : launch_ransag_p3p(h, seed, t0, nt, d_pose, d_acc, st);
+    e = h->kind == PURSE_3D3D   ? launch_ransag(h, seed, t0, nt, d_pose, d_acc, st)
+        : h->kind == PURSE_2D3D ? launch_ransag_p3p(h, seed, t0, nt, d_pose, d_acc, st)
+                                : launch_convex_seeds(h, seed, t0, nt, d_pose, d_acc, st);
     if (e == cudaSuccess) e = launch_compact(d_pose, d_acc, nt * slots, d_seeds, d_count, max_seeds, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&count, d_count, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -185,6 +240,7 @@ purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const
                           int n_samples, void* d_q, void* d_t, int16_t* d_trace, void* d_snap,
                           purse_stream_t stream) {
   if (!h || !p) return arg_error("purse_sample: NULL handle or params");
+  if (h->kind == PURSE_REG) return arg_error("purse_sample: regression PURSEs are sampled by purse_sample_plain");
   if (p->n_iter < 0) return arg_error("purse_sample: n_iter < 0");
   if (p->n_perturb < 1 || p->n_perturb > 256) return arg_error("purse_sample: n_perturb must be in [1, 256]");
   if (p->n_keep < 1 || p->n_keep > 32 || p->n_keep > p->n_perturb)

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -118,6 +119,8 @@ struct purse_s {
 namespace purse {
 
 void set_error(const std::string& msg);
+purse_status make_handle(int kind, int n, const std::vector<double>& t64, const purse_intrinsics& Kc, double rho_max,
+                         purse_t* out);
 purse_status cuda_fail(cudaError_t e, const char* where);
 purse_status ensure_scratch(purse_t h, size_t bytes);
 
@@ -135,6 +138,8 @@ cudaError_t launch_ransag(purse_t h, uint64_t seed, int trial0, int n_trials, do
                           cudaStream_t st);
 cudaError_t launch_ransag_p3p(purse_t h, uint64_t seed, int trial0, int n_trials, double* d_pose, uint8_t* d_acc,
                               cudaStream_t st);
+cudaError_t launch_convex_seeds(purse_t h, uint64_t seed, int trial0, int n_trials, double* d_pose, uint8_t* d_acc,
+                                cudaStream_t st);
 cudaError_t launch_compact(const double* d_pose, const uint8_t* d_acc, int n_trials, double* d_seeds,
                            int* d_count, int max_seeds, cudaStream_t st);
 size_t plain_scratch_bytes(const purse_params* p, int n_samples, int* chunk);

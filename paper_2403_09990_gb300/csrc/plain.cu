@@ -123,11 +123,38 @@ __global__ void __launch_bounds__(kPlainThreads)
   }
 }
 
-// Constraint table (rows (a_i or Z_i, r_i), then (b_i or (u_i, v_i, 0), r_i^2)) into shared memory.
-template <typename T>
+// Constraint table into shared memory: 3D-3D / 2D-3D rows (a_i or Z_i, r_i), then (b_i or (u_i, v_i, 0),
+// r_i^2), 8 N values; pose regression rows (t_i, beta_i^t), then the rows of R_i with beta_i^R in the first,
+// 16 N values.
+template <typename T, int KIND>
 __device__ __forceinline__ void stage_table(const T* __restrict__ tab, int N, T* s) {
-  for (int k = threadIdx.x; k < 8 * N; k += blockDim.x) s[k] = tab[k];
+  const int count = (KIND == 2 ? 16 : 8) * N;
+  for (int k = threadIdx.x; k < count; k += blockDim.x) s[k] = tab[k];
   __syncthreads();
+}
+
+// Pose regression (Example 3): the two margins of hypothesis i, beta_i^R - |R - R_i|_F and
+// beta_i^t - |t - t_i|, and whether both constraints hold.
+template <typename T>
+__device__ __forceinline__ void reg_margins(const T* s, int N, int i, const M3<T>& R, const V3<T>& t, T& mR, T& mt,
+                                            bool& ok) {
+  const T* ti = s + 4 * i;
+  const T ex = t.x - ti[0], ey = t.y - ti[1], ez = t.z - ti[2];
+  const T e2 = ex * ex + ey * ey + ez * ez;
+  T d2 = T(0);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const T* row = s + 4 * ((1 + r) * N + i);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T d = R.m[3 * r + c] - row[c];
+      d2 += d * d;
+    }
+  }
+  const T bR = s[4 * (N + i) + 3];
+  mR = bR - sqrt(d2);
+  mt = ti[3] - sqrt(e2);
+  ok = d2 <= bR * bR && e2 <= ti[3] * ti[3];
 }
 
 // dist(R, t, dS) of eq. 11: min_i (r_i - |g_i|), -inf when a 2D-3D keypoint is behind the camera.
@@ -137,13 +164,23 @@ __global__ void __launch_bounds__(kPlainThreads)
                       T* d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
-  stage_table(tab, N, s);
+  stage_table<T, KIND>(tab, N, s);
   const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   M3<T> R;
   V3<T> t;
   load_pose(pose + 12 * p, R, t);
   T best = T(INFINITY);
+  if (KIND == 2) {
+    for (int i = 0; i < N; ++i) {
+      T mR, mt;
+      bool ok;
+      reg_margins<T>(s, N, i, R, t, mR, mt, ok);
+      best = fmin(best, fmin(mR, mt));
+    }
+    d[p] = best;
+    return;
+  }
   for (int i = 0; i < N; ++i) {
     const T* a = s + 4 * i;
     const T* o = s + 4 * (N + i);
@@ -237,13 +274,23 @@ __global__ void __launch_bounds__(kPlainThreads)
                           long n, uint8_t* I) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
-  stage_table(tab, N, s);
+  stage_table<T, KIND>(tab, N, s);
   const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   M3<T> R;
   V3<T> t;
   load_pose(cand + 12 * p, R, t);
   bool ok = true;
+  if (KIND == 2) {
+    for (int i = 0; i < N; ++i) {
+      T mR, mt;
+      bool oki;
+      reg_margins<T>(s, N, i, R, t, mR, mt, oki);
+      ok = ok && oki;
+    }
+    I[p] = ok ? 1 : 0;
+    return;
+  }
   for (int i = 0; i < N; ++i) {
     const T* a = s + 4 * i;
     const T* o = s + 4 * (N + i);
@@ -327,7 +374,7 @@ static cudaError_t run_plain_t(purse_t h, const purse_params* p, const WalkStats
   const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
   const T* tab = sizeof(T) == 4 ? (const T*)h->tables.f32 : (const T*)h->tables.f64;
   const T fx = T(h->K.fx), fy = T(h->K.fy), cx = T(h->K.cx), cy = T(h->K.cy);
-  const size_t tab_smem = 8 * (size_t)N * sizeof(T);
+  const size_t tab_smem = (KIND == 2 ? 16 : 8) * (size_t)N * sizeof(T);
   cudaError_t e = cudaSuccess;
   char* base = reinterpret_cast<char*>(scratch);
   size_t off = 0;
@@ -365,8 +412,8 @@ static cudaError_t run_plain_t(purse_t h, const purse_params* p, const WalkStats
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    const unsigned long long n_evals =
-        (unsigned long long)n_samples * p->n_iter * ((unsigned long long)NP + (unsigned long long)NT * K) * N;
+    const unsigned long long n_evals = (unsigned long long)n_samples * p->n_iter *
+                                       ((unsigned long long)NP + (unsigned long long)NT * K) * (KIND == 2 ? 2 * N : N);
     plain_count_kernel<<<1, 1, 0, st>>>(h->d_evals, n_evals);
     e = cudaGetLastError();
   }
@@ -375,11 +422,14 @@ static cudaError_t run_plain_t(purse_t h, const purse_params* p, const WalkStats
 
 cudaError_t launch_plain_dist(purse_t h, const float* d_poses, long n_poses, float* d_dist, cudaStream_t st) {
   if (n_poses == 0) return cudaSuccess;
-  const size_t tab_smem = 8 * (size_t)h->n * sizeof(float);
+  const size_t tab_smem = (h->kind == 2 ? 16 : 8) * (size_t)h->n * sizeof(float);
   const float fx = float(h->K.fx), fy = float(h->K.fy), cx = float(h->K.cx), cy = float(h->K.cy);
   const unsigned grid = blocks_for(n_poses, kPlainThreads);
   if (h->kind == 0)
     plain_dist_kernel<float, 0><<<grid, kPlainThreads, tab_smem, st>>>(h->tables.f32, h->n, fx, fy, cx, cy, d_poses,
+                                                                        n_poses, d_dist);
+  else if (h->kind == 2)
+    plain_dist_kernel<float, 2><<<grid, kPlainThreads, tab_smem, st>>>(h->tables.f32, h->n, fx, fy, cx, cy, d_poses,
                                                                         n_poses, d_dist);
   else
     plain_dist_kernel<float, 1><<<grid, kPlainThreads, tab_smem, st>>>(h->tables.f32, h->n, fx, fy, cx, cy, d_poses,
@@ -410,12 +460,20 @@ cudaError_t launch_plain(purse_t h, const purse_params* p, const WalkStats* d_st
       if (smp == 0) PLAIN_RUN(float, 0, 0);
       PLAIN_RUN(float, 0, 1);
     }
+    if (kind == 2) {
+      if (smp == 0) PLAIN_RUN(float, 2, 0);
+      PLAIN_RUN(float, 2, 1);
+    }
     if (smp == 0) PLAIN_RUN(float, 1, 0);
     PLAIN_RUN(float, 1, 1);
   }
   if (kind == 0) {
     if (smp == 0) PLAIN_RUN(double, 0, 0);
     PLAIN_RUN(double, 0, 1);
+  }
+  if (kind == 2) {
+    if (smp == 0) PLAIN_RUN(double, 2, 0);
+    PLAIN_RUN(double, 2, 1);
   }
   if (smp == 0) PLAIN_RUN(double, 1, 0);
   PLAIN_RUN(double, 1, 1);

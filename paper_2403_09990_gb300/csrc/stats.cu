@@ -67,6 +67,13 @@ __device__ void stats_block(const double* seeds, int s0, const double* tab, int 
     for (int k = 0; k < 9; ++k) sh.S[k] = (k % 4 == 0) ? 1.0 : 0.0;
     if (kind == 0) {
       sh.sigma_t = rsum / n;
+    } else if (kind == 2) {
+      // pose regression: translation scale mean beta^t (rows 0..n-1 hold (t_i, beta_i^t)); rotation scale
+      // mean beta^R / sqrt(2), the angle of a Frobenius distance, written through rho_a
+      double rb = 0.0;
+      for (int i = 0; i < n; ++i) rb += tab[4 * (n + i) + 3];
+      sh.sigma_t = rsum / n;
+      sh.rho_a = sh.sigma_t * sqrt(2.0) / (rb / n);
     } else {
       sh.sigma_t = rsum / n * sh.tbar[2] / (0.5 * (fx + fy));
       // PCA scaling of the centre velocity (Section IV, Step II; appendix dS_t sampler)
@@ -464,6 +471,58 @@ cudaError_t launch_ransag_p3p(purse_t h, uint64_t seed, int trial0, int n_trials
   ransag_p3p_kernel<<<(n_trials + threads - 1) / threads, threads, 0, st>>>(
       h->tables.f64, h->n, h->K.fx, h->K.fy, h->K.cx, h->K.cy, (uint32_t)seed, (uint32_t)(seed >> 32), trial0,
       n_trials, d_pose, d_acc);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Step I for pose regression
+// Convex-combination sampler (Section IV, Step I, Example 3): trial tau draws weights uniform on the
+// simplex, w_i = e_i / sum_j e_j with e_i = -log u_i, u_i = ((word_i >> 8) + 1/2) 2^-24 from words
+// 0..n-1 of stream (5, 0, 0, tau); the candidate is t = sum w_i t_i, R = proj_SO3(sum w_i R_i) (the
+// rotation maximising tr(R^T M), Horn's quaternion method), accepted if it lies in the PURSE
+// (eq. PURSEreg, FP64).  Table rows: (t_i, beta_i^t), then the rows of R_i with beta_i^R in the first.
+__global__ void __launch_bounds__(128)
+    convex_seed_kernel(const double* tab, int n, uint32_t k0, uint32_t k1, int trial0, int n_trials, double* pose,
+                       uint8_t* acc) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= n_trials) return;
+  const uint32_t tau = (uint32_t)(trial0 + tid);
+  Stream s(k0, k1, kPhaseRansag, 0u, 0u, tau);
+  double se = 0.0, t[3] = {0.0, 0.0, 0.0}, M[9];
+  for (int k = 0; k < 9; ++k) M[k] = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const uint32_t w = s.next();
+    const double e = -log(((double)(w >> 8) + 0.5) * (1.0 / 16777216.0));
+    se += e;
+    for (int c = 0; c < 3; ++c) t[c] += e * tab[4 * i + c];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) M[3 * r + c] += e * tab[4 * ((1 + r) * n + i) + c];
+  }
+  for (int c = 0; c < 3; ++c) t[c] /= se;
+  for (int k = 0; k < 9; ++k) M[k] /= se;
+  const M3<double> R = qmat(rotation_maximising_trace(M));
+  bool ok = true;
+  for (int i = 0; i < n && ok; ++i) {
+    double e2 = 0.0, d2 = 0.0;
+    for (int c = 0; c < 3; ++c) e2 += (t[c] - tab[4 * i + c]) * (t[c] - tab[4 * i + c]);
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        const double d = R.m[3 * r + c] - tab[4 * ((1 + r) * n + i) + c];
+        d2 += d * d;
+      }
+    const double bt = tab[4 * i + 3], bR = tab[4 * (n + i) + 3];
+    ok = bR - sqrt(d2) >= 0.0 && bt - sqrt(e2) >= 0.0;
+  }
+  double* o = pose + 12 * (size_t)tid;
+  for (int k = 0; k < 9; ++k) o[k] = R.m[k];
+  for (int c = 0; c < 3; ++c) o[9 + c] = t[c];
+  acc[tid] = ok ? 1 : 0;
+}
+
+cudaError_t launch_convex_seeds(purse_t h, uint64_t seed, int trial0, int n_trials, double* d_pose, uint8_t* d_acc,
+                                cudaStream_t st) {
+  const int threads = 128;
+  convex_seed_kernel<<<(n_trials + threads - 1) / threads, threads, 0, st>>>(
+      h->tables.f64, h->n, (uint32_t)seed, (uint32_t)(seed >> 32), trial0, n_trials, d_pose, d_acc);
   return cudaGetLastError();
 }
 

@@ -12,7 +12,7 @@ import os
 
 from . import build as _build
 
-PURSE_3D3D, PURSE_2D3D = 0, 1
+PURSE_3D3D, PURSE_2D3D, PURSE_REG = 0, 1, 2
 STATUS = {0: "PURSE_OK", 1: "PURSE_ERR_ARG", 2: "PURSE_ERR_CUDA", 3: "PURSE_ERR_EMPTY", 4: "PURSE_ERR_TIMEOUT",
           5: "PURSE_ERR_NOMEM", 6: "PURSE_ERR_NUMERIC", 7: "PURSE_ERR_STATE"}
 
@@ -44,6 +44,7 @@ _LIB = None
 _VP = ctypes.c_void_p
 _SIGS = {
     "purse_create": [ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)],
+    "purse_create_regression": [ctypes.c_int, _VP, _VP, _VP, ctypes.POINTER(_VP)],
     "purse_destroy": [_VP],
     "purse_eval": [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP, _VP],
     "purse_dist": [_VP, ctypes.c_int, _VP, ctypes.c_longlong, _VP, _VP],
@@ -133,6 +134,18 @@ def purse_create(kind: int, model, obs, radii, K=None) -> int:
     h = _VP()
     _check(lib().purse_create(kind, radii.shape[0], model.ctypes.data, obs.ctypes.data, radii.ctypes.data, Kp,
                               ctypes.byref(h)), "purse_create")
+    return h.value
+
+
+def purse_create_regression(hyp, beta_rot, beta_t) -> int:
+    """Host arrays: hypotheses (n, 12) (R row-major, t), radii (n,) each -> handle."""
+    import numpy as np
+    hyp = np.ascontiguousarray(hyp, dtype=np.float64).reshape(-1, 12)
+    beta_rot = np.ascontiguousarray(beta_rot, dtype=np.float64)
+    beta_t = np.ascontiguousarray(beta_t, dtype=np.float64)
+    h = _VP()
+    _check(lib().purse_create_regression(hyp.shape[0], hyp.ctypes.data, beta_rot.ctypes.data, beta_t.ctypes.data,
+                                         ctypes.byref(h)), "purse_create_regression")
     return h.value
 
 
@@ -280,7 +293,12 @@ class Purse:
     def __init__(self, p):
         self.kind = int(p.kind)
         self.n = int(p.radii.shape[0])
-        self.h = purse_create(self.kind, p.model, p.obs, p.radii, p.K if self.kind == PURSE_2D3D else None)
+        if self.kind == PURSE_REG:
+            import numpy as np
+            hyp = np.concatenate([np.asarray(p.rot_hyp).reshape(-1, 9), np.asarray(p.obs).reshape(-1, 3)], axis=1)
+            self.h = purse_create_regression(hyp, p.radii_rot, p.radii)
+        else:
+            self.h = purse_create(self.kind, p.model, p.obs, p.radii, p.K if self.kind == PURSE_2D3D else None)
 
     def close(self):
         if self.h:

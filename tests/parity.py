@@ -22,14 +22,25 @@ import numpy as np
 
 from oracle import closure, philox
 from oracle import purse as op
-from oracle.purse import KIND_2D3D
+from oracle.purse import KIND_2D3D, KIND_REG
 
 EPS = {0: 2.0 ** -23, 1: 2.0 ** -52}
 
 
 def constraint_bands(purse, R, t, precision):
-    """(..., N) band of each constraint's margin at poses (R, t)."""
+    """(..., N) band of each constraint's margin at poses (R, t) ((..., 2N) for pose regression:
+    1e-6 beta + 8 eps times the norms of the two matrices, or of the two translations)."""
     eps = EPS[precision]
+    if purse.kind == KIND_REG:
+        R = np.asarray(R, dtype=np.float64)
+        t = np.asarray(t, dtype=np.float64)
+        bR = 1e-6 * purse.radii_rot + 8.0 * eps * (np.sqrt((R ** 2).sum(axis=(-2, -1)))[..., None]
+                                                   + np.sqrt((purse.rot_hyp ** 2).sum(axis=(-2, -1))))
+        bt = 1e-6 * purse.radii + 8.0 * eps * (np.linalg.norm(t, axis=-1)[..., None]
+                                               + np.linalg.norm(purse.obs, axis=-1))
+        lead = np.broadcast_shapes(bR.shape[:-1], bt.shape[:-1])
+        return np.concatenate([np.broadcast_to(bR, lead + bR.shape[-1:]),
+                               np.broadcast_to(bt, lead + bt.shape[-1:])], axis=-1)
     X = op.transform(purse.model, R, t)
     if purse.kind == KIND_2D3D:
         fx, fy, cx, cy = purse.K

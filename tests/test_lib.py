@@ -66,3 +66,18 @@ def test_argument_validation_without_gpu():
     with pytest.raises(P.PurseError) as e:
         P.purse_destroy(None) or P._check(1, "x")
     assert e.value.status == 1
+
+
+def test_regression_create_validation_without_gpu():
+    L = P.lib()
+    h = ctypes.c_void_p()
+    hyp = np.tile(np.concatenate([np.eye(3).reshape(9), np.zeros(3)]), (3, 1))
+    bR, bt = np.full(3, 0.1), np.full(3, 0.01)
+    assert L.purse_create_regression(0, hyp.ctypes.data, bR.ctypes.data, bt.ctypes.data, ctypes.byref(h)) == 1
+    bad = hyp.copy()
+    bad[1, 0] = 2.0                                    # not a rotation
+    assert L.purse_create_regression(3, bad.ctypes.data, bR.ctypes.data, bt.ctypes.data, ctypes.byref(h)) == 1
+    assert b"rotation" in L.purse_last_error()
+    z = np.array([0.1, 0.0, 0.1])
+    assert L.purse_create_regression(3, hyp.ctypes.data, z.ctypes.data, bt.ctypes.data, ctypes.byref(h)) == 1
+    assert L.purse_create_regression(3, None, bR.ctypes.data, bt.ctypes.data, ctypes.byref(h)) == 1
