@@ -124,11 +124,11 @@ def center_stats(purse, seeds, params: Params) -> Stats:
         rho_a = float(sigma_t * np.sqrt(2.0) / purse.radii_rot.mean())
         S = np.eye(3)
     elif purse.kind == KIND_3D3D:
-        sigma_t = float(purse.radii.mean())
+        sigma_t = float(noise_scales(purse).mean())
         S = np.eye(3)
     else:
         fx, fy, _, _ = purse.K
-        sigma_t = float(purse.radii.mean() * tbar[2] / (0.5 * (fx + fy)))
+        sigma_t = float(noise_scales(purse).mean() * tbar[2] / (0.5 * (fx + fy)))
         S = pca_scaling(t0, tbar, rho_a)
     if params.perturb_units:
         r_trans, r_rot = params.trans_perturb, params.rot_perturb
@@ -136,6 +136,16 @@ def center_stats(purse, seeds, params: Params) -> Stats:
         r_trans = params.trans_perturb * sigma_t
         r_rot = params.rot_perturb * sigma_t / rho_a
     return Stats(Rbar, tbar, S, sigma_t, rho_a, float(r_trans), float(r_rot))
+
+
+def noise_scales(purse):
+    """Radius of each noise region: r_i, or with a noise matrix (eq. 4) the geometric mean
+    r_i det(Lambda_i)^(-1/(2d)) of the semi-axes of {e : e^T Lambda_i e <= r_i^2}."""
+    lam = getattr(purse, "lam", None)
+    if lam is None:
+        return np.asarray(purse.radii, dtype=np.float64)
+    d = lam.shape[-1]
+    return purse.radii * np.linalg.det(lam) ** (-1.0 / (2 * d))
 
 
 def pca_scaling(t0, tbar, rho_a):

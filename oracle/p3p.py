@@ -134,6 +134,10 @@ def ransag_trial_candidates(purse, seed: int, trials):
     idx = philox.distinct_triple(words, purse.n)                                       # (T, 3)
     pts = np.stack([philox.disk_points(seed, philox.PHASE_RANSAG, c + 1, 0, tau)[0]
                     for c in range(3)], axis=1)                                         # (T, 3, 2)
+    lam = getattr(purse, "lam", None)
+    if lam is not None:  # a point of the noise ellipse {e : e^T Lambda e <= r^2}: e = r U^-1 u
+        U = np.swapaxes(np.linalg.cholesky(lam[idx]), -1, -2)
+        pts = np.linalg.solve(U, pts[..., None])[..., 0]
     z = purse.obs[idx] + purse.radii[idx][..., None] * pts
     f = bearings(purse.K, z)
     out = []

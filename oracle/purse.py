@@ -4,7 +4,8 @@
 * 2D-3D (Example 1, eq. 2): g_i = z_i - pi(K (R Z_i + t)) in pixels, with
   pi(P) = (P_x / P_z, P_y / P_z) and K = [[fx, 0, cx], [0, fy, cy], [0, 0, 1]];
   a keypoint with P_z <= 0 (behind the camera) violates its constraint.
-* PURSE (eq. 5) with Lambda_i = I, beta_i = r_i: all |g_i| <= r_i.
+* PURSE (eq. 5) with Lambda_i = I, beta_i = r_i: all |g_i| <= r_i; with general
+  positive definite Lambda_i (eq. 4) all sqrt(g_i^T Lambda_i g_i) <= r_i.
 * margins r_i - |g_i| (-inf behind the camera) and dist(R, t, dS) =
   min_i margins (eq. 11).
 * pose regression (Example 3, eq. PURSEreg): per hypothesis (R_i, t_i) two
@@ -30,12 +31,20 @@ def transform(model, R, t):
     return np.einsum('...ij,nj->...ni', R, model) + np.asarray(t)[..., None, :]
 
 
+def lam_norm(g, lam):
+    """|g|_Lambda = sqrt(g^T Lambda g) (eq. 4) of residuals g (..., N, d), Lambda (N, d, d)."""
+    return np.sqrt(np.maximum(np.einsum('...ni,nij,...nj->...n', g, lam, g), 0.0))
+
+
 def residual_norms(purse, R, t):
-    """|g_i| (..., N) and the in-front mask (all True for 3D-3D)."""
+    """|g_i| (..., N) -- |g_i|_Lambda_i when the PURSE carries noise matrices -- and the in-front
+    mask (all True for 3D-3D)."""
     X = transform(purse.model, R, t)
+    lam = getattr(purse, "lam", None)
     if purse.kind == KIND_3D3D:
         g = purse.obs - X
-        return np.linalg.norm(g, axis=-1), np.ones(g.shape[:-1], dtype=bool)
+        h = np.linalg.norm(g, axis=-1) if lam is None else lam_norm(g, lam)
+        return h, np.ones(g.shape[:-1], dtype=bool)
     fx, fy, cx, cy = purse.K
     Pz = X[..., 2]
     front = Pz > 0
@@ -44,6 +53,8 @@ def residual_norms(purse, R, t):
     v = fy * X[..., 1] / Pzs + cy
     gu = purse.obs[:, 0] - u
     gv = purse.obs[:, 1] - v
+    if lam is not None:
+        return lam_norm(np.stack([gu, gv], axis=-1), lam), front
     return np.sqrt(gu * gu + gv * gv), front
 
 

@@ -27,6 +27,10 @@ instances stand in for them with the sizes of the published settings:
   with radii beta_i^R (Frobenius distance of rotation matrices) and beta_i^t
   (metres) each exceeding the hypothesis' distance to the ground truth by a
   random slack, so the ground truth lies in the PURSE.
+* ``purse_3d3d_ellipsoidal`` / ``purse_2d3d_ellipsoidal`` -- the same instances with the noise
+  bounded in the general norm of eq. 4: random positive definite Lambda_i (eigenvalues in
+  [0.5, 2]), noise uniform in {e : sqrt(e^T Lambda_i e) <= r_i}; ``purse_octahedron_ellipsoidal``
+  -- the octahedral instance with one Lambda for every constraint (closed-form translation ball).
 * ``purse_reg_nested`` -- a regression PURSE whose first hypothesis is the
   ground truth with the smallest balls, each contained in every other
   hypothesis' ball: the PURSE is then that pair of balls and its geodesic balls
@@ -58,6 +62,7 @@ class Purse:
     t_gt: np.ndarray = field(default_factory=lambda: np.zeros(3))
     rot_hyp: np.ndarray | None = None    # (N, 3, 3) hypotheses R_i (KIND_REG)
     radii_rot: np.ndarray | None = None  # (N,) beta_i^R, Frobenius distance (KIND_REG)
+    lam: np.ndarray | None = None        # (N, d, d) noise matrices Lambda_i of eq. 4 (None: identity)
 
     @property
     def n(self) -> int:
@@ -163,6 +168,51 @@ def purse_reg_nested(n: int = 10, seed: int = 0, beta_rot: float = 0.04, beta_t:
     bt = np.linalg.norm(ti - ti[0], axis=1) + beta_t + 0.002
     bR[0], bt[0] = beta_rot, beta_t
     return Purse(KIND_REG, np.zeros((n, 3)), ti, bt, None, p.R_gt, p.t_gt, Ri, bR)
+
+
+def _spd(rng: np.random.Generator, n: int, d: int, lo: float, hi: float) -> np.ndarray:
+    """n random symmetric positive definite d x d matrices with eigenvalues uniform in [lo, hi]."""
+    Q, _ = np.linalg.qr(rng.normal(size=(n, d, d)))
+    ev = rng.uniform(lo, hi, (n, d))
+    return np.einsum('nij,nj,nkj->nik', Q, ev, Q)
+
+
+def _in_ellipsoid(rng: np.random.Generator, lam: np.ndarray, radii: np.ndarray) -> np.ndarray:
+    """One point uniform in each {e : e^T Lambda_i e <= r_i^2} (strictly inside)."""
+    n, d, _ = lam.shape
+    u = _in_ball(rng, n, d, np.ones(n))
+    U = np.linalg.cholesky(lam).transpose(0, 2, 1)        # Lambda = U^T U, U upper triangular
+    return radii[:, None] * np.linalg.solve(U, u[..., None])[..., 0]
+
+
+def purse_3d3d_ellipsoidal(n: int = 8, seed: int = 0, ev: tuple = (0.5, 2.0)) -> Purse:
+    """3D-3D PURSE with noise bounded in the norm of eq. 4: Lambda_i with eigenvalues in ev, noise
+    uniform in {e : |e|_Lambda_i <= r_i}."""
+    p = purse_3d3d(n, seed)
+    rng = np.random.default_rng(seed + 7919)
+    lam = _spd(rng, n, 3, *ev)
+    b = p.model @ p.R_gt.T + p.t_gt + _in_ellipsoid(rng, lam, p.radii)
+    return Purse(KIND_3D3D, p.model, b, p.radii, None, p.R_gt, p.t_gt, lam=lam)
+
+
+def purse_2d3d_ellipsoidal(n: int = 16, seed: int = 0, ev: tuple = (0.5, 2.0)) -> Purse:
+    """2D-3D PURSE with pixel noise bounded in the norm of eq. 4 (2 x 2 Lambda_i)."""
+    p = purse_2d3d(n, seed)
+    rng = np.random.default_rng(seed + 7919)
+    lam = _spd(rng, n, 2, *ev)
+    fx, fy, cx, cy = p.K
+    P = p.model @ p.R_gt.T + p.t_gt
+    pix = np.stack([fx * P[:, 0] / P[:, 2] + cx, fy * P[:, 1] / P[:, 2] + cy], axis=1)
+    z = pix + _in_ellipsoid(rng, lam, p.radii)
+    return Purse(KIND_2D3D, p.model, z, p.radii, p.K, p.R_gt, p.t_gt, lam=lam)
+
+
+def purse_octahedron_ellipsoidal(L: float = 0.1, r: float = 0.01, seed: int = 0, ev=(0.5, 2.0)) -> Purse:
+    """The octahedral PURSE with one noise matrix Lambda for all six constraints: its translations form
+    the ellipsoid {d : d^T Lambda d <= r^2}, whose enclosing ball has the radius r / sqrt(lambda_min)."""
+    p = purse_octahedron(L, r, seed)
+    lam = _spd(np.random.default_rng(seed + 1), 1, 3, *ev)
+    return Purse(KIND_3D3D, p.model, p.obs, p.radii, None, p.R_gt, p.t_gt, lam=np.repeat(lam, 6, axis=0))
 
 
 def purse_batch(n_purses: int = 4096, seed: int = 0, n_lo: int = 4, n_hi: int = 64) -> list[Purse]:
