@@ -78,6 +78,15 @@ typedef struct {
 purse_status purse_create(int kind, int n, const double* model, const double* obs,
                           const double* radii, const purse_intrinsics* K, purse_t* out);
 
+/* Noise bounded in the general norm of eq. 4, |e|_Lambda = sqrt(e^T Lambda_i e) <= r_i, for the
+ * constraints of a 3D-3D (Lambda_i 3 x 3) or 2D-3D (2 x 2, pixels) PURSE: lam (host, n x d x d,
+ * row-major, each symmetric positive definite; PURSE_ERR_ARG otherwise); NULL restores the
+ * identity.  Each Lambda_i is factored once on the host (Cholesky, Lambda = U^T U) and the factors
+ * are kept on the device.  With noise matrices: purse_sample_plain, purse_ransag (points drawn in
+ * the noise ellipsoids, acceptance in that norm) and purse_dist mode 0 use them; the fused
+ * purse_sample and purse_eval return PURSE_ERR_ARG.  Allocates device memory on the first call. */
+purse_status purse_set_noise(purse_t h, const double* lam);
+
 /* Create a handle of a pose-regression PURSE (Example 3, eq. PURSEreg): n pose hypotheses
  * (R_i, t_i), host n x 12 (R_i row-major, then t_i; each R_i a rotation to 1e-6), and radii
  * beta_rot (host n, the Frobenius distance |vec(R) - vec(R_i)| allowed) and beta_t (host n,

@@ -166,11 +166,61 @@ purse_status purse_create_regression(int n, const double* hyp, const double* bet
   return make_handle(PURSE_REG, n, t64, purse_intrinsics{0, 0, 0, 0}, 0.0, out);
 }
 
+purse_status purse_set_noise(purse_t h, const double* lam) {
+  if (!h) return arg_error("purse_set_noise: NULL handle");
+  if (h->kind == PURSE_REG) return arg_error("purse_set_noise: regression PURSEs take no noise matrices");
+  if (!lam) {  // back to the identity
+    if (h->ell64) cudaFree(h->ell64);
+    if (h->ell32) cudaFree(h->ell32);
+    h->ell64 = nullptr, h->ell32 = nullptr;
+    return PURSE_OK;
+  }
+  const int d = h->kind == PURSE_3D3D ? 3 : 2, n = h->n;
+  if (!finite_all(lam, (size_t)n * d * d)) return arg_error("purse_set_noise: non-finite input");
+  std::vector<double> u64(8 * (size_t)n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    const double* L = lam + (size_t)i * d * d;
+    for (int r = 0; r < d; ++r)
+      for (int c = 0; c < r; ++c)
+        if (std::fabs(L[r * d + c] - L[c * d + r]) > 1e-12 * (std::fabs(L[r * d + c]) + std::fabs(L[c * d + r])) + 1e-300)
+          return arg_error("purse_set_noise: a noise matrix is not symmetric");
+    // Cholesky Lambda = U^T U (U upper triangular, row by row)
+    double U[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int r = 0; r < d; ++r) {
+      double s2 = L[r * d + r];
+      for (int k = 0; k < r; ++k) s2 -= U[k][r] * U[k][r];
+      if (!(s2 > 0)) return arg_error("purse_set_noise: a noise matrix is not positive definite");
+      U[r][r] = std::sqrt(s2);
+      for (int c = r + 1; c < d; ++c) {
+        double v = L[r * d + c];
+        for (int k = 0; k < r; ++k) v -= U[k][r] * U[k][c];
+        U[r][c] = v / U[r][r];
+      }
+    }
+    double* o = &u64[8 * (size_t)i];
+    if (d == 3) {
+      o[0] = U[0][0], o[1] = U[0][1], o[2] = U[0][2], o[3] = U[1][1], o[4] = U[1][2], o[5] = U[2][2];
+    } else {
+      o[0] = U[0][0], o[1] = U[0][1], o[2] = U[1][1];
+    }
+  }
+  std::vector<float> u32(u64.size());
+  for (size_t k = 0; k < u64.size(); ++k) u32[k] = (float)u64[k];
+  cudaError_t e = cudaSuccess;
+  if (!h->ell64) e = cudaMalloc(&h->ell64, u64.size() * sizeof(double));
+  if (e == cudaSuccess && !h->ell32) e = cudaMalloc(&h->ell32, u32.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(h->ell64, u64.data(), u64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->ell32, u32.data(), u32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_set_noise");
+}
+
 purse_status purse_destroy(purse_t h) {
   if (!h) return PURSE_OK;
   if (h->tables.f64) cudaFree(h->tables.f64);
   if (h->tables.f32) cudaFree(h->tables.f32);
   if (h->d_status) cudaFree(h->d_status);
+  if (h->ell64) cudaFree(h->ell64);
+  if (h->ell32) cudaFree(h->ell32);
   if (h->d_scratch) cudaFree(h->d_scratch);
   delete h;
   return PURSE_OK;
@@ -182,7 +232,8 @@ purse_status purse_eval(purse_t h, int precision, const void* d_poses, int n_pos
   if (precision != 0 && precision != 1) return arg_error("purse_eval: precision must be 0 or 1");
   if (n_poses < 0) return arg_error("purse_eval: n_poses < 0");
   if (n_poses > 0 && !d_poses) return arg_error("purse_eval: NULL poses");
-  if (h->kind == PURSE_REG) return arg_error("purse_eval: not available for regression PURSEs (use purse_dist)");
+  if (h->kind == PURSE_REG || h->ell64)
+    return arg_error("purse_eval: not available for regression PURSEs or noise matrices (use purse_dist)");
   cudaError_t e = launch_eval(h, precision, d_poses, n_poses, d_margin, d_active, d_grad, (cudaStream_t)stream);
   return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_eval");
 }
@@ -194,7 +245,8 @@ purse_status purse_dist(purse_t h, int mode, const float* d_poses, long long n_p
   if (n_poses < 0) return arg_error("purse_dist: n_poses < 0");
   if (n_poses > 0 && (!d_poses || !d_dist)) return arg_error("purse_dist: NULL buffer");
   if ((reinterpret_cast<uintptr_t>(d_poses) & 15) != 0) return arg_error("purse_dist: d_poses must be 16-byte aligned");
-  if (mode != 0 && h->kind == PURSE_REG) return arg_error("purse_dist: regression PURSEs take mode 0");
+  if (mode != 0 && (h->kind == PURSE_REG || h->ell64))
+    return arg_error("purse_dist: regression PURSEs and noise matrices take mode 0");
   cudaError_t e = mode == 0 ? launch_plain_dist(h, d_poses, (long)n_poses, d_dist, (cudaStream_t)stream)
                             : launch_tc_dist(h, mode == 1 ? 3 : 1, d_poses, (long)n_poses, d_dist, (cudaStream_t)stream);
   return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_dist");
@@ -241,6 +293,7 @@ purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const
                           purse_stream_t stream) {
   if (!h || !p) return arg_error("purse_sample: NULL handle or params");
   if (h->kind == PURSE_REG) return arg_error("purse_sample: regression PURSEs are sampled by purse_sample_plain");
+  if (h->ell64) return arg_error("purse_sample: PURSEs with noise matrices are sampled by purse_sample_plain");
   if (p->n_iter < 0) return arg_error("purse_sample: n_iter < 0");
   if (p->n_perturb < 1 || p->n_perturb > 256) return arg_error("purse_sample: n_perturb must be in [1, 256]");
   if (p->n_keep < 1 || p->n_keep > 32 || p->n_keep > p->n_perturb)

@@ -102,6 +102,9 @@ struct purse_s {
   double rho_max = 0;  // largest model-point radius
   purse_intrinsics K{0, 0, 0, 0};
   purse::purse_tables tables;
+  // noise factors of eq. 4 (Lambda_i = U_i^T U_i, 8 values per constraint) or NULL (identity)
+  double* ell64 = nullptr;
+  float* ell32 = nullptr;
   int* d_status = nullptr;
   unsigned long long* d_evals = nullptr;  // evaluation counter of the last purse_sample
   // scratch owned by the handle, grown on demand
@@ -126,7 +129,7 @@ purse_status ensure_scratch(purse_t h, size_t bytes);
 
 // Launchers (one translation unit each).
 cudaError_t launch_stats(purse_t h, const double* d_seeds, int s0, const purse_params* p, WalkStats* d_stats,
-                         double* d_seed_data, cudaStream_t st);
+                         double* d_seed_data, cudaStream_t st);  // takes h->ell64 into the translation scale
 cudaError_t launch_walk(purse_t h, const purse_params* p, const WalkArgs& a, cudaStream_t st);
 cudaError_t launch_stats_batch(int n_purses, const BatchPurseInfo* info, const double* tab64, const double* seeds,
                                const BatchStatParams& sp, WalkStats* out, double* seed_data, cudaStream_t st);

@@ -157,14 +157,39 @@ __device__ __forceinline__ void reg_margins(const T* s, int N, int i, const M3<T
   ok = d2 <= bR * bR && e2 <= ti[3] * ti[3];
 }
 
-// dist(R, t, dS) of eq. 11: min_i (r_i - |g_i|), -inf when a 2D-3D keypoint is behind the camera.
+// |U e|^2 for the noise norm of eq. 4 (Lambda = U^T U, U upper triangular, 8 values per constraint:
+// 3D-3D u00 u01 u02 u11 u12 u22, 2D-3D u00 u01 u11).
+template <typename T>
+__device__ __forceinline__ T lam_norm2_3(const T* u, T e0, T e1, T e2) {
+  const T a = u[0] * e0 + u[1] * e1 + u[2] * e2, b = u[3] * e1 + u[4] * e2, c = u[5] * e2;
+  return a * a + b * b + c * c;
+}
+template <typename T>
+__device__ __forceinline__ T lam_norm2_2(const T* u, T e0, T e1) {
+  const T a = u[0] * e0 + u[1] * e1, b = u[2] * e1;
+  return a * a + b * b;
+}
+
+// Noise factors (8 N values) after the constraint table in shared memory, or NULL.
+template <typename T, int KIND>
+__device__ __forceinline__ const T* stage_noise(const T* __restrict__ ell, int N, T* s) {
+  if (KIND == 2 || ell == nullptr) return nullptr;
+  T* u = s + 8 * N;
+  for (int k = threadIdx.x; k < 8 * N; k += blockDim.x) u[k] = ell[k];
+  __syncthreads();
+  return u;
+}
+
+// dist(R, t, dS) of eq. 11: min_i (r_i - |g_i|), -inf when a 2D-3D keypoint is behind the camera;
+// |g_i| in the norm of eq. 4 when the PURSE carries noise matrices (ell != NULL).
 template <typename T, int KIND>
 __global__ void __launch_bounds__(kPlainThreads)
-    plain_dist_kernel(const T* __restrict__ tab, int N, T fx, T fy, T cx, T cy, const T* __restrict__ pose, long n,
-                      T* d) {
+    plain_dist_kernel(const T* __restrict__ tab, const T* __restrict__ ell, int N, T fx, T fy, T cx, T cy,
+                      const T* __restrict__ pose, long n, T* d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   stage_table<T, KIND>(tab, N, s);
+  const T* u = stage_noise<T, KIND>(ell, N, s);
   const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   M3<T> R;
@@ -188,10 +213,10 @@ __global__ void __launch_bounds__(kPlainThreads)
     T m;
     if (KIND == 0) {
       const T ex = X.x - o[0], ey = X.y - o[1], ez = X.z - o[2];
-      m = a[3] - sqrt(ex * ex + ey * ey + ez * ez);
+      m = a[3] - sqrt(u ? lam_norm2_3(u + 8 * i, ex, ey, ez) : ex * ex + ey * ey + ez * ez);
     } else if (X.z > T(0)) {
       const T gu = o[0] - (fx * X.x + cx * X.z) / X.z, gv = o[1] - (fy * X.y + cy * X.z) / X.z;
-      m = a[3] - sqrt(gu * gu + gv * gv);
+      m = a[3] - sqrt(u ? lam_norm2_2(u + 8 * i, gu, gv) : gu * gu + gv * gv);
     } else {
       m = -T(INFINITY);
     }
@@ -270,11 +295,12 @@ __global__ void __launch_bounds__(kPlainThreads)
 // in_purse of every candidate: all_i |g_i| <= r_i (2D-3D also P_z > 0), eq. 2/3/5.
 template <typename T, int KIND>
 __global__ void __launch_bounds__(kPlainThreads)
-    plain_in_purse_kernel(const T* __restrict__ tab, int N, T fx, T fy, T cx, T cy, const T* __restrict__ cand,
-                          long n, uint8_t* I) {
+    plain_in_purse_kernel(const T* __restrict__ tab, const T* __restrict__ ell, int N, T fx, T fy, T cx, T cy,
+                          const T* __restrict__ cand, long n, uint8_t* I) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   stage_table<T, KIND>(tab, N, s);
+  const T* u = stage_noise<T, KIND>(ell, N, s);
   const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   M3<T> R;
@@ -297,12 +323,12 @@ __global__ void __launch_bounds__(kPlainThreads)
     const V3<T> X = mul(R, V3<T>{a[0], a[1], a[2]}) + t;
     if (KIND == 0) {
       const T ex = X.x - o[0], ey = X.y - o[1], ez = X.z - o[2];
-      ok = ok && ex * ex + ey * ey + ez * ez <= o[3];
+      ok = ok && (u ? lam_norm2_3(u + 8 * i, ex, ey, ez) : ex * ex + ey * ey + ez * ez) <= o[3];
     } else {
       const bool front = X.z > T(0);
       const T Pz = front ? X.z : T(1);
       const T gu = o[0] - (fx * X.x + cx * X.z) / Pz, gv = o[1] - (fy * X.y + cy * X.z) / Pz;
-      ok = ok && front && gu * gu + gv * gv <= o[3];
+      ok = ok && front && (u ? lam_norm2_2(u + 8 * i, gu, gv) : gu * gu + gv * gv) <= o[3];
     }
   }
   I[p] = ok ? 1 : 0;
@@ -374,7 +400,8 @@ static cudaError_t run_plain_t(purse_t h, const purse_params* p, const WalkStats
   const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
   const T* tab = sizeof(T) == 4 ? (const T*)h->tables.f32 : (const T*)h->tables.f64;
   const T fx = T(h->K.fx), fy = T(h->K.fy), cx = T(h->K.cx), cy = T(h->K.cy);
-  const size_t tab_smem = (KIND == 2 ? 16 : 8) * (size_t)N * sizeof(T);
+  const T* ell = sizeof(T) == 4 ? (const T*)h->ell32 : (const T*)h->ell64;
+  const size_t tab_smem = ((KIND == 2 ? 16 : 8) + (ell ? 8 : 0)) * (size_t)N * sizeof(T);
   cudaError_t e = cudaSuccess;
   char* base = reinterpret_cast<char*>(scratch);
   size_t off = 0;
@@ -400,11 +427,12 @@ static cudaError_t run_plain_t(purse_t h, const purse_params* p, const WalkStats
       const long npose = (long)nw * NP, ncand = (long)nw * NT * K;
       plain_perturb_kernel<T, SAMPLER><<<blocks_for((long)nw * ((NP + 1) / 2), TH), TH, 0, st>>>(
           w0, nw, NP, it, key0, key1, d_stats, q, t, pose, pq);
-      plain_dist_kernel<T, KIND><<<blocks_for(npose, TH), TH, tab_smem, st>>>(tab, N, fx, fy, cx, cy, pose, npose, d);
+      plain_dist_kernel<T, KIND><<<blocks_for(npose, TH), TH, tab_smem, st>>>(tab, ell, N, fx, fy, cx, cy, pose,
+                                                                              npose, d);
       plain_topk_kernel<T><<<blocks_for(32L * nw, TH), TH, 0, st>>>(d, w0, nw, NP, K, J, trace, p->n_iter, it);
       plain_ladder_kernel<T, SAMPLER><<<blocks_for(ncand, TH), TH, 0, st>>>(w0, nw, NP, K, NT, p->gamma, q, t, vel,
                                                                             J, pose, cand);
-      plain_in_purse_kernel<T, KIND><<<blocks_for(ncand, TH), TH, tab_smem, st>>>(tab, N, fx, fy, cx, cy, cand,
+      plain_in_purse_kernel<T, KIND><<<blocks_for(ncand, TH), TH, tab_smem, st>>>(tab, ell, N, fx, fy, cx, cy, cand,
                                                                                   ncand, I);
       plain_select_kernel<T, SAMPLER><<<blocks_for(nw, TH), TH, 0, st>>>(w0, nw, NP, K, NT, p->gamma, I, J, pose, pq,
                                                                          vel, q, t, trace, p->n_iter, it);
@@ -422,18 +450,19 @@ static cudaError_t run_plain_t(purse_t h, const purse_params* p, const WalkStats
 
 cudaError_t launch_plain_dist(purse_t h, const float* d_poses, long n_poses, float* d_dist, cudaStream_t st) {
   if (n_poses == 0) return cudaSuccess;
-  const size_t tab_smem = (h->kind == 2 ? 16 : 8) * (size_t)h->n * sizeof(float);
+  const float* ell = h->kind == 2 ? nullptr : h->ell32;
+  const size_t tab_smem = ((h->kind == 2 ? 16 : 8) + (ell ? 8 : 0)) * (size_t)h->n * sizeof(float);
   const float fx = float(h->K.fx), fy = float(h->K.fy), cx = float(h->K.cx), cy = float(h->K.cy);
   const unsigned grid = blocks_for(n_poses, kPlainThreads);
   if (h->kind == 0)
-    plain_dist_kernel<float, 0><<<grid, kPlainThreads, tab_smem, st>>>(h->tables.f32, h->n, fx, fy, cx, cy, d_poses,
-                                                                        n_poses, d_dist);
+    plain_dist_kernel<float, 0><<<grid, kPlainThreads, tab_smem, st>>>(h->tables.f32, ell, h->n, fx, fy, cx, cy,
+                                                                        d_poses, n_poses, d_dist);
   else if (h->kind == 2)
-    plain_dist_kernel<float, 2><<<grid, kPlainThreads, tab_smem, st>>>(h->tables.f32, h->n, fx, fy, cx, cy, d_poses,
-                                                                        n_poses, d_dist);
+    plain_dist_kernel<float, 2><<<grid, kPlainThreads, tab_smem, st>>>(h->tables.f32, nullptr, h->n, fx, fy, cx, cy,
+                                                                        d_poses, n_poses, d_dist);
   else
-    plain_dist_kernel<float, 1><<<grid, kPlainThreads, tab_smem, st>>>(h->tables.f32, h->n, fx, fy, cx, cy, d_poses,
-                                                                        n_poses, d_dist);
+    plain_dist_kernel<float, 1><<<grid, kPlainThreads, tab_smem, st>>>(h->tables.f32, ell, h->n, fx, fy, cx, cy,
+                                                                        d_poses, n_poses, d_dist);
   return cudaGetLastError();
 }
 

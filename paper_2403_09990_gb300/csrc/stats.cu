@@ -27,7 +27,7 @@ __device__ void block_sum(double (&v)[NV], double* red) {
 // tab: FP64 constraint table (rows (a_i, r_i), then (b_i or z_i, r_i^2)).
 __device__ void stats_block(const double* seeds, int s0, const double* tab, int n, int kind, double fx, double fy,
                             double t_p, double th_p, int raw_units, WalkStats* out, double* seed_data, double* red,
-                            WalkStats& sh) {
+                            WalkStats& sh, const double* ell = nullptr) {
   const int tid = threadIdx.x;
   // sums of seed rotations and translations
   double acc[12];
@@ -61,7 +61,12 @@ __device__ void stats_block(const double* seeds, int s0, const double* tab, int 
     double ss = 0.0, rsum = 0.0;
     for (int i = 0; i < n; ++i) {
       for (int c = 0; c < 3; ++c) ss += (tab[4 * i + c] - mean[c]) * (tab[4 * i + c] - mean[c]);
-      rsum += tab[4 * i + 3];
+      // noise radius; with a noise matrix (eq. 4) the geometric-mean semi-axis r_i det(Lambda_i)^(-1/(2d)),
+      // det(Lambda_i) = (prod of the diagonal of its Cholesky factor)^2
+      double scale = 1.0;
+      if (ell && kind == 0) scale = 1.0 / cbrt(ell[8 * i] * ell[8 * i + 3] * ell[8 * i + 5]);
+      if (ell && kind == 1) scale = 1.0 / sqrt(ell[8 * i] * ell[8 * i + 2]);
+      rsum += tab[4 * i + 3] * scale;
     }
     sh.rho_a = sqrt(ss / n);
     for (int k = 0; k < 9; ++k) sh.S[k] = (k % 4 == 0) ? 1.0 : 0.0;
@@ -134,11 +139,12 @@ __device__ void stats_block(const double* seeds, int s0, const double* tab, int 
 }
 
 __global__ void __launch_bounds__(kStatsThreads)
-    stats_kernel(const double* seeds, int s0, const double* tab, int n, int kind, double fx, double fy, double t_p,
+    stats_kernel(const double* seeds, int s0, const double* tab, const double* ell, int n, int kind, double fx,
+                 double fy, double t_p,
                  double th_p, int raw_units, WalkStats* out, double* seed_data) {
   __shared__ double red[12 * kStatsThreads];
   __shared__ WalkStats sh;
-  stats_block(seeds, s0, tab, n, kind, fx, fy, t_p, th_p, raw_units, out, seed_data, red, sh);
+  stats_block(seeds, s0, tab, n, kind, fx, fy, t_p, th_p, raw_units, out, seed_data, red, sh, ell);
 }
 
 // One block per PURSE of a batch; one seed pose per PURSE.
@@ -162,7 +168,7 @@ cudaError_t launch_stats_batch(int n_purses, const BatchPurseInfo* info, const d
 
 cudaError_t launch_stats(purse_t h, const double* d_seeds, int s0, const purse_params* p, WalkStats* d_stats,
                          double* d_seed_data, cudaStream_t st) {
-  stats_kernel<<<1, kStatsThreads, 0, st>>>(d_seeds, s0, h->tables.f64, h->n, h->kind, h->K.fx, h->K.fy,
+  stats_kernel<<<1, kStatsThreads, 0, st>>>(d_seeds, s0, h->tables.f64, h->ell64, h->n, h->kind, h->K.fx, h->K.fy,
                                             p->trans_perturb, p->rot_perturb, p->perturb_units, d_stats, d_seed_data);
   return cudaGetLastError();
 }
@@ -173,8 +179,8 @@ __device__ __forceinline__ uint32_t uniform_index(uint32_t word, uint32_t n) {
 }
 
 __global__ void __launch_bounds__(128)
-    ransag_kernel(const double* tab, int n, uint32_t k0, uint32_t k1, int trial0, int n_trials, double* pose,
-                  uint8_t* acc) {
+    ransag_kernel(const double* tab, const double* ell, int n, uint32_t k0, uint32_t k1, int trial0, int n_trials,
+                  double* pose, uint8_t* acc) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= n_trials) return;
   const uint32_t tau = (uint32_t)(trial0 + tid);
@@ -196,10 +202,17 @@ __global__ void __launch_bounds__(128)
     const double* ai = tab + 4 * idx[c];
     const double* bi = tab + 4 * (n + idx[c]);
     const double r = ai[3];
+    double e0 = X / 1024.0, e1 = Y / 1024.0, e2 = Z / 1024.0;
+    if (ell) {  // a point of the noise ellipsoid: e = U^-1 u (back substitution)
+      const double* U = ell + 8 * idx[c];
+      e2 = e2 / U[5];
+      e1 = (e1 - U[4] * e2) / U[3];
+      e0 = (e0 - U[1] * e1 - U[2] * e2) / U[0];
+    }
     A[c][0] = ai[0], A[c][1] = ai[1], A[c][2] = ai[2];
-    B[c][0] = bi[0] + r * (X / 1024.0);
-    B[c][1] = bi[1] + r * (Y / 1024.0);
-    B[c][2] = bi[2] + r * (Z / 1024.0);
+    B[c][0] = bi[0] + r * e0;
+    B[c][1] = bi[1] + r * e1;
+    B[c][2] = bi[2] + r * e2;
   }
   double abar[3], bbar[3];
   for (int d = 0; d < 3; ++d) {
@@ -220,10 +233,16 @@ __global__ void __launch_bounds__(128)
   for (int i = 0; i < n && ok; ++i) {
     const double* ai = tab + 4 * i;
     const double* bi = tab + 4 * (n + i);
-    double e2 = 0.0;
-    for (int r = 0; r < 3; ++r) {
-      const double e = R.m[3 * r] * ai[0] + R.m[3 * r + 1] * ai[1] + R.m[3 * r + 2] * ai[2] + t[r] - bi[r];
-      e2 += e * e;
+    double e[3];
+    for (int r = 0; r < 3; ++r)
+      e[r] = R.m[3 * r] * ai[0] + R.m[3 * r + 1] * ai[1] + R.m[3 * r + 2] * ai[2] + t[r] - bi[r];
+    double e2;
+    if (ell) {
+      const double* U = ell + 8 * i;
+      const double a = U[0] * e[0] + U[1] * e[1] + U[2] * e[2], b = U[3] * e[1] + U[4] * e[2], c = U[5] * e[2];
+      e2 = a * a + b * b + c * c;
+    } else {
+      e2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
     }
     ok = e2 <= bi[3];
   }
@@ -237,7 +256,7 @@ cudaError_t launch_ransag(purse_t h, uint64_t seed, int trial0, int n_trials, do
                           cudaStream_t st) {
   const int threads = 128;
   ransag_kernel<<<(n_trials + threads - 1) / threads, threads, 0, st>>>(
-      h->tables.f64, h->n, (uint32_t)seed, (uint32_t)(seed >> 32), trial0, n_trials, d_pose, d_acc);
+      h->tables.f64, h->ell64, h->n, (uint32_t)seed, (uint32_t)(seed >> 32), trial0, n_trials, d_pose, d_acc);
   return cudaGetLastError();
 }
 
@@ -355,8 +374,8 @@ __device__ int quartic_real_roots(const double (&A)[5], double (&out)[4]) {
 // the pose maps P_i onto s_i f_i (Horn's fit).  Candidate slot k of the trial holds the k-th pose
 // and acc = 1 when it lies in the PURSE (eq. 2/5, FP64).  Up to four slots per trial.
 __global__ void __launch_bounds__(128)
-    ransag_p3p_kernel(const double* tab, int n, double fx, double fy, double cx, double cy, uint32_t k0, uint32_t k1,
-                      int trial0, int n_trials, double* pose, uint8_t* acc) {
+    ransag_p3p_kernel(const double* tab, const double* ell, int n, double fx, double fy, double cx, double cy,
+                      uint32_t k0, uint32_t k1, int trial0, int n_trials, double* pose, uint8_t* acc) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= n_trials) return;
   const uint32_t tau = (uint32_t)(trial0 + tid);
@@ -379,7 +398,13 @@ __global__ void __launch_bounds__(128)
     const double* bi = tab + 4 * (n + idx[c]);
     const double r = ai[3];
     P[c][0] = ai[0], P[c][1] = ai[1], P[c][2] = ai[2];
-    const double zx = bi[0] + r * (X / 1024.0), zy = bi[1] + r * (Y / 1024.0);
+    double e0 = X / 1024.0, e1 = Y / 1024.0;
+    if (ell) {  // a point of the noise ellipse: e = U^-1 u
+      const double* U = ell + 8 * idx[c];
+      e1 = e1 / U[2];
+      e0 = (e0 - U[1] * e1) / U[0];
+    }
+    const double zx = bi[0] + r * e0, zy = bi[1] + r * e1;
     const double rx = (zx - cx) / fx, ry = (zy - cy) / fy;
     const double nr = sqrt(rx * rx + ry * ry + 1.0);
     f[c][0] = rx / nr, f[c][1] = ry / nr, f[c][2] = 1.0 / nr;
@@ -452,7 +477,13 @@ __global__ void __launch_bounds__(128)
           ok = false;
         } else {
           const double gu = bi[0] - (fx * X0 / X2 + cx), gv = bi[1] - (fy * X1 / X2 + cy);
-          ok = ai[3] - sqrt(gu * gu + gv * gv) >= 0.0;
+          double g2 = gu * gu + gv * gv;
+          if (ell) {
+            const double* U = ell + 8 * i;
+            const double a = U[0] * gu + U[1] * gv, b = U[2] * gv;
+            g2 = a * a + b * b;
+          }
+          ok = ai[3] - sqrt(g2) >= 0.0;
         }
       }
       double* os = o + 12 * slot;
@@ -469,8 +500,8 @@ cudaError_t launch_ransag_p3p(purse_t h, uint64_t seed, int trial0, int n_trials
                               cudaStream_t st) {
   const int threads = 128;
   ransag_p3p_kernel<<<(n_trials + threads - 1) / threads, threads, 0, st>>>(
-      h->tables.f64, h->n, h->K.fx, h->K.fy, h->K.cx, h->K.cy, (uint32_t)seed, (uint32_t)(seed >> 32), trial0,
-      n_trials, d_pose, d_acc);
+      h->tables.f64, h->ell64, h->n, h->K.fx, h->K.fy, h->K.cx, h->K.cy, (uint32_t)seed, (uint32_t)(seed >> 32),
+      trial0, n_trials, d_pose, d_acc);
   return cudaGetLastError();
 }
 

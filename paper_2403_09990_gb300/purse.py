@@ -45,6 +45,7 @@ _VP = ctypes.c_void_p
 _SIGS = {
     "purse_create": [ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)],
     "purse_create_regression": [ctypes.c_int, _VP, _VP, _VP, ctypes.POINTER(_VP)],
+    "purse_set_noise": [_VP, _VP],
     "purse_destroy": [_VP],
     "purse_eval": [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP, _VP],
     "purse_dist": [_VP, ctypes.c_int, _VP, ctypes.c_longlong, _VP, _VP],
@@ -147,6 +148,16 @@ def purse_create_regression(hyp, beta_rot, beta_t) -> int:
     _check(lib().purse_create_regression(hyp.shape[0], hyp.ctypes.data, beta_rot.ctypes.data, beta_t.ctypes.data,
                                          ctypes.byref(h)), "purse_create_regression")
     return h.value
+
+
+def purse_set_noise(h, lam=None):
+    """Noise matrices Lambda_i (n, d, d) of eq. 4 for the handle, or None for the identity."""
+    import numpy as np
+    if lam is None:
+        _check(lib().purse_set_noise(h, None), "purse_set_noise")
+        return
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    _check(lib().purse_set_noise(h, lam.ctypes.data), "purse_set_noise")
 
 
 def purse_destroy(h: int):
@@ -299,6 +310,8 @@ class Purse:
             self.h = purse_create_regression(hyp, p.radii_rot, p.radii)
         else:
             self.h = purse_create(self.kind, p.model, p.obs, p.radii, p.K if self.kind == PURSE_2D3D else None)
+            if getattr(p, "lam", None) is not None:
+                purse_set_noise(self.h, p.lam)
 
     def close(self):
         if self.h:

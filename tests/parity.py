@@ -42,6 +42,9 @@ def constraint_bands(purse, R, t, precision):
         return np.concatenate([np.broadcast_to(bR, lead + bR.shape[-1:]),
                                np.broadcast_to(bt, lead + bt.shape[-1:])], axis=-1)
     X = op.transform(purse.model, R, t)
+    lam = getattr(purse, "lam", None)
+    # with noise matrices (eq. 4) a residual error grows by at most sqrt(lambda_max(Lambda_i))
+    lscale = 1.0 if lam is None else np.sqrt(np.linalg.eigvalsh(lam)[:, -1])
     if purse.kind == KIND_2D3D:
         fx, fy, cx, cy = purse.K
         Px = fx * X[..., 0] + cx * X[..., 2]
@@ -54,7 +57,7 @@ def constraint_bands(purse, R, t, precision):
         RA = X - np.asarray(t)[..., None, :]
         mag = (np.linalg.norm(RA, axis=-1) + np.linalg.norm(np.asarray(t), axis=-1)[..., None]
                + np.linalg.norm(purse.obs, axis=-1))
-    return 1e-6 * purse.radii + 8.0 * eps * mag
+    return 1e-6 * purse.radii + 8.0 * eps * mag * lscale
 
 
 def classify(purse, R, t, precision):

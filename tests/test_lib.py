@@ -81,3 +81,9 @@ def test_regression_create_validation_without_gpu():
     z = np.array([0.1, 0.0, 0.1])
     assert L.purse_create_regression(3, hyp.ctypes.data, z.ctypes.data, bt.ctypes.data, ctypes.byref(h)) == 1
     assert L.purse_create_regression(3, None, bR.ctypes.data, bt.ctypes.data, ctypes.byref(h)) == 1
+
+
+def test_noise_matrix_validation_without_gpu():
+    L = P.lib()
+    assert L.purse_set_noise(None, None) == 1
+    assert b"NULL handle" in L.purse_last_error()
