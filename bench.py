@@ -180,6 +180,20 @@ def cpu_cores():
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def combine_ranks(t_step, evals, dist, device):
+    """Whole-job step time and executed evaluations of replicas: the largest per-rank step time (every rank
+    ends its timed region before the slowest one) and the sum of the per-rank evaluations.  dist is the
+    initialised torch.distributed module (None for one process)."""
+    if dist is None:
+        return t_step, float(evals)
+    import torch
+    tt = torch.tensor([t_step], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ee = torch.tensor([float(evals)], device=device, dtype=torch.float64)
+    dist.all_reduce(ee)
+    return float(tt.item()), float(ee.item())
+
+
 def run_gpu(args, rank, world):
     import torch
     import paper_2403_09990_gb300.purse as P
@@ -255,16 +269,7 @@ def run_gpu(args, rank, world):
         evals += eR + eT
         evR += eR
         evT += eT
-    t_step = tot / args.steps / 1e3
-    if dist:
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
-        ee = torch.tensor([float(evals)], device=dev, dtype=torch.float64)
-        dist.all_reduce(ee)
-        evals_all = float(ee.item())
-    else:
-        evals_all = float(evals)
+    t_step, evals_all = combine_ranks(tot / args.steps / 1e3, evals, dist, dev)
     value = evals_alg * world / t_step
     executed_per_s = evals_all / (t_step * args.steps)
     # roofline of the dominant kernel (the slower of the two walk kernels)
