@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -83,7 +84,7 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -305,6 +306,7 @@ def run_gpu(args, rank, world):
         "clocks": ck, "wall_s_timed": wall,
     }
     out["megb_exact"] = run_exact(hR, qR, tT, res, dev)
+    out["ransag"] = run_ransag(dev)
     if not args.no_plain:
         out["plain_gpu"] = run_plain(args, p, dev, seeds, value / world, t_step)
     if rank == 0 and not args.no_e2e:
@@ -325,6 +327,32 @@ def run_gpu(args, rank, world):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def run_ransag(dev):
+    """Step I on the GPU, timed by the wall clock around the call (it synchronises): P3P RANSAG on the
+    bench's 2D-3D PURSE (N = 16) and Arun/Horn RANSAG on a 3D-3D PURSE (N = 8), 2^20 trials each (up to
+    2^20 seeds kept, so every trial runs)."""
+    import torch
+    import paper_2403_09990_gb300.purse as P
+    from paper_2403_09990_gb300 import synthetic as syn
+    trials = 1 << 20
+    seeds = torch.empty((trials, 12), dtype=torch.float64, device=dev)
+    out = {}
+    for name, p in (("2d3d_p3p", syn.purse_2d3d(N_KEYPOINTS, PURSE_SEED)), ("3d3d_arun", syn.purse_3d3d(8, 0))):
+        with P.Purse(p) as h:
+            try:
+                P.purse_ransag(h.h, 1, 1 << 16, trials, seeds)       # warm-up
+            except P.PurseError:
+                pass
+            t0 = time.perf_counter()
+            try:
+                n = P.purse_ransag(h.h, 2, trials, trials, seeds)
+            except P.PurseError:                                     # no trial inside the PURSE
+                n = 0
+            dt = time.perf_counter() - t0
+        out[name] = {"trials": trials, "ms": dt * 1e3, "trials_per_s": trials / dt, "seeds": n}
+    return out
 
 
 def run_exact(h, qR, tT, res, dev):

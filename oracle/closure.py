@@ -11,7 +11,7 @@ Restates, in the paper's order and notation,
   Delta T = gamma^(m-1) -> in_purse -> find_farthest (m0 = smallest feasible
   m, then the best-ranked feasible k).
 
-Readings of the paper used here (each listed in the design doc):
+Readings of the paper used here (where it is silent or ambiguous):
 * update_rotation(R*, omega, dT) = Exp(dT omega) R*, translation unchanged;
   update_translation(t*, R_jk, v, dT) = t* + dT v (R_jk unused).
 * perturbation(t_p) is a point uniform in the ball of radius t_p * sigma_t

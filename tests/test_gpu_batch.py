@@ -9,7 +9,7 @@ from oracle import closure, so3
 from paper_2403_09990_gb300 import purse as P
 from paper_2403_09990_gb300 import synthetic as syn
 from tests import parity
-from tests.gpu_helpers import params_from
+from tests.gpu_helpers import params_from, sample
 
 pytestmark = pytest.mark.gpu
 
@@ -156,5 +156,46 @@ def test_batch_gradients_equal_single_path():
                 assert torch.all(gyb[:, 2] == 0)
             assert float(rr1.abs().max()) > 0
             o += pu.n
+    finally:
+        P.purse_batch_destroy(b)
+
+
+def test_batch_full_size_sampled():
+    """The batched workload at full size and in the bench's launch configuration (4096 PURSEs of
+    4096 samples, autotuned launch, graph replay): eight sampled PURSEs equal the single-PURSE path
+    bit for bit, sixteen sampled walks of two of them are replayed by the oracle, every result is
+    finite and every ball radius is positive."""
+    n_purses, S, K = 4096, 4096, 200
+    purses = syn.purse_batch(n_purses, seed=7)
+    p3, p2 = presets()
+    seeds = torch.as_tensor(syn.seed_array(purses), dtype=torch.float64, device="cuda")
+    res = torch.full((n_purses, 9), np.nan, dtype=torch.float64, device="cuda")
+    pp3, pp2 = params_from(p3, 0, 0), params_from(p2, 0, 0)
+    b = P.purse_batch_create(purses)
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(n_purses, 8, replace=False))
+    try:
+        P.purse_batch_tune(b, pp3, pp2, 1, seeds, 1024)
+        P.purse_batch_solve(b, pp3, pp2, 55, seeds, S, K, res)
+        P.purse_batch_sync(b)
+        r = res.cpu().numpy()
+        assert np.all(np.isfinite(r)) and np.all(r[:, 7] > 0) and np.all(r[:, 8] > 0)
+        for n, p in enumerate(pick):
+            pu = purses[p]
+            bq, bt = torch.empty((S, 4), device="cuda"), torch.empty((S, 3), device="cuda")
+            bq2, bt2 = torch.empty((S, 4), device="cuda"), torch.empty((S, 3), device="cuda")
+            P.purse_batch_copy_samples(b, int(p), bq, bt, bq2, bt2)
+            torch.cuda.synchronize()
+            prm = p3 if pu.kind == 0 else p2
+            q, t = single(pu, prm, 0, 55 + int(p), S)
+            assert torch.equal(q, bq) and torch.equal(t, bt), p
+            if n < 2:  # oracle replay of sampled walks of this PURSE (the batch draws with key seed + p)
+                ids = np.sort(rng.choice(S, 8, replace=False))
+                with P.Purse(pu) as h:
+                    _, _, tr = sample(h.h, prm, 0, 0, 55 + int(p), pu.seed_pose()[None], S, trace_rows=ids)
+                R, tt, rep = parity.replay_walks(pu, pu.seed_pose()[None], prm, 55 + int(p), ids, tr, 0, 0)
+                assert rep.ok(), rep.inconsistent[:5]
+                qn = q.cpu().numpy()[ids].astype(np.float64)
+                assert parity.rot_angle(qn, so3.quat_from_R(R)).max() <= 1e-5
     finally:
         P.purse_batch_destroy(b)
