@@ -772,7 +772,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-walks", type=int, default=192, help="oracle walks per worker per sampler (cpu_baseline)")
-    ap.add_argument("--ref-walks", type=int, default=2, help="oracle walks per worker per sampler (reference arm)")
+    ap.add_argument("--ref-walks", type=int, default=64, help="oracle walks per worker per sampler (reference arm)")
     ap.add_argument("--cpu-workers", type=int, default=min(16, cpu_cores()))
     ap.add_argument("--walks", type=int, default=N_WALKS, help="walks per sampler (profiling of a smaller case)")
     ap.add_argument("--iters", type=int, default=N_ITER, help="walk iterations (profiling of a smaller case)")

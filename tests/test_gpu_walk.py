@@ -50,6 +50,12 @@ CASES = {
     "2d3d-R-fp64-n256": dict(kind=1, sampler=0, precision=1, prm=dict(n_iter=3), seeds="gt", n=256),
     "2d3d-t-fp32-n128": dict(kind=1, sampler=1, precision=0, prm=dict(n_iter=3), seeds="gt", n=128),
     "3d3d-R-fp32-n64": dict(kind=0, sampler=0, precision=0, prm=dict(n_iter=3), seeds="gt", n=64),
+    # degenerate settings: the fewest constraints, one perturbation kept of one, a single rung, gamma = 1
+    "3d3d-R-fp64-n3-np1-keep1-nt1": dict(kind=0, sampler=0, precision=1, seeds="gt", n=3,
+                                         prm=dict(n_perturb=1, n_keep=1, n_steps=1)),
+    "2d3d-t-fp32-n3-np2-keep2-nt2-gamma1": dict(kind=1, sampler=1, precision=0, seeds="gt", n=3,
+                                                prm=dict(n_perturb=2, n_keep=2, n_steps=2, gamma=1.0)),
+    "2d3d-R-fp32-np33-keep1": dict(kind=1, sampler=0, precision=0, seeds="gt", prm=dict(n_perturb=33, n_keep=1)),
 }
 
 
@@ -86,7 +92,8 @@ def test_walk_replay(name):
     assert np.all(cls >= 0)
     # the walks move: most end away from their seed
     moved = (tr[:, :, prm.n_keep] >= 0).any(axis=1).mean()
-    assert moved > 0.5
+    if prm.n_steps >= 3:  # with one or two rungs the full step may never fit
+        assert moved > 0.5
     print(f"{name}: robust fraction {rep.robust.mean():.3f}, moved {moved:.3f}")
 
 
