@@ -309,36 +309,32 @@ __device__ __forceinline__ void top_k(const Slab<T>& sl, int NP, int K, int lane
   }
 }
 
-// in_purse of one ladder chunk (one candidate per lane): constraint pairs in groups of two, a warp
-// vote after each group leaves the chunk once every candidate has violated a constraint.  Z: track
-// the cheirality minimum (2D-3D; off when the caller has bounded P_z away from 0).
+// in_purse of one ladder chunk (one candidate per lane): one constraint pair (two constraints on the
+// paired lanes) at a time, a warp vote after each pair leaves the chunk once every candidate has
+// violated a constraint.  The constraints come in ascending margin at the current pose, so most
+// candidates die on the first pairs; a vote per pair measured faster than one per two or more.
+// Z: track the cheirality minimum (2D-3D; off when the caller has bounded P_z away from 0).
 template <typename T, int KIND, bool Z>
 __device__ __forceinline__ void ladder_scan(const P2<T>* L, int NQ, int N, const P2<T> (&M2)[9], P2<T> bx, P2<T> by,
                                             P2<T> bz, P2<T>& cmax, P2<T>& zmin, bool& alive, int& done) {
   using T2 = P2<T>;
-  for (int g0 = 0; g0 < NQ; g0 += 2) {
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int qi = g0 + u;
-      if (qi < NQ) {
-        const T2* Lq = L + 8 * qi;
-        const T2 yx = Lq[0], yy = Lq[1], yz = Lq[2], o3 = Lq[3], o4 = Lq[4], o5 = Lq[5];
-        const T2 Px = fma2(M2[0], yx, fma2(M2[1], yy, fma2(M2[2], yz, bx)));
-        const T2 Py = fma2(M2[3], yx, fma2(M2[4], yy, fma2(M2[5], yz, by)));
-        const T2 Pz = fma2(M2[6], yx, fma2(M2[7], yy, fma2(M2[8], yz, bz)));
-        T2 c;
-        if (KIND == 1) {
-          const T2 ex = fma2(o3, Pz, Px), ey = fma2(o4, Pz, Py);
-          c = fma2(o5, mul2(Pz, Pz), fma2(ey, ey, mul2(ex, ex)));
-          if (Z) zmin = min2(zmin, Pz);
-        } else {
-          const T2 ex = add2(Px, o3), ey = add2(Py, o4), ez = add2(Pz, o5);
-          c = add2(fma2(ez, ez, fma2(ey, ey, mul2(ex, ex))), Lq[6]);
-        }
-        cmax = max2(cmax, c);
-      }
+  for (int qi = 0; qi < NQ; ++qi) {
+    const T2* Lq = L + 8 * qi;
+    const T2 yx = Lq[0], yy = Lq[1], yz = Lq[2], o3 = Lq[3], o4 = Lq[4], o5 = Lq[5];
+    const T2 Px = fma2(M2[0], yx, fma2(M2[1], yy, fma2(M2[2], yz, bx)));
+    const T2 Py = fma2(M2[3], yx, fma2(M2[4], yy, fma2(M2[5], yz, by)));
+    const T2 Pz = fma2(M2[6], yx, fma2(M2[7], yy, fma2(M2[8], yz, bz)));
+    T2 c;
+    if (KIND == 1) {
+      const T2 ex = fma2(o3, Pz, Px), ey = fma2(o4, Pz, Py);
+      c = fma2(o5, mul2(Pz, Pz), fma2(ey, ey, mul2(ex, ex)));
+      if (Z) zmin = min2(zmin, Pz);
+    } else {
+      const T2 ex = add2(Px, o3), ey = add2(Py, o4), ez = add2(Pz, o5);
+      c = add2(fma2(ez, ez, fma2(ey, ey, mul2(ex, ex))), Lq[6]);
     }
-    done = min(N, 2 * (g0 + 2));
+    cmax = max2(cmax, c);
+    done = min(N, 2 * (qi + 1));
     alive = alive && fmax(cmax.x, cmax.y) <= T(0) && (KIND == 0 || !Z || fmin(zmin.x, zmin.y) > T(0));
     if (!__any_sync(kFullMask, alive)) break;
   }
@@ -685,7 +681,7 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
     // ---- a6/a7: step ladder + in_purse with early exit, find_farthest
     int m0 = -1, k0 = -1;
     V3<T> base{T(0), T(0), T(0)};
-    M3<T> Ak;  // dS_t: (K) R_{j_k}
+    M3<T> Ak = M3<T>{{T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)}};  // dS_t: (K) R_{j_k}
     if (lane < ncand) {
       const T4<T> pj = sl.P[sl.J[ck]];
       if (SAMPLER == 0) {
@@ -701,6 +697,11 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
         }
       }
     }
+    T2 M2t[9];
+    if constexpr (SAMPLER == 1) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) M2t[c] = dup(Ak.m[c]);
+    }
     for (int mb = 0; mb < NT; mb += mc) {
       const int m = mb + cm;
       const bool active = lane < ncand && m < NT;
@@ -711,7 +712,6 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
           const T4<T> e0 = sl.E[4 * m + 1], e1 = sl.E[4 * m + 2], e2 = sl.E[4 * m + 3];
           M = M3<T>{{e0.x, e0.y, e0.z, e1.x, e1.y, e1.z, e2.x, e2.y, e2.z}};
         } else {
-          M = Ak;
           const T4<T> sv = sl.E[4 * m];
           const V3<T> Tm{t.x + sv.x, t.y + sv.y, t.z + sv.z};
           bm = KIND == 1 ? V3<T>{fx * Tm.x + cx * Tm.z, fy * Tm.y + cy * Tm.z, Tm.z} : Tm;
@@ -719,7 +719,7 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
       }
       T2 M2[9];
 #pragma unroll
-      for (int c = 0; c < 9; ++c) M2[c] = dup(M.m[c]);
+      for (int c = 0; c < 9; ++c) M2[c] = SAMPLER == 1 ? M2t[c] : dup(M.m[c]);
       const T2 bx = dup(bm.x), by = dup(bm.y), bz = dup(bm.z);
       T2 cmax = dup(-inf<T>()), zmin = dup(inf<T>());
       bool alive = active;
