@@ -481,6 +481,9 @@ def run_sweep(args):
     for kind in (kinds if "dist" in args.sweep_parts else ()):
         for n in ns:
             print(json.dumps(sweep_dist(P, syn, dev, stream, kind, n)), flush=True)
+    if "next" in args.sweep_parts:
+        for line in sweep_next(P, syn, dev, stream):
+            print(json.dumps(line), flush=True)
     p = syn.purse_2d3d(N_KEYPOINTS, 0)
     for lg in ((22, 24, 26) if "scale" in args.sweep_parts else ()):
         S = 1 << lg
@@ -491,6 +494,147 @@ def run_sweep(args):
                           "megb_gbs": ball_bytes / (m32 / 1e3) / 1e9,
                           "megb_bytes_note": "16 B per rotation sample + 12 B per translation sample, per GGD "
                                              "iteration and the final pass", "D": r32[7], "d": r32[8]}), flush=True)
+
+
+def _host_timed(fn):
+    t0 = time.perf_counter()
+    out = fn()
+    return out, time.perf_counter() - t0
+
+
+def sweep_next(P, syn, dev, stream):
+    """The rows beyond the main workload, each with its oracle timed beside it (the cpu_baseline leg of each
+    line: one host core, FP64, a bounded sample of the same input): P3P RANSAG (2D-3D Step I), the exact
+    Step III miniball of boundary samples, the pose-regression PURSE (Example 3) and 2D-3D constraints in the
+    norm of eq. 4; the last two run through the per-operation samplers, beside the fused isotropic walk of
+    the same size.  GPU parts: CUDA events (the RANSAG call synchronises, so it takes the wall clock)."""
+    import torch
+    from oracle import closure, megb as om, p3p as op3, ransag as ora
+    lines = []
+
+    def events(fn, reps):
+        times = []
+        for r in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if r:  # the first call warms up
+                times.append(e0.elapsed_time(e1))
+        return statistics.median(times)
+
+    def cpu(value, unit, sample):
+        return {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample}
+
+    # ---- P3P RANSAG on the bench's 2D-3D PURSE
+    p = syn.purse_2d3d(N_KEYPOINTS, PURSE_SEED)
+    trials = 1 << 20
+    seeds = torch.empty((trials, 12), dtype=torch.float64, device=dev)
+    with P.Purse(p) as h:
+        try:
+            P.purse_ransag(h.h, 1, 1 << 16, trials, seeds)           # warm-up
+        except P.PurseError:
+            pass
+        n, dt = _host_timed(lambda: P.purse_ransag(h.h, 2, trials, trials, seeds))
+    ot = 1 << 13
+    (os_, _), odt = _host_timed(lambda: op3.ransag_2d3d(p, 2, ot, ot))
+    lines.append({"sweep": "next", "row": "p3p_ransag", "workload": f"2D-3D PURSE N={N_KEYPOINTS}, {trials} trials",
+                  "gpu": {"ms": dt * 1e3, "trials_per_s": trials / dt, "seeds": n},
+                  "cpu_baseline": cpu(ot / odt, "trials/s", f"{ot} trials ({len(os_)} seeds)"),
+                  "gpu_over_oracle": (trials / dt) / (ot / odt)})
+
+    # ---- exact miniball of 2^20 boundary samples per set (fused walks, N_I = 5)
+    S = 1 << 20
+    qR = torch.empty((S, 4), dtype=torch.float32, device=dev)
+    tR = torch.empty((S, 3), dtype=torch.float32, device=dev)
+    qT = torch.empty((S, 4), dtype=torch.float32, device=dev)
+    tT = torch.empty((S, 3), dtype=torch.float32, device=dev)
+    res = torch.empty(9, dtype=torch.float64, device=dev)
+    ex = torch.empty(9, dtype=torch.float64, device=dev)
+    sd = torch.as_tensor(p.seed_pose()[None], dtype=torch.float64, device=dev)
+    with P.Purse(p) as h:
+        iso_ms = events(lambda: (P.purse_sample(h.h, closure_params(0, 5), 9, sd, 1, S, qR, tR, None, stream),
+                                 P.purse_sample(h.h, closure_params(1, 5), 9, sd, 1, S, qT, tT, None, stream)), 1)
+        P.megb_solve(h.h, 0, K_MEGB, qR, S, tT, S, res, None, stream)
+        ref = res[:4].contiguous()
+        ems = events(lambda: P.megb_solve_exact(h.h, 0, qR, S, tT, S, ex, ref, stream), 2)
+    m = 1 << 12
+    qn, tn = qR[:m].double().cpu().numpy(), tT[:m].double().cpu().numpy()
+    _, odt = _host_timed(lambda: (om.meb_exact_translation(tn), om.meb_exact_rotation(qn, qn[0])))
+    lines.append({"sweep": "next", "row": "exact_meb", "workload": f"{S} rotation + {S} translation samples "
+                  f"(2D-3D N={N_KEYPOINTS} boundary walks, N_I=5)",
+                  "gpu": {"ms": ems, "samples_per_s": 2 * S / (ems / 1e3), "D": float(ex[7]), "d": float(ex[8])},
+                  "cpu_baseline": cpu(2 * m / odt, "samples/s", f"the first {m} samples of each set (Welzl)"),
+                  "gpu_over_oracle": (2 * S / (ems / 1e3)) / (2 * m / odt)})
+
+    def plain_row(name, purse, prm, samplers, gpu_seeds, s0, seeds_np, walks, oracle_walks, note):
+        Sx = walks
+        q = torch.empty((Sx, 4), dtype=torch.float32, device=dev)
+        t = torch.empty((Sx, 3), dtype=torch.float32, device=dev)
+        q2 = torch.empty((Sx, 4), dtype=torch.float32, device=dev)
+        t2 = torch.empty((Sx, 3), dtype=torch.float32, device=dev)
+        r = torch.empty(9, dtype=torch.float64, device=dev)
+        with P.Purse(purse) as h:
+            def run():
+                P.purse_sample_plain(h.h, prm(0), 11, gpu_seeds, s0, Sx, q, t, None, stream)
+                if 1 in samplers:
+                    P.purse_sample_plain(h.h, prm(1), 11, gpu_seeds, s0, Sx, q2, t2, None, stream)
+                P.megb_solve(h.h, 0, K_MEGB, q, Sx, t2 if 1 in samplers else t, Sx, r, None, stream)
+            ms = events(run, 2)
+        per_walk = prm(0).n_iter * (prm(0).n_perturb + prm(0).n_keep * prm(0).n_steps) * (
+            2 * purse.n if purse.kind == syn.KIND_REG else purse.n)
+        evals = len(samplers) * Sx * per_walk
+        oprm = oracle_params(purse)
+        ids = np.arange(oracle_walks)
+
+        def oracle_run():
+            R, tt = closure.sample_rotation_boundary(purse, seeds_np, oprm, 11, ids)
+            qs, ts = closure.as_samples(R, tt)
+            if 1 in samplers:
+                R2, tt2 = closure.sample_translation_boundary(purse, seeds_np, oprm, 11, ids)
+                ts = closure.as_samples(R2, tt2)[1]
+            om.megb_rotation(qs, K_MEGB)
+            om.megb_translation(ts, K_MEGB)
+        _, odt = _host_timed(oracle_run)
+        oev = len(samplers) * oracle_walks * per_walk
+        return {"sweep": "next", "row": name, "workload": note, "gpu": {"ms": ms, "evals_per_s": evals / (ms / 1e3),
+                "path": "purse_sample_plain + megb_solve", "D": float(r[7]), "d": float(r[8])},
+                "cpu_baseline": cpu(oev / (odt), "evals/s", f"{oracle_walks} walks per sampler + both balls"),
+                "gpu_over_oracle": (evals / (ms / 1e3)) / (oev / odt)}
+
+    # ---- pose regression (10 hypotheses, LM preset: dS_R walks, both balls from them)
+    pr = syn.purse_reg(10, 0)
+    reg_seeds = torch.empty((2048, 12), dtype=torch.float64, device=dev)
+    with P.Purse(pr) as h:
+        s0 = P.purse_ransag(h.h, 3, 20000, 2048, reg_seeds)
+    oseeds, _ = ora.convex_seeds(pr, 3, 20000, 2048)
+
+    def reg_params(sampler):
+        return P.make_params(n_iter=5, n_perturb=150, n_keep=10, n_steps=10, omega0=0.5, v0=0.0, gamma=0.5,
+                             rot_perturb=0.0, trans_perturb=0.1, perturb_units=0, sampler=sampler, precision=0)
+    lines.append(plain_row("purse_reg", pr, reg_params, (0,), reg_seeds, s0, oseeds, 1 << 18, 2048,
+                           "pose regression, 10 hypotheses (Example 3), convex seeds, 2^18 dS_R walks (N_I=5, "
+                           "N_P=150, N_P*=10, N_T=10), both balls"))
+
+    # ---- 2D-3D with noise matrices (eq. 4), both samplers, beside the isotropic fused walk above
+    pl = syn.purse_2d3d_ellipsoidal(N_KEYPOINTS, 0)
+    lam_seeds = torch.as_tensor(pl.seed_pose()[None], dtype=torch.float64, device=dev)
+    row = plain_row("lambda_norm_2d3d", pl, lambda smp: closure_params(smp, 5), (0, 1), lam_seeds, 1,
+                    pl.seed_pose()[None], 1 << 20, 1024,
+                    f"2D-3D PURSE N={N_KEYPOINTS} with 2x2 noise matrices (eigenvalues 0.5-2), ground-truth seed, "
+                    "2^20 walks per sampler (N_I=5), both balls")
+    iso_evals = 2 * S * 5 * (N_PERTURB + N_KEEP * N_STEPS) * N_KEYPOINTS
+    row["isotropic_fused_walks"] = {"ms": iso_ms, "evals_per_s": iso_evals / (iso_ms / 1e3),
+                                    "note": "purse_sample (fused kernels) on the identity-norm PURSE of the same seed"}
+    lines.append(row)
+    return lines
+
+
+def oracle_params(purse):
+    from oracle import closure
+    from paper_2403_09990_gb300 import synthetic as syn
+    return closure.preset_reg() if purse.kind == syn.KIND_REG else closure.preset_2d3d()
 
 
 def sweep_dist(P, syn, dev, stream, kind, n, n_poses=1 << 24):
@@ -787,7 +931,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-grad", action="store_true", help="skip the batched differentiation measurement")
     ap.add_argument("--sweep", action="store_true", help="precision / scale sweep instead of the bench step")
-    ap.add_argument("--sweep-parts", default="precision,scale,dist", help="which parts of the sweep to run")
+    ap.add_argument("--sweep-parts", default="precision,scale,dist,next", help="which parts of the sweep to run")
     ap.add_argument("--dist-kind", type=int, default=None, help="dist sweep: one PURSE kind (0 3D-3D, 1 2D-3D)")
     ap.add_argument("--dist-n", type=int, default=None, help="dist sweep: one keypoint count")
     ap.add_argument("--grad-purses", type=int, default=1024)
