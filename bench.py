@@ -506,8 +506,8 @@ def sweep_next(P, syn, dev, stream):
     """The rows beyond the main workload, each with its oracle timed beside it (the cpu_baseline leg of each
     line: one host core, FP64, a bounded sample of the same input): P3P RANSAG (2D-3D Step I), the exact
     Step III miniball of boundary samples, the pose-regression PURSE (Example 3) and 2D-3D constraints in the
-    norm of eq. 4; the last two run through the per-operation samplers, beside the fused isotropic walk of
-    the same size.  GPU parts: CUDA events (the RANSAG call synchronises, so it takes the wall clock)."""
+    norm of eq. 4; pose regression runs through the per-operation samplers, the noise matrices through the
+    fused walk kernels beside the per-operation samplers and the isotropic fused walk of the same size.  GPU parts: CUDA events (the RANSAG call synchronises, so it takes the wall clock)."""
     import torch
     from oracle import closure, megb as om, p3p as op3, ransag as ora
     lines = []
@@ -568,7 +568,7 @@ def sweep_next(P, syn, dev, stream):
                   "cpu_baseline": cpu(2 * m / odt, "samples/s", f"the first {m} samples of each set (Welzl)"),
                   "gpu_over_oracle": (2 * S / (ems / 1e3)) / (2 * m / odt)})
 
-    def plain_row(name, purse, prm, samplers, gpu_seeds, s0, seeds_np, walks, oracle_walks, note):
+    def plain_row(name, purse, prm, samplers, gpu_seeds, s0, seeds_np, walks, oracle_walks, note, fused=False):
         Sx = walks
         q = torch.empty((Sx, 4), dtype=torch.float32, device=dev)
         t = torch.empty((Sx, 3), dtype=torch.float32, device=dev)
@@ -576,12 +576,14 @@ def sweep_next(P, syn, dev, stream):
         t2 = torch.empty((Sx, 3), dtype=torch.float32, device=dev)
         r = torch.empty(9, dtype=torch.float64, device=dev)
         with P.Purse(purse) as h:
-            def run():
-                P.purse_sample_plain(h.h, prm(0), 11, gpu_seeds, s0, Sx, q, t, None, stream)
+            def run(sample):
+                sample(h.h, prm(0), 11, gpu_seeds, s0, Sx, q, t, None, stream)
                 if 1 in samplers:
-                    P.purse_sample_plain(h.h, prm(1), 11, gpu_seeds, s0, Sx, q2, t2, None, stream)
+                    sample(h.h, prm(1), 11, gpu_seeds, s0, Sx, q2, t2, None, stream)
                 P.megb_solve(h.h, 0, K_MEGB, q, Sx, t2 if 1 in samplers else t, Sx, r, None, stream)
-            ms = events(run, 2)
+            ms = events(lambda: run(P.purse_sample_plain), 2)
+            ms_fused = events(lambda: run(P.purse_sample), 2) if fused else None
+            r_fused = r.cpu().numpy() if fused else None
         per_walk = prm(0).n_iter * (prm(0).n_perturb + prm(0).n_keep * prm(0).n_steps) * (
             2 * purse.n if purse.kind == syn.KIND_REG else purse.n)
         evals = len(samplers) * Sx * per_walk
@@ -598,10 +600,15 @@ def sweep_next(P, syn, dev, stream):
             om.megb_translation(ts, K_MEGB)
         _, odt = _host_timed(oracle_run)
         oev = len(samplers) * oracle_walks * per_walk
-        return {"sweep": "next", "row": name, "workload": note, "gpu": {"ms": ms, "evals_per_s": evals / (ms / 1e3),
-                "path": "purse_sample_plain + megb_solve", "D": float(r[7]), "d": float(r[8])},
-                "cpu_baseline": cpu(oev / (odt), "evals/s", f"{oracle_walks} walks per sampler + both balls"),
-                "gpu_over_oracle": (evals / (ms / 1e3)) / (oev / odt)}
+        plain = {"ms": ms, "evals_per_s": evals / (ms / 1e3), "path": "purse_sample_plain + megb_solve"}
+        out = {"sweep": "next", "row": name, "workload": note, "gpu": plain,
+               "cpu_baseline": cpu(oev / (odt), "evals/s", f"{oracle_walks} walks per sampler + both balls")}
+        if fused:
+            out["gpu"] = {"ms": ms_fused, "evals_per_s": evals / (ms_fused / 1e3), "path": "purse_sample + megb_solve",
+                          "D": float(r_fused[7]), "d": float(r_fused[8])}
+            out["gpu_plain"] = plain
+        out["gpu_over_oracle"] = out["gpu"]["evals_per_s"] / (oev / odt)
+        return out
 
     # ---- pose regression (10 hypotheses, LM preset: dS_R walks, both balls from them)
     pr = syn.purse_reg(10, 0)
@@ -623,10 +630,10 @@ def sweep_next(P, syn, dev, stream):
     row = plain_row("lambda_norm_2d3d", pl, lambda smp: closure_params(smp, 5), (0, 1), lam_seeds, 1,
                     pl.seed_pose()[None], 1 << 20, 1024,
                     f"2D-3D PURSE N={N_KEYPOINTS} with 2x2 noise matrices (eigenvalues 0.5-2), ground-truth seed, "
-                    "2^20 walks per sampler (N_I=5), both balls")
+                    "2^20 walks per sampler (N_I=5), both balls", fused=True)
     iso_evals = 2 * S * 5 * (N_PERTURB + N_KEEP * N_STEPS) * N_KEYPOINTS
     row["isotropic_fused_walks"] = {"ms": iso_ms, "evals_per_s": iso_evals / (iso_ms / 1e3),
-                                    "note": "purse_sample (fused kernels) on the identity-norm PURSE of the same seed"}
+                                    "note": "purse_sample on the identity-norm PURSE of the same seed, walks only"}
     lines.append(row)
     return lines
 

@@ -76,6 +76,7 @@ struct BatchArgs {
 
 struct WalkArgs {
   const void* table;
+  const void* ell;  // noise factors U_i of eq. 4 (8 values per constraint, the table's precision) or NULL
   int n;
   double fx, fy, cx, cy;
   double rho_max;  // largest model-point radius max_i |Z_i|

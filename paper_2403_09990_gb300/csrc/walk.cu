@@ -14,10 +14,10 @@
 //      a warp max (REDUX) pop the best head; ties go to the lower j;
 //   4. step ladder: candidates (k, m) are laid out lane = m_local * N_P* + k
 //      over chunks of 32 / N_P* rungs; in_purse is evaluated division-free
-//      two constraints at a time (paired FP32), four per group, and a chunk
-//      is left as soon
-//      as a warp vote shows that every candidate has violated one (in_purse
-//      is a conjunction, so the order and the early exit do not change it);
+//      two constraints at a time (paired FP32), and a chunk is left as soon
+//      as a warp vote after a pair shows that every candidate has violated
+//      one (in_purse is a conjunction, so the order and the early exit do
+//      not change it);
 //      the first chunk with a feasible candidate ends the ladder and __ffs
 //      of the ballot gives m0 (smallest m) then k0 (best-ranked k);
 //   5. update (R*, t*).
@@ -26,6 +26,9 @@
 //   dS_R, 2D-3D: K(R* Z_i + t* + delta_j) = Q_i + K delta_j
 //   dS_t, 2D-3D: K(R_p R* Z_i + t*)       = (K R_p) Y_i + K t*
 // and the same without K (minus b_i) for 3D-3D.
+// Noise matrices (eq. 4, LAM): the residual g_i enters every norm as U_i g_i
+// with Lambda_i = U_i^T U_i (upper triangular); for 2D-3D U_i acts on the
+// division-free pixel residual (e_x, e_y), which P_z > 0 only scales.
 #include <cfloat>
 #include <cstdio>
 
@@ -83,10 +86,16 @@ __device__ __forceinline__ T inf() {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Constraint table in shared memory: rows [0, N) (a or Z, r), [N, 2N) (b or z, r^2); with noise
+// matrices then two rows per constraint of U_i (3D: u00 u01 u02 u11 | u12 u22; 2D: u00 u01 u11).
 template <typename T>
-__host__ __device__ inline size_t walk_table_bytes(int n) {
-  return align_up(8 * (size_t)n * sizeof(T), 128);
+__host__ __device__ inline size_t walk_table_bytes(int n, bool lam = false) {
+  return align_up((lam ? 16 : 8) * (size_t)n * sizeof(T), 128);
 }
+
+// Pairs per constraint row of the slab tables D and L: 8, or 16 with the U_i entries (slots 8-13).
+template <bool LAM>
+constexpr int kRow = LAM ? 16 : 8;
 
 template <typename K>
 __device__ __forceinline__ void cas_desc(K& a, K& b) {
@@ -109,9 +118,10 @@ __device__ __forceinline__ void sort8_desc(K (&k)[8]) {
 //  D[r][0..7]  perturbation phase, constraint r broadcast to both halves of a pair:
 //              dS_R: (Q_x, Q_y, Q_z, r_i) with Q = K(R* Z + t*) or R* a + t* - b;
 //              dS_t: (Y_x, Y_y, Y_z, r_i) with Y = R* Z;
-//              then 2D-3D: (-u, -v), 3D-3D dS_t: (t* - b).
+//              then 2D-3D: (-u, -v), 3D-3D dS_t: (t* - b); with noise matrices U_i in slots 8-13.
 //  L[q][0..7]  ladder, constraints 2q and 2q + 1 in the two halves of a pair:
-//              (Y_x, Y_y, Y_z), then 2D-3D: (-u, -v, -r^2), 3D-3D: (-b_x, -b_y, -b_z, -r^2).
+//              (Y_x, Y_y, Y_z), then 2D-3D: (-u, -v, -r^2), 3D-3D: (-b_x, -b_y, -b_z, -r^2);
+//              with noise matrices U_i in slots 8-13.
 //  P[j]        perturbation j: translation offset (dS_R) or unit quaternion (dS_t)
 //  E[4m..]     ladder rung m: quaternion and rows of (K) E_m (dS_R) or s_m v (dS_t)
 template <typename T>
@@ -127,19 +137,19 @@ struct Slab {
 __host__ __device__ inline int ladder_pairs(int n) { return (n + 1) / 2; }
 
 template <typename T>
-__host__ __device__ inline size_t walk_slab_bytes2(int n, int n_perturb, int n_steps) {
-  const size_t p2 = 2 * sizeof(T), t4 = 4 * sizeof(T);
-  const size_t bytes = 8 * (size_t)n * p2 + 8 * (size_t)ladder_pairs(n) * p2 + (n_perturb + 4 * (size_t)n_steps) * t4 +
+__host__ __device__ inline size_t walk_slab_bytes2(int n, int n_perturb, int n_steps, bool lam = false) {
+  const size_t p2 = 2 * sizeof(T), t4 = 4 * sizeof(T), row = lam ? 16 : 8;
+  const size_t bytes = row * (size_t)n * p2 + row * (size_t)ladder_pairs(n) * p2 + (n_perturb + 4 * (size_t)n_steps) * t4 +
                        (size_t)n_perturb * sizeof(typename KeyOf<T>::type) + 32 * sizeof(int);
   return align_up(bytes, 128);
 }
 
-template <typename T>
+template <typename T, bool LAM = false>
 __device__ __forceinline__ Slab<T> carve(unsigned char* base, int N, int NP, int NT) {
   Slab<T> s;
   s.D = reinterpret_cast<P2<T>*>(base);
-  s.L = s.D + 8 * N;
-  s.P = reinterpret_cast<T4<T>*>(s.L + 8 * ladder_pairs(N));
+  s.L = s.D + kRow<LAM> * N;
+  s.P = reinterpret_cast<T4<T>*>(s.L + kRow<LAM> * ladder_pairs(N));
   s.E = s.P + NP;
   s.key = reinterpret_cast<typename KeyOf<T>::type*>(s.E + 4 * NT);
   s.J = reinterpret_cast<int*>(s.key + NP);
@@ -154,7 +164,7 @@ __device__ __forceinline__ Slab<T> carve(unsigned char* base, int N, int NP, int
 // every valid j.
 // ZCHK = false (dS_t, 2D-3D): the caller has bounded P_z away from 0 for every constraint and
 // perturbation, so the cheirality minimum is not tracked.
-template <typename T, int KIND, int SAMPLER, int NPAIR, bool ZCHK = true, class RK>
+template <typename T, int KIND, int SAMPLER, int NPAIR, bool ZCHK = true, bool LAM = false, class RK>
 __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Slab<T>& sl, int N, int NP, int lane,
                                           int pb, T r_pert, const V3<T>& t, T fx, T fy, T cx, T cy, T qzmin,
                                           int sh = 0) {
@@ -217,11 +227,15 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
   constexpr int kUnroll = 2;
 #pragma unroll kUnroll
   for (int i = sub; i < N; i += S) {
-    const T2* Di = sl.D + 8 * i;
+    const T2* Di = sl.D + kRow<LAM> * i;
     const T2 d0 = Di[0], d1 = Di[1], d2 = Di[2], rr = Di[3];
-    T2 d4, d5, d6;
+    T2 d4, d5, d6, u0, u1, u2, u3, u4, u5;
     if (KIND == 1 || SAMPLER == 1) d4 = Di[4], d5 = Di[5];
     if (KIND == 0 && SAMPLER == 1) d6 = Di[6];
+    if constexpr (LAM) {
+      u0 = Di[8], u1 = Di[9], u2 = Di[10];
+      if (KIND == 0) u3 = Di[11], u4 = Di[12], u5 = Di[13];
+    }
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
       T2 Px, Py, Pz;
@@ -235,12 +249,18 @@ __device__ __forceinline__ void dist_pass(const RK& rk, int it, int w, const Sla
       }
       T2 s2, qq;
       if (KIND == 1) {
-        const T2 ex = fma2(d4, Pz, Px), ey = fma2(d5, Pz, Py);
+        T2 ex = fma2(d4, Pz, Px), ey = fma2(d5, Pz, Py);
+        if constexpr (LAM) ex = fma2(u1, ey, mul2(u0, ex)), ey = mul2(u2, ey);
         s2 = fma2(ey, ey, mul2(ex, ex));
         qq = fma2(s2, mul2(Pz, Pz), tiny2);
         if (SAMPLER == 1 && ZCHK) zmin[p] = min2(zmin[p], Pz);
       } else {
-        s2 = fma2(Pz, Pz, fma2(Py, Py, mul2(Px, Px)));
+        if constexpr (LAM) {
+          const T2 ex = fma2(u2, Pz, fma2(u1, Py, mul2(u0, Px))), ey = fma2(u4, Pz, mul2(u3, Py)), ez = mul2(u5, Pz);
+          s2 = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
+        } else {
+          s2 = fma2(Pz, Pz, fma2(Py, Py, mul2(Px, Px)));
+        }
         qq = add2(s2, tiny2);
       }
       T2 m;  // r - |e| (2D-3D: |e| / P_z)
@@ -314,23 +334,29 @@ __device__ __forceinline__ void top_k(const Slab<T>& sl, int NP, int K, int lane
 // violated a constraint.  The constraints come in ascending margin at the current pose, so most
 // candidates die on the first pairs; a vote per pair measured faster than one per two or more.
 // Z: track the cheirality minimum (2D-3D; off when the caller has bounded P_z away from 0).
-template <typename T, int KIND, bool Z>
+template <typename T, int KIND, bool Z, bool LAM = false>
 __device__ __forceinline__ void ladder_scan(const P2<T>* L, int NQ, int N, const P2<T> (&M2)[9], P2<T> bx, P2<T> by,
                                             P2<T> bz, P2<T>& cmax, P2<T>& zmin, bool& alive, int& done) {
   using T2 = P2<T>;
   for (int qi = 0; qi < NQ; ++qi) {
-    const T2* Lq = L + 8 * qi;
+    const T2* Lq = L + kRow<LAM> * qi;
     const T2 yx = Lq[0], yy = Lq[1], yz = Lq[2], o3 = Lq[3], o4 = Lq[4], o5 = Lq[5];
     const T2 Px = fma2(M2[0], yx, fma2(M2[1], yy, fma2(M2[2], yz, bx)));
     const T2 Py = fma2(M2[3], yx, fma2(M2[4], yy, fma2(M2[5], yz, by)));
     const T2 Pz = fma2(M2[6], yx, fma2(M2[7], yy, fma2(M2[8], yz, bz)));
     T2 c;
     if (KIND == 1) {
-      const T2 ex = fma2(o3, Pz, Px), ey = fma2(o4, Pz, Py);
+      T2 ex = fma2(o3, Pz, Px), ey = fma2(o4, Pz, Py);
+      if constexpr (LAM) ex = fma2(Lq[9], ey, mul2(Lq[8], ex)), ey = mul2(Lq[10], ey);
       c = fma2(o5, mul2(Pz, Pz), fma2(ey, ey, mul2(ex, ex)));
       if (Z) zmin = min2(zmin, Pz);
     } else {
-      const T2 ex = add2(Px, o3), ey = add2(Py, o4), ez = add2(Pz, o5);
+      T2 ex = add2(Px, o3), ey = add2(Py, o4), ez = add2(Pz, o5);
+      if constexpr (LAM) {
+        const T2 gx = fma2(Lq[10], ez, fma2(Lq[9], ey, mul2(Lq[8], ex)));
+        const T2 gy = fma2(Lq[12], ez, mul2(Lq[11], ey));
+        ez = mul2(Lq[13], ez), ex = gx, ey = gy;
+      }
       c = add2(fma2(ez, ez, fma2(ey, ey, mul2(ex, ex))), Lq[6]);
     }
     cmax = max2(cmax, c);
@@ -494,7 +520,8 @@ __device__ __forceinline__ void snap_walk(const WalkCtx<T>& c, const T4<T>* tab,
 
 // One walk of Alg. 3 (dS_R) or Alg. 5 (dS_t): N_I iterations from seed (w mod |S0|), then emit.
 // tab: the PURSE's constraint table in shared memory; sl: this warp's slab.
-template <typename T, int KIND, int SAMPLER, class RK>
+// LAM: noise matrices; their factors follow the table (rows 2N + 2i, 2N + 2i + 1).
+template <typename T, int KIND, int SAMPLER, bool LAM, class RK>
 __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int w, const T4<T>* tab,
                                          const Slab<T>& sl, int lane, unsigned long long& evals) {
   using Key = typename KeyOf<T>::type;
@@ -566,10 +593,20 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
         const V3<T> X = mul(R, V3<T>{mz.x, mz.y, mz.z}) + t;
         float m;
         if (KIND == 1) {
-          const T Pz = X.z, ex = fx * X.x + cx * X.z - ob.x * Pz, ey = fy * X.y + cy * X.z - ob.y * Pz;
+          const T Pz = X.z;
+          T ex = fx * X.x + cx * X.z - ob.x * Pz, ey = fy * X.y + cy * X.z - ob.y * Pz;
+          if constexpr (LAM) {
+            const T4<T> ua = tab[2 * N + 2 * lane];
+            ex = ua.x * ex + ua.y * ey, ey = ua.z * ey;
+          }
           m = Pz > T(0) ? (float)(mz.w * Pz * mz.w * Pz - ex * ex - ey * ey) : -INFINITY;
         } else {
-          const T ex = X.x - ob.x, ey = X.y - ob.y, ez = X.z - ob.z;
+          T ex = X.x - ob.x, ey = X.y - ob.y, ez = X.z - ob.z;
+          if constexpr (LAM) {
+            const T4<T> ua = tab[2 * N + 2 * lane], ub = tab[2 * N + 2 * lane + 1];
+            const T gx = ua.x * ex + ua.y * ey + ua.z * ez, gy = ua.w * ey + ub.x * ez;
+            ex = gx, ey = gy, ez = ub.y * ez;
+          }
           m = (float)(ob.w - ex * ex - ey * ey - ez * ez);
         }
         kk = (orderable(m) & ~31u) | (uint32_t)lane;
@@ -592,7 +629,7 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
       const int i = N <= 32 ? perm : r;
       const T4<T> mz = tab[i], ob = tab[N + i];
       const V3<T> Y = mul(R, V3<T>{mz.x, mz.y, mz.z});
-      T2* Dr = sl.D + 8 * r;
+      T2* Dr = sl.D + kRow<LAM> * r;
       if (SAMPLER == 0) {
         if (KIND == 1) {
           const V3<T> X = Y + t;
@@ -612,20 +649,30 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
         Dr[4] = dup(t.x - ob.x), Dr[5] = dup(t.y - ob.y), Dr[6] = dup(t.z - ob.z);
       }
       // ladder table: constraint r in half (r & 1) of pair r / 2
-      T* Lq = reinterpret_cast<T*>(sl.L + 8 * (r >> 1)) + (r & 1);
+      T* Lq = reinterpret_cast<T*>(sl.L + kRow<LAM> * (r >> 1)) + (r & 1);
       Lq[0] = Y.x, Lq[2] = Y.y, Lq[4] = Y.z;
       if (KIND == 1) {
         Lq[6] = -ob.x, Lq[8] = -ob.y, Lq[10] = -ob.w;
       } else {
         Lq[6] = -ob.x, Lq[8] = -ob.y, Lq[10] = -ob.z, Lq[12] = -ob.w;
       }
+      if constexpr (LAM) {  // U_i in slots 8-13 of both tables
+        const T4<T> ua = tab[2 * N + 2 * i], ub = tab[2 * N + 2 * i + 1];
+        const T u[6] = {ua.x, ua.y, ua.z, ua.w, ub.x, ub.y};
+#pragma unroll
+        for (int k = 0; k < (KIND == 1 ? 3 : 6); ++k) Dr[8 + k] = dup(u[k]), Lq[16 + 2 * k] = u[k];
+      }
     }
     if ((N & 1) && lane == 0) {  // odd N: the second half of the last pair is always satisfied
-      T* Lq = reinterpret_cast<T*>(sl.L + 8 * (N >> 1)) + 1;
+      T* Lq = reinterpret_cast<T*>(sl.L + kRow<LAM> * (N >> 1)) + 1;
       Lq[0] = Lq[2] = Lq[4] = T(0);
       Lq[6] = Lq[8] = T(0);
       Lq[10] = T(-1e30);
       if (KIND == 0) Lq[10] = T(0), Lq[12] = T(-1e30);
+      if constexpr (LAM) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Lq[16 + 2 * k] = T(0);
+      }
     }
     if (SAMPLER == 0 && KIND == 1) {
 #pragma unroll
@@ -639,33 +686,33 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
     //      a time), then the ragged remainder of q pairs with 32 / q lanes (a power of two) per pair
     if constexpr (SAMPLER == 0) {
       if (nfull == 4)
-        dist_pass<T, KIND, SAMPLER, 4>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
+        dist_pass<T, KIND, SAMPLER, 4, true, LAM>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
       else if (nfull == 3)
-        dist_pass<T, KIND, SAMPLER, 3>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
+        dist_pass<T, KIND, SAMPLER, 3, true, LAM>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
       else if (nfull == 2)
-        dist_pass<T, KIND, SAMPLER, 2>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
+        dist_pass<T, KIND, SAMPLER, 2, true, LAM>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
       else if (nfull == 1)
-        dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
-      if (qtail) dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, nfull, r_pert, t, fx, fy, cx, cy, qzmin, tsh);
+        dist_pass<T, KIND, SAMPLER, 1, true, LAM>(rk, it, w, sl, N, NP, lane, 0, r_pert, t, fx, fy, cx, cy, qzmin);
+      if (qtail) dist_pass<T, KIND, SAMPLER, 1, true, LAM>(rk, it, w, sl, N, NP, lane, nfull, r_pert, t, fx, fy, cx, cy, qzmin, tsh);
     } else {
       // P_z = (R Z_i)_z + t*_z >= t*_z - max |Z_i| (rotations keep |Z_i|); the margin covers rounding
       if (KIND == 1 && t.z - rho_max > T(1e-3) * (fabs(t.z) + rho_max)) {
         for (int pb = 0; pb < nfull; pb += 2) {
           if (nfull - pb >= 2)
-            dist_pass<T, KIND, SAMPLER, 2, false>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
+            dist_pass<T, KIND, SAMPLER, 2, false, LAM>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
           else
-            dist_pass<T, KIND, SAMPLER, 1, false>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
+            dist_pass<T, KIND, SAMPLER, 1, false, LAM>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
         }
         if (qtail)
-          dist_pass<T, KIND, SAMPLER, 1, false>(rk, it, w, sl, N, NP, lane, nfull, r_pert, t, fx, fy, cx, cy, qzmin, tsh);
+          dist_pass<T, KIND, SAMPLER, 1, false, LAM>(rk, it, w, sl, N, NP, lane, nfull, r_pert, t, fx, fy, cx, cy, qzmin, tsh);
       } else {
         for (int pb = 0; pb < nfull; pb += 2) {
           if (nfull - pb >= 2)
-            dist_pass<T, KIND, SAMPLER, 2>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
+            dist_pass<T, KIND, SAMPLER, 2, true, LAM>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
           else
-            dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
+            dist_pass<T, KIND, SAMPLER, 1, true, LAM>(rk, it, w, sl, N, NP, lane, pb, r_pert, t, fx, fy, cx, cy, qzmin);
         }
-        if (qtail) dist_pass<T, KIND, SAMPLER, 1>(rk, it, w, sl, N, NP, lane, nfull, r_pert, t, fx, fy, cx, cy, qzmin, tsh);
+        if (qtail) dist_pass<T, KIND, SAMPLER, 1, true, LAM>(rk, it, w, sl, N, NP, lane, nfull, r_pert, t, fx, fy, cx, cy, qzmin, tsh);
       }
     }
     evals += (unsigned long long)NP * N;
@@ -731,9 +778,9 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
       const bool zsafe = KIND == 1 && SAMPLER == 0 &&
                          __all_sync(kFullMask, !active || bm.z - rho_max > T(1e-3) * (fabs(bm.z) + rho_max));
       if (zsafe)
-        ladder_scan<T, KIND, false>(sl.L, NQ, N, M2, bx, by, bz, cmax, zmin, alive, done);
+        ladder_scan<T, KIND, false, LAM>(sl.L, NQ, N, M2, bx, by, bz, cmax, zmin, alive, done);
       else
-        ladder_scan<T, KIND, true>(sl.L, NQ, N, M2, bx, by, bz, cmax, zmin, alive, done);
+        ladder_scan<T, KIND, true, LAM>(sl.L, NQ, N, M2, bx, by, bz, cmax, zmin, alive, done);
       evals += (unsigned long long)nact * done;
       const unsigned bal = __ballot_sync(kFullMask, alive);
       if (bal) {
@@ -768,7 +815,9 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
   }
 
   // ---- optional boundary snap (for the adjoint), then a8: emit
-  if (c.out_snap) snap_walk<T, KIND, SAMPLER>(c, tab, vel, q, t, w, lane);
+  if constexpr (!LAM) {  // the snap takes the identity norm (the host rejects it with noise matrices)
+    if (c.out_snap) snap_walk<T, KIND, SAMPLER>(c, tab, vel, q, t, w, lane);
+  }
   if (lane == 0) {
     T* oq = c.out_q + 4 * (size_t)w;
     T* ot = c.out_t + 3 * (size_t)w;
@@ -781,24 +830,26 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
   __syncwarp();
 }
 
-template <typename T, int KIND, int SAMPLER>
+template <typename T, int KIND, int SAMPLER, bool LAM>
 __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
     walk_kernel(const __grid_constant__ WalkArgs a, const int mc, const int slab_bytes) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   const int N = a.n;
-  const T4<T>* tab = reinterpret_cast<const T4<T>*>(smem + 128);  // rows [0,N): (a, r); [N,2N): (b or z, r^2)
+  // rows [0,N): (a, r); [N,2N): (b or z, r^2); with noise matrices [2N,4N): U_i
+  const T4<T>* tab = reinterpret_cast<const T4<T>*>(smem + 128);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const Slab<T> sl = carve<T>(smem + 128 + walk_table_bytes<T>(N) + (size_t)warp * slab_bytes, N, a.n_perturb,
-                              a.n_steps);
+  const Slab<T> sl = carve<T, LAM>(smem + 128 + walk_table_bytes<T>(N, LAM) + (size_t)warp * slab_bytes, N,
+                                   a.n_perturb, a.n_steps);
 
-  // ---- a0: stage the constraint table with a 1-D TMA bulk copy.
+  // ---- a0: stage the constraint table (and the noise factors) with 1-D TMA bulk copies.
   const uint32_t tbytes = 8u * N * sizeof(T);
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
   if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(bar, tbytes);
+    mbar_arrive_expect_tx(bar, LAM ? 2 * tbytes : tbytes);
     bulk_copy_g2s(smem + 128, a.table, tbytes, bar);
+    if (LAM) bulk_copy_g2s(smem + 128 + tbytes, a.ell, tbytes, bar);
   }
   if (!mbar_wait_bounded(bar, 0, 1 << 22)) {
     if (threadIdx.x == 0) atomicOr(a.status, kDevErrTimeout);
@@ -819,7 +870,7 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
   unsigned long long evals = 0;
   const int nw = blockDim.x >> 5;  // warps per block (fewer than kWalkWarps for large tables)
   for (int w = blockIdx.x * nw + warp; w < a.n_samples; w += gridDim.x * nw)
-    walk_one<T, KIND, SAMPLER>(c, rk, w, tab, sl, lane, evals);
+    walk_one<T, KIND, SAMPLER, LAM>(c, rk, w, tab, sl, lane, evals);
   if (lane == 0 && evals) atomicAdd(a.evals, evals);
 }
 
@@ -896,14 +947,14 @@ __global__ void __launch_bounds__(kWalkThreads, 2)
       float* snap = smp == 0 ? b.snap_rot : b.snap_tr;
       c.out_snap = snap ? snap + (size_t)kSnapStride * off : nullptr;
       if (in.kind == 0 && smp == 0)
-        walk_one<float, 0, 0>(c, rk, w, tab, sl, lane, evals);
+        walk_one<float, 0, 0, false>(c, rk, w, tab, sl, lane, evals);
       else if (in.kind == 0) {
-        if constexpr (TR3D) walk_one<float, 0, 1>(c, rk, w, tab, sl, lane, evals);
+        if constexpr (TR3D) walk_one<float, 0, 1, false>(c, rk, w, tab, sl, lane, evals);
       }
       else if (smp == 0)
-        walk_one<float, 1, 0>(c, rk, w, tab, sl, lane, evals);
+        walk_one<float, 1, 0, false>(c, rk, w, tab, sl, lane, evals);
       else
-        walk_one<float, 1, 1>(c, rk, w, tab, sl, lane, evals);
+        walk_one<float, 1, 1, false>(c, rk, w, tab, sl, lane, evals);
     }
   }
   if (lane == 0 && evals) atomicAdd(b.evals, evals);
@@ -929,16 +980,17 @@ cudaError_t launch_batch_walk(const BatchArgs& b, int chunk, int warps, int sm_c
                 : launch_batch_walk_t<false>(b, chunk, warps, sm_count, st);
 }
 
-template <typename T, int KIND, int SAMPLER>
+template <typename T, int KIND, int SAMPLER, bool LAM>
 static cudaError_t launch_walk_t(purse_t h, const purse_params* p, const WalkArgs& a, cudaStream_t st) {
   const int mc = p->n_keep >= 32 ? 1 : 32 / p->n_keep;
-  const size_t slab = walk_slab_bytes2<T>(a.n, p->n_perturb, p->n_steps);
+  const size_t slab = walk_slab_bytes2<T>(a.n, p->n_perturb, p->n_steps, LAM);
+  const size_t table = walk_table_bytes<T>(a.n, LAM);
   // as many warps per block (up to kWalkWarps) as the shared memory holds slabs for
   int warps = kWalkWarps;
-  while (warps > 1 && 128 + walk_table_bytes<T>(a.n) + warps * slab > kMaxSmemPerBlock) --warps;
-  const size_t smem = 128 + walk_table_bytes<T>(a.n) + warps * slab;
+  while (warps > 1 && 128 + table + warps * slab > kMaxSmemPerBlock) --warps;
+  const size_t smem = 128 + table + warps * slab;
   if (smem > kMaxSmemPerBlock) return cudaErrorInvalidConfiguration;
-  auto kern = walk_kernel<T, KIND, SAMPLER>;
+  auto kern = walk_kernel<T, KIND, SAMPLER, LAM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -952,15 +1004,22 @@ static cudaError_t launch_walk_t(purse_t h, const purse_params* p, const WalkArg
   return cudaGetLastError();
 }
 
-cudaError_t launch_walk(purse_t h, const purse_params* p, const WalkArgs& a, cudaStream_t st) {
+template <bool LAM>
+static cudaError_t launch_walk_l(purse_t h, const purse_params* p, const WalkArgs& a, cudaStream_t st) {
   const bool dbl = p->precision == 1;
   const int kind = h->kind, smp = p->sampler;
   if (!dbl) {
-    if (kind == 0) return smp == 0 ? launch_walk_t<float, 0, 0>(h, p, a, st) : launch_walk_t<float, 0, 1>(h, p, a, st);
-    return smp == 0 ? launch_walk_t<float, 1, 0>(h, p, a, st) : launch_walk_t<float, 1, 1>(h, p, a, st);
+    if (kind == 0)
+      return smp == 0 ? launch_walk_t<float, 0, 0, LAM>(h, p, a, st) : launch_walk_t<float, 0, 1, LAM>(h, p, a, st);
+    return smp == 0 ? launch_walk_t<float, 1, 0, LAM>(h, p, a, st) : launch_walk_t<float, 1, 1, LAM>(h, p, a, st);
   }
-  if (kind == 0) return smp == 0 ? launch_walk_t<double, 0, 0>(h, p, a, st) : launch_walk_t<double, 0, 1>(h, p, a, st);
-  return smp == 0 ? launch_walk_t<double, 1, 0>(h, p, a, st) : launch_walk_t<double, 1, 1>(h, p, a, st);
+  if (kind == 0)
+    return smp == 0 ? launch_walk_t<double, 0, 0, LAM>(h, p, a, st) : launch_walk_t<double, 0, 1, LAM>(h, p, a, st);
+  return smp == 0 ? launch_walk_t<double, 1, 0, LAM>(h, p, a, st) : launch_walk_t<double, 1, 1, LAM>(h, p, a, st);
+}
+
+cudaError_t launch_walk(purse_t h, const purse_params* p, const WalkArgs& a, cudaStream_t st) {
+  return a.ell ? launch_walk_l<true>(h, p, a, st) : launch_walk_l<false>(h, p, a, st);
 }
 
 }  // namespace purse

@@ -1,7 +1,7 @@
 """Noise bounded in the general norm of eq. 4 (purse_set_noise) on the GPU against the oracle:
-RANSAG seeds (ellipsoid draws and acceptance in that norm), the plain samplers replayed by the
-oracle, eq. 11 distances, and the closed-form translation ball of the octahedral PURSE with one
-noise matrix."""
+RANSAG seeds (ellipsoid draws and acceptance in that norm), the fused and the plain samplers
+replayed by the oracle, eq. 11 distances, and the closed-form translation ball of the octahedral
+PURSE with one noise matrix."""
 import numpy as np
 import pytest
 import torch
@@ -10,7 +10,7 @@ from oracle import closure, megb as om, p3p, purse as op, ransag, so3
 from paper_2403_09990_gb300 import purse as P
 from paper_2403_09990_gb300 import synthetic as syn
 from tests import parity
-from tests.gpu_helpers import params_from, to_dev
+from tests.gpu_helpers import params_from, sample, to_dev
 from tests.test_gpu_plain import sample_plain
 
 pytestmark = pytest.mark.gpu
@@ -59,6 +59,42 @@ def test_ellipsoidal_walks_replay(kind, precision, sampler):
     print(f"ellipsoidal kind {kind} sampler {sampler} precision {precision}: robust {rep.robust.mean():.3f}")
 
 
+FUSED = {
+    "3d3d-R-fp64": (0, 8, 1, 0), "3d3d-R-fp32": (0, 8, 0, 0), "3d3d-t-fp32": (0, 8, 0, 1),
+    "3d3d-t-fp64-n7": (0, 7, 1, 1), "2d3d-R-fp32": (1, 16, 0, 0), "2d3d-t-fp32": (1, 16, 0, 1),
+    "2d3d-R-fp64": (1, 16, 1, 0), "2d3d-t-fp64-n9": (1, 9, 1, 1), "2d3d-R-fp32-n128": (1, 128, 0, 0),
+}
+
+
+@pytest.mark.parametrize("name", list(FUSED))
+def test_ellipsoidal_fused_walks_replay(name):
+    """The fused walk kernels with noise matrices (odd N: the padded half of the last ladder pair;
+    N = 128: fewer warps per block for the larger tables), replayed by the oracle."""
+    kind, n_kp, precision, sampler = FUSED[name]
+    if kind == 0:
+        p = syn.purse_3d3d_ellipsoidal(n_kp, 2)
+        prm = closure.preset_3d3d(v0=0.02, rot_perturb=0.2) if sampler else closure.preset_3d3d()
+    else:
+        p = syn.purse_2d3d_ellipsoidal(n_kp, 2)
+        prm = closure.preset_2d3d(n_iter=3 if n_kp > 32 else 5)
+    seeds = p.seed_pose()[None]
+    n = 257
+    with P.Purse(p) as h:
+        q, t, tr = sample(h.h, prm, sampler, precision, 66, seeds, n)
+        evals = P.purse_last_evals(h.h)
+    assert evals > n * prm.n_iter * prm.n_perturb * p.n
+    R, tt, rep = parity.replay_walks(p, seeds, prm, 66, np.arange(n), tr, precision, sampler)
+    assert rep.ok(), rep.inconsistent[:10]
+    assert not rep.robust_mismatch, rep.robust_mismatch[:10]
+    tol = 1e-10 if precision else 1e-5
+    assert parity.rot_angle(q, so3.quat_from_R(R)).max() <= tol
+    assert np.abs(t - tt).max() <= tol
+    assert np.all(parity.classify(p, so3.R_from_quat(q), t, precision) >= 0)
+    moved = (tr[:, :, prm.n_keep] >= 0).any(axis=1).mean()
+    assert moved > 0.5
+    print(f"fused ellipsoidal {name}: robust {rep.robust.mean():.3f}, moved {moved:.3f}")
+
+
 def test_ellipsoidal_distance_mode0():
     p = syn.purse_2d3d_ellipsoidal(16, 3)
     rng = np.random.default_rng(0)
@@ -105,8 +141,10 @@ def test_noise_matrix_rules():
         sd = to_dev(p.seed_pose()[None])
         q = torch.empty((4, 4), dtype=torch.float32, device="cuda")
         t = torch.empty((4, 3), dtype=torch.float32, device="cuda")
-        with pytest.raises(P.PurseError):
-            P.purse_sample(h.h, params_from(closure.preset_3d3d(), 0, 0), 1, sd, 1, 4, q, t)
-        P.purse_set_noise(h.h, None)           # back to the identity: the fused samplers serve it again
+        snap = torch.empty((4, 12), dtype=torch.float32, device="cuda")
+        with pytest.raises(P.PurseError):     # the snap takes the identity norm
+            P.purse_sample(h.h, params_from(closure.preset_3d3d(), 0, 0), 1, sd, 1, 4, q, t, snap=snap)
         P.purse_sample(h.h, params_from(closure.preset_3d3d(), 0, 0), 1, sd, 1, 4, q, t)
+        P.purse_set_noise(h.h, None)           # back to the identity: the snap is served again
+        P.purse_sample(h.h, params_from(closure.preset_3d3d(), 0, 0), 1, sd, 1, 4, q, t, snap=snap)
         P.purse_sync(h.h)
