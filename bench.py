@@ -506,8 +506,8 @@ def sweep_next(P, syn, dev, stream):
     """The rows beyond the main workload, each with its oracle timed beside it (the cpu_baseline leg of each
     line: one host core, FP64, a bounded sample of the same input): P3P RANSAG (2D-3D Step I), the exact
     Step III miniball of boundary samples, the pose-regression PURSE (Example 3) and 2D-3D constraints in the
-    norm of eq. 4; pose regression runs through the per-operation samplers, the noise matrices through the
-    fused walk kernels beside the per-operation samplers and the isotropic fused walk of the same size.  GPU parts: CUDA events (the RANSAG call synchronises, so it takes the wall clock)."""
+    norm of eq. 4; the last two through the fused walk kernels beside the per-operation samplers (and, for
+    the noise matrices, the isotropic fused walk of the same size).  GPU parts: CUDA events (the RANSAG call synchronises, so it takes the wall clock)."""
     import torch
     from oracle import closure, megb as om, p3p as op3, ransag as ora
     lines = []
@@ -622,7 +622,7 @@ def sweep_next(P, syn, dev, stream):
                              rot_perturb=0.0, trans_perturb=0.1, perturb_units=0, sampler=sampler, precision=0)
     lines.append(plain_row("purse_reg", pr, reg_params, (0,), reg_seeds, s0, oseeds, 1 << 18, 2048,
                            "pose regression, 10 hypotheses (Example 3), convex seeds, 2^18 dS_R walks (N_I=5, "
-                           "N_P=150, N_P*=10, N_T=10), both balls"))
+                           "N_P=150, N_P*=10, N_T=10), both balls", fused=True))
 
     # ---- 2D-3D with noise matrices (eq. 4), both samplers, beside the isotropic fused walk above
     pl = syn.purse_2d3d_ellipsoidal(N_KEYPOINTS, 0)

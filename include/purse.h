@@ -92,7 +92,7 @@ purse_status purse_set_noise(purse_t h, const double* lam);
  * (R_i, t_i), host n x 12 (R_i row-major, then t_i; each R_i a rotation to 1e-6), and radii
  * beta_rot (host n, the Frobenius distance |vec(R) - vec(R_i)| allowed) and beta_t (host n,
  * metres), each > 0; n in [1, 256].  The PURSE is every (R, t) within both radii of every
- * hypothesis.  Sampled by purse_sample_plain (the fused purse_sample serves 3D-3D and 2D-3D);
+ * hypothesis.  Sampled by purse_sample (fused, no snap) or purse_sample_plain;
  * purse_ransag draws its seeds by convex combinations of the hypotheses; purse_dist takes mode 0;
  * megb_solve and megb_solve_exact take its samples like any other.  Allocates device memory. */
 purse_status purse_create_regression(int n, const double* hyp, const double* beta_rot,
@@ -162,7 +162,11 @@ purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds,
  * ray direction (3), h'(tau*) = d|g_j*|/d tau, d|g_j*|/d y_j* (3; 2 used for 2D-3D), 3 unused.
  * Pass the records to megb_backward.  The snap takes the identity norm: with noise matrices
  * (purse_set_noise) d_snap must be NULL (PURSE_ERR_ARG otherwise); the walks themselves measure
- * every residual in the norm of eq. 4.  Regression PURSEs are sampled by purse_sample_plain. */
+ * every residual in the norm of eq. 4.  Regression PURSEs (purse_create_regression) take no snap
+ * either; their walks evaluate the part of each hypothesis a perturbation moves (dS_R: the
+ * translations, dS_t: the rotations) per perturbation and the other part once per iteration, and
+ * the ladder's two factors once per rung and kept perturbation, so purse_last_evals counts those
+ * half-constraint evaluations. */
 purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const double* d_seeds,
                           int s0, int n_samples, void* d_q, void* d_t, int16_t* d_trace, void* d_snap,
                           purse_stream_t stream);

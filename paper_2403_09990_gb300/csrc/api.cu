@@ -292,7 +292,7 @@ purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const
                           int n_samples, void* d_q, void* d_t, int16_t* d_trace, void* d_snap,
                           purse_stream_t stream) {
   if (!h || !p) return arg_error("purse_sample: NULL handle or params");
-  if (h->kind == PURSE_REG) return arg_error("purse_sample: regression PURSEs are sampled by purse_sample_plain");
+  if (h->kind == PURSE_REG && d_snap) return arg_error("purse_sample: no boundary snap for regression PURSEs");
   if (h->ell64 && d_snap) return arg_error("purse_sample: the boundary snap takes the identity norm (no noise matrices)");
   if (p->n_iter < 0) return arg_error("purse_sample: n_iter < 0");
   if (p->n_perturb < 1 || p->n_perturb > 256) return arg_error("purse_sample: n_perturb must be in [1, 256]");

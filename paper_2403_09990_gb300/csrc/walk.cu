@@ -518,6 +518,29 @@ __device__ __forceinline__ void snap_walk(const WalkCtx<T>& c, const T4<T>* tab,
   for (int k = 9; k < kSnapStride; ++k) rec[k] = T(0);
 }
 
+// Start of walk w: pose of seed (w mod |S0|) and velocity omega = omega0 (u + u~) (Alg. 3) or
+// v = v0 S (dir + v~) (Alg. 5), u~ / v~ the first accepted unit lattice draw of the walk's stream.
+template <typename T, int SAMPLER>
+__device__ __forceinline__ void walk_start(const WalkCtx<T>& c, int w, Q4<T>& q, V3<T>& t, V3<T>& vel) {
+  const double* sd = c.seed_data + (size_t)(w % c.s0) * kSeedStride;
+  q = Q4<T>{T(sd[0]), T(sd[1]), T(sd[2]), T(sd[3])};
+  t = V3<T>{T(sd[4]), T(sd[5]), T(sd[6])};
+  Stream s(c.key0, c.key1, SAMPLER == 0 ? kPhaseOmega : kPhaseV, 0u, 0u, (uint32_t)w);
+  int X, Y, Z;
+  lattice_draw<true>(s, X, Y, Z);
+  const double nr = sqrt((double)(X * X + Y * Y + Z * Z));
+  const double ux = nr > 0 ? X / nr : 0.0, uy = nr > 0 ? Y / nr : 0.0, uz = nr > 0 ? Z / nr : 0.0;
+  if (SAMPLER == 0) {
+    vel = V3<T>{T(c.omega0 * (sd[7] + ux)), T(c.omega0 * (sd[8] + uy)), T(c.omega0 * (sd[9] + uz))};
+  } else {
+    const WalkStats* st = c.st;
+    const double d0 = sd[10] + ux, d1 = sd[11] + uy, d2 = sd[12] + uz;
+    vel = V3<T>{T(c.v0 * (st->S[0] * d0 + st->S[1] * d1 + st->S[2] * d2)),
+                T(c.v0 * (st->S[3] * d0 + st->S[4] * d1 + st->S[5] * d2)),
+                T(c.v0 * (st->S[6] * d0 + st->S[7] * d1 + st->S[8] * d2))};
+  }
+}
+
 // One walk of Alg. 3 (dS_R) or Alg. 5 (dS_t): N_I iterations from seed (w mod |S0|), then emit.
 // tab: the PURSE's constraint table in shared memory; sl: this warp's slab.
 // LAM: noise matrices; their factors follow the table (rows 2N + 2i, 2N + 2i + 1).
@@ -529,32 +552,15 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
   const int N = c.N, NQ = ladder_pairs(c.N);
   const int NP = c.NP, K = c.K, NT = c.NT, mc = c.mc;
   const T fx = c.fx, fy = c.fy, cx = c.cx, cy = c.cy, r_pert = c.r_pert;
-  const WalkStats* st = c.st;
   const int ncand = mc * K;
   const int cm = lane / K, ck = lane - (lane / K) * K;
   // perturbation pairs: nfull passes of 32, then qtail pairs with 2^tsh lanes each
   const int npairs = (NP + 1) / 2, nfull = npairs / 32, qtail = npairs % 32;
   const int tsh = qtail == 0 ? 0 : qtail <= 1 ? 5 : qtail <= 2 ? 4 : qtail <= 4 ? 3 : qtail <= 8 ? 2 : qtail <= 16 ? 1 : 0;
   // ---- a3: start pose and velocity, ladder table of this walk.
-  const double* sd = c.seed_data + (size_t)(w % c.s0) * kSeedStride;
-  Q4<T> q{T(sd[0]), T(sd[1]), T(sd[2]), T(sd[3])};
-  V3<T> t{T(sd[4]), T(sd[5]), T(sd[6])};
-  V3<T> vel;
-  {
-    Stream s(c.key0, c.key1, SAMPLER == 0 ? kPhaseOmega : kPhaseV, 0u, 0u, (uint32_t)w);
-    int X, Y, Z;
-    lattice_draw<true>(s, X, Y, Z);
-    const double nr = sqrt((double)(X * X + Y * Y + Z * Z));
-    const double ux = nr > 0 ? X / nr : 0.0, uy = nr > 0 ? Y / nr : 0.0, uz = nr > 0 ? Z / nr : 0.0;
-    if (SAMPLER == 0) {
-      vel = V3<T>{T(c.omega0 * (sd[7] + ux)), T(c.omega0 * (sd[8] + uy)), T(c.omega0 * (sd[9] + uz))};
-    } else {
-      const double d0 = sd[10] + ux, d1 = sd[11] + uy, d2 = sd[12] + uz;
-      vel = V3<T>{T(c.v0 * (st->S[0] * d0 + st->S[1] * d1 + st->S[2] * d2)),
-                  T(c.v0 * (st->S[3] * d0 + st->S[4] * d1 + st->S[5] * d2)),
-                  T(c.v0 * (st->S[6] * d0 + st->S[7] * d1 + st->S[8] * d2))};
-    }
-  }
+  Q4<T> q;
+  V3<T> t, vel;
+  walk_start<T, SAMPLER>(c, w, q, t, vel);
   const T rho_max = c.rho_max;
   for (int m = lane; m < NT; m += 32) {
     T sm = T(1);
@@ -874,6 +880,265 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
   if (lane == 0 && evals) atomicAdd(a.evals, evals);
 }
 
+// ---------------------------------------------------------------- pose-regression walks (Example 3)
+// Hypothesis i constrains the rotation, |R - R_i|_F <= beta_i^R, and the translation,
+// |t - t_i| <= beta_i^t.  A dS_R perturbation moves only t and a dS_t perturbation only R, so the
+// part that stays is evaluated once per iteration and the distance of perturbation j (eq. 11) is
+// min(that part's minimum margin, min_i of the moving part's margins); in_purse of a ladder
+// candidate (k, m) is the product of a factor of k and a factor of m (dS_R: the rung's rotation
+// and the kept perturbation's translation; dS_t the other way round), so the ladder evaluates
+// N_T + N_P* half-constraint sets, one rung and one kept perturbation per lane, and m0 / k0 are
+// the first set bits of the two warp ballots.  The same draws, decisions and trace as the
+// per-operation samplers.  Table (4 rows per hypothesis): [0, N) (t_i, beta_i^t), [N + r N + i)
+// row r of R_i with beta_i^R in the w of row 0.
+template <typename T>
+__host__ __device__ inline size_t reg_table_bytes(int n) {
+  return align_up(16 * (size_t)n * sizeof(T), 128);
+}
+template <typename T>
+__host__ __device__ inline size_t reg_slab_bytes(int n, int n_perturb) {
+  const size_t t4 = 4 * sizeof(T);
+  return align_up((size_t)n * t4 + (size_t)n_perturb * t4 + (size_t)n_perturb * sizeof(typename KeyOf<T>::type) +
+                      32 * sizeof(int),
+                  128);
+}
+
+// |R - R_i|_F^2 of hypothesis i (the order of the per-operation samplers).
+template <typename T>
+__device__ __forceinline__ T reg_rot_d2(const T4<T>* tab, int N, int i, const M3<T>& R) {
+  const T4<T> r0 = tab[N + i], r1 = tab[2 * N + i], r2 = tab[3 * N + i];
+  const T g[9] = {r0.x, r0.y, r0.z, r1.x, r1.y, r1.z, r2.x, r2.y, r2.z};
+  T d2 = T(0);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const T d = R.m[k] - g[k];
+    d2 += d * d;
+  }
+  return d2;
+}
+template <typename T>
+__device__ __forceinline__ T reg_trans_e2(const T4<T>* tab, int i, const V3<T>& t) {
+  const T4<T> ti = tab[i];
+  const T ex = t.x - ti.x, ey = t.y - ti.y, ez = t.z - ti.z;
+  return ex * ex + ey * ey + ez * ez;
+}
+template <typename T>
+__device__ __forceinline__ bool reg_rot_ok(const T4<T>* tab, int N, const M3<T>& R) {
+  bool ok = true;
+  for (int i = 0; i < N; ++i) {
+    const T b = tab[N + i].w;
+    ok = ok && reg_rot_d2(tab, N, i, R) <= b * b;
+  }
+  return ok;
+}
+template <typename T>
+__device__ __forceinline__ bool reg_trans_ok(const T4<T>* tab, int N, const V3<T>& t) {
+  bool ok = true;
+  for (int i = 0; i < N; ++i) {
+    const T b = tab[i].w;
+    ok = ok && reg_trans_e2(tab, i, t) <= b * b;
+  }
+  return ok;
+}
+
+template <typename T, int SAMPLER, class RK>
+__device__ __forceinline__ void reg_walk_one(const WalkCtx<T>& c, const RK& rk, int w, const T4<T>* tab, T4<T>* C,
+                                             const Slab<T>& sl, int lane, unsigned long long& evals) {
+  using Key = typename KeyOf<T>::type;
+  using T2 = P2<T>;
+  const int N = c.N, NP = c.NP, K = c.K, NT = c.NT;
+  const T r_pert = c.r_pert;
+  Q4<T> q;
+  V3<T> t, vel;
+  walk_start<T, SAMPLER>(c, w, q, t, vel);
+  T sm = T(1);  // this lane's rung scale gamma^lane
+  for (int k = 0; k < lane; ++k) sm *= T(c.gamma);
+  bool moved = true;
+  T fixed_min = inf<T>();  // minimum margin of the part the perturbations do not move
+  for (int it = 0; it < c.n_iter; ++it) {
+    const M3<T> R = qmat(q);
+    if (moved) {
+      T mn = inf<T>();
+      for (int i = lane; i < N; i += 32) {
+        if (SAMPLER == 0) {  // rotation margins of R*; the translation offsets t* - t_i
+          mn = fmin(mn, tab[N + i].w - sqrt(reg_rot_d2(tab, N, i, R)));
+          const T4<T> ti = tab[i];
+          C[i] = T4<T>{t.x - ti.x, t.y - ti.y, t.z - ti.z, ti.w};
+        } else {             // translation margins of t*
+          mn = fmin(mn, tab[i].w - sqrt(reg_trans_e2(tab, i, t)));
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) mn = fmin(mn, __shfl_xor_sync(kFullMask, mn, o));
+      fixed_min = mn;
+      evals += (unsigned long long)N;
+      __syncwarp();
+    }
+    // ---- perturbations and their distance (eq. 11), two per lane and pass on paired lanes
+    const T2 tiny2 = dup(tiny<T>());
+    for (int b = lane; 2 * b < NP; b += 32) {
+      const uint4 wd = philox4x32_10_rk(
+          make_uint4(0u, ((SAMPLER == 0 ? kPhaseRPerturb : kPhaseTPerturb) << 24) | (uint32_t)b, (uint32_t)it,
+                     (uint32_t)w),
+          rk);
+      T2 dmin = dup(inf<T>());
+      if constexpr (SAMPLER == 0) {
+        T dx[2], dy[2], dz[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          T ux, uy, uz;
+          hatbox_point<T>(h ? wd.z : wd.x, h ? wd.w : wd.y, ux, uy, uz);
+          dx[h] = r_pert * ux, dy[h] = r_pert * uy, dz[h] = r_pert * uz;
+          if (2 * b + h < NP) sl.P[2 * b + h] = T4<T>{dx[h], dy[h], dz[h], T(0)};
+        }
+        const T2 Dx = pr(dx[0], dx[1]), Dy = pr(dy[0], dy[1]), Dz = pr(dz[0], dz[1]);
+        for (int i = 0; i < N; ++i) {
+          const T4<T> ci = C[i];
+          const T2 ex = add2(dup(ci.x), Dx), ey = add2(dup(ci.y), Dy), ez = add2(dup(ci.z), Dz);
+          const T2 s2 = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
+          dmin = min2(dmin, fma2(pr(-s2.x, -s2.y), rsq2(add2(s2, tiny2)), dup(ci.w)));
+        }
+      } else {
+        T2 qw, qx, qy, qz, A[9], Rj[9];
+        hatbox_quat2<T>(wd, r_pert, qw, qx, qy, qz);
+        if (2 * b < NP) sl.P[2 * b] = T4<T>{qw.x, qx.x, qy.x, qz.x};
+        if (2 * b + 1 < NP) sl.P[2 * b + 1] = T4<T>{qw.y, qx.y, qy.y, qz.y};
+        qmat2<T>(qw, qx, qy, qz, A);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc)
+            Rj[3 * r + cc] = fma2(A[3 * r + 2], dup(R.m[6 + cc]),
+                                  fma2(A[3 * r + 1], dup(R.m[3 + cc]), mul2(A[3 * r], dup(R.m[cc]))));
+        for (int i = 0; i < N; ++i) {
+          const T4<T> r0 = tab[N + i], r1 = tab[2 * N + i], r2 = tab[3 * N + i];
+          const T g[9] = {r0.x, r0.y, r0.z, r1.x, r1.y, r1.z, r2.x, r2.y, r2.z};
+          T2 d2 = dup(T(0));
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            const T2 d = add2(Rj[k], dup(-g[k]));
+            d2 = fma2(d, d, d2);
+          }
+          dmin = min2(dmin, fma2(pr(-d2.x, -d2.y), rsq2(add2(d2, tiny2)), dup(r0.w)));
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (2 * b + h < NP) sl.key[2 * b + h] = orderable(fmin(h ? dmin.y : dmin.x, fixed_min));
+    }
+    evals += (unsigned long long)NP * N;
+    __syncwarp();
+    // ---- top_k_indices (ties to the lower j)
+    if (NP <= 160)
+      top_k<Key, 5>(sl, NP, K, lane);
+    else
+      top_k<Key, 8>(sl, NP, K, lane);
+    __syncwarp();
+    // ---- ladder: rung m = lane and kept perturbation k = lane, each against its half of the constraints
+    Q4<T> qm{T(1), T(0), T(0), T(0)};  // dS_R: the rung's rotation; dS_t: the kept perturbation's
+    V3<T> tm = t;                       // dS_R: the kept perturbation's translation; dS_t: the rung's
+    bool ok_m = false, ok_k = false;
+    if (lane < NT) {
+      if (SAMPLER == 0) {
+        qm = qnormalize(qmul(qexp(V3<T>{sm * vel.x, sm * vel.y, sm * vel.z}), q));
+        ok_m = reg_rot_ok(tab, N, qmat(qm));
+      } else {
+        tm = V3<T>{t.x + sm * vel.x, t.y + sm * vel.y, t.z + sm * vel.z};
+        ok_m = reg_trans_ok(tab, N, tm);
+      }
+    }
+    Q4<T> qk{T(1), T(0), T(0), T(0)};
+    V3<T> tk = t;
+    if (lane < K) {
+      const T4<T> pj = sl.P[sl.J[lane]];
+      if (SAMPLER == 0) {
+        tk = V3<T>{t.x + pj.x, t.y + pj.y, t.z + pj.z};
+        ok_k = reg_trans_ok(tab, N, tk);
+      } else {
+        qk = qnormalize(qmul(Q4<T>{pj.x, pj.y, pj.z, pj.w}, q));
+        ok_k = reg_rot_ok(tab, N, qmat(qk));
+      }
+    }
+    evals += (unsigned long long)(NT + K) * N;
+    const unsigned bm = __ballot_sync(kFullMask, ok_m), bk = __ballot_sync(kFullMask, ok_k);
+    int m0 = -1, k0 = -1;
+    if (bm && bk) m0 = __ffs(bm) - 1, k0 = __ffs(bk) - 1;
+    // ---- update (R*, t*): from lane m0 (the rung) and lane k0 (the kept perturbation)
+    moved = m0 >= 0;
+    if (moved) {
+      const Q4<T> qr = SAMPLER == 0 ? qm : qk;
+      const V3<T> tr = SAMPLER == 0 ? tk : tm;
+      const int lq = SAMPLER == 0 ? m0 : k0, lt = SAMPLER == 0 ? k0 : m0;
+      q = Q4<T>{__shfl_sync(kFullMask, qr.w, lq), __shfl_sync(kFullMask, qr.x, lq), __shfl_sync(kFullMask, qr.y, lq),
+                __shfl_sync(kFullMask, qr.z, lq)};
+      t = V3<T>{__shfl_sync(kFullMask, tr.x, lt), __shfl_sync(kFullMask, tr.y, lt), __shfl_sync(kFullMask, tr.z, lt)};
+    }
+    if (c.trace != nullptr && lane == 0) {
+      int16_t* trc = c.trace + ((size_t)w * c.n_iter + it) * (K + 2);
+      for (int r = 0; r < K; ++r) trc[r] = (int16_t)sl.J[r];
+      trc[K] = (int16_t)m0;
+      trc[K + 1] = (int16_t)k0;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    T* oq = c.out_q + 4 * (size_t)w;
+    T* ot = c.out_t + 3 * (size_t)w;
+    oq[0] = q.w, oq[1] = q.x, oq[2] = q.y, oq[3] = q.z;
+    ot[0] = t.x, ot[1] = t.y, ot[2] = t.z;
+    if (!(isfinite(q.w) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(t.x) && isfinite(t.y) &&
+          isfinite(t.z)))
+      atomicOr(c.status, kDevErrNumeric);
+  }
+  __syncwarp();
+}
+
+template <typename T, int SAMPLER>
+__global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
+    reg_walk_kernel(const __grid_constant__ WalkArgs a, const int slab_bytes) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  const int N = a.n;
+  const T4<T>* tab = reinterpret_cast<const T4<T>*>(smem + 128);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* slab = smem + 128 + reg_table_bytes<T>(N) + (size_t)warp * slab_bytes;
+  T4<T>* C = reinterpret_cast<T4<T>*>(slab);
+  Slab<T> sl;
+  sl.D = nullptr, sl.L = nullptr, sl.E = nullptr;
+  sl.P = C + N;
+  sl.key = reinterpret_cast<typename KeyOf<T>::type*>(sl.P + a.n_perturb);
+  sl.J = reinterpret_cast<int*>(sl.key + a.n_perturb);
+  // ---- stage the hypotheses with a 1-D TMA bulk copy
+  const uint32_t tbytes = 16u * N * sizeof(T);
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(bar, tbytes);
+    bulk_copy_g2s(smem + 128, a.table, tbytes, bar);
+  }
+  if (!mbar_wait_bounded(bar, 0, 1 << 22)) {
+    if (threadIdx.x == 0) atomicOr(a.status, kDevErrTimeout);
+    return;
+  }
+  WalkCtx<T> c;
+  c.N = N, c.NP = a.n_perturb, c.K = a.n_keep, c.NT = a.n_steps, c.mc = 1, c.n_iter = a.n_iter;
+  c.fx = c.fy = c.cx = c.cy = T(0);
+  c.rho_max = T(0);
+  c.r_pert = T(SAMPLER == 0 ? a.stats->r_trans : a.stats->r_rot);
+  c.omega0 = a.omega0, c.v0 = a.v0, c.gamma = a.gamma;
+  c.st = a.stats, c.seed_data = a.seed_data, c.s0 = a.s0;
+  c.key0 = a.key0, c.key1 = a.key1;
+  c.out_q = reinterpret_cast<T*>(a.out_q), c.out_t = reinterpret_cast<T*>(a.out_t);
+  c.trace = a.trace, c.status = a.status;
+  c.out_snap = nullptr;
+  const RkParam rk{a};
+  unsigned long long evals = 0;
+  const int nw = blockDim.x >> 5;
+  for (int w = blockIdx.x * nw + warp; w < a.n_samples; w += gridDim.x * nw)
+    reg_walk_one<T, SAMPLER>(c, rk, w, tab, C, sl, lane, evals);
+  if (lane == 0 && evals) atomicAdd(a.evals, evals);
+}
+
 // ---------------------------------------------------------------- batched walks (one persistent launch)
 // Work item i = (PURSE p, sampler, walk w) with p = i / (2 S), sampler = (i / S) & 1, w = i mod S;
 // the dS_t items of 3D-3D PURSEs are skipped (their two balls use the dS_R samples).  Each warp
@@ -1018,7 +1283,34 @@ static cudaError_t launch_walk_l(purse_t h, const purse_params* p, const WalkArg
   return smp == 0 ? launch_walk_t<double, 1, 0, LAM>(h, p, a, st) : launch_walk_t<double, 1, 1, LAM>(h, p, a, st);
 }
 
+template <typename T, int SAMPLER>
+static cudaError_t launch_reg_walk_t(purse_t h, const purse_params* p, const WalkArgs& a, cudaStream_t st) {
+  const size_t slab = reg_slab_bytes<T>(a.n, p->n_perturb);
+  const size_t table = reg_table_bytes<T>(a.n);
+  int warps = kWalkWarps;
+  while (warps > 1 && 128 + table + warps * slab > kMaxSmemPerBlock) --warps;
+  const size_t smem = 128 + table + warps * slab;
+  if (smem > kMaxSmemPerBlock) return cudaErrorInvalidConfiguration;
+  auto kern = reg_walk_kernel<T, SAMPLER>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long need = (a.n_samples + warps - 1) / warps;
+  const long cap = (long)per_sm * h->sm_count;
+  const int grid = (int)(need < cap ? need : cap);
+  kern<<<grid, 32 * warps, smem, st>>>(a, (int)slab);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_walk(purse_t h, const purse_params* p, const WalkArgs& a, cudaStream_t st) {
+  if (h->kind == PURSE_REG) {
+    if (p->precision == 1)
+      return p->sampler == 0 ? launch_reg_walk_t<double, 0>(h, p, a, st) : launch_reg_walk_t<double, 1>(h, p, a, st);
+    return p->sampler == 0 ? launch_reg_walk_t<float, 0>(h, p, a, st) : launch_reg_walk_t<float, 1>(h, p, a, st);
+  }
   return a.ell ? launch_walk_l<true>(h, p, a, st) : launch_walk_l<false>(h, p, a, st);
 }
 

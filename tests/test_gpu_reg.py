@@ -1,6 +1,6 @@
 """Pose-regression PURSE (Example 3) on the GPU against the oracle: convex-combination seeds,
-the plain per-operation samplers replayed by the oracle, and the closed-form balls of a
-nested PURSE through the GPU's own seeds, walks and exact balls."""
+the fused and the plain per-operation samplers replayed by the oracle, and the closed-form
+balls of a nested PURSE through the GPU's own seeds, walks and exact balls."""
 import numpy as np
 import pytest
 import torch
@@ -9,7 +9,7 @@ from oracle import closure, purse as op, ransag, so3
 from paper_2403_09990_gb300 import purse as P
 from paper_2403_09990_gb300 import synthetic as syn
 from tests import parity
-from tests.gpu_helpers import params_from, to_dev
+from tests.gpu_helpers import params_from, sample, to_dev
 from tests.test_gpu_plain import sample_plain
 
 pytestmark = pytest.mark.gpu
@@ -52,6 +52,47 @@ def test_regression_walks_replay(precision):
     print(f"regression precision {precision}: robust fraction {rep.robust.mean():.3f}")
 
 
+FUSED = {
+    "R-fp32": (10, 0, 0, {}), "R-fp64": (10, 1, 0, {}), "R-fp32-n3": (3, 0, 0, {}),
+    "R-fp64-n40-keep7-np100-nt9": (40, 1, 0, dict(n_keep=7, n_perturb=100, n_steps=9)),
+    "t-fp32": (10, 0, 1, dict(rot_perturb=0.2, v0=0.02)), "t-fp64": (10, 1, 1, dict(rot_perturb=0.2, v0=0.02)),
+    "R-fp32-np256-keep32-nt32": (10, 0, 0, dict(n_perturb=256, n_keep=32, n_steps=32)),
+}
+
+
+@pytest.mark.parametrize("name", list(FUSED))
+def test_regression_fused_walks_replay(name):
+    """The fused pose-regression walks (one part of each hypothesis per perturbation, separable
+    ladder) replayed by the oracle, and their evaluation count."""
+    n_hyp, precision, sampler, kw = FUSED[name]
+    p = syn.purse_reg(n_hyp, 4)
+    prm = closure.preset_reg(**kw)
+    seeds, _ = ransag.convex_seeds(p, 21, 20000, 40)
+    n = 257
+    with P.Purse(p) as h:
+        q, t, tr = sample(h.h, prm, sampler, precision, 78, seeds, n)
+        evals = P.purse_last_evals(h.h)
+    # per iteration N_P moving parts and N_T + N_P* ladder factors of N hypotheses; the part the
+    # perturbations do not move once in the first iteration and after every move
+    assert evals == (n * prm.n_iter * (prm.n_perturb + prm.n_steps + prm.n_keep) + fixed_count(tr, prm)) * p.n
+    R, tt, rep = parity.replay_walks(p, seeds, prm, 78, np.arange(n), tr, precision, sampler)
+    assert rep.ok(), rep.inconsistent[:10]
+    assert not rep.robust_mismatch, rep.robust_mismatch[:10]
+    tol = 1e-10 if precision else 1e-5
+    assert parity.rot_angle(q, so3.quat_from_R(R)).max() <= tol
+    assert np.abs(t - tt).max() <= tol
+    assert np.all(parity.classify(p, so3.R_from_quat(q), t, precision) >= 0)
+    moved = (tr[:, :, prm.n_keep] >= 0).any(axis=1).mean()
+    assert moved > 0.5
+    print(f"fused regression {name}: robust {rep.robust.mean():.3f}, moved {moved:.3f}")
+
+
+def fixed_count(tr, prm):
+    """Iterations that evaluate the unmoved part: the first and every one after a move."""
+    mv = tr[:, :, prm.n_keep] >= 0
+    return int(tr.shape[0] + mv[:, :-1].sum())
+
+
 def test_nested_regression_closed_form_on_gpu():
     """Seeds, walks and the exact balls all on the GPU: the rotation ball approaches the known
     angle 2 asin(beta / (2 sqrt 2)) from below, the translation ball stays within its radius."""
@@ -82,9 +123,11 @@ def test_regression_rejections():
         sd = to_dev(p.seed_pose()[None])
         q = torch.empty((8, 4), dtype=torch.float32, device="cuda")
         t = torch.empty((8, 3), dtype=torch.float32, device="cuda")
-        with pytest.raises(P.PurseError) as e:
-            P.purse_sample(h.h, params_from(closure.preset_reg(), 0, 0), 1, sd, 1, 8, q, t)
+        snap = torch.empty((8, 12), dtype=torch.float32, device="cuda")
+        with pytest.raises(P.PurseError) as e:   # no boundary snap for regression PURSEs
+            P.purse_sample(h.h, params_from(closure.preset_reg(), 0, 0), 1, sd, 1, 8, q, t, snap=snap)
         assert e.value.status == 1
+        P.purse_sample(h.h, params_from(closure.preset_reg(), 0, 0), 1, sd, 1, 8, q, t)
         poses = torch.zeros((4, 12), dtype=torch.float32, device="cuda")
         d = torch.empty(4, dtype=torch.float32, device="cuda")
         with pytest.raises(P.PurseError):
