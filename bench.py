@@ -485,7 +485,7 @@ def run_sweep(args):
         for line in sweep_next(P, syn, dev, stream):
             print(json.dumps(line), flush=True)
     p = syn.purse_2d3d(N_KEYPOINTS, 0)
-    for lg in ((22, 24, 26) if "scale" in args.sweep_parts else ()):
+    for lg in (tuple(int(x) for x in args.scale_lg.split(",")) if "scale" in args.sweep_parts else ()):
         S = 1 << lg
         r32, w32, m32 = solve(p, S, 0, 1)
         ball_bytes = (16 + 12) * S * (K + 1)
@@ -940,6 +940,7 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="precision / scale sweep instead of the bench step")
     ap.add_argument("--sweep-parts", default="precision,scale,dist,next", help="which parts of the sweep to run")
     ap.add_argument("--dist-kind", type=int, default=None, help="dist sweep: one PURSE kind (0 3D-3D, 1 2D-3D)")
+    ap.add_argument("--scale-lg", default="22,24,26", help="scale sweep: log2 of the samples per sampler")
     ap.add_argument("--dist-n", type=int, default=None, help="dist sweep: one keypoint count")
     ap.add_argument("--grad-purses", type=int, default=1024)
     ap.add_argument("--per-instance-purses", type=int, default=256,
