@@ -93,9 +93,10 @@ __host__ __device__ inline size_t walk_table_bytes(int n, bool lam = false) {
   return align_up((lam ? 16 : 8) * (size_t)n * sizeof(T), 128);
 }
 
-// Pairs per constraint row of the slab tables D and L: 8, or 16 with the U_i entries (slots 8-13).
+// Pairs per constraint row of the slab tables D and L: 8, or 14 with the U_i entries (slots 8-13;
+// 14 rather than 16 keeps rows i and i + 1 in different shared-memory banks).
 template <bool LAM>
-constexpr int kRow = LAM ? 16 : 8;
+constexpr int kRow = LAM ? 14 : 8;
 
 template <typename K>
 __device__ __forceinline__ void cas_desc(K& a, K& b) {
@@ -138,7 +139,7 @@ __host__ __device__ inline int ladder_pairs(int n) { return (n + 1) / 2; }
 
 template <typename T>
 __host__ __device__ inline size_t walk_slab_bytes2(int n, int n_perturb, int n_steps, bool lam = false) {
-  const size_t p2 = 2 * sizeof(T), t4 = 4 * sizeof(T), row = lam ? 16 : 8;
+  const size_t p2 = 2 * sizeof(T), t4 = 4 * sizeof(T), row = lam ? 14 : 8;
   const size_t bytes = row * (size_t)n * p2 + row * (size_t)ladder_pairs(n) * p2 + (n_perturb + 4 * (size_t)n_steps) * t4 +
                        (size_t)n_perturb * sizeof(typename KeyOf<T>::type) + 32 * sizeof(int);
   return align_up(bytes, 128);
