@@ -7,7 +7,8 @@
   seeds inside the PURSE in trial order;
 * nested hypotheses: the PURSE is one rotation ball of angle 2 asin(beta / (2 sqrt 2)) and
   one translation ball, so the exact balls of the walk samples lie inside them (Prop. 1),
-  the rotation ball close to it, and every sample is in the PURSE.
+  the rotation ball close to it, and every sample is in the PURSE; the dS_t walks fill the
+  translation ball the same way.
 """
 import numpy as np
 
@@ -56,3 +57,17 @@ def test_nested_hypotheses_closed_form_balls():
     assert D <= Dstar * (1 + 1e-9) and D >= 0.97 * Dstar, (D, Dstar)
     assert so3.dist_quat(C, so3.quat_from_R(p.R_gt)) <= 0.05 * Dstar
     assert d <= 0.006 * (1 + 1e-9) and np.linalg.norm(c - p.t_gt) <= 0.006
+
+
+def test_nested_hypotheses_translation_walks():
+    """The dS_t sampler on the nested PURSE: the translations fill one ball of radius beta_t around
+    t_gt, so the exact ball of the walk samples lies inside it and comes close to it (Prop. 1), and
+    every sample keeps its rotation within the rotation ball."""
+    p = syn.purse_reg_nested(10, 1, beta_rot=0.04, beta_t=0.006)
+    prm = closure.preset_reg(rot_perturb=0.2, v0=0.02)
+    seeds, _ = ransag.convex_seeds(p, 2, 5000, 50)
+    R, t = closure.sample_translation_boundary(p, seeds, prm, 9, np.arange(600))
+    assert np.all(op.in_purse(p, R, t))
+    c, d = om.meb_exact_translation(t)
+    assert d <= 0.006 * (1 + 1e-9) and d >= 0.97 * 0.006, d
+    assert np.linalg.norm(c - p.t_gt) <= 0.05 * 0.006
