@@ -37,7 +37,12 @@ Readings of the paper used here (where it is silent or ambiguous):
 
 Parity: pinned in tests/test_oracle_walk.py (octahedral PURSE with
 closed-form radii and Prop. 1, membership of every output sample, the
-needle shape of a 2D-3D PURSE, seeds-versus-walks spread).
+needle shape of a 2D-3D PURSE, seeds-versus-walks spread) and in
+tests/test_oracle_velocity.py (start velocities: unit random parts, mean
+projection 1 on the outward axis and direction, distance to the centre
+growing at rates omega0 and v0; PCA scaling against the axes and ratios of a
+known anisotropic seed cloud, the viewing ray with few seeds; both samplers
+on the appendix's unit-ball toy set).
 """
 from __future__ import annotations
 
