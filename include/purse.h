@@ -196,7 +196,9 @@ purse_status purse_last_evals(purse_t h, unsigned long long* evals, purse_stream
  * c_k = c_{k-1} + (farthest - c_{k-1}) / k.  d_result (device, 9 doubles):
  * C (4, w >= 0), c (3), D-hat (rad), d-hat (m).  d_farthest (device, may be NULL):
  * 2K int32, the farthest-sample indices of the rotation then the translation descent.
- * Either ball may be skipped with n = 0 (its result entries are 0).
+ * Either ball may be skipped with n = 0 (its result entries are 0); at most 2^31 - 2^21
+ * samples per ball (PURSE_ERR_ARG beyond; the same bound holds for megb_solve_exact,
+ * megb_backward and megb_solve_noalloc).
  * Uses handle-owned scratch; the input buffers must not change before megb_backward. */
 purse_status megb_solve(purse_t h, int precision, int n_iters, const void* d_q, int n_rot,
                         const void* d_t, int n_tr, double* d_result, int32_t* d_farthest,
@@ -253,7 +255,11 @@ purse_status megb_solve_exact(purse_t h, int precision, const void* d_q, int n_r
  * Scratch: one 64 KiB array in the library's device memory, which every GPU that loads the
  * library holds until the process exits.  Limits: n_iters <= 4096 (PURSE_ERR_ARG beyond).
  * The first call on a device looks up that array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the one array and a call
+ * make that first call before any stream capture.  The address is cached per device for the
+ * life of the process: do not call cudaDeviceReset between calls (the reset unloads the
+ * module, and the cached address would then point at freed memory).  The grid of the ball
+ * kernels is capped at min(4 x SMs, 512) blocks (megb_solve: 4 x SMs); the farthest samples,
+ * centres and radii are the same, ties going to the lowest index in both.  All calls share the one array and a call
  * leaves its contents behind (it re-initialises what must start at zero), so calls whose
  * work overlaps on the GPU (other streams, other host threads) race: serialise them. */
 purse_status megb_solve_noalloc(int precision, int n_iters, const void* d_q, int n_rot, const void* d_t, int n_tr,

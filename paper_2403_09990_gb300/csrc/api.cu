@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -13,10 +14,45 @@
 namespace purse {
 
 static thread_local std::string g_error = "";
+static thread_local const char* g_injected = nullptr;  // site of the last injected allocation refusal
 
 void set_error(const std::string& msg) { g_error = msg; }
 
+bool fault_at(const char* site) {
+  const char* f = std::getenv("PURSE_FAULT");
+  if (!f || !*f) return false;
+  const size_t n = std::strlen(site);
+  for (const char* p = f; *p;) {
+    const char* e = std::strchr(p, ',');
+    const size_t len = e ? (size_t)(e - p) : std::strlen(p);
+    if (len == n && std::strncmp(p, site, n) == 0) return true;
+    if (!e) break;
+    p = e + 1;
+  }
+  return false;
+}
+
+purse_status injected_fault(const char* site, const char* where) {
+  set_error(std::string(where) + ": injected fault (PURSE_FAULT=" + site + ")");
+  if (std::strcmp(site, "alloc") == 0) return PURSE_ERR_NOMEM;
+  if (std::strcmp(site, "empty_seed") == 0) return PURSE_ERR_EMPTY;
+  return PURSE_ERR_CUDA;
+}
+
+cudaError_t dev_alloc(void** ptr, size_t bytes) {
+  if (fault_at("alloc")) {
+    *ptr = nullptr;
+    g_injected = "alloc";
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(ptr, bytes);
+}
+
 purse_status cuda_fail(cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation && g_injected) {
+    g_injected = nullptr;
+    return injected_fault("alloc", where);
+  }
   set_error(std::string(where) + ": " + cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? PURSE_ERR_NOMEM : PURSE_ERR_CUDA;
 }
@@ -35,7 +71,7 @@ purse_status ensure_scratch(purse_t h, size_t bytes) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaFree(scratch)");
   }
   const size_t sz = bytes < (1 << 16) ? (1 << 16) : bytes + bytes / 4;
-  cudaError_t e = cudaMalloc(&h->d_scratch, sz);
+  cudaError_t e = dev_alloc(&h->d_scratch, sz);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(scratch)");
   h->scratch_bytes = sz;
   return PURSE_OK;
@@ -67,6 +103,12 @@ purse_status purse_create(int kind, int n, const double* model, const double* ob
   if (n < 3 || n > 256) return arg_error("purse_create: n must be in [3, 256]");
   if (!model || !obs || !radii) return arg_error("purse_create: NULL input array");
   const int od = kind == PURSE_3D3D ? 3 : 2;
+  std::vector<double> obs_fault;
+  if (fault_at("nan_input")) {  // the caller's array is left as it is
+    obs_fault.assign(obs, obs + (size_t)od * n);
+    obs_fault[0] = std::nan("");
+    obs = obs_fault.data();
+  }
   if (!finite_all(model, 3 * (size_t)n) || !finite_all(obs, (size_t)od * n) || !finite_all(radii, n))
     return arg_error("purse_create: non-finite input");
   for (int i = 0; i < n; ++i)
@@ -100,6 +142,7 @@ namespace purse {
 // A handle owning device copies (FP64 and FP32) of the constraint table t64.
 purse_status make_handle(int kind, int n, const std::vector<double>& t64, const purse_intrinsics& Kc, double rho_max,
                          purse_t* out) {
+  if (fault_at("alloc")) return injected_fault("alloc", "purse_create");
   std::vector<float> t32(t64.size());
   for (size_t k = 0; k < t64.size(); ++k) t32[k] = (float)t64[k];
   purse_s* h = new purse_s();
@@ -110,9 +153,9 @@ purse_status make_handle(int kind, int n, const std::vector<double>& t64, const 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaMalloc(&h->tables.f64, t64.size() * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&h->tables.f32, t32.size() * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_status, 256);
+  if (e == cudaSuccess) e = dev_alloc((void**)&h->tables.f64, t64.size() * sizeof(double));
+  if (e == cudaSuccess) e = dev_alloc((void**)&h->tables.f32, t32.size() * sizeof(float));
+  if (e == cudaSuccess) e = dev_alloc((void**)&h->d_status, 256);
   if (e == cudaSuccess) e = cudaMemcpy(h->tables.f64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->tables.f32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, 256);
@@ -136,6 +179,12 @@ purse_status purse_create_regression(int n, const double* hyp, const double* bet
   *out = nullptr;
   if (n < 1 || n > 256) return arg_error("purse_create_regression: n must be in [1, 256]");
   if (!hyp || !beta_rot || !beta_t) return arg_error("purse_create_regression: NULL input array");
+  std::vector<double> hyp_fault;
+  if (fault_at("nan_input")) {
+    hyp_fault.assign(hyp, hyp + 12 * (size_t)n);
+    hyp_fault[9] = std::nan("");
+    hyp = hyp_fault.data();
+  }
   if (!finite_all(hyp, 12 * (size_t)n) || !finite_all(beta_rot, n) || !finite_all(beta_t, n))
     return arg_error("purse_create_regression: non-finite input");
   for (int i = 0; i < n; ++i) {
@@ -207,8 +256,8 @@ purse_status purse_set_noise(purse_t h, const double* lam) {
   std::vector<float> u32(u64.size());
   for (size_t k = 0; k < u64.size(); ++k) u32[k] = (float)u64[k];
   cudaError_t e = cudaSuccess;
-  if (!h->ell64) e = cudaMalloc(&h->ell64, u64.size() * sizeof(double));
-  if (e == cudaSuccess && !h->ell32) e = cudaMalloc(&h->ell32, u32.size() * sizeof(float));
+  if (!h->ell64) e = dev_alloc((void**)&h->ell64, u64.size() * sizeof(double));
+  if (e == cudaSuccess && !h->ell32) e = dev_alloc((void**)&h->ell32, u32.size() * sizeof(float));
   if (e == cudaSuccess) e = cudaMemcpy(h->ell64, u64.data(), u64.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->ell32, u32.data(), u32.size() * sizeof(float), cudaMemcpyHostToDevice);
   return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_set_noise");
@@ -234,6 +283,7 @@ purse_status purse_eval(purse_t h, int precision, const void* d_poses, int n_pos
   if (n_poses > 0 && !d_poses) return arg_error("purse_eval: NULL poses");
   if (h->kind == PURSE_REG || h->ell64)
     return arg_error("purse_eval: not available for regression PURSEs or noise matrices (use purse_dist)");
+  if (fault_at("launch")) return injected_fault("launch", "purse_eval");
   cudaError_t e = launch_eval(h, precision, d_poses, n_poses, d_margin, d_active, d_grad, (cudaStream_t)stream);
   return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_eval");
 }
@@ -247,6 +297,7 @@ purse_status purse_dist(purse_t h, int mode, const float* d_poses, long long n_p
   if ((reinterpret_cast<uintptr_t>(d_poses) & 15) != 0) return arg_error("purse_dist: d_poses must be 16-byte aligned");
   if (mode != 0 && (h->kind == PURSE_REG || h->ell64))
     return arg_error("purse_dist: regression PURSEs and noise matrices take mode 0");
+  if (fault_at("launch")) return injected_fault("launch", "purse_dist");
   cudaError_t e = mode == 0 ? launch_plain_dist(h, d_poses, (long)n_poses, d_dist, (cudaStream_t)stream)
                             : launch_tc_dist(h, mode == 1 ? 3 : 1, d_poses, (long)n_poses, d_dist, (cudaStream_t)stream);
   return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_dist");
@@ -257,6 +308,11 @@ purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds,
   if (!h) return arg_error("purse_ransag: NULL handle");
   if (n_trials < 1 || max_seeds < 1) return arg_error("purse_ransag: n_trials and max_seeds must be >= 1");
   if (!d_seeds || !n_seeds) return arg_error("purse_ransag: NULL output");
+  if (fault_at("empty_seed")) {
+    *n_seeds = 0;
+    return injected_fault("empty_seed", "purse_ransag");
+  }
+  if (fault_at("launch")) return injected_fault("launch", "purse_ransag");
   cudaStream_t st = (cudaStream_t)stream;
   const int chunk = 1 << 16;
   const int slots = h->kind == PURSE_2D3D ? 4 : 1;  // candidate poses per trial (P3P: up to four)
@@ -311,6 +367,8 @@ purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const
   if (n_samples > 0 && (!d_q || !d_t)) return arg_error("purse_sample: NULL output");
   if ((long long)p->n_iter * (p->n_keep + 2) * (long long)n_samples > (1LL << 40))
     return arg_error("purse_sample: trace too large");
+  if (fault_at("empty_seed")) return injected_fault("empty_seed", "purse_sample");
+  if (fault_at("launch")) return injected_fault("launch", "purse_sample");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t stats_bytes = align256(sizeof(WalkStats));
   const size_t seed_bytes = align256((size_t)s0 * kSeedStride * sizeof(double));
@@ -324,6 +382,7 @@ purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const
   if (n_samples == 0) return PURSE_OK;
   WalkArgs a;
   a.table = p->precision == 0 ? (const void*)h->tables.f32 : (const void*)h->tables.f64;
+  a.table64 = h->tables.f64;
   a.ell = !h->ell64 ? nullptr : p->precision == 0 ? (const void*)h->ell32 : (const void*)h->ell64;
   a.n = h->n;
   a.fx = h->K.fx, a.fy = h->K.fy, a.cx = h->K.cx, a.cy = h->K.cy;
@@ -344,6 +403,7 @@ purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const
   a.out_snap = d_snap;
   a.status = h->d_status;
   a.evals = h->d_evals;
+  a.stall_probe = fault_at("stall") ? 1 : 0;
   e = launch_walk(h, p, a, st);
   if (e == cudaErrorInvalidConfiguration || e == cudaErrorInvalidValue) {
     set_error("purse_sample: walk configuration does not fit in shared memory");
@@ -371,6 +431,8 @@ purse_status purse_sample_plain(purse_t h, const purse_params* p, uint64_t seed,
   if (s0 < 1 || !d_seeds) return arg_error("purse_sample_plain: need at least one seed pose");
   if (n_samples < 0) return arg_error("purse_sample_plain: n_samples < 0");
   if (n_samples > 0 && (!d_q || !d_t)) return arg_error("purse_sample_plain: NULL output");
+  if (fault_at("empty_seed")) return injected_fault("empty_seed", "purse_sample_plain");
+  if (fault_at("launch")) return injected_fault("launch", "purse_sample_plain");
   cudaStream_t st = (cudaStream_t)stream;
   int chunk = 1;
   const size_t stats_bytes = align256(sizeof(WalkStats));
@@ -403,7 +465,10 @@ purse_status megb_solve(purse_t h, int precision, int n_iters, const void* d_q, 
   if (precision != 0 && precision != 1) return arg_error("megb_solve: precision must be 0 or 1");
   if (n_iters < 1 || n_iters > (1 << 20)) return arg_error("megb_solve: n_iters must be in [1, 2^20]");
   if (n_rot < 0 || n_tr < 0) return arg_error("megb_solve: negative sample count");
+  if (n_rot > kMaxBallSamples || n_tr > kMaxBallSamples)
+    return arg_error("megb_solve: more than 2^31 - 2^21 samples (32-bit sample indices)");
   if ((n_rot > 0 && !d_q) || (n_tr > 0 && !d_t) || !d_result) return arg_error("megb_solve: NULL buffer");
+  if (fault_at("launch")) return injected_fault("launch", "megb_solve");
   const size_t need = megb_scratch_bytes(n_iters, h->sm_count);
   // the walk scratch (stats, seeds) is not needed any more once sampling is enqueued,
   // but megb keeps its own region after it so both can coexist on one stream
@@ -424,7 +489,10 @@ purse_status megb_solve_exact(purse_t h, int precision, const void* d_q, int n_r
   if (!h) return arg_error("megb_solve_exact: NULL handle");
   if (precision != 0 && precision != 1) return arg_error("megb_solve_exact: precision must be 0 or 1");
   if (n_rot < 0 || n_tr < 0) return arg_error("megb_solve_exact: negative sample count");
+  if (n_rot > kMaxBallSamples || n_tr > kMaxBallSamples)
+    return arg_error("megb_solve_exact: more than 2^31 - 2^21 samples (32-bit sample indices)");
   if ((n_rot > 0 && !d_q) || (n_tr > 0 && !d_t) || !d_result) return arg_error("megb_solve_exact: NULL buffer");
+  if (fault_at("launch")) return injected_fault("launch", "megb_solve_exact");
   purse_status s = ensure_scratch(h, exact_scratch_bytes(h->sm_count));
   if (s != PURSE_OK) return s;
   cudaError_t e = launch_megb_exact(h, precision, d_q, n_rot, d_t, n_tr, d_ref, d_result, h->d_scratch,
@@ -440,10 +508,13 @@ purse_status megb_backward(purse_t h, int precision, int n_iters, const void* d_
   if (precision != 0 && precision != 1) return arg_error("megb_backward: precision must be 0 or 1");
   if (n_iters < 1 || n_iters > (1 << 20)) return arg_error("megb_backward: n_iters must be in [1, 2^20]");
   if (n_rot < 0 || n_tr < 0) return arg_error("megb_backward: negative sample count");
+  if (n_rot > kMaxBallSamples || n_tr > kMaxBallSamples)
+    return arg_error("megb_backward: more than 2^31 - 2^21 samples (32-bit sample indices)");
   if ((n_rot > 0 && (!d_q || !d_snap_rot)) || (n_tr > 0 && (!d_t || !d_snap_tr)))
     return arg_error("megb_backward: NULL samples or snap records");
   if (!d_farthest || !d_result || !d_grad_result || !d_grad_obs || !d_grad_radii)
     return arg_error("megb_backward: NULL buffer");
+  if (fault_at("launch")) return injected_fault("launch", "megb_backward");
   purse_status s = ensure_scratch(h, megb_backward_scratch_bytes(n_iters, h->sm_count, h->n));
   if (s != PURSE_OK) return s;
   cudaError_t e = launch_megb_backward(h, precision, n_iters, d_q, d_snap_rot, n_rot, d_t, d_snap_tr, n_tr, d_farthest,
@@ -457,6 +528,7 @@ purse_status purse_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t
   if (n_streams < 0 || n_words < 0 || (n_streams > 0 && n_words > 0 && !d_words))
     return arg_error("purse_rng_words: bad sizes or NULL output");
   if (j >= (1u << 24) || phase > 255u) return arg_error("purse_rng_words: j must be < 2^24 and phase < 256");
+  if (fault_at("launch")) return injected_fault("launch", "purse_rng_words");
   cudaError_t e = launch_rng_words(seed, phase, j, i, w0, n_streams, n_words, d_words, d_lattice, unit,
                                    (cudaStream_t)stream);
   return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_rng_words");

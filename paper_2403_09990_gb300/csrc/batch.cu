@@ -68,6 +68,7 @@ static BatchArgs make_args(purse_batch_t b, const purse_params* p3, const purse_
   BatchArgs a;
   a.info = b->d_info;
   a.table = b->d_tab32;
+  a.table64 = b->d_tab64;
   a.stats = b->d_stats;
   a.seed_data = b->d_seed_data;
   a.n_purses = b->n_purses;
@@ -101,7 +102,7 @@ static purse_status ensure_batch_buffers(purse_batch_t b, int n_samples, int n_i
     b->d_samples = nullptr;
     b->samples_cap = 0;
     const size_t bytes = (size_t)b->n_purses * n_samples * 14 * sizeof(float);
-    cudaError_t e = cudaMalloc(&b->d_samples, bytes);
+    cudaError_t e = dev_alloc((void**)&b->d_samples, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "purse_batch_solve (sample buffers)");
     b->samples_cap = n_samples;
   }
@@ -109,7 +110,7 @@ static purse_status ensure_batch_buffers(purse_batch_t b, int n_samples, int n_i
     if (b->d_far) cudaFree(b->d_far);
     b->d_far = nullptr;
     b->far_cap = 0;
-    cudaError_t e = cudaMalloc(&b->d_far, (size_t)b->n_purses * 2 * n_iters * sizeof(int32_t));
+    cudaError_t e = dev_alloc((void**)&b->d_far, (size_t)b->n_purses * 2 * n_iters * sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "purse_batch_solve (traces)");
     b->far_cap = n_iters;
   }
@@ -117,12 +118,12 @@ static purse_status ensure_batch_buffers(purse_batch_t b, int n_samples, int n_i
     if (b->d_snap) cudaFree(b->d_snap);
     b->d_snap = nullptr;
     b->snap_cap = 0;
-    cudaError_t e = cudaMalloc(&b->d_snap, 2 * (size_t)b->n_purses * n_samples * kSnapStride * sizeof(float));
+    cudaError_t e = dev_alloc((void**)&b->d_snap, 2 * (size_t)b->n_purses * n_samples * kSnapStride * sizeof(float));
     if (e != cudaSuccess) return cuda_fail(e, "purse_batch_solve (snap records)");
     b->snap_cap = n_samples;
   }
   if (b->grad && !b->d_fstar) {
-    cudaError_t e = cudaMalloc(&b->d_fstar, 2 * (size_t)b->n_purses * sizeof(int32_t));
+    cudaError_t e = dev_alloc((void**)&b->d_fstar, 2 * (size_t)b->n_purses * sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "purse_batch_solve (farthest samples)");
   }
   return PURSE_OK;
@@ -157,6 +158,12 @@ purse_status purse_batch_create(int n_purses, const int* kinds, const int* offse
   *out = nullptr;
   if (n_purses < 1) return barg("purse_batch_create: n_purses must be >= 1");
   if (!kinds || !offsets || !model || !obs || !radii) return barg("purse_batch_create: NULL input");
+  std::vector<double> obs_fault;
+  if (fault_at("nan_input") && offsets[n_purses] > 0) {  // the caller's array is left as it is
+    obs_fault.assign(obs, obs + 3 * (size_t)offsets[n_purses]);
+    obs_fault[0] = std::nan("");
+    obs = obs_fault.data();
+  }
   if (offsets[0] != 0) return barg("purse_batch_create: offsets[0] must be 0");
   int nmax = 0;
   for (int p = 0; p < n_purses; ++p) {
@@ -197,17 +204,18 @@ purse_status purse_batch_create(int n_purses, const int* kinds, const int* offse
     }
   }
   std::vector<float> t32(t64.begin(), t64.end());
+  if (fault_at("alloc")) return injected_fault("alloc", "purse_batch_create");
   purse_batch_s* b = new purse_batch_s();
   b->n_purses = n_purses, b->nmax = nmax, b->total_rows = 2 * total;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_info, info.size() * sizeof(BatchPurseInfo));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_tab64, t64.size() * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_tab32, t32.size() * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_stats, n_purses * sizeof(WalkStats));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_seed_data, (size_t)n_purses * kSeedStride * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 256);
+  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_info, info.size() * sizeof(BatchPurseInfo));
+  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_tab64, t64.size() * sizeof(double));
+  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_tab32, t32.size() * sizeof(float));
+  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_stats, n_purses * sizeof(WalkStats));
+  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_seed_data, (size_t)n_purses * kSeedStride * sizeof(double));
+  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_counter, 256);
   if (e == cudaSuccess) {
     b->d_seed = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(b->d_counter) + 64);
     b->d_evals = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(b->d_counter) + 128);
@@ -260,6 +268,7 @@ purse_status purse_batch_solve(purse_batch_t b, const purse_params* p3d, const p
   if (batch_walk_smem(b->nmax, p3d->n_perturb > p2d->n_perturb ? p3d->n_perturb : p2d->n_perturb,
                       p3d->n_steps > p2d->n_steps ? p3d->n_steps : p2d->n_steps, b->warps) > 227 * 1024)
     return barg("purse_batch_solve: the largest PURSE does not fit the walk kernel's shared memory");
+  if (fault_at("launch")) return injected_fault("launch", "purse_batch_solve");
   purse_status s = ensure_batch_buffers(b, n_samples, n_iters);
   if (s != PURSE_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
@@ -312,6 +321,7 @@ purse_status purse_batch_tune(purse_batch_t b, const purse_params* p3d, const pu
   std::string why;
   if (!params_ok(p3d, why) || !params_ok(p2d, why)) return barg("purse_batch_tune: " + why);
   if (n_samples < 1 || n_samples > 12288 || !d_seeds) return barg("purse_batch_tune: bad sample count or seeds");
+  if (fault_at("launch")) return injected_fault("launch", "purse_batch_tune");
   purse_status s = ensure_batch_buffers(b, n_samples, 1);
   if (s != PURSE_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
@@ -414,13 +424,14 @@ purse_status purse_batch_backward(purse_batch_t b, const double* d_results, cons
   if (!d_results || !d_grad_results || !d_grad_obs || !d_grad_radii) return barg("purse_batch_backward: NULL buffer");
   if (!b->last_grad || b->last_iters == 0)
     return (set_error("purse_batch_backward: no solve with gradients enabled yet"), PURSE_ERR_STATE);
+  if (fault_at("launch")) return injected_fault("launch", "purse_batch_backward");
   const int K = b->last_iters;
   const size_t need = (size_t)b->n_purses * (K + 1) * 4 * sizeof(double);
   if (need > b->cs_cap) {
     if (b->d_cs) cudaFree(b->d_cs);
     b->d_cs = nullptr;
     b->cs_cap = 0;
-    cudaError_t e = cudaMalloc(&b->d_cs, need);
+    cudaError_t e = dev_alloc((void**)&b->d_cs, need);
     if (e != cudaSuccess) return cuda_fail(e, "purse_batch_backward (scratch)");
     b->cs_cap = need;
   }

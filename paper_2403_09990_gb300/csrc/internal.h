@@ -37,6 +37,10 @@ constexpr int kSeedStride = 16;
 // Values per walk in the boundary-snap record (see purse_sample).
 constexpr int kSnapStride = 12;
 
+// Largest sample count of a ball call: sample indices are 32-bit and the grid-stride loops of
+// the ball kernels step by up to 2^20 past the last index.
+constexpr int kMaxBallSamples = 2147483647 - (1 << 21);
+
 // Per-PURSE description inside a batch (device array).
 struct BatchPurseInfo {
   int kind, n, table_off, pad;  // table rows [table_off, table_off + 2 n) of the concatenated tables
@@ -54,6 +58,7 @@ struct BatchStatParams {
 struct BatchArgs {
   const BatchPurseInfo* info;
   const float* table;  // FP32 tables, rows of 4 floats
+  const double* table64;  // the same tables in FP64 (read by the boundary snap)
   const WalkStats* stats;
   const double* seed_data;
   int n_purses, n_samples, nmax;
@@ -76,6 +81,7 @@ struct BatchArgs {
 
 struct WalkArgs {
   const void* table;
+  const double* table64;  // the FP64 table (read by the boundary snap at either walk precision)
   const void* ell;  // noise factors U_i of eq. 4 (8 values per constraint, the table's precision) or NULL
   int n;
   double fx, fy, cx, cy;
@@ -93,6 +99,7 @@ struct WalkArgs {
   void* out_snap;
   int* status;
   unsigned long long* evals;  // executed (pose, constraint) evaluations
+  int stall_probe;            // PURSE_FAULT=stall: a bounded wait that runs out after the staging
 };
 
 }  // namespace purse
@@ -123,6 +130,22 @@ struct purse_s {
 namespace purse {
 
 void set_error(const std::string& msg);
+
+// Host-side fault injection for the failure-detection tests.  The environment variable
+// PURSE_FAULT (read at every call) lists sites, comma-separated:
+//   alloc       every device allocation of the library is refused (PURSE_ERR_NOMEM) before
+//               cudaMalloc is called;
+//   launch      every call that would queue GPU work is refused (PURSE_ERR_CUDA) before it does;
+//   nan_input   the PURSE constructors see a NaN in their first observation (PURSE_ERR_ARG);
+//   empty_seed  Step I accepts no pose and purse_sample sees no seed (PURSE_ERR_EMPTY);
+//   stall       the walk kernels, after staging their table, wait on a barrier that nothing
+//               arrives at, give up after a short poll limit and flag a timeout
+//               (PURSE_ERR_TIMEOUT at the next purse_sync).
+// No site faults, traps or hangs the GPU: every refusal happens on the host, and the stall is a
+// bounded wait with no copy in flight.
+bool fault_at(const char* site);
+purse_status injected_fault(const char* site, const char* where);  // sets the message
+cudaError_t dev_alloc(void** ptr, size_t bytes);  // cudaMalloc, refused under PURSE_FAULT=alloc
 purse_status make_handle(int kind, int n, const std::vector<double>& t64, const purse_intrinsics& Kc, double rho_max,
                          purse_t* out);
 purse_status cuda_fail(cudaError_t e, const char* where);

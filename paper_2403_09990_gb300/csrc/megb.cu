@@ -273,14 +273,14 @@ static cudaError_t launch_megb_t(purse_t h, int n_iters, const T* q, int nq, con
   megb_zero_result<<<1, 32, 0, st>>>(result, nq == 0, nt == 0);
   const long cap = (long)megb_blocks_cap(h->sm_count);
   if (nq > 0) {
-    const long want = (nq + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
+    const long want = ((long)nq + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
     const int g = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     for (int k = 1; k <= n_iters; ++k)
       ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, k, f_int, f_out, result);
     ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, 0, f_int, f_out, result);
   }
   if (nt > 0) {
-    const long want = (nt + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
+    const long want = ((long)nt + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
     const int g = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     Part* parts_t = parts + cap;
     for (int k = 1; k <= n_iters; ++k)
@@ -470,12 +470,12 @@ static cudaError_t launch_megb_backward_t(purse_t h, int K, const T* q, const T*
   megb_state_from_result<<<1, 32, 0, st>>>(result, s);
   // farthest sample from the final centres, by the forward's own final pass
   if (nq > 0) {
-    const long want = (nq + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
+    const long want = ((long)nq + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
     const int gsz = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     ggd_step<T, 0><<<gsz, kMegbThreads, 0, st>>>(q, nq, s, parts, 0, f_int, nullptr, dummy);
   }
   if (nt > 0) {
-    const long want = (nt + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
+    const long want = ((long)nt + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
     const int gsz = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     ggd_step<T, 1><<<gsz, kMegbThreads, 0, st>>>(t, nt, s, parts + cap, 0, f_int, nullptr, dummy);
   }
@@ -667,7 +667,9 @@ static std::mutex g_noalloc_mu;
 static void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 static int g_noalloc_sms[kNoAllocMaxDevices] = {};
 
-// Device address of the static scratch on the current device (looked up once per device).
+// Device address of the static scratch on the current device (looked up once per device and
+// cached; the cache assumes the device's primary context lives as long as the process, i.e. no
+// cudaDeviceReset between calls, after which the module and its array are loaded anew).
 static cudaError_t noalloc_scratch(void** ptr, int* sms) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -695,18 +697,18 @@ static cudaError_t launch_megb_noalloc_t(int sms, int n_iters, const T* q, int n
   MegbState* s = reinterpret_cast<MegbState*>(scratch);
   Part* parts = reinterpret_cast<Part*>(reinterpret_cast<char*>(scratch) + kNoAllocStateBytes);
   int32_t* f_int = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(parts) + 2 * kNoAllocMaxBlocks * sizeof(Part));
-  const long cap = 2L * sms < kNoAllocMaxBlocks ? 2L * sms : kNoAllocMaxBlocks;
+  const long cap = 4L * sms < kNoAllocMaxBlocks ? 4L * sms : kNoAllocMaxBlocks;
   megb_init<T><<<1, 32, 0, st>>>(q, nq, t, nt, s);  // also zeroes the completion counters
   megb_zero_result<<<1, 32, 0, st>>>(result, nq == 0, nt == 0);
   if (nq > 0) {
-    const long want = (nq + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
+    const long want = ((long)nq + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
     const int g = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     for (int k = 1; k <= n_iters; ++k)
       ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, k, f_int, f_out, result);
     ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, 0, f_int, f_out, result);
   }
   if (nt > 0) {
-    const long want = (nt + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
+    const long want = ((long)nt + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
     const int g = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     Part* parts_t = parts + kNoAllocMaxBlocks;
     for (int k = 1; k <= n_iters; ++k)
@@ -730,10 +732,15 @@ extern "C" purse_status megb_solve_noalloc(int precision, int n_iters, const voi
     set_error("megb_solve_noalloc: n_iters must be in [1, 4096] (size of the static scratch)");
     return PURSE_ERR_ARG;
   }
+  if (n_rot > kMaxBallSamples || n_tr > kMaxBallSamples) {
+    set_error("megb_solve_noalloc: more than 2^31 - 2^21 samples (32-bit sample indices)");
+    return PURSE_ERR_ARG;
+  }
   if (n_rot < 0 || n_tr < 0 || (n_rot > 0 && !d_q) || (n_tr > 0 && !d_t) || !d_result) {
     set_error("megb_solve_noalloc: negative sample count or NULL buffer");
     return PURSE_ERR_ARG;
   }
+  if (fault_at("launch")) return injected_fault("launch", "megb_solve_noalloc");
   void* scratch = nullptr;
   int sms = 0;
   cudaError_t e = noalloc_scratch(&scratch, &sms);

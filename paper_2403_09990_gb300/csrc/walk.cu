@@ -125,6 +125,7 @@ __device__ __forceinline__ void sort8_desc(K (&k)[8]) {
 //              with noise matrices U_i in slots 8-13.
 //  P[j]        perturbation j: translation offset (dS_R) or unit quaternion (dS_t)
 //  E[4m..]     ladder rung m: quaternion and rows of (K) E_m (dS_R) or s_m v (dS_t)
+//  S[0..9]     FP64 walk state of FP32 walks: q* (4), t* (3), start velocity (3); then q*, t* rounded
 template <typename T>
 struct Slab {
   P2<T>* D;
@@ -133,16 +134,19 @@ struct Slab {
   T4<T>* E;
   typename KeyOf<T>::type* key;
   int* J;
+  double* S;
 };
 
 __host__ __device__ inline int ladder_pairs(int n) { return (n + 1) / 2; }
+
+constexpr int kStateDoubles = 14;  // Slab::S: 10 doubles, then the rounded pose as 7 floats
 
 template <typename T>
 __host__ __device__ inline size_t walk_slab_bytes2(int n, int n_perturb, int n_steps, bool lam = false) {
   const size_t p2 = 2 * sizeof(T), t4 = 4 * sizeof(T), row = lam ? 14 : 8;
   const size_t bytes = row * (size_t)n * p2 + row * (size_t)ladder_pairs(n) * p2 + (n_perturb + 4 * (size_t)n_steps) * t4 +
                        (size_t)n_perturb * sizeof(typename KeyOf<T>::type) + 32 * sizeof(int);
-  return align_up(bytes, 128);
+  return align_up(align_up(bytes, 8) + kStateDoubles * sizeof(double), 128);
 }
 
 template <typename T, bool LAM = false>
@@ -154,6 +158,7 @@ __device__ __forceinline__ Slab<T> carve(unsigned char* base, int N, int NP, int
   s.E = s.P + NP;
   s.key = reinterpret_cast<typename KeyOf<T>::type*>(s.E + 4 * NT);
   s.J = reinterpret_cast<int*>(s.key + NP);
+  s.S = reinterpret_cast<double*>(align_up(reinterpret_cast<size_t>(s.J + 32), 8));
   return s;
 }
 
@@ -382,6 +387,8 @@ struct WalkCtx {
   T* out_t;
   int16_t* trace;
   T* out_snap;  // NULL: no snap; else kSnapStride values per walk
+  const double* tab64;  // the PURSE's FP64 constraint table (global memory), read by the snap
+  const double* kd;     // fx, fy, cx, cy in FP64 (global or parameter memory), read by the snap
   int* status;
 };
 
@@ -430,27 +437,224 @@ __device__ __forceinline__ bool pose_in_purse(const T4<T>* tab, int N, const M3<
 
 // Boundary snap along the last-move ray (used to differentiate the balls): tau_hi = the
 // smallest ladder value whose pose leaves S, bisection of [0, tau_hi] keeping the feasible end,
-// j* = the constraint of smallest margin there.  Record (kSnapStride values): j* (-1: nothing
-// left S along the ladder, pose unchanged), ray kind (0 rotation, 1 translation), direction (3),
-// h'(tau*) = d|g_j*|/d tau, d|g_j*|/d y_j* (3; 2 used for 2D-3D).
-template <typename T, int KIND, int SAMPLER>
-__device__ __forceinline__ void snap_walk(const WalkCtx<T>& c, const T4<T>* tab, const V3<T>& dir, Q4<T>& q,
-                                          V3<T>& t, int w, int lane) {
+// j* = the constraint of smallest margin there (ties to the lower index).  Record (kSnapStride
+// values): j* (-1: nothing left S along the ladder, pose unchanged), ray kind (0 rotation,
+// 1 translation), direction (3), h'(tau*) = d|g_j*|/d tau, d|g_j*|/d y_j* (3; 2 used for 2D-3D).
+//
+// Rotation rays (dS_R) are evaluated in the walk precision.  Along a translation ray (dS_t) the
+// residual of every constraint is affine in tau -- 3D-3D g(tau) = g0 + tau v; 2D-3D
+// (e_x, e_y, P_z)(tau) = (e_x0, e_y0, P_z0) + tau (beta_x, beta_y, v_z) for the division-free pixel
+// residual e = P_xy - z_i P_z -- so the base residuals and slopes are formed once, in FP64 from the
+// FP64 table and pose, and the bisection steps only evaluate the affine model.  In FP32 a direct
+// evaluation would subtract projected coordinates of hundreds of px to get residuals of a few px,
+// and along the viewing ray of a 2D-3D PURSE that rounding moves the boundary by ~1e-6 m.
+template <typename T, int KIND>
+__device__ __forceinline__ void snap_record(const WalkCtx<T>& c, int j, const Q4<double>& qs, const V3<double>& ts,
+                                            const V3<double>& dir, int sampler, T* rec) {
+  using D = double;
   const int N = c.N;
-  const T fx = c.fx, fy = c.fy, cx = c.cx, cy = c.cy;
+  const T4<D>* tab = reinterpret_cast<const T4<D>*>(c.tab64);
+  const D fx = c.kd[0], fy = c.kd[1], cx = c.kd[2], cy = c.kd[3];
+  const M3<D> R = qmat(qs);
+  const T4<D> mz = tab[j], ob = tab[N + j];
+  const V3<D> RA = mul(R, V3<D>{mz.x, mz.y, mz.z});
+  const V3<D> X = RA + ts;
+  V3<D> wv, dy;  // d|g|/d(translation of the keypoint), d|g|/d y
+  if (KIND == 1) {
+    const D Px = fx * X.x + cx * X.z, Py = fy * X.y + cy * X.z, Pz = X.z;
+    const D e0 = Px / Pz - ob.x, e1 = Py / Pz - ob.y;
+    const D nrm = sqrt(e0 * e0 + e1 * e1);
+    const D n0 = e0 / nrm, n1 = e1 / nrm;
+    const V3<D> jn{n0 / Pz, n1 / Pz, -(Px * n0 + Py * n1) / (Pz * Pz)};
+    wv = V3<D>{fx * jn.x, fy * jn.y, cx * jn.x + cy * jn.y + jn.z};
+    dy = V3<D>{-n0, -n1, D(0)};
+  } else {
+    const V3<D> e = X - V3<D>{ob.x, ob.y, ob.z};
+    const D nrm = sqrt(dot(e, e));
+    wv = (D(1) / nrm) * e;
+    dy = (D(-1) / nrm) * e;
+  }
+  const D dh = sampler == 0 ? dot(cross(RA, wv), dir) : dot(wv, dir);
+  rec[0] = T(j), rec[1] = T(sampler), rec[2] = T(dir.x), rec[3] = T(dir.y), rec[4] = T(dir.z), rec[5] = T(dh);
+  rec[6] = T(dy.x), rec[7] = T(dy.y), rec[8] = T(dy.z);
+  for (int k = 9; k < kSnapStride; ++k) rec[k] = T(0);
+}
+
+// Smallest margin over the constraints spread across the lanes, ties to the lower index.
+__device__ __forceinline__ int warp_argmin(double m, int i) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const double om = __shfl_xor_sync(kFullMask, m, o);
+    const int oi = __shfl_xor_sync(kFullMask, i, o);
+    if (om < m || (om == m && oi < i)) m = om, i = oi;
+  }
+  return i;
+}
+
+// (Exp(theta k) - I) for a unit axis k: sin(theta) [k]x + 2 sin^2(theta / 2) (k k^T - I), written
+// without the cancellation of 1 - cos(theta) for small angles.
+template <typename T>
+__device__ __forceinline__ M3<T> exp_minus_identity(const V3<T>& k, T theta) {
+  const T s = sin(theta), h = sin(T(0.5) * theta), c2 = T(2) * h * h;
+  return M3<T>{{c2 * (k.x * k.x - T(1)), -s * k.z + c2 * k.x * k.y, s * k.y + c2 * k.x * k.z,
+                s * k.z + c2 * k.x * k.y, c2 * (k.y * k.y - T(1)), -s * k.x + c2 * k.y * k.z,
+                -s * k.y + c2 * k.x * k.z, s * k.x + c2 * k.y * k.z, c2 * (k.z * k.z - T(1))}};
+}
+
+// Rotation ray (Exp(tau omega) R*, t*): X_i(tau) = X_i(0) + (Exp(tau omega) - I) Y_i with
+// Y_i = R* Z_i, so the residual is its value at tau = 0 (formed in FP64) plus an increment that
+// is small near the sample, evaluated in the walk precision.  (q64, t64, w64) the FP64 pose and
+// angular velocity, coef a free area of the warp's slab (10 N values).
+template <typename T, int KIND>
+__device__ __forceinline__ void snap_rotation(const WalkCtx<T>& c, const Q4<double>& q64, const V3<double>& t64,
+                                              const V3<double>& w64, T* coef, Q4<T>& q, int w, int lane) {
+  using D = double;
+  const int N = c.N;
+  const T4<D>* tab = reinterpret_cast<const T4<D>*>(c.tab64);
+  const D fx = c.kd[0], fy = c.kd[1], cx = c.kd[2], cy = c.kd[3];
+  const M3<D> R = qmat(q64);
+  // coef[10 i ..]: base residual (3: e_x, e_y, P_z or g), Y_i (3), cx - u, cy - v (2D-3D), r or r^2
+  for (int i = lane; i < N; i += 32) {
+    const T4<D> mz = tab[i], ob = tab[N + i];
+    const V3<D> Y = mul(R, V3<D>{mz.x, mz.y, mz.z});
+    const V3<D> X = Y + t64;
+    T* k = coef + 10 * i;
+    if (KIND == 1) {
+      k[0] = T(fx * X.x + (cx - ob.x) * X.z), k[1] = T(fy * X.y + (cy - ob.y) * X.z), k[2] = T(X.z);
+      k[6] = T(cx - ob.x), k[7] = T(cy - ob.y), k[8] = T(mz.w);
+    } else {
+      k[0] = T(X.x - ob.x), k[1] = T(X.y - ob.y), k[2] = T(X.z - ob.z);
+      k[8] = T(ob.w);
+    }
+    k[3] = T(Y.x), k[4] = T(Y.y), k[5] = T(Y.z);
+  }
+  __syncwarp();
+  const D wn = sqrt(dot(w64, w64));
+  const V3<T> ax = wn > 0 ? V3<T>{T(w64.x / wn), T(w64.y / wn), T(w64.z / wn)} : V3<T>{T(1), T(0), T(0)};
+  const T fxt = T(fx), fyt = T(fy), wnt = T(wn);
+  auto residual = [&](const M3<T>& M, int i, T& ex, T& ey, T& ez) {
+    const T* k = coef + 10 * i;
+    const V3<T> dX = mul(M, V3<T>{k[3], k[4], k[5]});
+    if (KIND == 1) {
+      ex = k[0] + fxt * dX.x + k[6] * dX.z, ey = k[1] + fyt * dX.y + k[7] * dX.z, ez = k[2] + dX.z;
+    } else {
+      ex = k[0] + dX.x, ey = k[1] + dX.y, ez = k[2] + dX.z;
+    }
+  };
+  auto inside = [&](T tau) {
+    const M3<T> M = exp_minus_identity(ax, tau * wnt);
+    bool ok = true;
+    for (int i = lane; i < N; i += 32) {
+      T ex, ey, ez;
+      residual(M, i, ex, ey, ez);
+      const T r = coef[10 * i + 8];
+      if (KIND == 1) {
+        const T rz = r * ez;
+        ok = ok && ez > T(0) && ex * ex + ey * ey - rz * rz <= T(0);
+      } else {
+        ok = ok && ex * ex + ey * ey + ez * ez - r <= T(0);
+      }
+    }
+    return __all_sync(kFullMask, ok);
+  };
   T hi = T(-1);
   for (int m = c.NT - 1; m >= 0 && hi < T(0); --m) {
     T sm = T(1);
     for (int k = 0; k < m; ++k) sm *= T(c.gamma);
-    Q4<T> qx;
-    V3<T> tx;
-    ray_pose<T, SAMPLER>(q, t, dir, sm, qx, tx);
-    if (!pose_in_purse<T, KIND>(tab, N, qmat(qx), tx, fx, fy, cx, cy, lane)) hi = sm;
+    if (!inside(sm)) hi = sm;
   }
   T* rec = c.out_snap + (size_t)kSnapStride * w;
   if (hi < T(0)) {
     if (lane == 0) {
-      rec[0] = T(-1), rec[1] = T(SAMPLER);
+      rec[0] = T(-1), rec[1] = T(0);
+      for (int k = 2; k < kSnapStride; ++k) rec[k] = T(0);
+    }
+    __syncwarp();
+    return;
+  }
+  T lo = T(0);
+  const int nb = sizeof(T) == 4 ? 24 : 52;
+  for (int b = 0; b < nb; ++b) {
+    const T mid = T(0.5) * (lo + hi);
+    if (inside(mid))
+      lo = mid;
+    else
+      hi = mid;
+  }
+  // snapped rotation Exp(tau* omega) R* in FP64, rounded once
+  const D th = D(lo) * wn, hs = sin(0.5 * th), hc = cos(0.5 * th);
+  const Q4<D> inc = wn > 0 ? Q4<D>{hc, hs * w64.x / wn, hs * w64.y / wn, hs * w64.z / wn} : Q4<D>{1.0, 0.0, 0.0, 0.0};
+  const Q4<D> qs = qnormalize(qmul(inc, q64));
+  q = Q4<T>{T(qs.w), T(qs.x), T(qs.y), T(qs.z)};
+  // active constraint at tau* from the same residuals
+  const M3<T> M = exp_minus_identity(ax, lo * wnt);
+  double bm = INFINITY;
+  int bi = 0x7FFFFFFF;
+  for (int i = lane; i < N; i += 32) {
+    T ex, ey, ez;
+    residual(M, i, ex, ey, ez);
+    const double r = double(coef[10 * i + 8]);
+    const double m = KIND == 1 ? r - sqrt(double(ex) * ex + double(ey) * ey) / double(ez)
+                               : sqrt(r) - sqrt(double(ex) * ex + double(ey) * ey + double(ez) * ez);
+    if (m < bm) bm = m, bi = i;
+  }
+  const int j = warp_argmin(bm, bi);
+  if (lane == 0) snap_record<T, KIND>(c, j, qs, t64, w64, 0, rec);
+  __syncwarp();
+}
+
+// Translation ray (R*, t* + tau v) through the affine residuals; (q64, t64, v64) the FP64 pose and
+// direction, coef a free area of the warp's slab (7 N values).  The snapped translation is formed
+// in FP64 and rounded once.
+template <typename T, int KIND>
+__device__ __forceinline__ void snap_translation(const WalkCtx<T>& c, const Q4<double>& q64, const V3<double>& t64,
+                                                 const V3<double>& v64, T* coef, V3<T>& t, int w, int lane) {
+  using D = double;
+  const int N = c.N;
+  const T4<D>* tab = reinterpret_cast<const T4<D>*>(c.tab64);
+  const D fx = c.kd[0], fy = c.kd[1], cx = c.kd[2], cy = c.kd[3];
+  const M3<D> R = qmat(q64);
+  // coef[7 i ..]: base residual (3), slope (3), r (2D-3D) or r^2 (3D-3D)
+  for (int i = lane; i < N; i += 32) {
+    const T4<D> mz = tab[i], ob = tab[N + i];
+    const V3<D> X = mul(R, V3<D>{mz.x, mz.y, mz.z}) + t64;
+    T* k = coef + 7 * i;
+    if (KIND == 1) {
+      // e = (fx X_x + (cx - u) X_z, fy X_y + (cy - v) X_z), P_z = X_z
+      k[0] = T(fx * X.x + (cx - ob.x) * X.z), k[1] = T(fy * X.y + (cy - ob.y) * X.z), k[2] = T(X.z);
+      k[3] = T(fx * v64.x + (cx - ob.x) * v64.z), k[4] = T(fy * v64.y + (cy - ob.y) * v64.z), k[5] = T(v64.z);
+      k[6] = T(mz.w);
+    } else {
+      k[0] = T(X.x - ob.x), k[1] = T(X.y - ob.y), k[2] = T(X.z - ob.z);
+      k[3] = T(v64.x), k[4] = T(v64.y), k[5] = T(v64.z);
+      k[6] = T(ob.w);
+    }
+  }
+  __syncwarp();
+  auto inside = [&](T tau) {
+    bool ok = true;
+    for (int i = lane; i < N; i += 32) {
+      const T* k = coef + 7 * i;
+      const T ex = fma(tau, k[3], k[0]), ey = fma(tau, k[4], k[1]), ez = fma(tau, k[5], k[2]);
+      if (KIND == 1) {
+        const T rz = k[6] * ez;
+        ok = ok && ez > T(0) && ex * ex + ey * ey - rz * rz <= T(0);
+      } else {
+        ok = ok && ex * ex + ey * ey + ez * ez - k[6] <= T(0);
+      }
+    }
+    return __all_sync(kFullMask, ok);
+  };
+  T hi = T(-1);
+  for (int m = c.NT - 1; m >= 0 && hi < T(0); --m) {
+    T sm = T(1);
+    for (int k = 0; k < m; ++k) sm *= T(c.gamma);
+    if (!inside(sm)) hi = sm;
+  }
+  T* rec = c.out_snap + (size_t)kSnapStride * w;
+  if (hi < T(0)) {
+    if (lane == 0) {
+      rec[0] = T(-1), rec[1] = T(1);
       for (int k = 2; k < kSnapStride; ++k) rec[k] = T(0);
     }
     return;
@@ -459,70 +663,32 @@ __device__ __forceinline__ void snap_walk(const WalkCtx<T>& c, const T4<T>* tab,
   const int nb = sizeof(T) == 4 ? 24 : 52;
   for (int b = 0; b < nb; ++b) {
     const T mid = T(0.5) * (lo + hi);
-    Q4<T> qx;
-    V3<T> tx;
-    ray_pose<T, SAMPLER>(q, t, dir, mid, qx, tx);
-    if (pose_in_purse<T, KIND>(tab, N, qmat(qx), tx, fx, fy, cx, cy, lane))
+    if (inside(mid))
       lo = mid;
     else
       hi = mid;
   }
-  Q4<T> qs;
-  V3<T> ts;
-  ray_pose<T, SAMPLER>(q, t, dir, lo, qs, ts);
-  q = qs, t = ts;
-  const M3<T> R = qmat(qs);
-  // active constraint: smallest margin r_i - |g_i| (ties to the lower index)
-  unsigned long long best = ~0ull;
+  const V3<D> ts{t64.x + D(lo) * v64.x, t64.y + D(lo) * v64.y, t64.z + D(lo) * v64.z};
+  t = V3<T>{T(ts.x), T(ts.y), T(ts.z)};
+  // active constraint at tau* from the affine model (margins r - |e| / P_z, or r - |g|)
+  double bm = INFINITY;
+  int bi = 0x7FFFFFFF;
   for (int i = lane; i < N; i += 32) {
-    const T4<T> mz = tab[i], ob = tab[N + i];
-    const V3<T> X = mul(R, V3<T>{mz.x, mz.y, mz.z}) + ts;
-    T m;
-    if (KIND == 1) {
-      const T u = (fx * X.x + cx * X.z) / X.z, v = (fy * X.y + cy * X.z) / X.z;
-      m = mz.w - sqrt((ob.x - u) * (ob.x - u) + (ob.y - v) * (ob.y - v));
-    } else {
-      const V3<T> e = X - V3<T>{ob.x, ob.y, ob.z};
-      m = mz.w - sqrt(dot(e, e));
-    }
-    const unsigned long long key = ((unsigned long long)orderable((float)m) << 32) | (unsigned)i;
-    best = key < best ? key : best;
+    const T* k = coef + 7 * i;
+    const T ex = fma(lo, k[3], k[0]), ey = fma(lo, k[4], k[1]), ez = fma(lo, k[5], k[2]);
+    const double m = KIND == 1 ? double(k[6]) - sqrt(double(ex) * ex + double(ey) * ey) / double(ez)
+                               : sqrt(double(k[6])) - sqrt(double(ex) * ex + double(ey) * ey + double(ez) * ez);
+    if (m < bm) bm = m, bi = i;
   }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const unsigned long long v = __shfl_xor_sync(kFullMask, best, o);
-    best = v < best ? v : best;
-  }
-  if (lane != 0) return;
-  const int j = (int)(best & 0xFFFFFFFFull);
-  const T4<T> mz = tab[j], ob = tab[N + j];
-  const V3<T> RA = mul(R, V3<T>{mz.x, mz.y, mz.z});
-  const V3<T> X = RA + ts;
-  V3<T> wv, dy;  // d|g|/d(translation of the keypoint), d|g|/d y
-  if (KIND == 1) {
-    const T Px = fx * X.x + cx * X.z, Py = fy * X.y + cy * X.z, Pz = X.z;
-    const T e0 = Px / Pz - ob.x, e1 = Py / Pz - ob.y;
-    const T nrm = sqrt(e0 * e0 + e1 * e1);
-    const T n0 = e0 / nrm, n1 = e1 / nrm;
-    const V3<T> jn{n0 / Pz, n1 / Pz, -(Px * n0 + Py * n1) / (Pz * Pz)};
-    wv = V3<T>{fx * jn.x, fy * jn.y, cx * jn.x + cy * jn.y + jn.z};
-    dy = V3<T>{-n0, -n1, T(0)};
-  } else {
-    const V3<T> e = X - V3<T>{ob.x, ob.y, ob.z};
-    const T nrm = sqrt(dot(e, e));
-    wv = (T(1) / nrm) * e;
-    dy = (T(-1) / nrm) * e;
-  }
-  const T dh = SAMPLER == 0 ? dot(cross(RA, wv), dir) : dot(wv, dir);
-  rec[0] = T(j), rec[1] = T(SAMPLER), rec[2] = dir.x, rec[3] = dir.y, rec[4] = dir.z, rec[5] = dh;
-  rec[6] = dy.x, rec[7] = dy.y, rec[8] = dy.z;
-  for (int k = 9; k < kSnapStride; ++k) rec[k] = T(0);
+  const int j = warp_argmin(bm, bi);
+  if (lane == 0) snap_record<T, KIND>(c, j, q64, ts, v64, 1, rec);
+  __syncwarp();
 }
 
 // Start of walk w: pose of seed (w mod |S0|) and velocity omega = omega0 (u + u~) (Alg. 3) or
 // v = v0 S (dir + v~) (Alg. 5), u~ / v~ the first accepted unit lattice draw of the walk's stream.
 template <typename T, int SAMPLER>
-__device__ __forceinline__ void walk_start(const WalkCtx<T>& c, int w, Q4<T>& q, V3<T>& t, V3<T>& vel) {
+__device__ __forceinline__ void walk_start(const WalkCtx<T>& c, int w, Q4<T>& q, V3<T>& t, V3<double>& vel) {
   const double* sd = c.seed_data + (size_t)(w % c.s0) * kSeedStride;
   q = Q4<T>{T(sd[0]), T(sd[1]), T(sd[2]), T(sd[3])};
   t = V3<T>{T(sd[4]), T(sd[5]), T(sd[6])};
@@ -532,13 +698,13 @@ __device__ __forceinline__ void walk_start(const WalkCtx<T>& c, int w, Q4<T>& q,
   const double nr = sqrt((double)(X * X + Y * Y + Z * Z));
   const double ux = nr > 0 ? X / nr : 0.0, uy = nr > 0 ? Y / nr : 0.0, uz = nr > 0 ? Z / nr : 0.0;
   if (SAMPLER == 0) {
-    vel = V3<T>{T(c.omega0 * (sd[7] + ux)), T(c.omega0 * (sd[8] + uy)), T(c.omega0 * (sd[9] + uz))};
+    vel = V3<double>{c.omega0 * (sd[7] + ux), c.omega0 * (sd[8] + uy), c.omega0 * (sd[9] + uz)};
   } else {
     const WalkStats* st = c.st;
     const double d0 = sd[10] + ux, d1 = sd[11] + uy, d2 = sd[12] + uz;
-    vel = V3<T>{T(c.v0 * (st->S[0] * d0 + st->S[1] * d1 + st->S[2] * d2)),
-                T(c.v0 * (st->S[3] * d0 + st->S[4] * d1 + st->S[5] * d2)),
-                T(c.v0 * (st->S[6] * d0 + st->S[7] * d1 + st->S[8] * d2))};
+    vel = V3<double>{c.v0 * (st->S[0] * d0 + st->S[1] * d1 + st->S[2] * d2),
+                     c.v0 * (st->S[3] * d0 + st->S[4] * d1 + st->S[5] * d2),
+                     c.v0 * (st->S[6] * d0 + st->S[7] * d1 + st->S[8] * d2)};
   }
 }
 
@@ -560,8 +726,23 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
   const int tsh = qtail == 0 ? 0 : qtail <= 1 ? 5 : qtail <= 2 ? 4 : qtail <= 4 ? 3 : qtail <= 8 ? 2 : qtail <= 16 ? 1 : 0;
   // ---- a3: start pose and velocity, ladder table of this walk.
   Q4<T> q;
-  V3<T> t, vel;
-  walk_start<T, SAMPLER>(c, w, q, t, vel);
+  V3<T> t;
+  V3<T> vel;
+  // FP32 walks carry their pose (and start velocity) in FP64 in the slab: lane 0 applies each move
+  // there and every lane takes the rounded pose.  Repeated FP32 pose updates would accumulate
+  // ~1e-7 rad per move, and along the viewing ray of a 2D-3D PURSE that moves the boundary the
+  // walk reaches by ~1e-6 m.
+  constexpr bool kState64 = sizeof(T) == 4;
+  {
+    V3<double> vd;
+    walk_start<T, SAMPLER>(c, w, q, t, vd);
+    vel = V3<T>{T(vd.x), T(vd.y), T(vd.z)};
+    if (kState64 && lane == 0) {
+      const double* sd = c.seed_data + (size_t)(w % c.s0) * kSeedStride;
+      for (int k = 0; k < 7; ++k) sl.S[k] = sd[k];
+      sl.S[7] = vd.x, sl.S[8] = vd.y, sl.S[9] = vd.z;
+    }
+  }
   const T rho_max = c.rho_max;
   for (int m = lane; m < NT; m += 32) {
     T sm = T(1);
@@ -802,7 +983,33 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
     moved = m0 >= 0;
     if (m0 >= 0) {
       const T4<T> pj = sl.P[sl.J[k0]];
-      if (SAMPLER == 0) {
+      if constexpr (kState64) {
+        if (lane == 0) {
+          double* S = sl.S;
+          const Q4<double> q0{S[0], S[1], S[2], S[3]};
+          Q4<double> q1;
+          if (SAMPLER == 0) {
+            const T4<T> e = sl.E[4 * m0];
+            q1 = qmul(Q4<double>{double(e.x), double(e.y), double(e.z), double(e.w)}, q0);
+            S[4] += double(pj.x), S[5] += double(pj.y), S[6] += double(pj.z);
+          } else {
+            q1 = qmul(Q4<double>{double(pj.x), double(pj.y), double(pj.z), double(pj.w)}, q0);
+            const T4<T> sv = sl.E[4 * m0];  // gamma^m0 v in T (a step of at most |v|)
+            S[4] += double(sv.x), S[5] += double(sv.y), S[6] += double(sv.z);
+          }
+          // the factor is a unit quaternion to FP32 rounding, so |q1|^2 = 1 + d with |d| ~ 1e-7 and
+          // one Newton step of 1/sqrt from 1 renormalises to ~d^2 (no FP64 square root or division)
+          const double n2 = q1.w * q1.w + q1.x * q1.x + q1.y * q1.y + q1.z * q1.z;
+          const double f = (q1.w < 0.0 ? -1.0 : 1.0) * (1.5 - 0.5 * n2);
+          S[0] = f * q1.w, S[1] = f * q1.x, S[2] = f * q1.y, S[3] = f * q1.z;
+          T* F = reinterpret_cast<T*>(S + 10);  // the rounded pose, read by every lane
+          for (int k = 0; k < 7; ++k) F[k] = T(S[k]);
+        }
+        __syncwarp();
+        const T* F = reinterpret_cast<const T*>(sl.S + 10);
+        q = Q4<T>{F[0], F[1], F[2], F[3]};
+        t = V3<T>{F[4], F[5], F[6]};
+      } else if (SAMPLER == 0) {
         const T4<T> e = sl.E[4 * m0];
         q = qnormalize(qmul(Q4<T>{e.x, e.y, e.z, e.w}, q));
         t = V3<T>{t.x + pj.x, t.y + pj.y, t.z + pj.z};
@@ -823,7 +1030,25 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
 
   // ---- optional boundary snap (for the adjoint), then a8: emit
   if constexpr (!LAM) {  // the snap takes the identity norm (the host rejects it with noise matrices)
-    if (c.out_snap) snap_walk<T, KIND, SAMPLER>(c, tab, vel, q, t, w, lane);
+    if (c.out_snap) {
+      Q4<double> q64;
+      V3<double> t64, v64;
+      if constexpr (kState64) {
+        const double* S = sl.S;
+        q64 = Q4<double>{S[0], S[1], S[2], S[3]}, t64 = V3<double>{S[4], S[5], S[6]};
+        v64 = V3<double>{S[7], S[8], S[9]};
+      } else {
+        Q4<T> q0;
+        V3<T> t0;
+        walk_start<T, SAMPLER>(c, w, q0, t0, v64);  // the start velocity in FP64
+        q64 = Q4<double>{double(q.w), double(q.x), double(q.y), double(q.z)};
+        t64 = V3<double>{double(t.x), double(t.y), double(t.z)};
+      }
+      if constexpr (SAMPLER == 0)
+        snap_rotation<T, KIND>(c, q64, t64, v64, reinterpret_cast<T*>(sl.D), q, w, lane);
+      else
+        snap_translation<T, KIND>(c, q64, t64, v64, reinterpret_cast<T*>(sl.D), t, w, lane);
+    }
   }
   if (lane == 0) {
     T* oq = c.out_q + 4 * (size_t)w;
@@ -859,8 +1084,21 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
     if (LAM) bulk_copy_g2s(smem + 128 + tbytes, a.ell, tbytes, bar);
   }
   if (!mbar_wait_bounded(bar, 0, 1 << 22)) {
-    if (threadIdx.x == 0) atomicOr(a.status, kDevErrTimeout);
+    // thread 0 gives the copies still in flight one more bounded wait, so that none lands in this
+    // CTA's shared memory after it has exited
+    if (threadIdx.x == 0) {
+      atomicOr(a.status, kDevErrTimeout);
+      mbar_wait_bounded(bar, 0, 1 << 22);
+    }
     return;
+  }
+  if (a.stall_probe) {  // PURSE_FAULT=stall: a second barrier that nothing arrives at, short poll limit
+    if (threadIdx.x == 0) mbar_init(bar + 1, 1);
+    __syncthreads();
+    if (!mbar_wait_bounded(bar + 1, 0, 1 << 10)) {
+      if (threadIdx.x == 0) atomicOr(a.status, kDevErrTimeout);
+      return;
+    }
   }
   WalkCtx<T> c;
   c.N = N, c.NP = a.n_perturb, c.K = a.n_keep, c.NT = a.n_steps, c.mc = mc, c.n_iter = a.n_iter;
@@ -873,6 +1111,7 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
   c.out_q = reinterpret_cast<T*>(a.out_q), c.out_t = reinterpret_cast<T*>(a.out_t);
   c.trace = a.trace, c.status = a.status;
   c.out_snap = reinterpret_cast<T*>(a.out_snap);
+  c.tab64 = a.table64, c.kd = &a.fx;
   const RkParam rk{a};
   unsigned long long evals = 0;
   const int nw = blockDim.x >> 5;  // warps per block (fewer than kWalkWarps for large tables)
@@ -950,8 +1189,13 @@ __device__ __forceinline__ void reg_walk_one(const WalkCtx<T>& c, const RK& rk, 
   const int N = c.N, NP = c.NP, K = c.K, NT = c.NT;
   const T r_pert = c.r_pert;
   Q4<T> q;
-  V3<T> t, vel;
-  walk_start<T, SAMPLER>(c, w, q, t, vel);
+  V3<T> t;
+  V3<T> vel;
+  {
+    V3<double> vd;
+    walk_start<T, SAMPLER>(c, w, q, t, vd);
+    vel = V3<T>{T(vd.x), T(vd.y), T(vd.z)};
+  }
   T sm = T(1);  // this lane's rung scale gamma^lane
   for (int k = 0; k < lane; ++k) sm *= T(c.gamma);
   bool moved = true;
@@ -1105,7 +1349,7 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
   unsigned char* slab = smem + 128 + reg_table_bytes<T>(N) + (size_t)warp * slab_bytes;
   T4<T>* C = reinterpret_cast<T4<T>*>(slab);
   Slab<T> sl;
-  sl.D = nullptr, sl.L = nullptr, sl.E = nullptr;
+  sl.D = nullptr, sl.L = nullptr, sl.E = nullptr, sl.S = nullptr;
   sl.P = C + N;
   sl.key = reinterpret_cast<typename KeyOf<T>::type*>(sl.P + a.n_perturb);
   sl.J = reinterpret_cast<int*>(sl.key + a.n_perturb);
@@ -1118,8 +1362,21 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
     bulk_copy_g2s(smem + 128, a.table, tbytes, bar);
   }
   if (!mbar_wait_bounded(bar, 0, 1 << 22)) {
-    if (threadIdx.x == 0) atomicOr(a.status, kDevErrTimeout);
+    // thread 0 gives the copies still in flight one more bounded wait, so that none lands in this
+    // CTA's shared memory after it has exited
+    if (threadIdx.x == 0) {
+      atomicOr(a.status, kDevErrTimeout);
+      mbar_wait_bounded(bar, 0, 1 << 22);
+    }
     return;
+  }
+  if (a.stall_probe) {  // PURSE_FAULT=stall: a second barrier that nothing arrives at, short poll limit
+    if (threadIdx.x == 0) mbar_init(bar + 1, 1);
+    __syncthreads();
+    if (!mbar_wait_bounded(bar + 1, 0, 1 << 10)) {
+      if (threadIdx.x == 0) atomicOr(a.status, kDevErrTimeout);
+      return;
+    }
   }
   WalkCtx<T> c;
   c.N = N, c.NP = a.n_perturb, c.K = a.n_keep, c.NT = a.n_steps, c.mc = 1, c.n_iter = a.n_iter;
@@ -1132,6 +1389,7 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
   c.out_q = reinterpret_cast<T*>(a.out_q), c.out_t = reinterpret_cast<T*>(a.out_t);
   c.trace = a.trace, c.status = a.status;
   c.out_snap = nullptr;
+  c.tab64 = nullptr, c.kd = nullptr;
   const RkParam rk{a};
   unsigned long long evals = 0;
   const int nw = blockDim.x >> 5;
@@ -1202,6 +1460,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2)
         c.st = b.stats + p, c.seed_data = b.seed_data + (size_t)p * kSeedStride, c.s0 = 1;
         c.key0 = (uint32_t)key, c.key1 = (uint32_t)(key >> 32);
         c.trace = nullptr, c.status = b.status;
+        c.tab64 = b.table64 + 4 * (size_t)in.table_off, c.kd = &b.info[p].fx;
         sl = carve<float>(slab_base, c.N, c.NP, c.NT);
         cur = p;
         __syncwarp();

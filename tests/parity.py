@@ -21,6 +21,8 @@ from __future__ import annotations
 import numpy as np
 
 from oracle import closure, philox
+from oracle import megb as megb_o
+from oracle import so3 as so3_o
 from oracle import purse as op
 from oracle.purse import KIND_2D3D, KIND_REG
 
@@ -250,3 +252,42 @@ def rot_angle(qa, qb):
 def lattice_points(seed, phase, j, i, w, unit=False):
     pts, used = philox.ball_points(seed, phase, j, i, w, unit=unit)
     return pts, used
+
+
+def rot_keys(C, qs):
+    d = so3_o.quat_mul(so3_o.quat_conj(C)[None], qs)
+    return (d[:, 1:] ** 2).sum(1)
+
+
+def check_rotation(q64, res, f, precision):
+    """GGD protocol for the rotation ball: every farthest choice f_k of the GPU is within the
+    rounding band of the FP64 maximum key from the replayed centre C_{k-1}; the replayed centre
+    and its radius match the GPU's result.  Returns (C, D)."""
+    K = len(f)
+    qs = megb_o.canonical(q64)
+    Cs = megb_o.megb_rotation_replay(qs, f)
+    for k in range(1, K + 1):
+        keys = rot_keys(Cs[k - 1], qs)
+        band = 64 * EPS[precision] * (np.sqrt(keys.max()) + EPS[precision])
+        assert keys[f[k - 1]] >= keys.max() - band, (k, keys[f[k - 1]], keys.max())
+    C = Cs[-1]
+    assert rot_angle(res[:4], C) <= 1e-9
+    D = megb_o.rotation_distances(C, qs).max()
+    assert abs(res[7] - D) <= 1e-5 * D + 1e-12, (res[7], D)
+    return C, D
+
+
+def check_translation(t64, res, f, precision):
+    """The same protocol for the translation ball (Badoiu-Clarkson steps).  Returns (c, d)."""
+    K = len(f)
+    cs = megb_o.megb_translation_replay(t64, f)
+    scale = np.abs(t64).max()
+    for k in range(1, K + 1):
+        keys = ((t64 - cs[k - 1]) ** 2).sum(1)
+        band = 16 * EPS[precision] * scale * (np.sqrt(keys.max()) + EPS[precision] * scale)
+        assert keys[f[k - 1]] >= keys.max() - band
+    c = cs[-1]
+    assert np.abs(res[4:7] - c).max() <= 1e-12 * (1 + scale)
+    d = np.sqrt(((t64 - c) ** 2).sum(1)).max()
+    assert abs(res[8] - d) <= 1e-5 * d + 1e-12
+    return c, d

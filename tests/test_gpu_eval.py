@@ -53,7 +53,7 @@ def test_eval_matches_oracle(kind, n, precision):
     assert np.array_equal(finite, np.isfinite(m_gpu))
     assert np.all(m_gpu[~finite] == -np.inf)
     band = constraint_bands(p, Rq, tq, precision)
-    assert np.all(np.abs(m_gpu - m_ref)[finite] <= band[finite])
+    assert np.all(np.abs(m_gpu[finite] - m_ref[finite]) <= band[finite])
     # active constraint: unique where the two smallest margins are separated by more than the bands
     srt = np.sort(np.where(finite, m_ref, -1e300), axis=1)
     clear = (srt[:, 1] - srt[:, 0]) > 2 * band.max(axis=1)
@@ -65,6 +65,16 @@ def test_eval_matches_oracle(kind, n, precision):
     rows = np.arange(npose)
     ok = clear & np.isfinite(m_ref[rows, a_ref])
     g_ref = G[rows, a_ref][ok]
-    tol = 1e-9 if precision == 1 else 2e-3
-    scale = np.abs(g_ref).max(axis=1, keepdims=True)
-    assert np.all(np.abs(g_gpu[ok] - g_ref) <= tol * scale)
+    # Bound from the arithmetic: the gradient is (R a_j x w, w) with w the unit residual direction
+    # (2D-3D: pulled back through the projection and K).  The residual g_j is a difference of
+    # terms of size mag_j, so its rounding error is within the band's 8 eps mag_j, and the unit
+    # direction moves by at most twice that over |g_j|; the remaining products add a few eps.
+    eps = 2.0 ** -23 if precision == 0 else 2.0 ** -52
+    a_ok = a_ref[ok]
+    r_act = p.radii[a_ok]
+    e_norm = r_act - m_ref[rows, a_ref][ok]                     # |g_j| of the active constraint
+    rounding = band[rows, a_ref][ok] - 1e-6 * r_act             # 8 eps mag_j
+    rel = 2.0 * rounding / e_norm + 64 * eps
+    scale = np.abs(g_ref).max(axis=1)
+    err = np.abs(g_gpu[ok] - g_ref).max(axis=1)
+    assert np.all(err <= rel * scale), (err / scale / rel).max()

@@ -10,45 +10,9 @@ from paper_2403_09990_gb300 import purse as P
 from paper_2403_09990_gb300 import synthetic as syn
 from tests import parity
 from tests.gpu_helpers import megb
+from tests.parity import EPS, check_rotation, check_translation, rot_keys  # noqa: F401
 
 pytestmark = pytest.mark.gpu
-
-EPS = {0: 2.0 ** -23, 1: 2.0 ** -52}
-
-
-def rot_keys(C, qs):
-    d = so3.quat_mul(so3.quat_conj(C)[None], qs)
-    return (d[:, 1:] ** 2).sum(1)
-
-
-def check_rotation(q64, res, f, precision):
-    K = len(f)
-    qs = om.canonical(q64)
-    Cs = om.megb_rotation_replay(qs, f)
-    for k in range(1, K + 1):
-        keys = rot_keys(Cs[k - 1], qs)
-        band = 64 * EPS[precision] * (np.sqrt(keys.max()) + EPS[precision])
-        assert keys[f[k - 1]] >= keys.max() - band, (k, keys[f[k - 1]], keys.max())
-    C = Cs[-1]
-    assert parity.rot_angle(res[:4], C) <= 1e-9
-    D = om.rotation_distances(C, qs).max()
-    assert abs(res[7] - D) <= 1e-5 * D + 1e-12, (res[7], D)
-    return C, D
-
-
-def check_translation(t64, res, f, precision):
-    K = len(f)
-    cs = om.megb_translation_replay(t64, f)
-    scale = np.abs(t64).max()
-    for k in range(1, K + 1):
-        keys = ((t64 - cs[k - 1]) ** 2).sum(1)
-        band = 16 * EPS[precision] * scale * (np.sqrt(keys.max()) + EPS[precision] * scale)
-        assert keys[f[k - 1]] >= keys.max() - band
-    c = cs[-1]
-    assert np.abs(res[4:7] - c).max() <= 1e-12 * (1 + scale)
-    d = np.sqrt(((t64 - c) ** 2).sum(1)).max()
-    assert abs(res[8] - d) <= 1e-5 * d + 1e-12
-    return c, d
 
 
 def cluster(n, seed, spread=(0.02, 0.05, 0.1)):

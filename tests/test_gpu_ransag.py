@@ -1,9 +1,10 @@
 """GPU RANSAG (Step I) against the oracle: same accepted trials and candidates, same poses.
 
-3D-3D (Arun/Horn fit) and 2D-3D (P3P).  For 2D-3D the comparison stops at the first
-trial whose outcome is fragile in FP64 -- a quartic with a near-double root (two real roots,
-or a complex pair, within 1e-6), or a candidate within 1e-9 r of the PURSE boundary -- since
-either side may then legitimately decide otherwise; such trials are rare and counted.  The
+3D-3D (Arun/Horn fit) and 2D-3D (P3P).  For 2D-3D the comparison skips the trials whose
+outcome is fragile in FP64 -- a quartic with a near-double root (two real roots, or a complex
+pair, within 1e-6), or a candidate within 1e-9 r of the PURSE boundary -- since either side may
+then legitimately decide otherwise; such trials are rare and counted, and every other accepted
+seed (at least 90 % of them) is compared.  The
 P3P poses agree to rounding in the bulk and to 1e-6 where the view is ill-conditioned."""
 import numpy as np
 import pytest
@@ -84,15 +85,46 @@ def test_ransag_2d3d_matches_oracle(n, max_seeds, trials):
     frag = fragile_trials(p, 11, last)
     if not frag:
         assert got == len(ref)
-        m = got
-    else:  # compare the seeds of the trials before the first fragile one
-        m = int((acc[:, 0] < frag[0]).sum())
-        assert got >= m
-    if m:
+    pairs = align_seeds(g, ref, acc, frag)
+    # every accepted seed of a trial decided outside the FP64 band is compared; the fragile
+    # trials are rare, so at least 90 % of the oracle's seeds are
+    robust = int(sum(1 for k in range(len(ref)) if acc[k, 0] not in set(frag)))
+    assert len(pairs) >= min(robust, max(1, int(0.9 * len(ref)))) if len(ref) else len(pairs) == 0, \
+        (len(pairs), robust, len(ref))
+    d = np.zeros(0)
+    if pairs:
+        gi, ri = np.array(pairs).T
         # P3P loses digits near degenerate views (the pose moves like 1/A'(v) at a root v of the
         # quartic), so identical FP64 arithmetic on the two sides agrees to rounding in the bulk and
         # to 1e-6 at worst; a different candidate would differ by the noise radius scale (> 1e-3)
-        d = np.abs(g[:m] - ref[:m]).max(axis=1)
+        d = np.abs(g[gi] - ref[ri]).max(axis=1)
         assert np.median(d) <= 1e-10 and d.max() <= 1e-6, (np.median(d), d.max())
-    print(f"n {n}: {got} seeds from {trials} trials, {len(frag)} fragile trials, "
-          f"max |pose difference| {d.max() if m else 0:.2e}")
+    print(f"n {n}: {got} seeds from {trials} trials, {len(frag)} fragile trials, {len(pairs)} of "
+          f"{len(ref)} seeds compared, max |pose difference| {d.max() if len(d) else 0:.2e}")
+
+
+def align_seeds(g, ref, acc, frag):
+    """(GPU index, oracle index) pairs of the seeds of the trials decided outside the FP64 band.
+
+    Both sides list seeds in (trial, ascending root) order.  The oracle's seeds of fragile trials
+    are skipped; on the GPU side up to four candidates per fragile trial passed since the last
+    compared seed may be skipped (a fragile trial may yield other candidates there).  Any other
+    difference in the sequence fails."""
+    frag = np.asarray(sorted(frag), dtype=np.int64)
+    fset = set(frag.tolist())
+    pairs = []
+    i, last_trial = 0, -1
+    for j in range(len(ref)):
+        tr = int(acc[j, 0])
+        if tr in fset:
+            continue
+        if i >= len(g):
+            break
+        skips = 4 * int(((frag > last_trial) & (frag < tr)).sum())
+        k = i
+        while k < len(g) and k - i <= skips and np.abs(g[k] - ref[j]).max() > 1e-6:
+            k += 1
+        assert k < len(g) and k - i <= skips, f"GPU seed sequence differs at oracle seed {j} (trial {tr})"
+        pairs.append((k, j))
+        i, last_trial = k + 1, tr
+    return pairs

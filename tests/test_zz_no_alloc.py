@@ -5,8 +5,9 @@ reserve all memory at start-up (cudaMalloc / cudaFree may synchronise the
 device and take unbounded time), and hosts whose device memory belongs to
 another allocator.  megb_solve_noalloc keeps its scratch in a static 64 KiB
 device array instead; here it is checked, through the C ABI, against
-megb_solve on two calls in a row (the second call finds the first call's
-leftovers in the shared array).
+megb_solve on calls in a row (each call finds the previous call's leftovers in
+the shared array), up to 2^20 samples, where its grid is smaller than
+megb_solve's.
 """
 import numpy as np
 import pytest
@@ -61,6 +62,12 @@ def test_noalloc_matches_megb_solve_on_two_calls_in_a_row():
         ref, got, f_ref, f_got = _both(h.h, 1, 57, q2, 77777, None, 0)
         _assert_same(ref, got, f_ref, f_got, 77777, 0, 57)
         assert np.all(got[4:7] == 0) and got[8] == 0
+        # call 3: 2^20 samples (the size of the single-PURSE workload), where the grid of this
+        # entry point (at most 512 blocks) is smaller than megb_solve's (4 x SMs) and the
+        # grid-stride loops take several samples per thread
+        q3, t3 = _cluster(1 << 20, 3, 0)
+        ref, got, f_ref, f_got = _both(h.h, 0, 200, q3, 1 << 20, t3, 1 << 20)
+        _assert_same(ref, got, f_ref, f_got, 1 << 20, 1 << 20, 200)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
@@ -69,4 +76,5 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert L.megb_solve_noalloc(0, 4097, buf, 10, buf, 10, buf, None, None) == 1
     assert b"4096" in L.purse_last_error()
     assert L.megb_solve_noalloc(0, 0, buf, 10, buf, 10, buf, None, None) == 1
+    assert L.megb_solve_noalloc(0, 10, buf, 2**31 - 2**20, buf, 10, buf, None, None) == 1
     assert L.megb_solve_noalloc(2, 10, buf, 10, buf, 10, buf, None, None) == 1
