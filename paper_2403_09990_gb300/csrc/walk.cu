@@ -125,7 +125,7 @@ __device__ __forceinline__ void sort8_desc(K (&k)[8]) {
 //              with noise matrices U_i in slots 8-13.
 //  P[j]        perturbation j: translation offset (dS_R) or unit quaternion (dS_t)
 //  E[4m..]     ladder rung m: quaternion and rows of (K) E_m (dS_R) or s_m v (dS_t)
-//  S[0..9]     FP64 walk state of FP32 walks: q* (4), t* (3), start velocity (3); then q*, t* rounded
+//  S           walk state of FP32 walks: q*, t* as double-float pairs, start velocity in FP64
 template <typename T>
 struct Slab {
   P2<T>* D;
@@ -139,7 +139,9 @@ struct Slab {
 
 __host__ __device__ inline int ladder_pairs(int n) { return (n + 1) / 2; }
 
-constexpr int kStateDoubles = 14;  // Slab::S: 10 doubles, then the rounded pose as 7 floats
+// Slab::S of FP32 walks: the pose as double-float pairs (floats 0-3 q* hi, 4-7 q* lo, 8-10 t* hi,
+// 11-13 t* lo), then the start velocity in FP64 (doubles 8-10).
+constexpr int kStateDoubles = 11;
 
 template <typename T>
 __host__ __device__ inline size_t walk_slab_bytes2(int n, int n_perturb, int n_steps, bool lam = false) {
@@ -685,6 +687,58 @@ __device__ __forceinline__ void snap_translation(const WalkCtx<T>& c, const Q4<d
   __syncwarp();
 }
 
+// Double-float arithmetic (a value carried as an unevaluated sum hi + lo of two floats, ~48
+// significant bits) from the error-free transformations of Knuth (two_sum) and of the fused
+// multiply-add (two_prod); the file is compiled without contraction, so + and * round as written.
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return DF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DF quick_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+  const float p = a * b;
+  return DF{p, fmaf(a, b, -p)};
+}
+// a0 b0 + a1 b1 + a2 b2 + a3 b3 for float a and double-float b (the lo parts of b enter once).
+__device__ __forceinline__ DF df_dot4(float a0, DF b0, float a1, DF b1, float a2, DF b2, float a3, DF b3) {
+  const DF p0 = two_prod(a0, b0.h), p1 = two_prod(a1, b1.h), p2 = two_prod(a2, b2.h), p3 = two_prod(a3, b3.h);
+  const DF s1 = two_sum(p0.h, p1.h), s2 = two_sum(s1.h, p2.h), s3 = two_sum(s2.h, p3.h);
+  const float lo = ((s1.l + s2.l) + (s3.l + p0.l)) + ((p1.l + p2.l) + p3.l) +
+                   (a0 * b0.l + a1 * b1.l + a2 * b2.l + a3 * b3.l);
+  return quick_two_sum(s3.h, lo);
+}
+
+// One move of an FP32 walk's pose, p (x) q and t + dt, in double-float on lane 0.  p is a unit
+// quaternion to FP32 rounding, so |p (x) q|^2 = 1 + d with |d| ~ 1e-7, and q (1 - d/2) renormalises
+// to ~d^2; the sign keeps w >= 0.  F: floats of Slab::S.
+__device__ __forceinline__ void df_move(float* F, float pw, float px, float py, float pz, float dx, float dy,
+                                        float dz) {
+  const DF qw{F[0], F[4]}, qx{F[1], F[5]}, qy{F[2], F[6]}, qz{F[3], F[7]};
+  DF r[4] = {df_dot4(pw, qw, -px, qx, -py, qy, -pz, qz), df_dot4(pw, qx, px, qw, py, qz, -pz, qy),
+             df_dot4(pw, qy, py, qw, pz, qx, -px, qz), df_dot4(pw, qz, pz, qw, px, qy, -py, qx)};
+  const DF n2 = df_dot4(r[0].h, r[0], r[1].h, r[1], r[2].h, r[2], r[3].h, r[3]);
+  const float d = (n2.h - 1.0f) + (n2.l + (r[0].h * r[0].l + r[1].h * r[1].l + r[2].h * r[2].l + r[3].h * r[3].l));
+  const float sg = r[0].h < 0.0f ? -1.0f : 1.0f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const DF v = quick_two_sum(r[k].h, r[k].l - 0.5f * d * r[k].h);
+    F[k] = sg * v.h, F[4 + k] = sg * v.l;
+  }
+  const float dt[3] = {dx, dy, dz};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const DF s = two_sum(F[8 + k], dt[k]);
+    const DF v = quick_two_sum(s.h, s.l + F[11 + k]);
+    F[8 + k] = v.h, F[11 + k] = v.l;
+  }
+}
+
 // Start of walk w: pose of seed (w mod |S0|) and velocity omega = omega0 (u + u~) (Alg. 3) or
 // v = v0 S (dir + v~) (Alg. 5), u~ / v~ the first accepted unit lattice draw of the walk's stream.
 template <typename T, int SAMPLER>
@@ -728,10 +782,11 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
   Q4<T> q;
   V3<T> t;
   V3<T> vel;
-  // FP32 walks carry their pose (and start velocity) in FP64 in the slab: lane 0 applies each move
-  // there and every lane takes the rounded pose.  Repeated FP32 pose updates would accumulate
-  // ~1e-7 rad per move, and along the viewing ray of a 2D-3D PURSE that moves the boundary the
-  // walk reaches by ~1e-6 m.
+  // FP32 walks carry their pose in double-float pairs in the slab (and the start velocity in FP64):
+  // lane 0 applies each move there and every lane takes the hi parts.  Repeated FP32 pose updates
+  // would accumulate ~1e-7 rad per move, and along the viewing ray of a 2D-3D PURSE that moves the
+  // boundary the walk reaches by ~1e-6 m.  (FP64 arithmetic would do, but one FP64 instruction of
+  // one lane occupies the FP64 unit of this part far longer than the ~240 FP32 operations of a move.)
   constexpr bool kState64 = sizeof(T) == 4;
   {
     V3<double> vd;
@@ -739,8 +794,10 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
     vel = V3<T>{T(vd.x), T(vd.y), T(vd.z)};
     if (kState64 && lane == 0) {
       const double* sd = c.seed_data + (size_t)(w % c.s0) * kSeedStride;
-      for (int k = 0; k < 7; ++k) sl.S[k] = sd[k];
-      sl.S[7] = vd.x, sl.S[8] = vd.y, sl.S[9] = vd.z;
+      float* F = reinterpret_cast<float*>(sl.S);
+      for (int k = 0; k < 4; ++k) F[k] = float(sd[k]), F[4 + k] = float(sd[k] - double(F[k]));
+      for (int k = 0; k < 3; ++k) F[8 + k] = float(sd[4 + k]), F[11 + k] = float(sd[4 + k] - double(F[8 + k]));
+      sl.S[8] = vd.x, sl.S[9] = vd.y, sl.S[10] = vd.z;
     }
   }
   const T rho_max = c.rho_max;
@@ -984,31 +1041,19 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
     if (m0 >= 0) {
       const T4<T> pj = sl.P[sl.J[k0]];
       if constexpr (kState64) {
+        float* F = reinterpret_cast<float*>(sl.S);
         if (lane == 0) {
-          double* S = sl.S;
-          const Q4<double> q0{S[0], S[1], S[2], S[3]};
-          Q4<double> q1;
           if (SAMPLER == 0) {
-            const T4<T> e = sl.E[4 * m0];
-            q1 = qmul(Q4<double>{double(e.x), double(e.y), double(e.z), double(e.w)}, q0);
-            S[4] += double(pj.x), S[5] += double(pj.y), S[6] += double(pj.z);
+            const T4<T> e = sl.E[4 * m0];  // (w, x, y, z) of E_m0
+            df_move(F, e.x, e.y, e.z, e.w, pj.x, pj.y, pj.z);
           } else {
-            q1 = qmul(Q4<double>{double(pj.x), double(pj.y), double(pj.z), double(pj.w)}, q0);
-            const T4<T> sv = sl.E[4 * m0];  // gamma^m0 v in T (a step of at most |v|)
-            S[4] += double(sv.x), S[5] += double(sv.y), S[6] += double(sv.z);
+            const T4<T> sv = sl.E[4 * m0];  // gamma^m0 v
+            df_move(F, pj.x, pj.y, pj.z, pj.w, sv.x, sv.y, sv.z);
           }
-          // the factor is a unit quaternion to FP32 rounding, so |q1|^2 = 1 + d with |d| ~ 1e-7 and
-          // one Newton step of 1/sqrt from 1 renormalises to ~d^2 (no FP64 square root or division)
-          const double n2 = q1.w * q1.w + q1.x * q1.x + q1.y * q1.y + q1.z * q1.z;
-          const double f = (q1.w < 0.0 ? -1.0 : 1.0) * (1.5 - 0.5 * n2);
-          S[0] = f * q1.w, S[1] = f * q1.x, S[2] = f * q1.y, S[3] = f * q1.z;
-          T* F = reinterpret_cast<T*>(S + 10);  // the rounded pose, read by every lane
-          for (int k = 0; k < 7; ++k) F[k] = T(S[k]);
         }
         __syncwarp();
-        const T* F = reinterpret_cast<const T*>(sl.S + 10);
         q = Q4<T>{F[0], F[1], F[2], F[3]};
-        t = V3<T>{F[4], F[5], F[6]};
+        t = V3<T>{F[8], F[9], F[10]};
       } else if (SAMPLER == 0) {
         const T4<T> e = sl.E[4 * m0];
         q = qnormalize(qmul(Q4<T>{e.x, e.y, e.z, e.w}, q));
@@ -1034,9 +1079,11 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
       Q4<double> q64;
       V3<double> t64, v64;
       if constexpr (kState64) {
-        const double* S = sl.S;
-        q64 = Q4<double>{S[0], S[1], S[2], S[3]}, t64 = V3<double>{S[4], S[5], S[6]};
-        v64 = V3<double>{S[7], S[8], S[9]};
+        const float* F = reinterpret_cast<const float*>(sl.S);
+        q64 = qnormalize(Q4<double>{double(F[0]) + F[4], double(F[1]) + F[5], double(F[2]) + F[6],
+                                    double(F[3]) + F[7]});
+        t64 = V3<double>{double(F[8]) + F[11], double(F[9]) + F[12], double(F[10]) + F[13]};
+        v64 = V3<double>{sl.S[8], sl.S[9], sl.S[10]};
       } else {
         Q4<T> q0;
         V3<T> t0;
