@@ -51,6 +51,13 @@ SM_COUNT_NOMINAL = 152
 # --no-plain --no-grad (one pass).  Taken on the current kernels; a kernel change needs a new capture.
 WALK_DRAM_BYTES = {"R": 425.98e3 + 256, "t": 959.23e3}
 FP32_LANES_PER_SM = 128
+# C1: 3D-3D PURSE (N = 8, seed 0) in FP64, |S0| = 2048 RANSAG seeds, N_W = 2 walks each (4096 samples of the
+# dS_R sampler, N_I = 5, 3DMatch preset), both balls with K = 200; flops per 3D-3D evaluation: 26 for in_purse
+# (R a + t - b, the squared norm and the test) and 28 for the margin of eq. 11
+C1_N, C1_SEEDS, C1_NW, C1_ITERS, C1_K = 8, 2048, 2, 5, 200
+FLOPS_DIST_3D, FLOPS_INPURSE_3D = 28, 26
+# FP64 FMA results per clock per SM of this part (GB300: 1.25 TFLOP/s over 152 SMs at about 2 GHz)
+FP64_FMA_PER_SM = 2
 
 
 def workload_config():
@@ -307,6 +314,8 @@ def run_gpu(args, rank, world):
     }
     out["megb_exact"] = run_exact(hR, qR, tT, res, dev)
     out["ransag"] = run_ransag(dev)
+    if not args.no_c1:
+        out["c1"] = run_c1(dev, sms, clock_mhz, with_oracle=rank == 0 and not args.no_cpu_baseline)
     if not args.no_plain:
         out["plain_gpu"] = run_plain(args, p, dev, seeds, value / world, t_step)
     if rank == 0 and not args.no_e2e:
@@ -352,6 +361,79 @@ def run_ransag(dev):
                 n = 0
             dt = time.perf_counter() - t0
         out[name] = {"trials": trials, "ms": dt * 1e3, "trials_per_s": trials / dt, "seeds": n}
+    return out
+
+
+def run_c1(dev, sms, clock_mhz, with_oracle):
+    """Config C1 end to end in FP64 on the GPU: RANSAG to |S0| = 2048 seeds (wall clock around its
+    synchronising call), 4096 dS_R walks of N_I = 5 and both balls with K = 200 (CUDA events), per solve;
+    the walk kernel's executed evaluations (28 / 26 FLOP) against the FP64 FMA rate of the part; beside it
+    the oracle on the same workload (one host core, FP64) with its balls."""
+    import torch
+    import paper_2403_09990_gb300.purse as P
+    from paper_2403_09990_gb300 import synthetic as syn
+    stream = torch.cuda.current_stream()
+    p = syn.purse_3d3d(C1_N, 0)
+    prm = P.make_params(n_iter=C1_ITERS, n_perturb=N_PERTURB, n_keep=N_KEEP, n_steps=N_STEPS, omega0=0.5, v0=0.0,
+                        gamma=0.5, rot_perturb=0.0, trans_perturb=0.1, perturb_units=0, sampler=0, precision=1)
+    S = C1_SEEDS * C1_NW
+    seeds = torch.empty((C1_SEEDS, 12), dtype=torch.float64, device=dev)
+    q = torch.empty((S, 4), dtype=torch.float64, device=dev)
+    t = torch.empty((S, 3), dtype=torch.float64, device=dev)
+    res = torch.empty(9, dtype=torch.float64, device=dev)
+    rows = []
+    with P.Purse(p) as h:
+        for r in range(4):
+            t0 = time.perf_counter()
+            s0 = P.purse_ransag(h.h, 1, 1 << 20, C1_SEEDS, seeds)
+            ransag_ms = (time.perf_counter() - t0) * 1e3
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            P.purse_sample(h.h, prm, 3, seeds, s0, S, q, t, None, stream)
+            e[1].record(stream)
+            P.megb_solve(h.h, 1, C1_K, q, S, t, S, res, None, stream)
+            e[2].record(stream)
+            ev = P.purse_last_evals(h.h, stream)
+            P.purse_sync(h.h, stream)
+            if r:
+                rows.append((ransag_ms, e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), ev))
+        x = res.cpu().numpy()
+    ransag_ms = statistics.median(r[0] for r in rows)
+    walk_ms = statistics.median(r[1] for r in rows)
+    ball_ms = statistics.median(r[2] for r in rows)
+    ev = rows[-1][3]
+    dist = S * C1_ITERS * N_PERTURB * C1_N
+    flops = dist * FLOPS_DIST_3D + (ev - dist) * FLOPS_INPURSE_3D
+    peak = sms * FP64_FMA_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+    achieved = flops / (walk_ms / 1e3) / 1e12
+    solve_ms = ransag_ms + walk_ms + ball_ms
+    alg = S * C1_ITERS * (N_PERTURB + N_KEEP * N_STEPS) * C1_N
+    out = {"workload": "3D-3D PURSE N=8 (seed 0), FP64: RANSAG to 2048 seeds, 4096 dS_R walks (N_I=5, N_P=150, "
+                       "N_P*=10, N_T=15), rotation + translation MEGB, 200 GGD iterations",
+           "ms_per_solve": solve_ms, "solves_per_s": 1e3 / solve_ms,
+           "breakdown_ms": {"ransag": ransag_ms, "walk": walk_ms, "megb": ball_ms},
+           "evals_per_s": alg / (walk_ms / 1e3), "evals_executed_per_s": ev / (walk_ms / 1e3),
+           "D_hat": float(x[7]), "d_hat": float(x[8]),
+           "roofline": {"bound": "fp64 alu", "kernel": "walk_kernel<double, 3D-3D, dS_R>", "achieved": achieved,
+                        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                        "flops_per_eval": {"dist": FLOPS_DIST_3D, "in_purse": FLOPS_INPURSE_3D},
+                        "peak_source": f"{sms} SMs x {FP64_FMA_PER_SM} FP64 FMA x 2 x {clock_mhz:.0f} MHz"}}
+    if with_oracle:
+        from oracle import closure, megb as om, ransag
+        t0 = time.perf_counter()
+        seeds_o, _ = ransag.ransag_3d3d(p, 1, 1 << 20, C1_SEEDS)
+        t1 = time.perf_counter()
+        R, tt = closure.sample_rotation_boundary(p, seeds_o, closure.preset_3d3d(n_iter=C1_ITERS), 3, np.arange(S))
+        t2 = time.perf_counter()
+        qo, to = closure.as_samples(R, tt)
+        _, Do, _ = om.megb_rotation(qo, C1_K)
+        _, do, _ = om.megb_translation(to, C1_K)
+        t3 = time.perf_counter()
+        out["cpu_baseline"] = {"ms_per_solve": (t3 - t0) * 1e3, "breakdown_ms": {"ransag": (t1 - t0) * 1e3,
+                               "walk": (t2 - t1) * 1e3, "megb": (t3 - t2) * 1e3},
+                               "evals_per_s": alg / (t2 - t1), "cores": 1, "kind": "oracle",
+                               "sample": "the whole C1 solve", "D_hat": float(Do), "d_hat": float(do)}
+        out["gpu_over_oracle"] = (t3 - t0) * 1e3 / solve_ms
     return out
 
 
@@ -936,6 +1018,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-operation comparator")
     ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--no-c1", action="store_true", help="skip the FP64 3D-3D configuration (C1)")
     ap.add_argument("--no-grad", action="store_true", help="skip the batched differentiation measurement")
     ap.add_argument("--sweep", action="store_true", help="precision / scale sweep instead of the bench step")
     ap.add_argument("--sweep-parts", default="precision,scale,dist,next", help="which parts of the sweep to run")

@@ -22,8 +22,18 @@ struct MegbState {
   double C[4];
   double c[4];
   unsigned int counter[2];
-  int fstar[2];  // farthest sample from the final centre (rotation, translation)
+  int fstar[2];       // farthest sample from the final centre (rotation, translation)
+  unsigned int gen[2];  // iterations published by the persistent kernel
 };
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 struct Part {
   double key;
@@ -53,6 +63,7 @@ __global__ void megb_init(const T* q, int nq, const T* t, int nt, MegbState* s) 
   }
   s->c[3] = 0.0;
   s->counter[0] = s->counter[1] = 0;
+  s->gen[0] = s->gen[1] = 0;
 }
 
 // Squared sine of half the geodesic distance between centre (cw, cv) and q.
@@ -69,26 +80,34 @@ __device__ __forceinline__ T rot_key(T cw, T cx, T cy, T cz, const T* qs) {
 // Relative rotation d = C* (x) q_f on the short path (w >= 0), its sine norm and angle.
 struct RelRot {
   Q4<double> d;
-  double sn, th;
+  double sn, inv_sn, th;
 };
 __device__ __forceinline__ RelRot rel_rot(const Q4<double>& c, const Q4<double>& qf) {
   RelRot r;
   r.d = qmul(Q4<double>{c.w, -c.x, -c.y, -c.z}, qf);
   if (r.d.w < 0) r.d = Q4<double>{-r.d.w, -r.d.x, -r.d.y, -r.d.z};
-  r.sn = sqrt(r.d.x * r.d.x + r.d.y * r.d.y + r.d.z * r.d.z);
+  const double s2 = r.d.x * r.d.x + r.d.y * r.d.y + r.d.z * r.d.z;
+  r.inv_sn = s2 > 0.0 ? rsqrt(s2) : 0.0;
+  r.sn = s2 * r.inv_sn;
   r.th = 2.0 * atan2(r.sn, r.d.w);
   return r;
 }
 
-// GGD step k on SO(3): SLERP(C, q_f, 1/k) = C Exp(Log(C^T R_f) / k).
+// GGD step k on SO(3): SLERP(C, q_f, 1/k) = C Exp(Log(C^T R_f) / k).  Written for few FP64
+// instructions (each costs the same whatever the number of active lanes): one sincos, products by
+// reciprocals, and no renormalisation -- both factors are unit quaternions to FP64 rounding, so the
+// norm drifts by ~1e-16 per step; only the sign is kept (w >= 0).
 __device__ __forceinline__ Q4<double> slerp_step(const Q4<double>& c, const RelRot& r, int k) {
   Q4<double> step{1.0, 0.0, 0.0, 0.0};
   if (r.sn > 0.0) {
-    const double h = 0.5 * r.th / k;
-    const double sh = sin(h) / r.sn;
-    step = Q4<double>{cos(h), sh * r.d.x, sh * r.d.y, sh * r.d.z};
+    double sh, ch;
+    sincos(r.th * (0.5 / k), &sh, &ch);
+    sh *= r.inv_sn;
+    step = Q4<double>{ch, sh * r.d.x, sh * r.d.y, sh * r.d.z};
   }
-  return qnormalize(qmul(c, step));
+  Q4<double> o = qmul(c, step);
+  if (o.w < 0.0) o = Q4<double>{-o.w, -o.x, -o.y, -o.z};
+  return o;
 }
 
 // Key of sample i: squared sine of half the angle to the centre (rotation) or squared distance.
@@ -114,29 +133,37 @@ __device__ __forceinline__ T sample_key(const T* __restrict__ x, int i, bool vec
   return dx * dx + dy * dy + dz * dz;
 }
 
-// MODE 0: rotation ball, MODE 1: translation ball.  k >= 1: GGD step k; k == 0: final radius.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kMegbThreads)
-    ggd_step(const T* __restrict__ x, int n, MegbState* s, Part* parts, int k, int32_t* f_int, int32_t* f_out,
-             double* result) {
-  __shared__ double wkey[kMegbThreads / 32];
-  __shared__ int widx[kMegbThreads / 32];
-  __shared__ bool last;
+// One GGD iteration of a ball over this block's slice of the samples.  MODE 0: rotation ball, MODE 1:
+// translation ball.  k >= 1: GGD step k; k == 0: final radius.  Every block reduces its slice to a
+// (key, index) partial; the last block to take a ticket reduces the partials and takes the step in
+// FP64 (its thread 0 writes the state).  Returns true in the block that took the step.  COHERENT:
+// the centre is read from L2 (the persistent kernel reads a centre written by another block in the
+// same launch).
+template <typename T, int MODE, bool COHERENT>
+__device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbState* s, Part* parts, int k,
+                                         int32_t* f_int, int32_t* f_out, double* result, double* wkey, int* widx,
+                                         bool* last, int bid, int nb) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   T c0, c1, c2, c3;
   if (MODE == 0) {
-    c0 = T(s->C[0]), c1 = T(s->C[1]), c2 = T(s->C[2]), c3 = T(s->C[3]);
+    if (COHERENT)
+      c0 = T(__ldcg(&s->C[0])), c1 = T(__ldcg(&s->C[1])), c2 = T(__ldcg(&s->C[2])), c3 = T(__ldcg(&s->C[3]));
+    else
+      c0 = T(s->C[0]), c1 = T(s->C[1]), c2 = T(s->C[2]), c3 = T(s->C[3]);
   } else {
-    c0 = T(s->c[0]), c1 = T(s->c[1]), c2 = T(s->c[2]), c3 = T(0);
+    if (COHERENT)
+      c0 = T(__ldcg(&s->c[0])), c1 = T(__ldcg(&s->c[1])), c2 = T(__ldcg(&s->c[2])), c3 = T(0);
+    else
+      c0 = T(s->c[0]), c1 = T(s->c[1]), c2 = T(s->c[2]), c3 = T(0);
   }
   // per-thread maximum in the key precision (the conversion to FP64 is exact and keeps the order)
   T bkt = T(-1);
   int bi = INT_MAX;
-  const int stride = gridDim.x * blockDim.x;
+  const int stride = nb * blockDim.x;
   // Four samples in flight per thread (indices ascending, so the strict > keeps the lowest index
   // among equal keys); quaternions are read as 16-byte vectors when the array allows it.
   const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
-  int i = blockIdx.x * blockDim.x + tid;
+  int i = bid * blockDim.x + tid;
   const bool grouped = MODE == 1 && sizeof(T) == 4 && vec;
   if (grouped) {
     // FP32 translations: groups of four samples = three 16-byte vectors per thread, two groups in
@@ -200,16 +227,16 @@ __global__ void __launch_bounds__(kMegbThreads)
   if (tid == 0) {
     for (int w = 1; w < kMegbThreads / 32; ++w)
       if (better(wkey[w], widx[w], bk, bi)) bk = wkey[w], bi = widx[w];
-    parts[blockIdx.x] = Part{bk, bi, 0};
+    parts[bid] = Part{bk, bi, 0};
     __threadfence();
     const unsigned ticket = atomicAdd(&s->counter[MODE], 1u);
-    last = ticket == gridDim.x - 1;
+    *last = ticket == (unsigned)nb - 1;
   }
   __syncthreads();
-  if (!last) return;
+  if (!*last) return false;
   __threadfence();
   bk = -1.0, bi = INT_MAX;
-  for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+  for (int b = tid; b < nb; b += blockDim.x) {
     // partials of other blocks: read from L2, bypassing this SM's L1
     const double pk = __ldcg(&parts[b].key);
     const int pi = __ldcg(&parts[b].idx);
@@ -221,15 +248,17 @@ __global__ void __launch_bounds__(kMegbThreads)
     const int oi = __shfl_xor_sync(kFullMask, bi, o);
     if (better(ok, oi, bk, bi)) bk = ok, bi = oi;
   }
+  __syncthreads();  // every warp has read wkey / widx of the first reduction
   if (lane == 0) wkey[warp] = bk, widx[warp] = bi;
   __syncthreads();
-  if (tid != 0) return;
+  if (tid != 0) return true;
   for (int w = 1; w < kMegbThreads / 32; ++w)
     if (better(wkey[w], widx[w], bk, bi)) bk = wkey[w], bi = widx[w];
   s->counter[MODE] = 0;
+  auto ld = [](const double* p) { return COHERENT ? __ldcg(p) : *p; };
   if (MODE == 0) {
     const T* qs = x + 4 * (size_t)bi;
-    const Q4<double> c{s->C[0], s->C[1], s->C[2], s->C[3]};
+    const Q4<double> c{ld(&s->C[0]), ld(&s->C[1]), ld(&s->C[2]), ld(&s->C[3])};
     const Q4<double> qf = qnormalize(Q4<double>{(double)qs[0], (double)qs[1], (double)qs[2], (double)qs[3]});
     const RelRot r = rel_rot(c, qf);
     if (k > 0) {
@@ -241,11 +270,15 @@ __global__ void __launch_bounds__(kMegbThreads)
     }
   } else {
     const T* p = x + 3 * (size_t)bi;
+    const double c0d = ld(&s->c[0]), c1d = ld(&s->c[1]), c2d = ld(&s->c[2]);
     if (k > 0) {
-      for (int d = 0; d < 3; ++d) s->c[d] = s->c[d] + ((double)p[d] - s->c[d]) / k;
+      const double rk = 1.0 / k;
+      s->c[0] = c0d + ((double)p[0] - c0d) * rk;
+      s->c[1] = c1d + ((double)p[1] - c1d) * rk;
+      s->c[2] = c2d + ((double)p[2] - c2d) * rk;
     } else {
-      const double dx = (double)p[0] - s->c[0], dy = (double)p[1] - s->c[1], dz = (double)p[2] - s->c[2];
-      result[4] = s->c[0], result[5] = s->c[1], result[6] = s->c[2];
+      const double dx = (double)p[0] - c0d, dy = (double)p[1] - c1d, dz = (double)p[2] - c2d;
+      result[4] = c0d, result[5] = c1d, result[6] = c2d;
       result[8] = sqrt(dx * dx + dy * dy + dz * dz);
     }
   }
@@ -255,6 +288,69 @@ __global__ void __launch_bounds__(kMegbThreads)
   } else {
     s->fstar[MODE] = bi;
   }
+  return true;
+}
+
+// One launch per iteration (the state is complete at every kernel boundary).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kMegbThreads)
+    ggd_step(const T* __restrict__ x, int n, MegbState* s, Part* parts, int k, int32_t* f_int, int32_t* f_out,
+             double* result) {
+  __shared__ double wkey[kMegbThreads / 32];
+  __shared__ int widx[kMegbThreads / 32];
+  __shared__ bool last;
+  ggd_iter<T, MODE, false>(x, n, s, parts, k, f_int, f_out, result, wkey, widx, &last, blockIdx.x, gridDim.x);
+}
+
+// All K iterations and the radius pass of a ball on blocks [b0, b0 + nb) of a cooperative launch
+// (every block resident).  After each iteration the block that took the step publishes it by
+// bumping s->gen[MODE] (release); the others wait for it with a bounded poll (acquire) and, if the
+// poll limit runs out, flag a timeout in the status word and leave (the result is then not written).
+template <typename T, int MODE>
+__device__ __forceinline__ void ggd_ball(const T* __restrict__ x, int n, MegbState* s, Part* parts, int n_iters,
+                                         int32_t* f_int, int32_t* f_out, double* result, int* status, int bid, int nb,
+                                         double* wkey, int* widx, bool* last, bool* stop) {
+  for (int it = 1; it <= n_iters + 1; ++it) {
+    const int k = it <= n_iters ? it : 0;
+    const bool took = ggd_iter<T, MODE, true>(x, n, s, parts, k, f_int, f_out, result, wkey, widx, last, bid, nb);
+    if (it == n_iters + 1) break;
+    if (threadIdx.x == 0) {
+      *stop = false;
+      if (took) {
+        __threadfence();
+        st_release(&s->gen[MODE], (unsigned)it);
+      } else {
+        int polls = 0;
+        while (ld_acquire(&s->gen[MODE]) < (unsigned)it) {
+          if (++polls > (1 << 22)) {
+            atomicOr(status, kDevErrTimeout);
+            *stop = true;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+    }
+    __syncthreads();
+    if (*stop) return;
+  }
+}
+
+// Both balls in one launch: blocks [0, gq) descend the rotation ball, blocks [gq, gridDim.x) the
+// translation ball (each group with its own ticket and iteration counter).
+template <typename T>
+__global__ void __launch_bounds__(kMegbThreads)
+    ggd_persistent(const T* __restrict__ q, int nq, const T* __restrict__ t, int nt, int gq, MegbState* s,
+                   Part* parts_q, Part* parts_t, int n_iters, int32_t* f_int, int32_t* f_out, double* result,
+                   int* status) {
+  __shared__ double wkey[kMegbThreads / 32];
+  __shared__ int widx[kMegbThreads / 32];
+  __shared__ bool last, stop;
+  if ((int)blockIdx.x < gq)
+    ggd_ball<T, 0>(q, nq, s, parts_q, n_iters, f_int, f_out, result, status, blockIdx.x, gq, wkey, widx, &last, &stop);
+  else
+    ggd_ball<T, 1>(t, nt, s, parts_t, n_iters, f_int + n_iters, f_out ? f_out + n_iters : nullptr, result, status,
+                   blockIdx.x - gq, gridDim.x - gq, wkey, widx, &last, &stop);
 }
 
 __global__ void megb_zero_result(double* result, int skip_rot, int skip_tr) {
@@ -272,6 +368,48 @@ static cudaError_t launch_megb_t(purse_t h, int n_iters, const T* q, int nq, con
   megb_init<T><<<1, 32, 0, st>>>(q, nq, t, nt, s);
   megb_zero_result<<<1, 32, 0, st>>>(result, nq == 0, nt == 0);
   const long cap = (long)megb_blocks_cap(h->sm_count);
+  // one cooperative launch for both balls when every block fits on the GPU at once
+  static int resident[2] = {-1, -1};  // co-resident ggd_persistent blocks per SM (FP32, FP64)
+  int& per_sm = resident[sizeof(T) == 8];
+  if (per_sm < 0) {
+    int coop = 0, dev = 0, nbk = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess && coop)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbk, ggd_persistent<T>, kMegbThreads, 0);
+    if (e != cudaSuccess) return e;
+    per_sm = coop ? nbk : 0;
+  }
+  const long room = (long)per_sm * h->sm_count;
+  // FP32 samples: four per thread (the pass streams them); FP64 samples: one per thread, since every
+  // FP64 instruction of a warp occupies the SM's FP64 unit for tens of cycles and the keys need
+  // spreading over as many SMs as the samples allow
+  const long per_block = (long)kMegbThreads * (sizeof(T) == 8 ? 1 : 4);
+  const long want_q = nq > 0 ? ((long)nq + per_block - 1) / per_block : 0;
+  const long want_t = nt > 0 ? ((long)nt + per_block - 1) / per_block : 0;
+  if ((nq > 0 || nt > 0) && room >= 2) {
+    // split the resident blocks between the balls (the farthest sample does not depend on the split)
+    long gq = nq > 0 ? (want_q < cap ? want_q : cap) : 0, gt = nt > 0 ? (want_t < cap ? want_t : cap) : 0;
+    if (gq < 1 && nq > 0) gq = 1;
+    if (gt < 1 && nt > 0) gt = 1;
+    if (gq + gt > room) {  // each group stays within cap (its partials array)
+      if (nq > 0 && nt > 0) {
+        const long half = room / 2;
+        gq = gq < half ? gq : half;
+        gt = gt < room - gq ? gt : room - gq;
+      } else if (nq > 0) {
+        gq = room;
+      } else {
+        gt = room;
+      }
+    }
+    int gqi = (int)gq, nqi = nq, nti = nt, ni = n_iters;
+    Part* parts_t = parts + cap;
+    int* status = h->d_status;
+    void* args[] = {(void*)&q, &nqi, (void*)&t, &nti, &gqi, &s, &parts, &parts_t, &ni, &f_int, &f_out, &result, &status};
+    return cudaLaunchCooperativeKernel((const void*)ggd_persistent<T>, dim3((unsigned)(gq + gt)), dim3(kMegbThreads),
+                                       args, 0, st);
+  }
   if (nq > 0) {
     const long want = ((long)nq + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
     const int g = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
@@ -563,7 +701,8 @@ __device__ void ggd_block(const T* __restrict__ x, int n, int K, double* result,
       } else {
         const T* pp = x + 3 * (size_t)bi;
         if (k <= K) {
-          for (int d = 0; d < 3; ++d) c[d] = c[d] + ((double)pp[d] - c[d]) / k;
+          const double rk = 1.0 / k;  // the same arithmetic as the single-PURSE ball
+          for (int d = 0; d < 3; ++d) c[d] = c[d] + ((double)pp[d] - c[d]) * rk;
         } else {
           const double dx = (double)pp[0] - c[0], dy = (double)pp[1] - c[1], dz = (double)pp[2] - c[2];
           result[4] = c[0], result[5] = c[1], result[6] = c[2];
