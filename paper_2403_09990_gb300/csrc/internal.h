@@ -27,12 +27,16 @@ struct WalkStats {
   double tbar[3];
   double S[9];
   double sigma_t, rho_a, r_trans, r_rot;
+  float Sf[9];  // S rounded, for the FP32 walks
 };
 
-// Per-seed data: unit quaternion (w >= 0) and translation of the seed, the
-// axis u of R_0 R-bar^T (0 below 1e-9 rad) and the unit direction of
-// t_0 - t-bar (0 when degenerate).  16 doubles.
-constexpr int kSeedStride = 16;
+// Per-seed data (kSeedStride doubles): doubles 0-3 unit quaternion (w >= 0) and 4-6
+// translation of the seed, 7-9 the axis u of R_0 R-bar^T (0 below 1e-9 rad), 10-12 the unit
+// direction of t_0 - t-bar (0 when degenerate); from double 16 on, floats for the FP32 walks:
+// 0-3 quaternion hi, 4-7 quaternion lo, 8-10 translation hi, 11-13 translation lo (hi + lo the
+// double-float split of the FP64 values), 14-16 u, 17-19 direction.
+constexpr int kSeedStride = 32;
+constexpr int kSeedFloats = 16;  // double offset of the float part
 
 // Values per walk in the boundary-snap record (see purse_sample).
 constexpr int kSnapStride = 12;

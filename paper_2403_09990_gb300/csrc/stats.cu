@@ -109,6 +109,7 @@ __device__ void stats_block(const double* seeds, int s0, const double* tab, int 
     }
     sh.r_trans = raw_units ? t_p : t_p * sh.sigma_t;
     sh.r_rot = raw_units ? th_p : th_p * sh.sigma_t / sh.rho_a;
+    for (int k = 0; k < 9; ++k) sh.Sf[k] = (float)sh.S[k];
     *out = sh;
   }
   __syncthreads();
@@ -134,7 +135,15 @@ __device__ void stats_block(const double* seeds, int s0, const double* tab, int 
     const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     const bool has_d = dn > thr;
     for (int c = 0; c < 3; ++c) o[10 + c] = has_d ? d[c] / dn : 0.0;
-    for (int c = 13; c < kSeedStride; ++c) o[c] = 0.0;
+    for (int c = 13; c < kSeedFloats; ++c) o[c] = 0.0;
+    float* f = reinterpret_cast<float*>(o + kSeedFloats);
+    for (int c = 0; c < 7; ++c) {
+      const float hi = (float)o[c];
+      f[(c < 4 ? c : c + 4)] = hi;
+      f[(c < 4 ? c + 4 : c + 7)] = (float)(o[c] - (double)hi);
+    }
+    for (int c = 0; c < 6; ++c) f[14 + c] = (float)o[7 + c];
+    for (int c = 20; c < 2 * (kSeedStride - kSeedFloats); ++c) f[c] = 0.0f;
   }
 }
 

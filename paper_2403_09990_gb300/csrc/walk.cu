@@ -125,7 +125,7 @@ __device__ __forceinline__ void sort8_desc(K (&k)[8]) {
 //              with noise matrices U_i in slots 8-13.
 //  P[j]        perturbation j: translation offset (dS_R) or unit quaternion (dS_t)
 //  E[4m..]     ladder rung m: quaternion and rows of (K) E_m (dS_R) or s_m v (dS_t)
-//  S           walk state of FP32 walks: q*, t* as double-float pairs, start velocity in FP64
+//  S           walk state of FP32 walks: q*, t* as double-float pairs
 template <typename T>
 struct Slab {
   P2<T>* D;
@@ -140,8 +140,8 @@ struct Slab {
 __host__ __device__ inline int ladder_pairs(int n) { return (n + 1) / 2; }
 
 // Slab::S of FP32 walks: the pose as double-float pairs (floats 0-3 q* hi, 4-7 q* lo, 8-10 t* hi,
-// 11-13 t* lo), then the start velocity in FP64 (doubles 8-10).
-constexpr int kStateDoubles = 11;
+// 11-13 t* lo).
+constexpr int kStateDoubles = 8;
 
 template <typename T>
 __host__ __device__ inline size_t walk_slab_bytes2(int n, int n_perturb, int n_steps, bool lam = false) {
@@ -381,6 +381,7 @@ struct WalkCtx {
   T fx, fy, cx, cy, r_pert;
   T rho_max;  // largest model-point radius (bounds P_z from below for the cheirality test)
   double omega0, v0, gamma;
+  T om0, vv0, gam;  // the same in T (converted once per block)
   const WalkStats* st;
   const double* seed_data;
   int s0;
@@ -562,7 +563,7 @@ __device__ __forceinline__ void snap_rotation(const WalkCtx<T>& c, const Q4<doub
   T hi = T(-1);
   for (int m = c.NT - 1; m >= 0 && hi < T(0); --m) {
     T sm = T(1);
-    for (int k = 0; k < m; ++k) sm *= T(c.gamma);
+    for (int k = 0; k < m; ++k) sm *= c.gam;
     if (!inside(sm)) hi = sm;
   }
   T* rec = c.out_snap + (size_t)kSnapStride * w;
@@ -650,7 +651,7 @@ __device__ __forceinline__ void snap_translation(const WalkCtx<T>& c, const Q4<d
   T hi = T(-1);
   for (int m = c.NT - 1; m >= 0 && hi < T(0); --m) {
     T sm = T(1);
-    for (int k = 0; k < m; ++k) sm *= T(c.gamma);
+    for (int k = 0; k < m; ++k) sm *= c.gam;
     if (!inside(sm)) hi = sm;
   }
   T* rec = c.out_snap + (size_t)kSnapStride * w;
@@ -739,26 +740,53 @@ __device__ __forceinline__ void df_move(float* F, float pw, float px, float py, 
   }
 }
 
-// Start of walk w: pose of seed (w mod |S0|) and velocity omega = omega0 (u + u~) (Alg. 3) or
-// v = v0 S (dir + v~) (Alg. 5), u~ / v~ the first accepted unit lattice draw of the walk's stream.
+// Start velocity of walk w in FP64: omega = omega0 (u + u~) (Alg. 3) or v = v0 S (dir + v~) (Alg. 5),
+// u~ / v~ the first accepted unit lattice draw of the walk's stream.
 template <typename T, int SAMPLER>
-__device__ __forceinline__ void walk_start(const WalkCtx<T>& c, int w, Q4<T>& q, V3<T>& t, V3<double>& vel) {
+__device__ __forceinline__ V3<double> start_velocity64(const WalkCtx<T>& c, int w) {
   const double* sd = c.seed_data + (size_t)(w % c.s0) * kSeedStride;
-  q = Q4<T>{T(sd[0]), T(sd[1]), T(sd[2]), T(sd[3])};
-  t = V3<T>{T(sd[4]), T(sd[5]), T(sd[6])};
   Stream s(c.key0, c.key1, SAMPLER == 0 ? kPhaseOmega : kPhaseV, 0u, 0u, (uint32_t)w);
   int X, Y, Z;
   lattice_draw<true>(s, X, Y, Z);
   const double nr = sqrt((double)(X * X + Y * Y + Z * Z));
   const double ux = nr > 0 ? X / nr : 0.0, uy = nr > 0 ? Y / nr : 0.0, uz = nr > 0 ? Z / nr : 0.0;
-  if (SAMPLER == 0) {
-    vel = V3<double>{c.omega0 * (sd[7] + ux), c.omega0 * (sd[8] + uy), c.omega0 * (sd[9] + uz)};
+  if (SAMPLER == 0)
+    return V3<double>{c.omega0 * (sd[7] + ux), c.omega0 * (sd[8] + uy), c.omega0 * (sd[9] + uz)};
+  const WalkStats* st = c.st;
+  const double d0 = sd[10] + ux, d1 = sd[11] + uy, d2 = sd[12] + uz;
+  return V3<double>{c.v0 * (st->S[0] * d0 + st->S[1] * d1 + st->S[2] * d2),
+                    c.v0 * (st->S[3] * d0 + st->S[4] * d1 + st->S[5] * d2),
+                    c.v0 * (st->S[6] * d0 + st->S[7] * d1 + st->S[8] * d2)};
+}
+
+// Start of walk w: pose of seed (w mod |S0|) and the start velocity, in T.  FP32 walks take the
+// rounded seed data and compute the velocity in FP32 (no FP64 instruction: on this part each one
+// occupies the FP64 unit for tens of cycles); FP64 walks take start_velocity64.
+template <typename T, int SAMPLER>
+__device__ __forceinline__ void walk_start(const WalkCtx<T>& c, int w, Q4<T>& q, V3<T>& t, V3<T>& vel) {
+  const double* sd = c.seed_data + (size_t)(w % c.s0) * kSeedStride;
+  if constexpr (sizeof(T) == 8) {
+    q = Q4<T>{sd[0], sd[1], sd[2], sd[3]};
+    t = V3<T>{sd[4], sd[5], sd[6]};
+    const V3<double> v = start_velocity64<T, SAMPLER>(c, w);
+    vel = V3<T>{v.x, v.y, v.z};
   } else {
-    const WalkStats* st = c.st;
-    const double d0 = sd[10] + ux, d1 = sd[11] + uy, d2 = sd[12] + uz;
-    vel = V3<double>{c.v0 * (st->S[0] * d0 + st->S[1] * d1 + st->S[2] * d2),
-                     c.v0 * (st->S[3] * d0 + st->S[4] * d1 + st->S[5] * d2),
-                     c.v0 * (st->S[6] * d0 + st->S[7] * d1 + st->S[8] * d2)};
+    const float* f = reinterpret_cast<const float*>(sd + kSeedFloats);
+    q = Q4<T>{f[0], f[1], f[2], f[3]};
+    t = V3<T>{f[8], f[9], f[10]};
+    Stream s(c.key0, c.key1, SAMPLER == 0 ? kPhaseOmega : kPhaseV, 0u, 0u, (uint32_t)w);
+    int X, Y, Z;
+    lattice_draw<true>(s, X, Y, Z);
+    const float nr = sqrtf((float)(X * X + Y * Y + Z * Z));  // the integer is exact in FP32
+    const float ux = nr > 0 ? X / nr : 0.0f, uy = nr > 0 ? Y / nr : 0.0f, uz = nr > 0 ? Z / nr : 0.0f;
+    if (SAMPLER == 0) {
+      vel = V3<T>{c.om0 * (f[14] + ux), c.om0 * (f[15] + uy), c.om0 * (f[16] + uz)};
+    } else {
+      const float* S = c.st->Sf;
+      const float d0 = f[17] + ux, d1 = f[18] + uy, d2 = f[19] + uz;
+      vel = V3<T>{c.vv0 * (S[0] * d0 + S[1] * d1 + S[2] * d2), c.vv0 * (S[3] * d0 + S[4] * d1 + S[5] * d2),
+                  c.vv0 * (S[6] * d0 + S[7] * d1 + S[8] * d2)};
+    }
   }
 }
 
@@ -788,22 +816,16 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
   // boundary the walk reaches by ~1e-6 m.  (FP64 arithmetic would do, but one FP64 instruction of
   // one lane occupies the FP64 unit of this part far longer than the ~240 FP32 operations of a move.)
   constexpr bool kState64 = sizeof(T) == 4;
-  {
-    V3<double> vd;
-    walk_start<T, SAMPLER>(c, w, q, t, vd);
-    vel = V3<T>{T(vd.x), T(vd.y), T(vd.z)};
-    if (kState64 && lane == 0) {
-      const double* sd = c.seed_data + (size_t)(w % c.s0) * kSeedStride;
-      float* F = reinterpret_cast<float*>(sl.S);
-      for (int k = 0; k < 4; ++k) F[k] = float(sd[k]), F[4 + k] = float(sd[k] - double(F[k]));
-      for (int k = 0; k < 3; ++k) F[8 + k] = float(sd[4 + k]), F[11 + k] = float(sd[4 + k] - double(F[8 + k]));
-      sl.S[8] = vd.x, sl.S[9] = vd.y, sl.S[10] = vd.z;
-    }
+  walk_start<T, SAMPLER>(c, w, q, t, vel);
+  if (kState64 && lane == 0) {
+    const float* f = reinterpret_cast<const float*>(c.seed_data + (size_t)(w % c.s0) * kSeedStride + kSeedFloats);
+    float* F = reinterpret_cast<float*>(sl.S);
+    for (int k = 0; k < 14; ++k) F[k] = f[k];
   }
   const T rho_max = c.rho_max;
   for (int m = lane; m < NT; m += 32) {
     T sm = T(1);
-    for (int k = 0; k < m; ++k) sm *= T(c.gamma);
+    for (int k = 0; k < m; ++k) sm *= c.gam;
     if (SAMPLER == 0) {
       const Q4<T> e = qexp(V3<T>{sm * vel.x, sm * vel.y, sm * vel.z});
       M3<T> E = qmat(e);
@@ -1083,11 +1105,9 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
         q64 = qnormalize(Q4<double>{double(F[0]) + F[4], double(F[1]) + F[5], double(F[2]) + F[6],
                                     double(F[3]) + F[7]});
         t64 = V3<double>{double(F[8]) + F[11], double(F[9]) + F[12], double(F[10]) + F[13]};
-        v64 = V3<double>{sl.S[8], sl.S[9], sl.S[10]};
+        v64 = start_velocity64<T, SAMPLER>(c, w);
       } else {
-        Q4<T> q0;
-        V3<T> t0;
-        walk_start<T, SAMPLER>(c, w, q0, t0, v64);  // the start velocity in FP64
+        v64 = start_velocity64<T, SAMPLER>(c, w);
         q64 = Q4<double>{double(q.w), double(q.x), double(q.y), double(q.z)};
         t64 = V3<double>{double(t.x), double(t.y), double(t.z)};
       }
@@ -1153,6 +1173,7 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
   c.rho_max = T(a.rho_max);
   c.r_pert = T(SAMPLER == 0 ? a.stats->r_trans : a.stats->r_rot);
   c.omega0 = a.omega0, c.v0 = a.v0, c.gamma = a.gamma;
+  c.om0 = T(a.omega0), c.vv0 = T(a.v0), c.gam = T(a.gamma);
   c.st = a.stats, c.seed_data = a.seed_data, c.s0 = a.s0;
   c.key0 = a.key0, c.key1 = a.key1;
   c.out_q = reinterpret_cast<T*>(a.out_q), c.out_t = reinterpret_cast<T*>(a.out_t);
@@ -1238,13 +1259,9 @@ __device__ __forceinline__ void reg_walk_one(const WalkCtx<T>& c, const RK& rk, 
   Q4<T> q;
   V3<T> t;
   V3<T> vel;
-  {
-    V3<double> vd;
-    walk_start<T, SAMPLER>(c, w, q, t, vd);
-    vel = V3<T>{T(vd.x), T(vd.y), T(vd.z)};
-  }
+  walk_start<T, SAMPLER>(c, w, q, t, vel);
   T sm = T(1);  // this lane's rung scale gamma^lane
-  for (int k = 0; k < lane; ++k) sm *= T(c.gamma);
+  for (int k = 0; k < lane; ++k) sm *= c.gam;
   bool moved = true;
   T fixed_min = inf<T>();  // minimum margin of the part the perturbations do not move
   for (int it = 0; it < c.n_iter; ++it) {
@@ -1431,6 +1448,7 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
   c.rho_max = T(0);
   c.r_pert = T(SAMPLER == 0 ? a.stats->r_trans : a.stats->r_rot);
   c.omega0 = a.omega0, c.v0 = a.v0, c.gamma = a.gamma;
+  c.om0 = T(a.omega0), c.vv0 = T(a.v0), c.gam = T(a.gamma);
   c.st = a.stats, c.seed_data = a.seed_data, c.s0 = a.s0;
   c.key0 = a.key0, c.key1 = a.key1;
   c.out_q = reinterpret_cast<T*>(a.out_q), c.out_t = reinterpret_cast<T*>(a.out_t);
@@ -1504,6 +1522,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2)
         c.fx = float(in.fx), c.fy = float(in.fy), c.cx = float(in.cx), c.cy = float(in.cy);
         c.rho_max = float(in.rho_max);
         c.omega0 = b.omega0[kd], c.v0 = b.v0[kd], c.gamma = b.gamma[kd];
+        c.om0 = float(b.omega0[kd]), c.vv0 = float(b.v0[kd]), c.gam = float(b.gamma[kd]);
         c.st = b.stats + p, c.seed_data = b.seed_data + (size_t)p * kSeedStride, c.s0 = 1;
         c.key0 = (uint32_t)key, c.key1 = (uint32_t)(key >> 32);
         c.trace = nullptr, c.status = b.status;
