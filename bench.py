@@ -224,7 +224,10 @@ def run_gpu(args, rank, world):
     res = torch.empty(9, dtype=torch.float64, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     pR, pT = closure_params(0), closure_params(1)
-    launches_per_step = 2 + 2 + (2 * (K_MEGB + 1) + 2)
+    launches_per_step = 2 + 2 + 3
+    # autotuner: launch shapes measured on this workload (walks with 10 iterations: the shape depends on
+    # the kind, N and the sample count, not on the iteration count) and used by the timed step
+    tuning = None if args.no_tune else run_tune(hR, hT, seeds, qR, tR, qT, tT, res, stream)
 
     def step(seed, ev=None):
         if ev:
@@ -312,6 +315,8 @@ def run_gpu(args, rank, world):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": ck, "wall_s_timed": wall,
     }
+    if tuning is not None:
+        out["tuning"] = tuning
     out["megb_exact"] = run_exact(hR, qR, tT, res, dev)
     out["ransag"] = run_ransag(dev)
     if not args.no_c1:
@@ -361,6 +366,21 @@ def run_ransag(dev):
                 n = 0
             dt = time.perf_counter() - t0
         out[name] = {"trials": trials, "ms": dt * 1e3, "trials_per_s": trials / dt, "seeds": n}
+    return out
+
+
+def run_tune(hR, hT, seeds, qR, tR, qT, tT, res, stream):
+    """purse_tune_walk for both walk kernels and purse_tune_megb for the two balls of the step: the
+    chosen shape and its time beside the default shape's (CUDA events; the walks with 10 iterations)."""
+    import paper_2403_09990_gb300.purse as P
+    out = {}
+    for key, h, smp, q, t in (("walk_dS_R", hR, 0, qR, tR), ("walk_dS_t", hT, 1, qT, tT)):
+        r = P.purse_tune_walk(h.h, closure_params(smp, n_iter=10), 5, seeds, 1, N_WALKS, q, t, stream)
+        out[key] = {"shape": "warps per block", "config": r["config"], "ms": r["ms"],
+                    "default_config": r["default_config"], "default_ms": r["default_ms"], "n_iter": 10}
+    r = P.purse_tune_megb(hR.h, 0, K_MEGB, qR, N_WALKS, tT, N_WALKS, res, stream)
+    out["megb"] = {"shape": "samples per thread (blocks per ball)", "config": r["config"], "ms": r["ms"],
+                   "default_config": r["default_config"], "default_ms": r["default_ms"]}
     return out
 
 
@@ -1018,6 +1038,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-operation comparator")
     ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default launch shapes)")
     ap.add_argument("--no-c1", action="store_true", help="skip the FP64 3D-3D configuration (C1)")
     ap.add_argument("--no-grad", action="store_true", help="skip the batched differentiation measurement")
     ap.add_argument("--sweep", action="store_true", help="precision / scale sweep instead of the bench step")

@@ -273,6 +273,48 @@ purse_status megb_solve_noalloc(int precision, int n_iters, const void* d_q, int
 purse_status purse_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t i, uint32_t w0, int n_streams,
                              int n_words, uint32_t* d_words, int32_t* d_lattice, int unit, purse_stream_t stream);
 
+/* ---- Autotuner.  Launch shapes chosen by measurement, cached per (operation, PURSE kind,
+ * keypoint-count bucket ceil(log2 n), sample-count bucket floor(log2 samples), variant, GPU name).
+ * The paper has no counterpart (its experiments fix the CuPy launch shapes).  Operations:
+ *   0 walk -- warps per walk block, {8, 4, 2}; used by purse_sample (variant = sampler + 2 precision)
+ *   1 megb -- samples per thread of the persistent ball kernel, i.e. blocks per ball, FP32
+ *             {1 .. 64}, FP64 {1 .. 8}; used by megb_solve (variant = precision)
+ *   2 dist -- resident CTAs per SM of the tensor-core distance kernel, {4, 3, 2, 1}; used by
+ *             purse_dist modes 1 and 2 (variant = 3 split passes or 1)
+ *   3 batch -- reserved (purse_batch_tune keeps its choice in the batch).
+ * No shape changes a result.  The cache lives in the process; if the environment variable
+ * PURSE_TUNE_CACHE names a file, it is read at the first lookup and every tuning call appends its
+ * choice to it.  Tuning calls run the operation once with the current shape (argument checks and
+ * warm-up), then once per candidate with CUDA events on the stream (the faster of two timed runs
+ * after one untimed), store the fastest and report it (out may be NULL); they synchronise the
+ * stream and leave the outputs of the last run in the buffers. */
+typedef struct {
+  int op;             /* the operation */
+  int config;         /* the chosen shape */
+  float ms;           /* its time */
+  int default_config; /* the shape used without tuning */
+  float default_ms;   /* its time (-1 if not measured) */
+  int n_tried;        /* candidates that fitted and ran */
+} purse_tune_result;
+
+/* purse_sample's arguments (d_trace and d_snap are not used). */
+purse_status purse_tune_walk(purse_t h, const purse_params* p, uint64_t seed, const double* d_seeds, int s0,
+                             int n_samples, void* d_q, void* d_t, purse_tune_result* out, purse_stream_t stream);
+/* megb_solve's arguments (d_farthest is not used). */
+purse_status purse_tune_megb(purse_t h, int precision, int n_iters, const void* d_q, int n_rot, const void* d_t,
+                             int n_tr, double* d_result, purse_tune_result* out, purse_stream_t stream);
+/* purse_dist's arguments, mode 1 or 2. */
+purse_status purse_tune_dist(purse_t h, int mode, const float* d_poses, long long n_poses, float* d_dist,
+                             purse_tune_result* out, purse_stream_t stream);
+/* Cache access without a GPU call: gpu = NULL means the current device's name.  get returns
+ * PURSE_ERR_STATE when there is no entry; clear empties the process cache (the file is read again
+ * at the next lookup). */
+purse_status purse_tune_cache_get(int op, int kind, int n, long long n_samples, int variant, const char* gpu,
+                                  purse_tune_result* out);
+purse_status purse_tune_cache_put(int op, int kind, int n, long long n_samples, int variant, const char* gpu,
+                                  int config, float ms);
+purse_status purse_tune_cache_clear(void);
+
 /* ---- Batches: many PURSEs solved by one graph of three launches (centre statistics, one
  * persistent walk launch over all (PURSE, sampler, walk) items, one block per ball).
  * PURSE p has kind kinds[p] and constraints offsets[p] .. offsets[p+1]-1 (3..256 each) of

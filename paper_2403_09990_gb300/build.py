@@ -12,7 +12,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpurse.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["api.cu", "walk.cu", "stats.cu", "eval.cu", "megb.cu", "batch.cu", "plain.cu", "tc.cu", "exact.cu"]
+SOURCES = ["api.cu", "walk.cu", "stats.cu", "eval.cu", "megb.cu", "batch.cu", "plain.cu", "tc.cu", "exact.cu",
+           "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", f"-I{INCLUDE}"]
 # The walk and ball kernels are instantiated in several launches (single PURSE, batch, the plain

@@ -155,6 +155,19 @@ purse_status make_handle(int kind, int n, const std::vector<double>& t64, const 
 purse_status cuda_fail(cudaError_t e, const char* where);
 purse_status ensure_scratch(purse_t h, size_t bytes);
 
+// Autotuner cache (tune.cu).  Operations: walk (warps per block), megb (samples per thread of the
+// persistent ball kernel), dist (resident tensor-core CTAs per SM), batch (reserved).
+enum TuneOp { kTuneWalk = 0, kTuneMegb = 1, kTuneDist = 2, kTuneBatch = 3 };
+struct TuneEntry {
+  int cfg;
+  float ms, default_ms;
+};
+// The shape a launcher uses: a tuning call's forced candidate, else the cached choice for
+// (op, kind, n, samples, variant, this GPU), else fallback.
+int tuned_config(int op, int kind, int n, long long samples, int variant, int fallback);
+bool tune_lookup(int op, int kind, int n, long long samples, int variant, const char* gpu, TuneEntry* out);
+void tune_store(int op, int kind, int n, long long samples, int variant, const char* gpu, const TuneEntry& e);
+
 // Launchers (one translation unit each).
 cudaError_t launch_stats(purse_t h, const double* d_seeds, int s0, const purse_params* p, WalkStats* d_stats,
                          double* d_seed_data, cudaStream_t st);  // takes h->ell64 into the translation scale

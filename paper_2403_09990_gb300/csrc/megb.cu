@@ -384,7 +384,8 @@ static cudaError_t launch_megb_t(purse_t h, int n_iters, const T* q, int nq, con
   // FP32 samples: four per thread (the pass streams them); FP64 samples: one per thread, since every
   // FP64 instruction of a warp occupies the SM's FP64 unit for tens of cycles and the keys need
   // spreading over as many SMs as the samples allow
-  const long per_block = (long)kMegbThreads * (sizeof(T) == 8 ? 1 : 4);
+  const int spt = tuned_config(kTuneMegb, h->kind, h->n, nq > nt ? nq : nt, sizeof(T) == 8, sizeof(T) == 8 ? 1 : 4);
+  const long per_block = (long)kMegbThreads * (spt < 1 ? 1 : spt);
   const long want_q = nq > 0 ? ((long)nq + per_block - 1) / per_block : 0;
   const long want_t = nt > 0 ? ((long)nt + per_block - 1) / per_block : 0;
   if ((nq > 0 || nt > 0) && room >= 2) {

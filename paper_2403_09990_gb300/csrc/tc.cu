@@ -327,6 +327,7 @@ cudaError_t launch_tc_dist(purse_t h, int passes, const float* d_poses, long n_p
   per_sm = std::min(per_sm, 2048 / kTcThreads);
   per_sm = std::min(per_sm, (int)(512u / tcols));
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  per_sm = std::max(1, std::min(per_sm, tuned_config(kTuneDist, h->kind, n, n_poses, passes, per_sm)));
   const long tiles = (n_poses + 127) / 128;
   const long cap = (long)per_sm * h->sm_count;
   const int grid = (int)(tiles < cap ? tiles : cap);

@@ -1576,8 +1576,9 @@ static cudaError_t launch_walk_t(purse_t h, const purse_params* p, const WalkArg
   const int mc = p->n_keep >= 32 ? 1 : 32 / p->n_keep;
   const size_t slab = walk_slab_bytes2<T>(a.n, p->n_perturb, p->n_steps, LAM);
   const size_t table = walk_table_bytes<T>(a.n, LAM);
-  // as many warps per block (up to kWalkWarps) as the shared memory holds slabs for
-  int warps = kWalkWarps;
+  // warps per block: the tuned choice (8 by default), no more than the shared memory holds slabs for
+  int warps = tuned_config(kTuneWalk, h->kind, a.n, a.n_samples, p->sampler + 2 * p->precision, kWalkWarps);
+  warps = warps < 1 ? 1 : warps > kWalkWarps ? kWalkWarps : warps;
   while (warps > 1 && 128 + table + warps * slab > kMaxSmemPerBlock) --warps;
   const size_t smem = 128 + table + warps * slab;
   if (smem > kMaxSmemPerBlock) return cudaErrorInvalidConfiguration;
@@ -1613,7 +1614,8 @@ template <typename T, int SAMPLER>
 static cudaError_t launch_reg_walk_t(purse_t h, const purse_params* p, const WalkArgs& a, cudaStream_t st) {
   const size_t slab = reg_slab_bytes<T>(a.n, p->n_perturb);
   const size_t table = reg_table_bytes<T>(a.n);
-  int warps = kWalkWarps;
+  int warps = tuned_config(kTuneWalk, h->kind, a.n, a.n_samples, p->sampler + 2 * p->precision, kWalkWarps);
+  warps = warps < 1 ? 1 : warps > kWalkWarps ? kWalkWarps : warps;
   while (warps > 1 && 128 + table + warps * slab > kMaxSmemPerBlock) --warps;
   const size_t smem = 128 + table + warps * slab;
   if (smem > kMaxSmemPerBlock) return cudaErrorInvalidConfiguration;

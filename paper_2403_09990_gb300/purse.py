@@ -34,6 +34,14 @@ class purse_params(ctypes.Structure):
                 ("perturb_units", ctypes.c_int), ("sampler", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
+class purse_tune_result(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("config", ctypes.c_int), ("ms", ctypes.c_float), ("default_config", ctypes.c_int),
+                ("default_ms", ctypes.c_float), ("n_tried", ctypes.c_int)]
+
+
+TUNE_WALK, TUNE_MEGB, TUNE_DIST, TUNE_BATCH = 0, 1, 2, 3
+
+
 def make_params(n_iter=5, n_perturb=150, n_keep=10, n_steps=15, omega0=1.0, v0=2.0, gamma=0.5, rot_perturb=0.2,
                 trans_perturb=0.1, perturb_units=0, sampler=0, precision=0) -> purse_params:
     return purse_params(n_iter, n_perturb, n_keep, n_steps, omega0, v0, gamma, rot_perturb, trans_perturb,
@@ -76,6 +84,16 @@ _SIGS = {
     "purse_batch_copy_snap": [_VP, ctypes.c_int, _VP, _VP, _VP],
     "purse_batch_backward": [_VP, _VP, _VP, _VP, _VP, _VP],
     "purse_batch_sync": [_VP, ctypes.POINTER(ctypes.c_ulonglong), _VP],
+    "purse_tune_walk": [_VP, ctypes.POINTER(purse_params), ctypes.c_uint64, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP,
+                        ctypes.POINTER(purse_tune_result), _VP],
+    "purse_tune_megb": [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP,
+                        ctypes.POINTER(purse_tune_result), _VP],
+    "purse_tune_dist": [_VP, ctypes.c_int, _VP, ctypes.c_longlong, _VP, ctypes.POINTER(purse_tune_result), _VP],
+    "purse_tune_cache_get": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_char_p,
+                             ctypes.POINTER(purse_tune_result)],
+    "purse_tune_cache_put": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_char_p,
+                             ctypes.c_int, ctypes.c_float],
+    "purse_tune_cache_clear": [],
     "purse_last_error": [],
     "purse_version": [],
 }
@@ -221,6 +239,51 @@ def megb_solve_noalloc(precision, n_iters, q, n_rot, t, n_tr, result, farthest=N
 def purse_rng_words(seed, phase, j, i, w0, n_streams, n_words, words, lattice=None, unit=0, stream=None):
     _check(lib().purse_rng_words(seed, phase, j, i, w0, n_streams, n_words, _ptr(words), _ptr(lattice), unit,
                                  _stream(stream)), "purse_rng_words")
+
+
+def _tune_dict(r):
+    return {"op": r.op, "config": r.config, "ms": r.ms, "default_config": r.default_config, "default_ms": r.default_ms,
+            "n_tried": r.n_tried}
+
+
+def purse_tune_walk(h, params: purse_params, seed, seeds, s0, n_samples, q, t, stream=None) -> dict:
+    r = purse_tune_result()
+    _check(lib().purse_tune_walk(h, ctypes.byref(params), seed, _ptr(seeds), s0, n_samples, _ptr(q), _ptr(t),
+                                 ctypes.byref(r), _stream(stream)), "purse_tune_walk")
+    return _tune_dict(r)
+
+
+def purse_tune_megb(h, precision, n_iters, q, n_rot, t, n_tr, result, stream=None) -> dict:
+    r = purse_tune_result()
+    _check(lib().purse_tune_megb(h, precision, n_iters, _ptr(q), n_rot, _ptr(t), n_tr, _ptr(result), ctypes.byref(r),
+                                 _stream(stream)), "purse_tune_megb")
+    return _tune_dict(r)
+
+
+def purse_tune_dist(h, mode, poses, n_poses, dist, stream=None) -> dict:
+    r = purse_tune_result()
+    _check(lib().purse_tune_dist(h, mode, _ptr(poses), n_poses, _ptr(dist), ctypes.byref(r), _stream(stream)),
+           "purse_tune_dist")
+    return _tune_dict(r)
+
+
+def purse_tune_cache_get(op, kind, n, n_samples, variant, gpu=None):
+    """The cached choice as a dict, or None."""
+    r = purse_tune_result()
+    st = lib().purse_tune_cache_get(op, kind, n, n_samples, variant, gpu.encode() if gpu else None, ctypes.byref(r))
+    if st == 7:
+        return None
+    _check(st, "purse_tune_cache_get")
+    return _tune_dict(r)
+
+
+def purse_tune_cache_put(op, kind, n, n_samples, variant, gpu, config, ms=0.0):
+    _check(lib().purse_tune_cache_put(op, kind, n, n_samples, variant, gpu.encode() if gpu else None, config, ms),
+           "purse_tune_cache_put")
+
+
+def purse_tune_cache_clear():
+    _check(lib().purse_tune_cache_clear(), "purse_tune_cache_clear")
 
 
 def purse_sync(h, stream=None):
