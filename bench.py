@@ -46,10 +46,13 @@ FLOPS_DIST, FLOPS_INPURSE = 28, 24
 N_PERTURB, N_KEEP, N_STEPS = 150, 10, 15
 SM_COUNT_NOMINAL = 152
 # DRAM bytes (read + write) per launch of each walk kernel on this workload, from one ncu capture of the
-# full-size bench step: ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
-# -k regex:walk_kernel -s 6 -c 2 python bench.py --steps 1 --warmup 3 --no-e2e --no-batch --no-cpu-baseline
-# --no-plain --no-grad (one pass).  Taken on the current kernels; a kernel change needs a new capture.
-WALK_DRAM_BYTES = {"R": 425.98e3 + 256, "t": 959.23e3}
+# timed step's two walk launches: ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+# -k regex:walk_kernel -s 6 -c 2 python bench.py --steps 2 --warmup 3 --no-e2e --no-batch --no-cpu-baseline
+# --no-plain --no-grad --no-c1 --no-tune (one pass).  The counters belong to the kernel built from the sources
+# whose SHA-256 (walk.cu, dev.cuh, internal.h concatenated) begins with WALK_DRAM_SRC; any other source gives
+# traffic null.
+WALK_DRAM_BYTES = {"R": 179456 + 1536, "t": 610048 + 1024}
+WALK_DRAM_SRC = "0abdc04772bdf9f1"
 FP32_LANES_PER_SM = 128
 # C1: 3D-3D PURSE (N = 8, seed 0) in FP64, |S0| = 2048 RANSAG seeds, N_W = 2 walks each (4096 samples of the
 # dS_R sampler, N_I = 5, 3DMatch preset), both balls with K = 200; flops per 3D-3D evaluation: 26 for in_purse
@@ -58,6 +61,17 @@ C1_N, C1_SEEDS, C1_NW, C1_ITERS, C1_K = 8, 2048, 2, 5, 200
 FLOPS_DIST_3D, FLOPS_INPURSE_3D = 28, 26
 # FP64 FMA results per clock per SM of this part (GB300: 1.25 TFLOP/s over 152 SMs at about 2 GHz)
 FP64_FMA_PER_SM = 2
+
+
+def walk_traffic(kern):
+    """The captured DRAM bytes per launch of the walk kernel, or None if its sources changed since."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2403_09990_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("walk.cu", "dev.cuh", "internal.h"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return WALK_DRAM_BYTES[kern] if h.hexdigest()[:16] == WALK_DRAM_SRC else None
 
 
 def workload_config():
@@ -310,7 +324,7 @@ def run_gpu(args, rank, world):
         "roofline": {"bound": "alu", "kernel": f"walk_kernel<float, 2D-3D, dS_{kern}>", "achieved": achieved,
                      "flops_per_eval": {"dist": FLOPS_DIST, "in_purse": FLOPS_INPURSE},
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                     "traffic": WALK_DRAM_BYTES[kern], "traffic_unit": "bytes per launch",
+                     "traffic": walk_traffic(kern), "traffic_unit": "bytes per launch",
                      "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz (max SM clock)"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": ck, "wall_s_timed": wall,
