@@ -12,10 +12,11 @@
   constraints, |vec(R) - vec(R_i)| <= beta_i^R (Frobenius) and
   |t - t_i| <= beta_i^t; the margins are the N rotation margins followed by
   the N translation margins.
-* SE(3) gradient of h_i = |g_i| under the world-frame left perturbation
-  R <- Exp(phi) R, t <- t + rho, returned as d h_i / d(phi, rho) (6 values).
+* SE(3) gradient of h_i = |g_i| (with noise matrices |g_i|_Lambda_i) under the world-frame left
+  perturbation R <- Exp(phi) R, t <- t + rho, returned as d h_i / d(phi, rho) (6 values).
 Pinned in tests/test_oracle_purse.py against a direct scalar restatement of
-eq. 2/3, cheirality cases and central finite differences of the gradient.
+eq. 2/3, cheirality cases and central finite differences of the gradient (also
+with noise matrices).
 """
 from __future__ import annotations
 
@@ -85,26 +86,34 @@ def in_purse(purse, R, t):
     return (margins(purse, R, t) >= 0.0).all(axis=-1)
 
 
+def norm_direction(e, lam):
+    """d|e| / de: e / |e|, or with noise matrices (eq. 4) Lambda e / |e|_Lambda."""
+    if lam is None:
+        return e / np.linalg.norm(e, axis=-1, keepdims=True)
+    le = np.einsum('nij,...nj->...ni', lam, e)
+    return le / np.sqrt(np.einsum('...ni,...ni->...n', e, le))[..., None]
+
+
 def margin_gradient(purse, R, t):
-    """d|g_i| / d(phi, rho) under R <- Exp(phi) R, t <- t + rho; shape (..., N, 6)."""
+    """d|g_i| / d(phi, rho) under R <- Exp(phi) R, t <- t + rho; shape (..., N, 6).  With noise
+    matrices the norm is |g_i|_Lambda_i, whose gradient in g is Lambda_i g_i / |g_i|_Lambda_i."""
     X = transform(purse.model, R, t)
     RA = X - np.asarray(t)[..., None, :]
+    lam = getattr(purse, "lam", None)
     # d X / d phi = -[R a]x ; d X / d rho = I
     dX = np.concatenate([-_hat(RA), np.broadcast_to(np.eye(3), RA.shape + (3,))], -1)  # (...,N,3,6)
     if purse.kind == KIND_3D3D:
         e = X - purse.obs                       # = -g_i ; |g_i| = |e|
-        n = np.linalg.norm(e, axis=-1, keepdims=True)
-        return np.einsum('...i,...ij->...j', e / n, dX)
+        return np.einsum('...i,...ij->...j', norm_direction(e, lam), dX)
     fx, fy, cx, cy = purse.K
     Kp = np.array([[fx, 0, cx], [0, fy, cy], [0, 0, 1.0]])
     P = X @ Kp.T
     Px, Py, Pz = P[..., 0], P[..., 1], P[..., 2]
     e = np.stack([Px / Pz - purse.obs[:, 0], Py / Pz - purse.obs[:, 1]], -1)  # = -g_i
-    n = np.linalg.norm(e, axis=-1, keepdims=True)
     z = np.zeros_like(Pz)
     J = np.stack([np.stack([1 / Pz, z, -Px / Pz ** 2], -1),
                   np.stack([z, 1 / Pz, -Py / Pz ** 2], -1)], -2)   # (...,N,2,3)
-    return np.einsum('...i,...ij,jk,...kl->...l', e / n, J, Kp, dX)
+    return np.einsum('...i,...ij,jk,...kl->...l', norm_direction(e, lam), J, Kp, dX)
 
 
 def _hat(v):

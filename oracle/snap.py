@@ -15,11 +15,12 @@ to the boundary:
   the smallest margin there.
 At the snapped sample h_j*(x(tau*)) = r_j*, so by the implicit-function
 theorem d tau*/d r_j* = 1 / h'(tau*) and d tau*/d y_j* = -(d h_j*/d y_j*) / h'(tau*)
-with h'(tau) = d h_j*(x(tau)) / d tau.
+with h'(tau) = d h_j*(x(tau)) / d tau.  With noise matrices (eq. 4) h is the norm
+|g|_Lambda, whose gradient in the residual g is Lambda g / |g|_Lambda.
 
 Parity: pinned in tests/test_oracle_snap.py (snapped samples on the
 boundary and inside S; central finite differences of tau* against the
-implicit derivatives).
+implicit derivatives, identity norm and noise matrices).
 """
 from __future__ import annotations
 
@@ -76,6 +77,11 @@ def ray_derivatives(purse, Rs, ts, direction, jstar, rotation: bool):
     else:
         fx, fy, cx, cy = purse.K
         e = purse.obs[j] - np.stack([fx * X[:, 0] / X[:, 2] + cx, fy * X[:, 1] / X[:, 2] + cy], 1)
-    dh_dy = e / np.linalg.norm(e, axis=1, keepdims=True)
+    lam = getattr(purse, "lam", None)
+    if lam is None:
+        dh_dy = e / np.linalg.norm(e, axis=1, keepdims=True)
+    else:  # |g|_Lambda: the gradient in g = y - (projection of) X is Lambda g / |g|_Lambda
+        le = np.einsum('wij,wj->wi', lam[j], e)
+        dh_dy = le / np.sqrt((e * le).sum(axis=1, keepdims=True))
     valid = jstar >= 0
     return np.where(valid, dh_dtau, 0.0), np.where(valid[:, None], dh_dy, 0.0)

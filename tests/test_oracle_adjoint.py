@@ -88,21 +88,21 @@ def test_translation_adjoint_matches_central_differences(K):
             assert abs(fd - g[s, i]) <= 1e-7 * (1 + abs(fd))
 
 
-def _pipeline_case(kind):
+def _pipeline_case(kind, lam=False):
     if kind == 0:
-        p = syn.purse_3d3d(8, 3)
+        p = syn.purse_3d3d_ellipsoidal(8, 3) if lam else syn.purse_3d3d(8, 3)
         pr = closure.preset_3d3d(n_iter=3, rot_perturb=0.002, trans_perturb=0.002, perturb_units=1)
         pt = closure.preset_3d3d(n_iter=3, v0=0.02, rot_perturb=0.002, trans_perturb=0.002, perturb_units=1)
     else:
-        p = syn.purse_2d3d(10, 3)
+        p = syn.purse_2d3d_ellipsoidal(10, 3) if lam else syn.purse_2d3d(10, 3)
         pr = closure.preset_2d3d(n_iter=3, rot_perturb=0.002, trans_perturb=0.002, perturb_units=1)
         pt = pr
     return p, p.seed_pose()[None], pr, pt
 
 
-@pytest.mark.parametrize("kind", [0, 1])
-def test_pipeline_gradient_matches_central_differences(kind):
-    p, seeds, pr, pt = _pipeline_case(kind)
+@pytest.mark.parametrize("kind,lam", [(0, False), (1, False), (0, True), (1, True)])
+def test_pipeline_gradient_matches_central_differences(kind, lam):
+    p, seeds, pr, pt = _pipeline_case(kind, lam)
     W, K, seed = 48, 40, 11
     fw = adjoint.closure_balls(p, seeds, pr, pt, seed, W, K)
     g_res = np.array([0.2, -0.4, 0.1, 0.3, 0.5, -0.2, 0.7, 1.0, 1.0])
@@ -127,7 +127,7 @@ def test_pipeline_gradient_matches_central_differences(kind):
                     obs[j, c] += sgn * h
                 else:
                     radii[j] += sgn * h
-                vals.append(loss(syn.Purse(p.kind, p.model, obs, radii, p.K)))
+                vals.append(loss(syn.Purse(p.kind, p.model, obs, radii, p.K, lam=p.lam)))
             if not (vals[0][1] and vals[1][1]):
                 continue
             fd = (vals[0][0] - vals[1][0]) / (2 * h)

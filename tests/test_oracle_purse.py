@@ -74,9 +74,12 @@ def test_dist_and_membership_consistent():
     assert 0 < (d >= 0).mean() < 1
 
 
-@pytest.mark.parametrize("kind", [0, 1])
-def test_gradient_matches_central_differences(kind):
-    p = syn.purse_3d3d(8, 6) if kind == 0 else syn.purse_2d3d(16, 6)
+@pytest.mark.parametrize("kind,lam", [(0, False), (1, False), (0, True), (1, True)])
+def test_gradient_matches_central_differences(kind, lam):
+    if lam:
+        p = syn.purse_3d3d_ellipsoidal(8, 6) if kind == 0 else syn.purse_2d3d_ellipsoidal(16, 6)
+    else:
+        p = syn.purse_3d3d(8, 6) if kind == 0 else syn.purse_2d3d(16, 6)
     rng = np.random.default_rng(7)
     R = so3.exp_so3(rng.normal(size=3) * 0.01) @ p.R_gt
     t = p.t_gt + rng.normal(size=3) * 0.002

@@ -9,12 +9,12 @@ from oracle import closure, purse as op, snap
 from paper_2403_09990_gb300 import synthetic as syn
 
 
-def walked(kind, sampler, n=24):
+def walked(kind, sampler, n=24, lam=False):
     if kind == 0:
-        p = syn.purse_3d3d(8, 2)
+        p = syn.purse_3d3d_ellipsoidal(8, 2) if lam else syn.purse_3d3d(8, 2)
         prm = closure.preset_3d3d(n_iter=3, v0=0.02, rot_perturb=0.002, trans_perturb=0.001, perturb_units=1)
     else:
-        p = syn.purse_2d3d(16, 2)
+        p = syn.purse_2d3d_ellipsoidal(16, 2) if lam else syn.purse_2d3d(16, 2)
         prm = closure.preset_2d3d(n_iter=3, rot_perturb=0.002, trans_perturb=0.001, perturb_units=1)
     seeds = p.seed_pose()[None]
     st = closure.center_stats(p, seeds, prm)
@@ -29,9 +29,12 @@ def walked(kind, sampler, n=24):
     return p, prm, R, t, d
 
 
-@pytest.mark.parametrize("kind,sampler", [(0, 0), (0, 1), (1, 0), (1, 1)])
-def test_snapped_samples_are_on_the_boundary(kind, sampler):
-    p, prm, R, t, d = walked(kind, sampler)
+CASES = [(k, s, lam) for lam in (False, True) for k in (0, 1) for s in (0, 1)]
+
+
+@pytest.mark.parametrize("kind,sampler,lam", CASES)
+def test_snapped_samples_are_on_the_boundary(kind, sampler, lam):
+    p, prm, R, t, d = walked(kind, sampler, lam=lam)
     Rs, ts, tau, j = snap.snap(p, R, t, d, closure.step_ladder(prm), rotation=sampler == 0)
     assert (j >= 0).mean() > 0.8
     assert np.all(op.in_purse(p, Rs, ts))
@@ -42,9 +45,9 @@ def test_snapped_samples_are_on_the_boundary(kind, sampler):
     assert np.all(m.min(axis=1)[ok] == mj[ok])
 
 
-@pytest.mark.parametrize("kind,sampler", [(0, 0), (0, 1), (1, 0), (1, 1)])
-def test_snap_derivatives_match_finite_differences(kind, sampler):
-    p, prm, R, t, d = walked(kind, sampler, n=8)
+@pytest.mark.parametrize("kind,sampler,lam", CASES)
+def test_snap_derivatives_match_finite_differences(kind, sampler, lam):
+    p, prm, R, t, d = walked(kind, sampler, n=8, lam=lam)
     ladder = closure.step_ladder(prm)
     rot = sampler == 0
     Rs, ts, tau, j = snap.snap(p, R, t, d, ladder, rotation=rot)
@@ -55,7 +58,7 @@ def test_snap_derivatives_match_finite_differences(kind, sampler):
         jj = int(j[w])
         taus = []
         for sgn in (1, -1):
-            pr = syn.Purse(p.kind, p.model, p.obs, p.radii.copy(), p.K)
+            pr = syn.Purse(p.kind, p.model, p.obs, p.radii.copy(), p.K, lam=p.lam)
             pr.radii[jj] += sgn * h
             _, _, tw, jw = snap.snap(pr, R[w:w + 1], t[w:w + 1], d[w:w + 1], ladder, rotation=rot)
             taus.append(tw[0] if jw[0] == jj else np.nan)
@@ -68,7 +71,7 @@ def test_snap_derivatives_match_finite_differences(kind, sampler):
         for sgn in (1, -1):
             obs = p.obs.copy()
             obs[jj, c] += sgn * h
-            pr = syn.Purse(p.kind, p.model, obs, p.radii, p.K)
+            pr = syn.Purse(p.kind, p.model, obs, p.radii, p.K, lam=p.lam)
             _, _, tw, jw = snap.snap(pr, R[w:w + 1], t[w:w + 1], d[w:w + 1], ladder, rotation=rot)
             taus.append(tw[0] if jw[0] == jj else np.nan)
         fd_y = (taus[0] - taus[1]) / (2 * h)
