@@ -82,9 +82,10 @@ purse_status purse_create(int kind, int n, const double* model, const double* ob
  * constraints of a 3D-3D (Lambda_i 3 x 3) or 2D-3D (2 x 2, pixels) PURSE: lam (host, n x d x d,
  * row-major, each symmetric positive definite; PURSE_ERR_ARG otherwise); NULL restores the
  * identity.  Each Lambda_i is factored once on the host (Cholesky, Lambda = U^T U) and the factors
- * are kept on the device.  With noise matrices: purse_sample (without the snap), purse_sample_plain,
- * purse_ransag (points drawn in the noise ellipsoids, acceptance in that norm) and purse_dist mode 0
- * use them; purse_sample with d_snap, purse_eval and purse_dist modes 1-2 return PURSE_ERR_ARG.
+ * are kept on the device.  With noise matrices: purse_sample (with or without the snap),
+ * megb_backward, purse_sample_plain, purse_ransag (points drawn in the noise ellipsoids, acceptance
+ * in that norm) and purse_dist mode 0 use them; purse_eval and purse_dist modes 1-2 return
+ * PURSE_ERR_ARG.
  * Allocates device memory on the first call. */
 purse_status purse_set_noise(purse_t h, const double* lam);
 
@@ -160,10 +161,11 @@ purse_status purse_ransag(purse_t h, uint64_t seed, int n_trials, int max_seeds,
  * end, which replaces the sample in d_q / d_t.  Record per walk, 12 values in the sample precision:
  * j* (the active constraint, -1 if no ladder pose left S), ray kind (0 rotation, 1 translation),
  * ray direction (3), h'(tau*) = d|g_j*|/d tau, d|g_j*|/d y_j* (3; 2 used for 2D-3D), 3 unused.
- * Pass the records to megb_backward.  The snap takes the identity norm: with noise matrices
- * (purse_set_noise) d_snap must be NULL (PURSE_ERR_ARG otherwise); the walks themselves measure
- * every residual in the norm of eq. 4.  Regression PURSEs (purse_create_regression) take no snap
- * either; their walks evaluate the part of each hypothesis a perturbation moves (dS_R: the
+ * Pass the records to megb_backward.  The snap works in the constraints' norm: with noise
+ * matrices (purse_set_noise) h = |g_j*|_Lambda and d h / d y = Lambda g / h (eq. 4).  The ray's
+ * residuals are formed once per sample in FP64 (from the FP64 table and pose) and the bisection
+ * evaluates small increments in the walk precision; the snapped pose is formed in FP64.
+ * Regression PURSEs (purse_create_regression) take no snap; their walks evaluate the part of each hypothesis a perturbation moves (dS_R: the
  * translations, dS_t: the rotations) per perturbation and the other part once per iteration, and
  * the ladder's two factors once per rung and kept perturbation, so purse_last_evals counts those
  * half-constraint evaluations. */

@@ -349,7 +349,6 @@ purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const
                           purse_stream_t stream) {
   if (!h || !p) return arg_error("purse_sample: NULL handle or params");
   if (h->kind == PURSE_REG && d_snap) return arg_error("purse_sample: no boundary snap for regression PURSEs");
-  if (h->ell64 && d_snap) return arg_error("purse_sample: the boundary snap takes the identity norm (no noise matrices)");
   if (p->n_iter < 0) return arg_error("purse_sample: n_iter < 0");
   if (p->n_perturb < 1 || p->n_perturb > 256) return arg_error("purse_sample: n_perturb must be in [1, 256]");
   if (p->n_keep < 1 || p->n_keep > 32 || p->n_keep > p->n_perturb)
@@ -384,6 +383,7 @@ purse_status purse_sample(purse_t h, const purse_params* p, uint64_t seed, const
   a.table = p->precision == 0 ? (const void*)h->tables.f32 : (const void*)h->tables.f64;
   a.table64 = h->tables.f64;
   a.ell = !h->ell64 ? nullptr : p->precision == 0 ? (const void*)h->ell32 : (const void*)h->ell64;
+  a.ell64 = h->ell64;
   a.n = h->n;
   a.fx = h->K.fx, a.fy = h->K.fy, a.cx = h->K.cx, a.cy = h->K.cy;
   a.rho_max = h->rho_max;

@@ -87,6 +87,7 @@ struct WalkArgs {
   const void* table;
   const double* table64;  // the FP64 table (read by the boundary snap at either walk precision)
   const void* ell;  // noise factors U_i of eq. 4 (8 values per constraint, the table's precision) or NULL
+  const double* ell64;  // the same in FP64 (read by the boundary snap) or NULL
   int n;
   double fx, fy, cx, cy;
   double rho_max;  // largest model-point radius max_i |Z_i|

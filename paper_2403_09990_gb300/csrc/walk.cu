@@ -392,6 +392,7 @@ struct WalkCtx {
   T* out_snap;  // NULL: no snap; else kSnapStride values per walk
   const double* tab64;  // the PURSE's FP64 constraint table (global memory), read by the snap
   const double* kd;     // fx, fy, cx, cy in FP64 (global or parameter memory), read by the snap
+  const double* ell64;  // noise factors U_i in FP64 (8 per constraint) or NULL, read by the snap
   int* status;
 };
 
@@ -451,9 +452,17 @@ __device__ __forceinline__ bool pose_in_purse(const T4<T>* tab, int N, const M3<
 // FP64 table and pose, and the bisection steps only evaluate the affine model.  In FP32 a direct
 // evaluation would subtract projected coordinates of hundreds of px to get residuals of a few px,
 // and along the viewing ray of a 2D-3D PURSE that rounding moves the boundary by ~1e-6 m.
-template <typename T, int KIND>
+// U x for the upper-triangular noise factor U of a constraint (eq. 4): u = (u00 u01 u02 u11 u12 u22)
+// in 3D, (u00 u01 u11) in 2D.
+__device__ __forceinline__ V3<double> umul3(const double* u, const V3<double>& x) {
+  return V3<double>{u[0] * x.x + u[1] * x.y + u[2] * x.z, u[3] * x.y + u[4] * x.z, u[5] * x.z};
+}
+
+template <typename T, int KIND, bool LAM>
 __device__ __forceinline__ void snap_record(const WalkCtx<T>& c, int j, const Q4<double>& qs, const V3<double>& ts,
                                             const V3<double>& dir, int sampler, T* rec) {
+  // In FP64 from the FP64 table and snapped pose: h' = d|g|/d tau is a difference of terms tens of
+  // times larger when the ray grazes the boundary, and the adjoint divides by it.
   using D = double;
   const int N = c.N;
   const T4<D>* tab = reinterpret_cast<const T4<D>*>(c.tab64);
@@ -462,20 +471,34 @@ __device__ __forceinline__ void snap_record(const WalkCtx<T>& c, int j, const Q4
   const T4<D> mz = tab[j], ob = tab[N + j];
   const V3<D> RA = mul(R, V3<D>{mz.x, mz.y, mz.z});
   const V3<D> X = RA + ts;
+  // d|g|/de with e = -g: e / |e|, or Lambda e / |e|_Lambda = U^T (U e) / |U e| with noise matrices
   V3<D> wv, dy;  // d|g|/d(translation of the keypoint), d|g|/d y
+  const double* u = LAM ? c.ell64 + 8 * (size_t)j : nullptr;
   if (KIND == 1) {
     const D Px = fx * X.x + cx * X.z, Py = fy * X.y + cy * X.z, Pz = X.z;
     const D e0 = Px / Pz - ob.x, e1 = Py / Pz - ob.y;
-    const D nrm = sqrt(e0 * e0 + e1 * e1);
-    const D n0 = e0 / nrm, n1 = e1 / nrm;
+    D n0, n1;
+    if (LAM) {
+      const D f0 = u[0] * e0 + u[1] * e1, f1 = u[2] * e1;
+      const D nrm = sqrt(f0 * f0 + f1 * f1);
+      n0 = u[0] * f0 / nrm, n1 = (u[1] * f0 + u[2] * f1) / nrm;
+    } else {
+      const D nrm = sqrt(e0 * e0 + e1 * e1);
+      n0 = e0 / nrm, n1 = e1 / nrm;
+    }
     const V3<D> jn{n0 / Pz, n1 / Pz, -(Px * n0 + Py * n1) / (Pz * Pz)};
     wv = V3<D>{fx * jn.x, fy * jn.y, cx * jn.x + cy * jn.y + jn.z};
     dy = V3<D>{-n0, -n1, D(0)};
   } else {
     const V3<D> e = X - V3<D>{ob.x, ob.y, ob.z};
-    const D nrm = sqrt(dot(e, e));
-    wv = (D(1) / nrm) * e;
-    dy = (D(-1) / nrm) * e;
+    if (LAM) {
+      const V3<D> f = umul3(u, e);
+      const V3<D> g{u[0] * f.x, u[1] * f.x + u[3] * f.y, u[2] * f.x + u[4] * f.y + u[5] * f.z};
+      wv = (D(1) / sqrt(dot(f, f))) * g;
+    } else {
+      wv = (D(1) / sqrt(dot(e, e))) * e;
+    }
+    dy = D(-1) * wv;
   }
   const D dh = sampler == 0 ? dot(cross(RA, wv), dir) : dot(wv, dir);
   rec[0] = T(j), rec[1] = T(sampler), rec[2] = T(dir.x), rec[3] = T(dir.y), rec[4] = T(dir.z), rec[5] = T(dh);
@@ -508,20 +531,26 @@ __device__ __forceinline__ M3<T> exp_minus_identity(const V3<T>& k, T theta) {
 // Y_i = R* Z_i, so the residual is its value at tau = 0 (formed in FP64) plus an increment that
 // is small near the sample, evaluated in the walk precision.  (q64, t64, w64) the FP64 pose and
 // angular velocity, coef a free area of the warp's slab (10 N values).
-template <typename T, int KIND>
-__device__ __forceinline__ void snap_rotation(const WalkCtx<T>& c, const Q4<double>& q64, const V3<double>& t64,
-                                              const V3<double>& w64, T* coef, Q4<T>& q, int w, int lane) {
+template <typename T, int KIND, bool LAM>
+__device__ __forceinline__ void snap_rotation(const WalkCtx<T>& c, const T4<T>* tab_s, const Q4<double>& q64,
+                                              const V3<double>& t64, const V3<T>& wt, T* coef, Q4<T>& q, V3<T>& t,
+                                              int w, int lane) {
+  const V3<double> w64{double(wt.x), double(wt.y), double(wt.z)};
+  constexpr int kS = LAM ? 16 : 10;  // coefficients per constraint
   using D = double;
   const int N = c.N;
   const T4<D>* tab = reinterpret_cast<const T4<D>*>(c.tab64);
   const D fx = c.kd[0], fy = c.kd[1], cx = c.kd[2], cy = c.kd[3];
   const M3<D> R = qmat(q64);
-  // coef[10 i ..]: base residual (3: e_x, e_y, P_z or g), Y_i (3), cx - u, cy - v (2D-3D), r or r^2
+  // coef[kS i ..]: base residual (3: e_x, e_y, P_z or g), Y_i (3), cx - u, cy - v (2D-3D), r or r^2,
+  // then with noise matrices the factor U_i (3 or 6 entries)
   for (int i = lane; i < N; i += 32) {
     const T4<D> mz = tab[i], ob = tab[N + i];
     const V3<D> Y = mul(R, V3<D>{mz.x, mz.y, mz.z});
     const V3<D> X = Y + t64;
-    T* k = coef + 10 * i;
+    T* k = coef + kS * i;
+    if (LAM)
+      for (int e = 0; e < (KIND == 1 ? 3 : 6); ++e) k[9 + e] = T(c.ell64[8 * (size_t)i + e]);
     if (KIND == 1) {
       k[0] = T(fx * X.x + (cx - ob.x) * X.z), k[1] = T(fy * X.y + (cy - ob.y) * X.z), k[2] = T(X.z);
       k[6] = T(cx - ob.x), k[7] = T(cy - ob.y), k[8] = T(mz.w);
@@ -536,12 +565,17 @@ __device__ __forceinline__ void snap_rotation(const WalkCtx<T>& c, const Q4<doub
   const V3<T> ax = wn > 0 ? V3<T>{T(w64.x / wn), T(w64.y / wn), T(w64.z / wn)} : V3<T>{T(1), T(0), T(0)};
   const T fxt = T(fx), fyt = T(fy), wnt = T(wn);
   auto residual = [&](const M3<T>& M, int i, T& ex, T& ey, T& ez) {
-    const T* k = coef + 10 * i;
+    const T* k = coef + kS * i;
     const V3<T> dX = mul(M, V3<T>{k[3], k[4], k[5]});
     if (KIND == 1) {
       ex = k[0] + fxt * dX.x + k[6] * dX.z, ey = k[1] + fyt * dX.y + k[7] * dX.z, ez = k[2] + dX.z;
+      if (LAM) ex = k[9] * ex + k[10] * ey, ey = k[11] * ey;  // U (e_x, e_y); P_z untouched
     } else {
       ex = k[0] + dX.x, ey = k[1] + dX.y, ez = k[2] + dX.z;
+      if (LAM) {
+        const T gx = k[9] * ex + k[10] * ey + k[11] * ez, gy = k[12] * ey + k[13] * ez;
+        ez = k[14] * ez, ex = gx, ey = gy;
+      }
     }
   };
   auto inside = [&](T tau) {
@@ -550,7 +584,7 @@ __device__ __forceinline__ void snap_rotation(const WalkCtx<T>& c, const Q4<doub
     for (int i = lane; i < N; i += 32) {
       T ex, ey, ez;
       residual(M, i, ex, ey, ez);
-      const T r = coef[10 * i + 8];
+      const T r = coef[kS * i + 8];
       if (KIND == 1) {
         const T rz = r * ez;
         ok = ok && ez > T(0) && ex * ex + ey * ey - rz * rz <= T(0);
@@ -587,8 +621,10 @@ __device__ __forceinline__ void snap_rotation(const WalkCtx<T>& c, const Q4<doub
   // snapped rotation Exp(tau* omega) R* in FP64, rounded once
   const D th = D(lo) * wn, hs = sin(0.5 * th), hc = cos(0.5 * th);
   const Q4<D> inc = wn > 0 ? Q4<D>{hc, hs * w64.x / wn, hs * w64.y / wn, hs * w64.z / wn} : Q4<D>{1.0, 0.0, 0.0, 0.0};
-  const Q4<D> qs = qnormalize(qmul(inc, q64));
+  Q4<D> qs = qmul(inc, q64);  // both factors unit to FP64 rounding
+  if (qs.w < 0) qs = Q4<D>{-qs.w, -qs.x, -qs.y, -qs.z};
   q = Q4<T>{T(qs.w), T(qs.x), T(qs.y), T(qs.z)};
+  t = V3<T>{T(t64.x), T(t64.y), T(t64.z)};
   // active constraint at tau* from the same residuals
   const M3<T> M = exp_minus_identity(ax, lo * wnt);
   double bm = INFINITY;
@@ -596,22 +632,24 @@ __device__ __forceinline__ void snap_rotation(const WalkCtx<T>& c, const Q4<doub
   for (int i = lane; i < N; i += 32) {
     T ex, ey, ez;
     residual(M, i, ex, ey, ez);
-    const double r = double(coef[10 * i + 8]);
+    const double r = double(coef[kS * i + 8]);
     const double m = KIND == 1 ? r - sqrt(double(ex) * ex + double(ey) * ey) / double(ez)
                                : sqrt(r) - sqrt(double(ex) * ex + double(ey) * ey + double(ez) * ez);
     if (m < bm) bm = m, bi = i;
   }
   const int j = warp_argmin(bm, bi);
-  if (lane == 0) snap_record<T, KIND>(c, j, qs, t64, w64, 0, rec);
+  if (lane == 0) snap_record<T, KIND, LAM>(c, j, qs, t64, w64, 0, rec);
   __syncwarp();
 }
 
 // Translation ray (R*, t* + tau v) through the affine residuals; (q64, t64, v64) the FP64 pose and
 // direction, coef a free area of the warp's slab (7 N values).  The snapped translation is formed
 // in FP64 and rounded once.
-template <typename T, int KIND>
-__device__ __forceinline__ void snap_translation(const WalkCtx<T>& c, const Q4<double>& q64, const V3<double>& t64,
-                                                 const V3<double>& v64, T* coef, V3<T>& t, int w, int lane) {
+template <typename T, int KIND, bool LAM>
+__device__ __forceinline__ void snap_translation(const WalkCtx<T>& c, const T4<T>* tab_s, const Q4<double>& q64,
+                                                 const V3<double>& t64, const V3<T>& vt, T* coef, Q4<T>& q,
+                                                 V3<T>& t, int w, int lane) {
+  const V3<double> v64{double(vt.x), double(vt.y), double(vt.z)};
   using D = double;
   const int N = c.N;
   const T4<D>* tab = reinterpret_cast<const T4<D>*>(c.tab64);
@@ -622,14 +660,23 @@ __device__ __forceinline__ void snap_translation(const WalkCtx<T>& c, const Q4<d
     const T4<D> mz = tab[i], ob = tab[N + i];
     const V3<D> X = mul(R, V3<D>{mz.x, mz.y, mz.z}) + t64;
     T* k = coef + 7 * i;
+    const double* u = LAM ? c.ell64 + 8 * (size_t)i : nullptr;
     if (KIND == 1) {
-      // e = (fx X_x + (cx - u) X_z, fy X_y + (cy - v) X_z), P_z = X_z
-      k[0] = T(fx * X.x + (cx - ob.x) * X.z), k[1] = T(fy * X.y + (cy - ob.y) * X.z), k[2] = T(X.z);
-      k[3] = T(fx * v64.x + (cx - ob.x) * v64.z), k[4] = T(fy * v64.y + (cy - ob.y) * v64.z), k[5] = T(v64.z);
+      // e = (fx X_x + (cx - u) X_z, fy X_y + (cy - v) X_z), P_z = X_z; with noise matrices U e
+      D e0 = fx * X.x + (cx - ob.x) * X.z, e1 = fy * X.y + (cy - ob.y) * X.z;
+      D b0 = fx * v64.x + (cx - ob.x) * v64.z, b1 = fy * v64.y + (cy - ob.y) * v64.z;
+      if (LAM) {
+        e0 = u[0] * e0 + u[1] * e1, e1 = u[2] * e1;
+        b0 = u[0] * b0 + u[1] * b1, b1 = u[2] * b1;
+      }
+      k[0] = T(e0), k[1] = T(e1), k[2] = T(X.z);
+      k[3] = T(b0), k[4] = T(b1), k[5] = T(v64.z);
       k[6] = T(mz.w);
     } else {
-      k[0] = T(X.x - ob.x), k[1] = T(X.y - ob.y), k[2] = T(X.z - ob.z);
-      k[3] = T(v64.x), k[4] = T(v64.y), k[5] = T(v64.z);
+      V3<D> g0 = X - V3<D>{ob.x, ob.y, ob.z}, g1 = v64;
+      if (LAM) g0 = umul3(u, g0), g1 = umul3(u, g1);
+      k[0] = T(g0.x), k[1] = T(g0.y), k[2] = T(g0.z);
+      k[3] = T(g1.x), k[4] = T(g1.y), k[5] = T(g1.z);
       k[6] = T(ob.w);
     }
   }
@@ -673,6 +720,7 @@ __device__ __forceinline__ void snap_translation(const WalkCtx<T>& c, const Q4<d
   }
   const V3<D> ts{t64.x + D(lo) * v64.x, t64.y + D(lo) * v64.y, t64.z + D(lo) * v64.z};
   t = V3<T>{T(ts.x), T(ts.y), T(ts.z)};
+  q = Q4<T>{T(q64.w), T(q64.x), T(q64.y), T(q64.z)};
   // active constraint at tau* from the affine model (margins r - |e| / P_z, or r - |g|)
   double bm = INFINITY;
   int bi = 0x7FFFFFFF;
@@ -684,7 +732,7 @@ __device__ __forceinline__ void snap_translation(const WalkCtx<T>& c, const Q4<d
     if (m < bm) bm = m, bi = i;
   }
   const int j = warp_argmin(bm, bi);
-  if (lane == 0) snap_record<T, KIND>(c, j, q64, ts, v64, 1, rec);
+  if (lane == 0) snap_record<T, KIND, LAM>(c, j, q64, ts, v64, 1, rec);
   __syncwarp();
 }
 
@@ -715,28 +763,51 @@ __device__ __forceinline__ DF df_dot4(float a0, DF b0, float a1, DF b1, float a2
   return quick_two_sum(s3.h, lo);
 }
 
-// One move of an FP32 walk's pose, p (x) q and t + dt, in double-float on lane 0.  p is a unit
-// quaternion to FP32 rounding, so |p (x) q|^2 = 1 + d with |d| ~ 1e-7, and q (1 - d/2) renormalises
-// to ~d^2; the sign keeps w >= 0.  F: floats of Slab::S.
-__device__ __forceinline__ void df_move(float* F, float pw, float px, float py, float pz, float dx, float dy,
+// One move of an FP32 walk's pose, p (x) q and t + dt, in double-float, spread over the warp: lane
+// k < 4 forms quaternion component k, lane 4 + k translation component k.  p is a unit quaternion to
+// FP32 rounding, so |p (x) q|^2 = 1 + d with |d| ~ 1e-7, and q (1 - d/2) renormalises to ~d^2 (the
+// squared norm is summed over lanes 0-3 with two shuffles); the sign keeps w >= 0.  F: floats of
+// Slab::S, read by every lane before any lane writes.
+__device__ __forceinline__ void df_move(float* F, int lane, float pw, float px, float py, float pz, float dx, float dy,
                                         float dz) {
   const DF qw{F[0], F[4]}, qx{F[1], F[5]}, qy{F[2], F[6]}, qz{F[3], F[7]};
-  DF r[4] = {df_dot4(pw, qw, -px, qx, -py, qy, -pz, qz), df_dot4(pw, qx, px, qw, py, qz, -pz, qy),
-             df_dot4(pw, qy, py, qw, pz, qx, -px, qz), df_dot4(pw, qz, pz, qw, px, qy, -py, qx)};
-  const DF n2 = df_dot4(r[0].h, r[0], r[1].h, r[1], r[2].h, r[2], r[3].h, r[3]);
-  const float d = (n2.h - 1.0f) + (n2.l + (r[0].h * r[0].l + r[1].h * r[1].l + r[2].h * r[2].l + r[3].h * r[3].l));
-  const float sg = r[0].h < 0.0f ? -1.0f : 1.0f;
+  // component lane of p (x) q: w = pw qw - px qx - py qy - pz qz, x = pw qx + px qw + py qz - pz qy,
+  // y = pw qy + py qw + pz qx - px qz, z = pw qz + pz qw + px qy - py qx
+  const int k = lane & 3;
+  const float a1 = k == 0 ? -px : k == 1 ? px : k == 2 ? py : pz;
+  const float a2 = k == 0 ? -py : k == 1 ? py : k == 2 ? pz : px;
+  const float a3 = k == 0 ? -pz : k == 1 ? -pz : k == 2 ? -px : -py;
+  const DF b0 = k == 0 ? qw : k == 1 ? qx : k == 2 ? qy : qz;
+  const DF b1 = k == 0 ? qx : qw;
+  const DF b2 = k == 0 ? qy : k == 1 ? qz : k == 2 ? qx : qy;
+  const DF b3 = k == 0 ? qz : k == 1 ? qy : k == 2 ? qz : qx;
+  DF r = df_dot4(pw, b0, a1, b1, a2, b2, a3, b3);
+  if (lane >= 4) r = DF{0.0f, 0.0f};
+  // |r|^2 over lanes 0-3: h^2 exactly (two_prod) plus 2 h l
+  DF sq = two_prod(r.h, r.h);
+  float lo = sq.l + 2.0f * r.h * r.l;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const DF v = quick_two_sum(r[k].h, r[k].l - 0.5f * d * r[k].h);
-    F[k] = sg * v.h, F[4 + k] = sg * v.l;
+  for (int o = 1; o <= 2; o <<= 1) {
+    const float oh = __shfl_xor_sync(kFullMask, sq.h, o), ol = __shfl_xor_sync(kFullMask, lo, o);
+    const DF t = two_sum(sq.h, oh);
+    sq.h = t.h, lo = lo + ol + t.l;
   }
-  const float dt[3] = {dx, dy, dz};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const DF s = two_sum(F[8 + k], dt[k]);
-    const DF v = quick_two_sum(s.h, s.l + F[11 + k]);
-    F[8 + k] = v.h, F[11 + k] = v.l;
+  const float d = (sq.h - 1.0f) + lo;
+  const float sg = __shfl_sync(kFullMask, r.h, 0) < 0.0f ? -1.0f : 1.0f;
+  float th = 0.0f, tl = 0.0f;
+  if (lane >= 4 && lane < 7) {
+    const int c = lane - 4;
+    const float dt = c == 0 ? dx : c == 1 ? dy : dz;
+    const DF s = two_sum(F[8 + c], dt);
+    const DF v = quick_two_sum(s.h, s.l + F[11 + c]);
+    th = v.h, tl = v.l;
+  }
+  __syncwarp();
+  if (lane < 4) {
+    const DF v = quick_two_sum(r.h, r.l - 0.5f * d * r.h);
+    F[lane] = sg * v.h, F[4 + lane] = sg * v.l;
+  } else if (lane < 7) {
+    F[8 + lane - 4] = th, F[11 + lane - 4] = tl;
   }
 }
 
@@ -810,14 +881,17 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
   Q4<T> q;
   V3<T> t;
   V3<T> vel;
-  // FP32 walks carry their pose in double-float pairs in the slab (and the start velocity in FP64):
-  // lane 0 applies each move there and every lane takes the hi parts.  Repeated FP32 pose updates
-  // would accumulate ~1e-7 rad per move, and along the viewing ray of a 2D-3D PURSE that moves the
-  // boundary the walk reaches by ~1e-6 m.  (FP64 arithmetic would do, but one FP64 instruction of
-  // one lane occupies the FP64 unit of this part far longer than the ~240 FP32 operations of a move.)
+  // FP32 walks whose samples are snapped to the boundary carry their pose in double-float pairs in the
+  // slab: the warp applies each move there (lanes 0-6, df_move) and every lane takes the hi parts.
+  // Repeated FP32 pose updates accumulate ~1e-7 rad per move, and the snap places the sample where
+  // the ray from that pose meets the boundary -- along the viewing ray of a 2D-3D PURSE ~1e-6 m off.
+  // Without the snap a sample is an interior point chosen by the walk's discrete decisions and the
+  // FP32 pose is kept (the double-float moves cost ~9 % of a short batch walk).  (FP64 arithmetic
+  // would do, but one FP64 instruction of one lane occupies this part's FP64 unit far longer.)
   constexpr bool kState64 = sizeof(T) == 4;
+  const bool df = kState64 && c.out_snap != nullptr;
   walk_start<T, SAMPLER>(c, w, q, t, vel);
-  if (kState64 && lane == 0) {
+  if (df && lane == 0) {
     const float* f = reinterpret_cast<const float*>(c.seed_data + (size_t)(w % c.s0) * kSeedStride + kSeedFloats);
     float* F = reinterpret_cast<float*>(sl.S);
     for (int k = 0; k < 14; ++k) F[k] = f[k];
@@ -1062,16 +1136,14 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
     moved = m0 >= 0;
     if (m0 >= 0) {
       const T4<T> pj = sl.P[sl.J[k0]];
-      if constexpr (kState64) {
+      if (df) {
         float* F = reinterpret_cast<float*>(sl.S);
-        if (lane == 0) {
-          if (SAMPLER == 0) {
-            const T4<T> e = sl.E[4 * m0];  // (w, x, y, z) of E_m0
-            df_move(F, e.x, e.y, e.z, e.w, pj.x, pj.y, pj.z);
-          } else {
-            const T4<T> sv = sl.E[4 * m0];  // gamma^m0 v
-            df_move(F, pj.x, pj.y, pj.z, pj.w, sv.x, sv.y, sv.z);
-          }
+        if (SAMPLER == 0) {
+          const T4<T> e = sl.E[4 * m0];  // (w, x, y, z) of E_m0
+          df_move(F, lane, e.x, e.y, e.z, e.w, pj.x, pj.y, pj.z);
+        } else {
+          const T4<T> sv = sl.E[4 * m0];  // gamma^m0 v
+          df_move(F, lane, pj.x, pj.y, pj.z, pj.w, sv.x, sv.y, sv.z);
         }
         __syncwarp();
         q = Q4<T>{F[0], F[1], F[2], F[3]};
@@ -1096,25 +1168,24 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
   }
 
   // ---- optional boundary snap (for the adjoint), then a8: emit
-  if constexpr (!LAM) {  // the snap takes the identity norm (the host rejects it with noise matrices)
+  {
     if (c.out_snap) {
+      // the ray starts from the pose in FP64 (the double-float state of FP32 walks) and follows the
+      // walk's velocity in T (its rounding moves the snapped point by ~1e-7 of the step)
       Q4<double> q64;
-      V3<double> t64, v64;
+      V3<double> t64;
       if constexpr (kState64) {
         const float* F = reinterpret_cast<const float*>(sl.S);
-        q64 = qnormalize(Q4<double>{double(F[0]) + F[4], double(F[1]) + F[5], double(F[2]) + F[6],
-                                    double(F[3]) + F[7]});
+        q64 = Q4<double>{double(F[0]) + F[4], double(F[1]) + F[5], double(F[2]) + F[6], double(F[3]) + F[7]};
         t64 = V3<double>{double(F[8]) + F[11], double(F[9]) + F[12], double(F[10]) + F[13]};
-        v64 = start_velocity64<T, SAMPLER>(c, w);
       } else {
-        v64 = start_velocity64<T, SAMPLER>(c, w);
         q64 = Q4<double>{double(q.w), double(q.x), double(q.y), double(q.z)};
         t64 = V3<double>{double(t.x), double(t.y), double(t.z)};
       }
       if constexpr (SAMPLER == 0)
-        snap_rotation<T, KIND>(c, q64, t64, v64, reinterpret_cast<T*>(sl.D), q, w, lane);
+        snap_rotation<T, KIND, LAM>(c, tab, q64, t64, vel, reinterpret_cast<T*>(sl.D), q, t, w, lane);
       else
-        snap_translation<T, KIND>(c, q64, t64, v64, reinterpret_cast<T*>(sl.D), t, w, lane);
+        snap_translation<T, KIND, LAM>(c, tab, q64, t64, vel, reinterpret_cast<T*>(sl.D), q, t, w, lane);
     }
   }
   if (lane == 0) {
@@ -1179,7 +1250,7 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
   c.out_q = reinterpret_cast<T*>(a.out_q), c.out_t = reinterpret_cast<T*>(a.out_t);
   c.trace = a.trace, c.status = a.status;
   c.out_snap = reinterpret_cast<T*>(a.out_snap);
-  c.tab64 = a.table64, c.kd = &a.fx;
+  c.tab64 = a.table64, c.kd = &a.fx, c.ell64 = a.ell64;
   const RkParam rk{a};
   unsigned long long evals = 0;
   const int nw = blockDim.x >> 5;  // warps per block (fewer than kWalkWarps for large tables)
@@ -1454,7 +1525,7 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
   c.out_q = reinterpret_cast<T*>(a.out_q), c.out_t = reinterpret_cast<T*>(a.out_t);
   c.trace = a.trace, c.status = a.status;
   c.out_snap = nullptr;
-  c.tab64 = nullptr, c.kd = nullptr;
+  c.tab64 = nullptr, c.kd = nullptr, c.ell64 = nullptr;
   const RkParam rk{a};
   unsigned long long evals = 0;
   const int nw = blockDim.x >> 5;
@@ -1526,7 +1597,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2)
         c.st = b.stats + p, c.seed_data = b.seed_data + (size_t)p * kSeedStride, c.s0 = 1;
         c.key0 = (uint32_t)key, c.key1 = (uint32_t)(key >> 32);
         c.trace = nullptr, c.status = b.status;
-        c.tab64 = b.table64 + 4 * (size_t)in.table_off, c.kd = &b.info[p].fx;
+        c.tab64 = b.table64 + 4 * (size_t)in.table_off, c.kd = &b.info[p].fx, c.ell64 = nullptr;
         sl = carve<float>(slab_base, c.N, c.NP, c.NT);
         cur = p;
         __syncwarp();

@@ -131,20 +131,29 @@ def test_ellipsoidal_octahedron_translation_ball_on_gpu():
     assert d <= dstar * (1 + 1e-9) and d >= 0.97 * dstar, (d, dstar)
 
 
-def test_noise_matrix_rules():
+def test_noise_matrix_rules_and_identity_matrices_reproduce_the_identity_norm():
+    """Lambda_i = I through the noise-matrix kernels (walks and boundary snap) gives the samples and
+    snap records of the identity norm: U = I multiplies by one and adds zero, exactly."""
     p = syn.purse_3d3d(8, 1)
+    prm = closure.preset_3d3d(n_iter=4, v0=0.02, rot_perturb=0.002, trans_perturb=0.002, perturb_units=1)
+    W = 512
     with P.Purse(p) as h:
         bad = np.repeat(np.diag([1.0, -1.0, 1.0])[None], 8, axis=0)
         with pytest.raises(P.PurseError):
             P.purse_set_noise(h.h, bad)
-        P.purse_set_noise(h.h, np.repeat(np.eye(3)[None], 8, axis=0))
         sd = to_dev(p.seed_pose()[None])
-        q = torch.empty((4, 4), dtype=torch.float32, device="cuda")
-        t = torch.empty((4, 3), dtype=torch.float32, device="cuda")
-        snap = torch.empty((4, 12), dtype=torch.float32, device="cuda")
-        with pytest.raises(P.PurseError):     # the snap takes the identity norm
-            P.purse_sample(h.h, params_from(closure.preset_3d3d(), 0, 0), 1, sd, 1, 4, q, t, snap=snap)
-        P.purse_sample(h.h, params_from(closure.preset_3d3d(), 0, 0), 1, sd, 1, 4, q, t)
-        P.purse_set_noise(h.h, None)           # back to the identity: the snap is served again
-        P.purse_sample(h.h, params_from(closure.preset_3d3d(), 0, 0), 1, sd, 1, 4, q, t, snap=snap)
-        P.purse_sync(h.h)
+        outs = {}
+        for lam in (None, np.repeat(np.eye(3)[None], 8, axis=0)):
+            P.purse_set_noise(h.h, lam)
+            for sampler in (0, 1):
+                q = torch.empty((W, 4), dtype=torch.float32, device="cuda")
+                t = torch.empty((W, 3), dtype=torch.float32, device="cuda")
+                snap = torch.full((W, 12), np.nan, dtype=torch.float32, device="cuda")
+                P.purse_sample(h.h, params_from(prm, sampler, 0), 3, sd, 1, W, q, t, snap=snap)
+                P.purse_sync(h.h)
+                outs[(lam is None, sampler)] = (q.cpu().numpy(), t.cpu().numpy(), snap.cpu().numpy())
+        for sampler in (0, 1):
+            a, b = outs[(True, sampler)], outs[(False, sampler)]
+            assert (a[2][:, 0] >= 0).mean() > 0.5
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y), (sampler, np.abs(x - y).max())
