@@ -881,14 +881,15 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
   Q4<T> q;
   V3<T> t;
   V3<T> vel;
-  // FP32 walks whose samples are snapped to the boundary carry their pose in double-float pairs in the
-  // slab: the warp applies each move there (lanes 0-6, df_move) and every lane takes the hi parts.
-  // Repeated FP32 pose updates accumulate ~1e-7 rad per move, and the snap places the sample where
-  // the ray from that pose meets the boundary -- along the viewing ray of a 2D-3D PURSE ~1e-6 m off.
-  // Without the snap a sample is an interior point chosen by the walk's discrete decisions and the
-  // FP32 pose is kept (the double-float moves cost ~9 % of a short batch walk).  (FP64 arithmetic
+  // FP32 2D-3D walks whose samples are snapped to the boundary carry their pose in double-float pairs
+  // in the slab: the warp applies each move there (lanes 0-6, df_move) and every lane takes the hi
+  // parts.  Repeated FP32 pose updates accumulate ~1e-7 rad per move, and the snap places the sample
+  // where the ray from that pose meets the boundary -- along the viewing ray of a 2D-3D PURSE ~1e-6 m
+  // off.  A 3D-3D PURSE has no such long axis (the same error moves its snapped samples by ~1e-7 m),
+  // and without the snap a sample is an interior point chosen by the walk's discrete decisions, so
+  // those walks keep the FP32 pose (the double-float moves cost ~9 % of a short batch walk).  (FP64 arithmetic
   // would do, but one FP64 instruction of one lane occupies this part's FP64 unit far longer.)
-  constexpr bool kState64 = sizeof(T) == 4;
+  constexpr bool kState64 = sizeof(T) == 4 && KIND == 1;
   const bool df = kState64 && c.out_snap != nullptr;
   walk_start<T, SAMPLER>(c, w, q, t, vel);
   if (df && lane == 0) {
