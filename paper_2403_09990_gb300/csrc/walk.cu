@@ -337,39 +337,54 @@ __device__ __forceinline__ void top_k(const Slab<T>& sl, int NP, int K, int lane
   }
 }
 
-// in_purse of one ladder chunk (one candidate per lane): one constraint pair (two constraints on the
-// paired lanes) at a time, a warp vote after each pair leaves the chunk once every candidate has
-// violated a constraint.  The constraints come in ascending margin at the current pose, so most
-// candidates die on the first pairs; a vote per pair measured faster than one per two or more.
+// in_purse of one ladder candidate against constraint pair Lq (two constraints on the paired
+// lanes): the division-free value c (<= 0 inside) of both halves folded into the running maximum
+// cmax, and for 2D-3D (Z) P_z into the running minimum zmin.
+template <typename T, int KIND, bool Z, bool LAM>
+__device__ __forceinline__ void ladder_pair(const P2<T>* Lq, const P2<T> (&M2)[9], P2<T> bx, P2<T> by, P2<T> bz,
+                                            P2<T>& cmax, P2<T>& zmin) {
+  using T2 = P2<T>;
+  const T2 yx = Lq[0], yy = Lq[1], yz = Lq[2], o3 = Lq[3], o4 = Lq[4], o5 = Lq[5];
+  const T2 Px = fma2(M2[0], yx, fma2(M2[1], yy, fma2(M2[2], yz, bx)));
+  const T2 Py = fma2(M2[3], yx, fma2(M2[4], yy, fma2(M2[5], yz, by)));
+  const T2 Pz = fma2(M2[6], yx, fma2(M2[7], yy, fma2(M2[8], yz, bz)));
+  T2 c;
+  if (KIND == 1) {
+    T2 ex = fma2(o3, Pz, Px), ey = fma2(o4, Pz, Py);
+    if constexpr (LAM) ex = fma2(Lq[9], ey, mul2(Lq[8], ex)), ey = mul2(Lq[10], ey);
+    c = fma2(o5, mul2(Pz, Pz), fma2(ey, ey, mul2(ex, ex)));
+    if (Z) zmin = min2(zmin, Pz);
+  } else {
+    T2 ex = add2(Px, o3), ey = add2(Py, o4), ez = add2(Pz, o5);
+    if constexpr (LAM) {
+      const T2 gx = fma2(Lq[10], ez, fma2(Lq[9], ey, mul2(Lq[8], ex)));
+      const T2 gy = fma2(Lq[12], ez, mul2(Lq[11], ey));
+      ez = mul2(Lq[13], ez), ex = gx, ey = gy;
+    }
+    c = add2(fma2(ez, ez, fma2(ey, ey, mul2(ex, ex))), Lq[6]);
+  }
+  cmax = max2(cmax, c);
+}
+
+// A candidate survives the pairs seen so far while every value is <= 0 (and, 2D-3D, every P_z > 0).
+template <typename T, int KIND, bool Z>
+__device__ __forceinline__ bool ladder_ok(P2<T> cmax, P2<T> zmin) {
+  return fmax(cmax.x, cmax.y) <= T(0) && (KIND == 0 || !Z || fmin(zmin.x, zmin.y) > T(0));
+}
+
+// in_purse of one ladder chunk (one candidate per lane) over the constraint pairs q0 .. NQ - 1, a warp
+// vote after each pair leaving the chunk once every candidate has violated a constraint.  The
+// constraints come in ascending margin at the current pose, so most candidates die on the first
+// pairs; a vote per pair measured faster than one per two or more.  The result of a pair range
+// started after pairs that a candidate passed equals that of the whole range (running max / min).
 // Z: track the cheirality minimum (2D-3D; off when the caller has bounded P_z away from 0).
 template <typename T, int KIND, bool Z, bool LAM = false>
-__device__ __forceinline__ void ladder_scan(const P2<T>* L, int NQ, int N, const P2<T> (&M2)[9], P2<T> bx, P2<T> by,
-                                            P2<T> bz, P2<T>& cmax, P2<T>& zmin, bool& alive, int& done) {
-  using T2 = P2<T>;
-  for (int qi = 0; qi < NQ; ++qi) {
-    const T2* Lq = L + kRow<LAM> * qi;
-    const T2 yx = Lq[0], yy = Lq[1], yz = Lq[2], o3 = Lq[3], o4 = Lq[4], o5 = Lq[5];
-    const T2 Px = fma2(M2[0], yx, fma2(M2[1], yy, fma2(M2[2], yz, bx)));
-    const T2 Py = fma2(M2[3], yx, fma2(M2[4], yy, fma2(M2[5], yz, by)));
-    const T2 Pz = fma2(M2[6], yx, fma2(M2[7], yy, fma2(M2[8], yz, bz)));
-    T2 c;
-    if (KIND == 1) {
-      T2 ex = fma2(o3, Pz, Px), ey = fma2(o4, Pz, Py);
-      if constexpr (LAM) ex = fma2(Lq[9], ey, mul2(Lq[8], ex)), ey = mul2(Lq[10], ey);
-      c = fma2(o5, mul2(Pz, Pz), fma2(ey, ey, mul2(ex, ex)));
-      if (Z) zmin = min2(zmin, Pz);
-    } else {
-      T2 ex = add2(Px, o3), ey = add2(Py, o4), ez = add2(Pz, o5);
-      if constexpr (LAM) {
-        const T2 gx = fma2(Lq[10], ez, fma2(Lq[9], ey, mul2(Lq[8], ex)));
-        const T2 gy = fma2(Lq[12], ez, mul2(Lq[11], ey));
-        ez = mul2(Lq[13], ez), ex = gx, ey = gy;
-      }
-      c = add2(fma2(ez, ez, fma2(ey, ey, mul2(ex, ex))), Lq[6]);
-    }
-    cmax = max2(cmax, c);
+__device__ __forceinline__ void ladder_scan(const P2<T>* L, int q0, int NQ, int N, const P2<T> (&M2)[9], P2<T> bx,
+                                            P2<T> by, P2<T> bz, P2<T>& cmax, P2<T>& zmin, bool& alive, int& done) {
+  for (int qi = q0; qi < NQ; ++qi) {
+    ladder_pair<T, KIND, Z, LAM>(L + kRow<LAM> * qi, M2, bx, by, bz, cmax, zmin);
     done = min(N, 2 * (qi + 1));
-    alive = alive && fmax(cmax.x, cmax.y) <= T(0) && (KIND == 0 || !Z || fmin(zmin.x, zmin.y) > T(0));
+    alive = alive && ladder_ok<T, KIND, Z>(cmax, zmin);
     if (!__any_sync(kFullMask, alive)) break;
   }
 }
@@ -1091,11 +1106,14 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
 #pragma unroll
       for (int c = 0; c < 9; ++c) M2t[c] = dup(Ak.m[c]);
     }
-    for (int mb = 0; mb < NT; mb += mc) {
+    // Candidate of this lane in the chunk of rungs [mb, mb + mc): the rung's (K) E_m (dS_R) or the
+    // kept perturbation's (K) R_{j_k} (dS_t) as M2, and the candidate translation b (projected by K
+    // for 2D-3D).
+    auto chunk = [&](int mb, T2 (&M2)[9], V3<T>& bm) {
       const int m = mb + cm;
       const bool active = lane < ncand && m < NT;
       M3<T> M = M3<T>{{T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)}};
-      V3<T> bm = base;
+      bm = base;
       if (active) {
         if (SAMPLER == 0) {
           const T4<T> e0 = sl.E[4 * m + 1], e1 = sl.E[4 * m + 2], e2 = sl.E[4 * m + 3];
@@ -1106,25 +1124,53 @@ __device__ __forceinline__ void walk_one(const WalkCtx<T>& c, const RK& rk, int 
           bm = KIND == 1 ? V3<T>{fx * Tm.x + cx * Tm.z, fy * Tm.y + cy * Tm.z, Tm.z} : Tm;
         }
       }
-      T2 M2[9];
 #pragma unroll
       for (int c = 0; c < 9; ++c) M2[c] = SAMPLER == 1 ? M2t[c] : dup(M.m[c]);
-      const T2 bx = dup(bm.x), by = dup(bm.y), bz = dup(bm.z);
+      return active;
+    };
+    // First pass: constraint pair 0 (the two constraints of smallest margin at the current pose) for
+    // the candidates of every chunk, with no vote between chunks; on the walk workloads almost every
+    // candidate fails there.  Bit s of surv: this lane's candidate of chunk s passed it.
+    const int nch = (NT + mc - 1) / mc;
+    uint32_t surv = 0;
+#pragma unroll 2
+    for (int s = 0; s < nch; ++s) {
+      T2 M2[9];
+      V3<T> bm;
+      const bool active = chunk(s * mc, M2, bm);
       T2 cmax = dup(-inf<T>()), zmin = dup(inf<T>());
-      bool alive = active;
-      const int nact = K * min(mc, NT - mb);
-      int done = 0;
-      // 2D-3D: P_z >= (candidate translation)_z - max |Z_i| (the rotation rows are unit vectors);
-      // when that bound is positive for every candidate of the chunk, cheirality is not tracked
-      // (dS_R only: the dS_t kernel measured slower with the second ladder instantiation)
-      const bool zsafe = KIND == 1 && SAMPLER == 0 &&
-                         __all_sync(kFullMask, !active || bm.z - rho_max > T(1e-3) * (fabs(bm.z) + rho_max));
-      if (zsafe)
-        ladder_scan<T, KIND, false, LAM>(sl.L, NQ, N, M2, bx, by, bz, cmax, zmin, alive, done);
-      else
-        ladder_scan<T, KIND, true, LAM>(sl.L, NQ, N, M2, bx, by, bz, cmax, zmin, alive, done);
-      evals += (unsigned long long)nact * done;
-      const unsigned bal = __ballot_sync(kFullMask, alive);
+      ladder_pair<T, KIND, true, LAM>(sl.L, M2, dup(bm.x), dup(bm.y), dup(bm.z), cmax, zmin);
+      surv |= (uint32_t)(active && ladder_ok<T, KIND, true>(cmax, zmin)) << s;
+    }
+    evals += (unsigned long long)K * NT * min(N, 2);
+    // Then the chunks in rung order, each only if some candidate passed pair 0, over pairs 1 ..; the
+    // first chunk with a feasible candidate ends the ladder (the same m0, k0 as scanning every chunk
+    // over every pair: in_purse is a conjunction and each value is the same expression).
+    for (int s = 0; s < nch; ++s) {
+      unsigned bal = __ballot_sync(kFullMask, (surv >> s) & 1u);
+      if (!bal) continue;
+      const int mb = s * mc;
+      if (NQ > 1) {
+        T2 M2[9];
+        V3<T> bm;
+        const bool active = chunk(mb, M2, bm);
+        const T2 bx = dup(bm.x), by = dup(bm.y), bz = dup(bm.z);
+        T2 cmax = dup(-inf<T>()), zmin = dup(inf<T>());
+        bool alive = ((surv >> s) & 1u) != 0;
+        const int nact = K * min(mc, NT - mb);
+        int done = 2;
+        // 2D-3D: P_z >= (candidate translation)_z - max |Z_i| (the rotation rows are unit vectors);
+        // when that bound is positive for every candidate of the chunk, cheirality is not tracked
+        // (dS_R only: the dS_t kernel measured slower with the second ladder instantiation)
+        const bool zsafe = KIND == 1 && SAMPLER == 0 &&
+                           __all_sync(kFullMask, !active || bm.z - rho_max > T(1e-3) * (fabs(bm.z) + rho_max));
+        if (zsafe)
+          ladder_scan<T, KIND, false, LAM>(sl.L, 1, NQ, N, M2, bx, by, bz, cmax, zmin, alive, done);
+        else
+          ladder_scan<T, KIND, true, LAM>(sl.L, 1, NQ, N, M2, bx, by, bz, cmax, zmin, alive, done);
+        evals += (unsigned long long)nact * (done - 2);
+        bal = __ballot_sync(kFullMask, alive);
+      }
       if (bal) {
         const int l = __ffs(bal) - 1;
         m0 = mb + l / K;
