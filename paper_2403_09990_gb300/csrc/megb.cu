@@ -5,8 +5,9 @@
 //                C_k = SLERP(C_{k-1}, q_{f_k}, 1/k)
 //   translation: f_k = argmax_s |t_s - c_{k-1}|^2,  c_k = c_{k-1} + (t_f - c_{k-1}) / k
 // One launch per iteration: every block reduces its slice to a (key, index)
-// partial; the last block to finish (atomic ticket, no waiting) reduces the
-// partials and takes the step in FP64.  A final pass computes the radius from
+// partial (FP32 samples: one 64-bit atomic maximum per block; FP64 samples: an
+// array of partials); the last block to finish (atomic ticket, no waiting) takes
+// the farthest sample and the step in FP64.  A final pass computes the radius from
 // the farthest sample with an FP64 log map.  Ties go to the lowest index.
 #include <climits>
 #include <mutex>
@@ -24,6 +25,9 @@ struct MegbState {
   unsigned int counter[2];
   int fstar[2];       // farthest sample from the final centre (rotation, translation)
   unsigned int gen[2];  // iterations published by the persistent kernel
+  // FP32 samples: farthest (key bits, complement of the index) of the iteration so far, per ball and
+  // iteration parity; the block that takes the step reads and clears it
+  unsigned long long best[2][2];
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -64,6 +68,7 @@ __global__ void megb_init(const T* q, int nq, const T* t, int nt, MegbState* s) 
   s->c[3] = 0.0;
   s->counter[0] = s->counter[1] = 0;
   s->gen[0] = s->gen[1] = 0;
+  s->best[0][0] = s->best[0][1] = s->best[1][0] = s->best[1][1] = 0ull;
 }
 
 // Squared sine of half the geodesic distance between centre (cw, cv) and q.
@@ -135,7 +140,8 @@ __device__ __forceinline__ T sample_key(const T* __restrict__ x, int i, bool vec
 
 // One GGD iteration of a ball over this block's slice of the samples.  MODE 0: rotation ball, MODE 1:
 // translation ball.  k >= 1: GGD step k; k == 0: final radius.  Every block reduces its slice to a
-// (key, index) partial; the last block to take a ticket reduces the partials and takes the step in
+// (key, index) maximum -- FP32 samples: packed into one 64-bit atomic maximum; FP64 samples: a
+// partial per block -- and the last block to take a ticket takes the farthest sample and the step in
 // FP64 (its thread 0 writes the state).  Returns true in the block that took the step.  COHERENT:
 // the centre is read from L2 (the persistent kernel reads a centre written by another block in the
 // same launch).
@@ -215,7 +221,41 @@ __device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbSta
     const T key = sample_key<T, MODE>(x, i, vec, c0, c1, c2, c3);
     if (key > bkt) bkt = key, bi = i;
   }
-  double bk = (double)bkt;
+  double bk;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 keys are >= 0 (or never taken: NaN fails key > bkt), so their bit patterns order like the
+    // values; (key bits, complement of the index) packed in 64 bits is largest for the farthest
+    // sample, ties to the lowest index -- the rule of better(), reduced with integer operations only
+    // (each FP64 instruction of a warp occupies this part's FP64 unit for tens of cycles).  An empty
+    // thread packs 0, below every sample.
+    const bool has = bi != INT_MAX;
+    const uint32_t kb = has ? __float_as_uint(bkt) : 0u;
+    const uint32_t mk = __reduce_max_sync(kFullMask, kb);
+    const uint32_t mi = __reduce_max_sync(kFullMask, has && kb == mk ? ~(uint32_t)bi : 0u);
+    unsigned long long* wpk = reinterpret_cast<unsigned long long*>(wkey);
+    if (lane == 0) wpk[warp] = ((unsigned long long)mk << 32) | mi;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long b = wpk[0];
+      for (int w = 1; w < kMegbThreads / 32; ++w) b = wpk[w] > b ? wpk[w] : b;
+      unsigned long long* slot = &s->best[MODE][k & 1];
+      atomicMax(slot, b);
+      __threadfence();
+      const unsigned ticket = atomicAdd(&s->counter[MODE], 1u);
+      *last = ticket == (unsigned)nb - 1;
+      if (*last) {
+        __threadfence();
+        // every block's maximum is in (its atomicMax came before its ticket); clear the slot for the
+        // iteration after next
+        b = atomicExch(slot, 0ull);
+        bi = b == 0ull ? 0 : (int)~(uint32_t)b;
+      }
+    }
+    __syncthreads();
+    if (!*last) return false;
+    if (tid != 0) return true;
+  } else {
+  bk = (double)bkt;
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     const double ok = __shfl_xor_sync(kFullMask, bk, o);
@@ -254,6 +294,7 @@ __device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbSta
   if (tid != 0) return true;
   for (int w = 1; w < kMegbThreads / 32; ++w)
     if (better(wkey[w], widx[w], bk, bi)) bk = wkey[w], bi = widx[w];
+  }
   s->counter[MODE] = 0;
   auto ld = [](const double* p) { return COHERENT ? __ldcg(p) : *p; };
   if (MODE == 0) {
@@ -587,6 +628,7 @@ __global__ void megb_state_from_result(const double* result, MegbState* s) {
   s->c[3] = 0.0;
   s->counter[0] = s->counter[1] = 0;
   s->fstar[0] = s->fstar[1] = 0;
+  s->best[0][0] = s->best[0][1] = s->best[1][0] = s->best[1][1] = 0ull;
 }
 
 size_t megb_backward_scratch_bytes(int n_iters, int sm_count, int n) {
@@ -645,10 +687,10 @@ constexpr int kGgdBlockThreads = 512;
 
 template <typename T, int MODE>
 __device__ void ggd_block(const T* __restrict__ x, int n, int K, double* result, int32_t* f_out, int32_t* fstar, T* xs) {
+  static_assert(sizeof(T) == 4, "the packed reduction below takes FP32 keys");
   constexpr int D = MODE == 0 ? 4 : 3;
   __shared__ double c[4];
   __shared__ double wkey[kGgdBlockThreads / 32];
-  __shared__ int widx[kGgdBlockThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int k = tid; k < n * D; k += blockDim.x) xs[k] = x[k];
   if (tid == 0) {
@@ -675,18 +717,19 @@ __device__ void ggd_block(const T* __restrict__ x, int n, int K, double* result,
       }
       if (key > bkt) bkt = key, bi = i;
     }
-    double bk = (double)bkt;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const double ok = __shfl_xor_sync(kFullMask, bk, o);
-      const int oi = __shfl_xor_sync(kFullMask, bi, o);
-      if (better(ok, oi, bk, bi)) bk = ok, bi = oi;
-    }
-    if (lane == 0) wkey[warp] = bk, widx[warp] = bi;
+    // (key bits, complement of the index) in 64 bits, as in ggd_iter: the farthest sample with ties to
+    // the lowest index, reduced with integer operations only
+    const bool has = bi != INT_MAX;
+    const uint32_t kb = has ? __float_as_uint(float(bkt)) : 0u;
+    const uint32_t mk = __reduce_max_sync(kFullMask, kb);
+    const uint32_t mi = __reduce_max_sync(kFullMask, has && kb == mk ? ~(uint32_t)bi : 0u);
+    unsigned long long* wpk = reinterpret_cast<unsigned long long*>(wkey);
+    if (lane == 0) wpk[warp] = ((unsigned long long)mk << 32) | mi;
     __syncthreads();
     if (tid == 0) {
-      for (int w2 = 1; w2 < (int)(blockDim.x / 32); ++w2)
-        if (better(wkey[w2], widx[w2], bk, bi)) bk = wkey[w2], bi = widx[w2];
+      unsigned long long b = wpk[0];
+      for (int w2 = 1; w2 < (int)(blockDim.x / 32); ++w2) b = wpk[w2] > b ? wpk[w2] : b;
+      bi = b == 0ull ? 0 : (int)~(uint32_t)b;
       if (MODE == 0) {
         const T* qs = x + 4 * (size_t)bi;
         const Q4<double> cq{c[0], c[1], c[2], c[3]};
