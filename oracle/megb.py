@@ -10,6 +10,10 @@
   of Section II.
 * megb_translation: the Euclidean version (Badoiu-Clarkson,
   c_k = c_{k-1} + (t_far - c_{k-1}) / k).
+* megb_rotation_mean / megb_translation_mean: the same descents with the output
+  rule of Alg. 6 (the appendix's SDP-based descent): the centre is the
+  projection onto SO(3) of the sum of the last iterates (ten in the paper),
+  the translation centre the mean of the last iterates.
 * welzl_meb / meb_bruteforce: exact minimum enclosing ball in R^d.
 * meb_exact_translation / meb_exact_rotation: Step III as the paper states it
   (Section IV, Step III): the exact minimum enclosing ball of the translation
@@ -29,7 +33,7 @@ import itertools
 
 import numpy as np
 
-from .so3 import dist_quat, slerp
+from .so3 import R_from_quat, dist_quat, proj_so3, quat_from_R, slerp
 
 
 def canonical(q):
@@ -75,6 +79,30 @@ def megb_translation(ts, K: int):
         c = c + (ts[fk] - c) / k
     d = float(np.sqrt(((ts - c) ** 2).sum(axis=1)).max())
     return c, d, f
+
+
+def megb_rotation_mean(qs, K: int, n_last: int):
+    """GGD on SO(3) with the output rule of Alg. 6: K iterations as in megb_rotation, then the
+    centre R* = proj_SO3(sum of the rotation matrices of the last n_last iterates
+    C_{K-n_last+1} .. C_K; fewer when K + 1 < n_last, C_0 included), and D-hat the largest geodesic
+    distance from R*.  Returns (R* as a quaternion with w >= 0, D-hat, farthest sequence)."""
+    _, _, f = megb_rotation(qs, K)
+    Cs = megb_rotation_replay(qs, f)
+    M = sum(R_from_quat(c) for c in Cs[max(0, K - n_last + 1):])
+    C = canonical(quat_from_R(proj_so3(M)))
+    D = float(rotation_distances(C, canonical(qs)).max())
+    return C, D, f
+
+
+def megb_translation_mean(ts, K: int, n_last: int):
+    """Badoiu-Clarkson with the same output rule in R^3 (projection = identity): the mean of the
+    last n_last centres c_{K-n_last+1} .. c_K (c_0 included when K + 1 < n_last), and d-hat the
+    largest distance from it.  Returns (centre, d-hat, farthest sequence)."""
+    _, _, f = megb_translation(ts, K)
+    cs = megb_translation_replay(ts, f)
+    c = cs[max(0, K - n_last + 1):].mean(axis=0)
+    ts = np.asarray(ts, dtype=np.float64)
+    return c, float(np.sqrt(((ts - c) ** 2).sum(axis=1)).max()), f
 
 
 def megb_translation_replay(ts, f):

@@ -158,3 +158,55 @@ def test_exact_rotation_ball_sign_and_left_invariance():
     # never worse than the geodesic-descent ball by more than its (1 + 1/sqrt K) bound
     Cg, Dg, _ = megb.megb_rotation(qs, 400)
     assert D <= Dg * (1 + 1e-9) and Dg <= D * (1 + 1 / np.sqrt(400))
+
+
+def _random_quats(rng, n, spread):
+    v = rng.normal(size=(n, 3)) * spread
+    q = np.array([so3.quat_exp(x) for x in v])
+    return q * np.where(q[:, :1] < 0, -1.0, 1.0)
+
+
+def test_mean_output_rule_with_one_iterate_is_the_plain_descent():
+    rng = np.random.default_rng(5)
+    qs, ts = _random_quats(rng, 300, 0.2), rng.normal(size=(300, 3))
+    C, D, f = megb.megb_rotation(qs, 50)
+    Cm, Dm, fm = megb.megb_rotation_mean(qs, 50, 1)
+    assert np.array_equal(f, fm) and np.allclose(C, Cm, atol=1e-14) and abs(D - Dm) < 1e-14
+    c, d, g = megb.megb_translation(ts, 50)
+    cm, dm, gm = megb.megb_translation_mean(ts, 50, 1)
+    assert np.array_equal(g, gm) and np.allclose(c, cm, atol=1e-14) and abs(d - dm) < 1e-14
+
+
+def test_mean_output_rule_projection_equals_quaternion_eigenvector():
+    # proj_SO3(sum R(q_t)) maximises trace(R(p)^T sum R(q_t)) = sum (4 (p.q_t)^2 - 1) over unit p, so
+    # its quaternion is the principal eigenvector of sum q_t q_t^T (Horn's identity, no SVD)
+    rng = np.random.default_rng(6)
+    qs = _random_quats(rng, 500, 0.3)
+    K, n_last = 60, 10
+    C, D, f = megb.megb_rotation_mean(qs, K, n_last)
+    Cs = megb.megb_rotation_replay(qs, f)[K - n_last + 1:]
+    w, V = np.linalg.eigh(Cs.T @ Cs)
+    e = V[:, -1] * (1.0 if V[0, -1] >= 0 else -1.0)
+    assert np.abs(C - e).max() < 1e-12
+    assert abs(D - so3.dist_quat(C[None], megb.canonical(qs)).max()) < 1e-14
+    # an enclosing ball: at least half the largest pairwise distance
+    diam = max(so3.dist_quat(q[None], megb.canonical(qs)).max() for q in megb.canonical(qs)[:100])
+    assert D >= 0.5 * diam - 1e-12
+
+
+def test_mean_output_rule_two_samples_closed_form():
+    # two samples a, b: C_0 = a, C_1 = b, C_2 = their geodesic midpoint; the three are symmetric about
+    # the midpoint, so the mean of the last three is the midpoint and the radius half the distance
+    a = so3.quat_exp(np.array([0.3, -0.1, 0.2]))
+    b = so3.quat_exp(np.array([-0.2, 0.25, 0.05]))
+    qs = megb.canonical(np.stack([a, b]))
+    C, D, _ = megb.megb_rotation_mean(qs, 2, 3)
+    mid = megb.canonical(so3.slerp(qs[0], qs[1], 0.5))
+    th = so3.dist_quat(qs[0][None], qs[1][None])[0]
+    assert np.abs(C - mid).max() < 1e-13 and abs(D - 0.5 * th) < 1e-13
+    ts = np.array([[0.1, 0.2, 0.3], [-0.5, 0.4, 1.0]])
+    c, d, _ = megb.megb_translation_mean(ts, 2, 3)
+    assert np.abs(c - ts.mean(0)).max() < 1e-15 and abs(d - 0.5 * np.linalg.norm(ts[1] - ts[0])) < 1e-15
+    # more iterates requested than exist: all of C_0 .. C_K
+    c2, _, _ = megb.megb_translation_mean(ts, 2, 10)
+    assert np.abs(c2 - ts.mean(0)).max() < 1e-15
