@@ -206,6 +206,20 @@ purse_status megb_solve(purse_t h, int precision, int n_iters, const void* d_q, 
                         const void* d_t, int n_tr, double* d_result, int32_t* d_farthest,
                         purse_stream_t stream);
 
+/* megb_solve with the output rule of Alg. 6 (the appendix's SDP-based descent, whose listing
+ * returns the projection onto SO(3) of the sum of its last 10 iterates): the same K iterations and
+ * farthest samples, then the rotation centre is proj_SO3(sum of R(C_t), t = K - n_last + 1 .. K) --
+ * computed as the eigenvector of the largest eigenvalue of sum C_t C_t^T, the unit quaternion that
+ * maximises the same trace -- and the translation centre the mean of c_t over the same t; when
+ * K + 1 < n_last, all iterates C_0 .. C_K are used.  The radii are the largest distances from these
+ * centres (a final pass).  n_last = 1 gives megb_solve's result; n_last = 10 is the paper's rule.
+ * Arguments and d_result / d_farthest layouts as for megb_solve, plus n_last >= 1 (PURSE_ERR_ARG
+ * otherwise).  megb_backward differentiates megb_solve only: after a megb_solve_mean with
+ * n_last > 1 on the handle it returns PURSE_ERR_ARG until the next megb_solve. */
+purse_status megb_solve_mean(purse_t h, int precision, int n_iters, int n_last, const void* d_q,
+                             int n_rot, const void* d_t, int n_tr, double* d_result,
+                             int32_t* d_farthest, purse_stream_t stream);
+
 /* Reverse-mode derivative of the balls of megb_solve with respect to the PURSE observations y_i
  * and radii r_i (the paper has no adjoint; the samples come from the discrete walks of Alg. 3/5,
  * so they are differentiated through the boundary snap of purse_sample's d_snap records).

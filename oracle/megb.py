@@ -81,12 +81,14 @@ def megb_translation(ts, K: int):
     return c, d, f
 
 
-def megb_rotation_mean(qs, K: int, n_last: int):
+def megb_rotation_mean(qs, K: int, n_last: int, f=None):
     """GGD on SO(3) with the output rule of Alg. 6: K iterations as in megb_rotation, then the
     centre R* = proj_SO3(sum of the rotation matrices of the last n_last iterates
     C_{K-n_last+1} .. C_K; fewer when K + 1 < n_last, C_0 included), and D-hat the largest geodesic
-    distance from R*.  Returns (R* as a quaternion with w >= 0, D-hat, farthest sequence)."""
-    _, _, f = megb_rotation(qs, K)
+    distance from R*.  Returns (R* as a quaternion with w >= 0, D-hat, farthest sequence).
+    f: a farthest sequence to replay instead of the free run's (tests replay the GPU's)."""
+    if f is None:
+        _, _, f = megb_rotation(qs, K)
     Cs = megb_rotation_replay(qs, f)
     M = sum(R_from_quat(c) for c in Cs[max(0, K - n_last + 1):])
     C = canonical(quat_from_R(proj_so3(M)))
@@ -94,11 +96,12 @@ def megb_rotation_mean(qs, K: int, n_last: int):
     return C, D, f
 
 
-def megb_translation_mean(ts, K: int, n_last: int):
+def megb_translation_mean(ts, K: int, n_last: int, f=None):
     """Badoiu-Clarkson with the same output rule in R^3 (projection = identity): the mean of the
     last n_last centres c_{K-n_last+1} .. c_K (c_0 included when K + 1 < n_last), and d-hat the
-    largest distance from it.  Returns (centre, d-hat, farthest sequence)."""
-    _, _, f = megb_translation(ts, K)
+    largest distance from it.  Returns (centre, d-hat, farthest sequence); f as in megb_rotation_mean."""
+    if f is None:
+        _, _, f = megb_translation(ts, K)
     cs = megb_translation_replay(ts, f)
     c = cs[max(0, K - n_last + 1):].mean(axis=0)
     ts = np.asarray(ts, dtype=np.float64)

@@ -459,29 +459,44 @@ purse_status purse_last_evals(purse_t h, unsigned long long* evals, purse_stream
   return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_last_evals");
 }
 
-purse_status megb_solve(purse_t h, int precision, int n_iters, const void* d_q, int n_rot, const void* d_t, int n_tr,
-                        double* d_result, int32_t* d_farthest, purse_stream_t stream) {
-  if (!h) return arg_error("megb_solve: NULL handle");
-  if (precision != 0 && precision != 1) return arg_error("megb_solve: precision must be 0 or 1");
-  if (n_iters < 1 || n_iters > (1 << 20)) return arg_error("megb_solve: n_iters must be in [1, 2^20]");
-  if (n_rot < 0 || n_tr < 0) return arg_error("megb_solve: negative sample count");
+static purse_status megb_solve_impl(const char* fn, purse_t h, int precision, int n_iters, int n_last, const void* d_q,
+                                    int n_rot, const void* d_t, int n_tr, double* d_result, int32_t* d_farthest,
+                                    purse_stream_t stream) {
+  const std::string f(fn);
+  if (!h) return arg_error(f + ": NULL handle");
+  if (precision != 0 && precision != 1) return arg_error(f + ": precision must be 0 or 1");
+  if (n_iters < 1 || n_iters > (1 << 20)) return arg_error(f + ": n_iters must be in [1, 2^20]");
+  if (n_last < 1) return arg_error(f + ": n_last must be >= 1");
+  if (n_rot < 0 || n_tr < 0) return arg_error(f + ": negative sample count");
   if (n_rot > kMaxBallSamples || n_tr > kMaxBallSamples)
-    return arg_error("megb_solve: more than 2^31 - 2^21 samples (32-bit sample indices)");
-  if ((n_rot > 0 && !d_q) || (n_tr > 0 && !d_t) || !d_result) return arg_error("megb_solve: NULL buffer");
-  if (fault_at("launch")) return injected_fault("launch", "megb_solve");
+    return arg_error(f + ": more than 2^31 - 2^21 samples (32-bit sample indices)");
+  if ((n_rot > 0 && !d_q) || (n_tr > 0 && !d_t) || !d_result) return arg_error(f + ": NULL buffer");
+  if (fault_at("launch")) return injected_fault("launch", fn);
   const size_t need = megb_scratch_bytes(n_iters, h->sm_count);
   // the walk scratch (stats, seeds) is not needed any more once sampling is enqueued,
   // but megb keeps its own region after it so both can coexist on one stream
   purse_status s = ensure_scratch(h, need);
   if (s != PURSE_OK) return s;
   cudaError_t e = launch_megb(h, precision, n_iters, d_q, n_rot, d_t, n_tr, d_result, d_farthest, h->d_scratch,
-                              (cudaStream_t)stream);
-  if (e != cudaSuccess) return cuda_fail(e, "megb_solve");
+                              (cudaStream_t)stream, n_last);
+  if (e != cudaSuccess) return cuda_fail(e, fn);
   h->megb_iters = n_iters;
   h->megb_precision = precision;
   h->megb_q = d_q, h->megb_t = d_t;
   h->megb_nrot = n_rot, h->megb_ntr = n_tr;
+  h->megb_navg = n_last;
   return PURSE_OK;
+}
+
+purse_status megb_solve(purse_t h, int precision, int n_iters, const void* d_q, int n_rot, const void* d_t, int n_tr,
+                        double* d_result, int32_t* d_farthest, purse_stream_t stream) {
+  return megb_solve_impl("megb_solve", h, precision, n_iters, 1, d_q, n_rot, d_t, n_tr, d_result, d_farthest, stream);
+}
+
+purse_status megb_solve_mean(purse_t h, int precision, int n_iters, int n_last, const void* d_q, int n_rot,
+                             const void* d_t, int n_tr, double* d_result, int32_t* d_farthest, purse_stream_t stream) {
+  return megb_solve_impl("megb_solve_mean", h, precision, n_iters, n_last, d_q, n_rot, d_t, n_tr, d_result, d_farthest,
+                         stream);
 }
 
 purse_status megb_solve_exact(purse_t h, int precision, const void* d_q, int n_rot, const void* d_t, int n_tr,
@@ -505,6 +520,8 @@ purse_status megb_backward(purse_t h, int precision, int n_iters, const void* d_
                            const double* d_result, const double* d_grad_result, double* d_grad_obs,
                            double* d_grad_radii, purse_stream_t stream) {
   if (!h) return arg_error("megb_backward: NULL handle");
+  if (h->megb_navg != 1)
+    return arg_error("megb_backward: the last ball solve on this handle was megb_solve_mean (not differentiated)");
   if (precision != 0 && precision != 1) return arg_error("megb_backward: precision must be 0 or 1");
   if (n_iters < 1 || n_iters > (1 << 20)) return arg_error("megb_backward: n_iters must be in [1, 2^20]");
   if (n_rot < 0 || n_tr < 0) return arg_error("megb_backward: negative sample count");

@@ -129,6 +129,7 @@ struct purse_s {
   const void* megb_q = nullptr;
   const void* megb_t = nullptr;
   int megb_nrot = 0, megb_ntr = 0;
+  int megb_navg = 1;  // 1: the last solve returned C_K, c_K (megb_backward differentiates only that)
   int sm_count = 0;
 };
 
@@ -198,8 +199,10 @@ cudaError_t launch_eval(purse_t h, int precision, const void* d_poses, int n_pos
 cudaError_t launch_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t i, uint32_t w0, int n_streams,
                              int n_words, uint32_t* d_words, int32_t* d_lattice, int unit, cudaStream_t st);
 size_t megb_scratch_bytes(int n_iters, int sm_count);
+// navg > 1: the output rule of Alg. 6 (centre from the last navg iterates; megb_solve_mean)
 cudaError_t launch_megb(purse_t h, int precision, int n_iters, const void* d_q, int n_rot, const void* d_t,
-                        int n_tr, double* d_result, int32_t* d_farthest, void* scratch, cudaStream_t st);
+                        int n_tr, double* d_result, int32_t* d_farthest, void* scratch, cudaStream_t st,
+                        int navg = 1);
 size_t exact_scratch_bytes(int sm_count);
 cudaError_t launch_megb_exact(purse_t h, int precision, const void* d_q, long n_rot, const void* d_t, long n_tr,
                               const double* d_ref, double* d_result, void* scratch, cudaStream_t st);

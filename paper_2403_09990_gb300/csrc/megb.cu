@@ -28,6 +28,9 @@ struct MegbState {
   // FP32 samples: farthest (key bits, complement of the index) of the iteration so far, per ball and
   // iteration parity; the block that takes the step reads and clears it
   unsigned long long best[2][2];
+  // output rule of Alg. 6 (megb_solve_mean): sums over the last iterates -- of q q^T (upper triangle of
+  // the 4 x 4 matrix, 10 values) for the rotation ball and of c for the translation ball
+  double acc[13];
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -69,6 +72,7 @@ __global__ void megb_init(const T* q, int nq, const T* t, int nt, MegbState* s) 
   s->counter[0] = s->counter[1] = 0;
   s->gen[0] = s->gen[1] = 0;
   s->best[0][0] = s->best[0][1] = s->best[1][0] = s->best[1][1] = 0ull;
+  for (int i = 0; i < 13; ++i) s->acc[i] = 0.0;
 }
 
 // Squared sine of half the geodesic distance between centre (cw, cv) and q.
@@ -115,6 +119,61 @@ __device__ __forceinline__ Q4<double> slerp_step(const Q4<double>& c, const RelR
   return o;
 }
 
+// Output rule of Alg. 6 (the appendix's descent): the centre is the projection onto SO(3) of the sum
+// of the rotation matrices of the last navg iterates C_{K-navg+1} .. C_K (all of C_0 .. C_K when there
+// are fewer), i.e. the unit quaternion maximising sum (4 (p . C_t)^2 - 1) over p: the eigenvector of the
+// largest eigenvalue of sum C_t C_t^T.  Called by the thread that takes step k with the previous and
+// the new iterate; adds them to the sums in s->acc and returns, at k == K, the projected mean (the new
+// iterate before).  The translation ball averages its last centres the same way (no projection).
+template <bool COHERENT>
+__device__ __forceinline__ Q4<double> mean_rule_rotation(MegbState* s, const Q4<double>& prev, const Q4<double>& cn,
+                                                         int k, int K, int navg) {
+  const int first = K - navg + 1;
+  double a[10];
+  for (int e = 0; e < 10; ++e) a[e] = COHERENT ? __ldcg(&s->acc[e]) : s->acc[e];
+  auto add = [&](const Q4<double>& q) {
+    const double v[4] = {q.w, q.x, q.y, q.z};
+    int e = 0;
+    for (int i = 0; i < 4; ++i)
+      for (int j = i; j < 4; ++j) a[e++] += v[i] * v[j];
+  };
+  if (k == 1 && first <= 0) add(prev);
+  if (k >= first) add(cn);
+  if (k < K) {
+    for (int e = 0; e < 10; ++e) s->acc[e] = a[e];
+    return cn;
+  }
+  double N[4][4], V[4][4];
+  int e = 0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = i; j < 4; ++j) N[i][j] = N[j][i] = a[e++];
+  jacobi_eigen<4>(N, V);
+  int best = 0;
+  for (int i = 1; i < 4; ++i)
+    if (N[i][i] > N[best][best]) best = i;
+  Q4<double> q = qnormalize(Q4<double>{V[0][best], V[1][best], V[2][best], V[3][best]});
+  if (q.w < 0.0) q = Q4<double>{-q.w, -q.x, -q.y, -q.z};
+  return q;
+}
+
+template <bool COHERENT>
+__device__ __forceinline__ void mean_rule_translation(MegbState* s, const double* prev, double* cn, int k, int K,
+                                                      int navg) {
+  const int first = K - navg + 1;
+  double a[3];
+  for (int d = 0; d < 3; ++d) a[d] = COHERENT ? __ldcg(&s->acc[10 + d]) : s->acc[10 + d];
+  for (int d = 0; d < 3; ++d) {
+    if (k == 1 && first <= 0) a[d] += prev[d];
+    if (k >= first) a[d] += cn[d];
+  }
+  if (k < K) {
+    for (int d = 0; d < 3; ++d) s->acc[10 + d] = a[d];
+    return;
+  }
+  const double cnt = double(first <= 0 ? K + 1 : navg);
+  for (int d = 0; d < 3; ++d) cn[d] = a[d] / cnt;
+}
+
 // Key of sample i: squared sine of half the angle to the centre (rotation) or squared distance.
 template <typename T, int MODE>
 __device__ __forceinline__ T sample_key(const T* __restrict__ x, int i, bool vec, T c0, T c1, T c2, T c3) {
@@ -146,9 +205,9 @@ __device__ __forceinline__ T sample_key(const T* __restrict__ x, int i, bool vec
 // the centre is read from L2 (the persistent kernel reads a centre written by another block in the
 // same launch).
 template <typename T, int MODE, bool COHERENT>
-__device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbState* s, Part* parts, int k,
-                                         int32_t* f_int, int32_t* f_out, double* result, double* wkey, int* widx,
-                                         bool* last, int bid, int nb) {
+__device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbState* s, Part* parts, int k, int K,
+                                         int navg, int32_t* f_int, int32_t* f_out, double* result, double* wkey,
+                                         int* widx, bool* last, int bid, int nb) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   T c0, c1, c2, c3;
   if (MODE == 0) {
@@ -303,7 +362,8 @@ __device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbSta
     const Q4<double> qf = qnormalize(Q4<double>{(double)qs[0], (double)qs[1], (double)qs[2], (double)qs[3]});
     const RelRot r = rel_rot(c, qf);
     if (k > 0) {
-      const Q4<double> cn = slerp_step(c, r, k);
+      Q4<double> cn = slerp_step(c, r, k);
+      if (navg > 1) cn = mean_rule_rotation<COHERENT>(s, c, cn, k, K, navg);
       s->C[0] = cn.w, s->C[1] = cn.x, s->C[2] = cn.y, s->C[3] = cn.z;
     } else {
       result[0] = c.w, result[1] = c.x, result[2] = c.y, result[3] = c.z;
@@ -314,9 +374,12 @@ __device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbSta
     const double c0d = ld(&s->c[0]), c1d = ld(&s->c[1]), c2d = ld(&s->c[2]);
     if (k > 0) {
       const double rk = 1.0 / k;
-      s->c[0] = c0d + ((double)p[0] - c0d) * rk;
-      s->c[1] = c1d + ((double)p[1] - c1d) * rk;
-      s->c[2] = c2d + ((double)p[2] - c2d) * rk;
+      double cn[3] = {c0d + ((double)p[0] - c0d) * rk, c1d + ((double)p[1] - c1d) * rk, c2d + ((double)p[2] - c2d) * rk};
+      if (navg > 1) {
+        const double prev[3] = {c0d, c1d, c2d};
+        mean_rule_translation<COHERENT>(s, prev, cn, k, K, navg);
+      }
+      s->c[0] = cn[0], s->c[1] = cn[1], s->c[2] = cn[2];
     } else {
       const double dx = (double)p[0] - c0d, dy = (double)p[1] - c1d, dz = (double)p[2] - c2d;
       result[4] = c0d, result[5] = c1d, result[6] = c2d;
@@ -335,12 +398,12 @@ __device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbSta
 // One launch per iteration (the state is complete at every kernel boundary).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kMegbThreads)
-    ggd_step(const T* __restrict__ x, int n, MegbState* s, Part* parts, int k, int32_t* f_int, int32_t* f_out,
-             double* result) {
+    ggd_step(const T* __restrict__ x, int n, MegbState* s, Part* parts, int k, int K, int navg, int32_t* f_int,
+             int32_t* f_out, double* result) {
   __shared__ double wkey[kMegbThreads / 32];
   __shared__ int widx[kMegbThreads / 32];
   __shared__ bool last;
-  ggd_iter<T, MODE, false>(x, n, s, parts, k, f_int, f_out, result, wkey, widx, &last, blockIdx.x, gridDim.x);
+  ggd_iter<T, MODE, false>(x, n, s, parts, k, K, navg, f_int, f_out, result, wkey, widx, &last, blockIdx.x, gridDim.x);
 }
 
 // All K iterations and the radius pass of a ball on blocks [b0, b0 + nb) of a cooperative launch
@@ -349,11 +412,12 @@ __global__ void __launch_bounds__(kMegbThreads)
 // poll limit runs out, flag a timeout in the status word and leave (the result is then not written).
 template <typename T, int MODE>
 __device__ __forceinline__ void ggd_ball(const T* __restrict__ x, int n, MegbState* s, Part* parts, int n_iters,
-                                         int32_t* f_int, int32_t* f_out, double* result, int* status, int bid, int nb,
+                                         int navg, int32_t* f_int, int32_t* f_out, double* result, int* status, int bid, int nb,
                                          double* wkey, int* widx, bool* last, bool* stop) {
   for (int it = 1; it <= n_iters + 1; ++it) {
     const int k = it <= n_iters ? it : 0;
-    const bool took = ggd_iter<T, MODE, true>(x, n, s, parts, k, f_int, f_out, result, wkey, widx, last, bid, nb);
+    const bool took =
+        ggd_iter<T, MODE, true>(x, n, s, parts, k, n_iters, navg, f_int, f_out, result, wkey, widx, last, bid, nb);
     if (it == n_iters + 1) break;
     if (threadIdx.x == 0) {
       *stop = false;
@@ -382,15 +446,15 @@ __device__ __forceinline__ void ggd_ball(const T* __restrict__ x, int n, MegbSta
 template <typename T>
 __global__ void __launch_bounds__(kMegbThreads)
     ggd_persistent(const T* __restrict__ q, int nq, const T* __restrict__ t, int nt, int gq, MegbState* s,
-                   Part* parts_q, Part* parts_t, int n_iters, int32_t* f_int, int32_t* f_out, double* result,
-                   int* status) {
+                   Part* parts_q, Part* parts_t, int n_iters, int navg, int32_t* f_int, int32_t* f_out,
+                   double* result, int* status) {
   __shared__ double wkey[kMegbThreads / 32];
   __shared__ int widx[kMegbThreads / 32];
   __shared__ bool last, stop;
   if ((int)blockIdx.x < gq)
-    ggd_ball<T, 0>(q, nq, s, parts_q, n_iters, f_int, f_out, result, status, blockIdx.x, gq, wkey, widx, &last, &stop);
+    ggd_ball<T, 0>(q, nq, s, parts_q, n_iters, navg, f_int, f_out, result, status, blockIdx.x, gq, wkey, widx, &last, &stop);
   else
-    ggd_ball<T, 1>(t, nt, s, parts_t, n_iters, f_int + n_iters, f_out ? f_out + n_iters : nullptr, result, status,
+    ggd_ball<T, 1>(t, nt, s, parts_t, n_iters, navg, f_int + n_iters, f_out ? f_out + n_iters : nullptr, result, status,
                    blockIdx.x - gq, gridDim.x - gq, wkey, widx, &last, &stop);
 }
 
@@ -401,8 +465,8 @@ __global__ void megb_zero_result(double* result, int skip_rot, int skip_tr) {
 }
 
 template <typename T>
-static cudaError_t launch_megb_t(purse_t h, int n_iters, const T* q, int nq, const T* t, int nt, double* result,
-                                 int32_t* f_out, void* scratch, cudaStream_t st) {
+static cudaError_t launch_megb_t(purse_t h, int n_iters, int navg, const T* q, int nq, const T* t, int nt,
+                                 double* result, int32_t* f_out, void* scratch, cudaStream_t st) {
   MegbState* s = reinterpret_cast<MegbState*>(scratch);
   Part* parts = reinterpret_cast<Part*>(reinterpret_cast<char*>(scratch) + sizeof(MegbState));
   int32_t* f_int = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(parts) + 2 * megb_blocks_cap(h->sm_count) * sizeof(Part));
@@ -445,10 +509,11 @@ static cudaError_t launch_megb_t(purse_t h, int n_iters, const T* q, int nq, con
         gt = room;
       }
     }
-    int gqi = (int)gq, nqi = nq, nti = nt, ni = n_iters;
+    int gqi = (int)gq, nqi = nq, nti = nt, ni = n_iters, na = navg;
     Part* parts_t = parts + cap;
     int* status = h->d_status;
-    void* args[] = {(void*)&q, &nqi, (void*)&t, &nti, &gqi, &s, &parts, &parts_t, &ni, &f_int, &f_out, &result, &status};
+    void* args[] = {(void*)&q, &nqi, (void*)&t, &nti, &gqi, &s, &parts, &parts_t, &ni, &na, &f_int, &f_out, &result,
+                    &status};
     return cudaLaunchCooperativeKernel((const void*)ggd_persistent<T>, dim3((unsigned)(gq + gt)), dim3(kMegbThreads),
                                        args, 0, st);
   }
@@ -456,27 +521,27 @@ static cudaError_t launch_megb_t(purse_t h, int n_iters, const T* q, int nq, con
     const long want = ((long)nq + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
     const int g = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     for (int k = 1; k <= n_iters; ++k)
-      ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, k, f_int, f_out, result);
-    ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, 0, f_int, f_out, result);
+      ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, k, n_iters, navg, f_int, f_out, result);
+    ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, 0, n_iters, navg, f_int, f_out, result);
   }
   if (nt > 0) {
     const long want = ((long)nt + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
     const int g = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     Part* parts_t = parts + cap;
     for (int k = 1; k <= n_iters; ++k)
-      ggd_step<T, 1><<<g, kMegbThreads, 0, st>>>(t, nt, s, parts_t, k, f_int + n_iters, f_out ? f_out + n_iters : nullptr,
-                                                  result);
-    ggd_step<T, 1><<<g, kMegbThreads, 0, st>>>(t, nt, s, parts_t, 0, f_int + n_iters, nullptr, result);
+      ggd_step<T, 1><<<g, kMegbThreads, 0, st>>>(t, nt, s, parts_t, k, n_iters, navg, f_int + n_iters,
+                                                  f_out ? f_out + n_iters : nullptr, result);
+    ggd_step<T, 1><<<g, kMegbThreads, 0, st>>>(t, nt, s, parts_t, 0, n_iters, navg, f_int + n_iters, nullptr, result);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_megb(purse_t h, int precision, int n_iters, const void* d_q, int n_rot, const void* d_t, int n_tr,
-                        double* d_result, int32_t* d_farthest, void* scratch, cudaStream_t st) {
+                        double* d_result, int32_t* d_farthest, void* scratch, cudaStream_t st, int navg) {
   if (precision == 0)
-    return launch_megb_t<float>(h, n_iters, (const float*)d_q, n_rot, (const float*)d_t, n_tr, d_result, d_farthest,
+    return launch_megb_t<float>(h, n_iters, navg, (const float*)d_q, n_rot, (const float*)d_t, n_tr, d_result, d_farthest,
                                 scratch, st);
-  return launch_megb_t<double>(h, n_iters, (const double*)d_q, n_rot, (const double*)d_t, n_tr, d_result, d_farthest,
+  return launch_megb_t<double>(h, n_iters, navg, (const double*)d_q, n_rot, (const double*)d_t, n_tr, d_result, d_farthest,
                                scratch, st);
 }
 
@@ -629,6 +694,7 @@ __global__ void megb_state_from_result(const double* result, MegbState* s) {
   s->counter[0] = s->counter[1] = 0;
   s->fstar[0] = s->fstar[1] = 0;
   s->best[0][0] = s->best[0][1] = s->best[1][0] = s->best[1][1] = 0ull;
+  for (int i = 0; i < 13; ++i) s->acc[i] = 0.0;
 }
 
 size_t megb_backward_scratch_bytes(int n_iters, int sm_count, int n) {
@@ -653,12 +719,12 @@ static cudaError_t launch_megb_backward_t(purse_t h, int K, const T* q, const T*
   if (nq > 0) {
     const long want = ((long)nq + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
     const int gsz = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
-    ggd_step<T, 0><<<gsz, kMegbThreads, 0, st>>>(q, nq, s, parts, 0, f_int, nullptr, dummy);
+    ggd_step<T, 0><<<gsz, kMegbThreads, 0, st>>>(q, nq, s, parts, 0, K, 1, f_int, nullptr, dummy);
   }
   if (nt > 0) {
     const long want = ((long)nt + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
     const int gsz = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
-    ggd_step<T, 1><<<gsz, kMegbThreads, 0, st>>>(t, nt, s, parts + cap, 0, f_int, nullptr, dummy);
+    ggd_step<T, 1><<<gsz, kMegbThreads, 0, st>>>(t, nt, s, parts + cap, 0, K, 1, f_int, nullptr, dummy);
   }
   const int dim = h->kind == PURSE_2D3D ? 2 : 3;
   megb_adjoint_kernel<T><<<1, 64, 0, st>>>(q, snap_r, nq, t, snap_t, nt, K, f, s, result, g, Cs, acc, h->n, dim, gy,
@@ -887,17 +953,17 @@ static cudaError_t launch_megb_noalloc_t(int sms, int n_iters, const T* q, int n
     const long want = ((long)nq + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
     const int g = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     for (int k = 1; k <= n_iters; ++k)
-      ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, k, f_int, f_out, result);
-    ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, 0, f_int, f_out, result);
+      ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, k, n_iters, 1, f_int, f_out, result);
+    ggd_step<T, 0><<<g, kMegbThreads, 0, st>>>(q, nq, s, parts, 0, n_iters, 1, f_int, f_out, result);
   }
   if (nt > 0) {
     const long want = ((long)nt + kMegbThreads * 4 - 1) / (kMegbThreads * 4);
     const int g = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     Part* parts_t = parts + kNoAllocMaxBlocks;
     for (int k = 1; k <= n_iters; ++k)
-      ggd_step<T, 1><<<g, kMegbThreads, 0, st>>>(t, nt, s, parts_t, k, f_int + n_iters,
+      ggd_step<T, 1><<<g, kMegbThreads, 0, st>>>(t, nt, s, parts_t, k, n_iters, 1, f_int + n_iters,
                                                   f_out ? f_out + n_iters : nullptr, result);
-    ggd_step<T, 1><<<g, kMegbThreads, 0, st>>>(t, nt, s, parts_t, 0, f_int + n_iters, nullptr, result);
+    ggd_step<T, 1><<<g, kMegbThreads, 0, st>>>(t, nt, s, parts_t, 0, n_iters, 1, f_int + n_iters, nullptr, result);
   }
   return cudaGetLastError();
 }

@@ -64,6 +64,8 @@ _SIGS = {
                            _VP, _VP, _VP],
     "purse_last_evals": [_VP, ctypes.POINTER(ctypes.c_ulonglong), _VP],
     "megb_solve": [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP],
+    "megb_solve_mean": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
+                        _VP],
     "megb_backward": [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP, _VP,
                       _VP, _VP, _VP, _VP],
     "megb_solve_exact": [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP],
@@ -217,6 +219,11 @@ def purse_last_evals(h, stream=None) -> int:
 def megb_solve(h, precision, n_iters, q, n_rot, t, n_tr, result, farthest=None, stream=None):
     _check(lib().megb_solve(h, precision, n_iters, _ptr(q), n_rot, _ptr(t), n_tr, _ptr(result), _ptr(farthest),
                             _stream(stream)), "megb_solve")
+
+
+def megb_solve_mean(h, precision, n_iters, n_last, q, n_rot, t, n_tr, result, farthest=None, stream=None):
+    _check(lib().megb_solve_mean(h, precision, n_iters, n_last, _ptr(q), n_rot, _ptr(t), n_tr, _ptr(result),
+                                 _ptr(farthest), _stream(stream)), "megb_solve_mean")
 
 
 def megb_backward(h, precision, n_iters, q, snap_rot, n_rot, t, snap_tr, n_tr, farthest, result, grad_result,

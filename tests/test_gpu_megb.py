@@ -86,3 +86,44 @@ def test_rotation_ball_with_radius_near_pi(precision):
         res, f = megb(h.h, precision, K, q, None)
     _, D = check_rotation(q, res, f[:K], precision)
     assert D > 3.0
+
+
+def megb_mean(handle, precision, K, n_last, q_np, t_np):
+    import torch
+    from tests.gpu_helpers import DT, to_dev
+    q, t = to_dev(q_np, DT[precision]), to_dev(t_np, DT[precision])
+    res = torch.full((9,), np.nan, dtype=torch.float64, device="cuda")
+    far = torch.full((2 * K,), -1, dtype=torch.int32, device="cuda")
+    P.megb_solve_mean(handle, precision, K, n_last, q, q_np.shape[0], t, t_np.shape[0], res, far)
+    P.purse_sync(handle)
+    return res.cpu().numpy(), far.cpu().numpy().astype(np.int64)
+
+
+@pytest.mark.parametrize("n,K,n_last,precision", [(4096, 200, 10, 1), (4096, 200, 10, 0), (1 << 18, 200, 10, 0),
+                                                  (1000, 5, 10, 0), (3001, 50, 1, 0), (20000, 37, 12, 1)])
+def test_megb_mean_output_rule(n, K, n_last, precision):
+    """Alg. 6's output rule: the same farthest samples as megb_solve, then the centres from the last
+    n_last iterates, against the oracle replaying the GPU's (band-checked) farthest sequence."""
+    q, t = cluster(n, n + 1)
+    dt = np.float32 if precision == 0 else np.float64
+    q32, t32 = q.astype(dt), t.astype(dt)
+    with P.Purse(syn.purse_3d3d(8, 0)) as h:
+        res, far = megb(h.h, precision, K, q32, t32)
+        resm, farm = megb_mean(h.h, precision, K, n_last, q32, t32)
+        # megb_backward differentiates megb_solve's plain output only
+        with pytest.raises(P.PurseError):
+            P.megb_backward(h.h, precision, K, None, None, 0, None, None, 0, None, None, None, None, None)
+    assert np.array_equal(far, farm)
+    q64, t64 = q32.astype(np.float64), t32.astype(np.float64)
+    check_rotation(q64, res, far[:K], precision)
+    check_translation(t64, res, far[K:], precision)
+    if n_last == 1:
+        assert np.array_equal(res, resm)
+    C, D, _ = om.megb_rotation_mean(q64, K, n_last, f=far[:K])
+    c, d, _ = om.megb_translation_mean(t64, K, n_last, f=far[K:])
+    assert so3.dist_quat(resm[:4][None], C[None])[0] <= 1e-9
+    assert resm[0] >= 0 and abs(np.linalg.norm(resm[:4]) - 1) < 1e-12
+    assert np.abs(resm[4:7] - c).max() <= 1e-9 * (1 + np.abs(c).max())
+    assert abs(resm[7] - D) <= 1e-5 * D + 1e-12 and abs(resm[8] - d) <= 1e-5 * d + 1e-12
+    if n_last > 1 and K >= n_last:
+        assert so3.dist_quat(resm[:4][None], res[:4][None])[0] > 0  # a different centre than C_K
