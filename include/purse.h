@@ -348,6 +348,17 @@ purse_status purse_batch_create(int n_purses, const int* kinds, const int* offse
 
 purse_status purse_batch_destroy(purse_batch_t b);
 
+/* Noise bounded in the general norm of eq. 4 for every PURSE of the batch (the batched form of
+ * purse_set_noise): d_lam is a HOST array of 9 doubles per keypoint in the CSR order of
+ * purse_batch_create, the symmetric positive definite Lambda_i row-major as a 3 x 3 block (2D-3D
+ * keypoints: its top-left 2 x 2 block is read, in pixels^-2).  The factors Lambda_i = U_i^T U_i are
+ * taken on the host and kept in batch-owned device memory; walks, centre statistics, boundary snap
+ * and purse_batch_backward then work in the Lambda-norm, with the same samples as purse_sample on
+ * a handle given the same matrices by purse_set_noise.  NULL returns the batch to Lambda_i = I.
+ * Errors: PURSE_ERR_ARG (non-finite, not symmetric or not positive definite), PURSE_ERR_NOMEM.
+ * The next purse_batch_solve captures its graph anew. */
+purse_status purse_batch_set_noise(purse_batch_t b, const double* lam);
+
 /* Alg. 1 for every PURSE of the batch, FP32 walks: n_samples walks per PURSE and sampler from the
  * seed pose d_seeds[p] (device, n_purses x 12 doubles), the parameters p3d / p2d by kind (their
  * sampler and precision fields must be 0), Philox key seed + p for PURSE p (so PURSE p gets the

@@ -215,6 +215,41 @@ purse_status purse_create_regression(int n, const double* hyp, const double* bet
   return make_handle(PURSE_REG, n, t64, purse_intrinsics{0, 0, 0, 0}, 0.0, out);
 }
 
+}  // extern "C"
+
+namespace purse {
+// Noise factor of one constraint (eq. 4): the Cholesky factor Lambda = U^T U, U upper triangular, of
+// the d x d matrix L (row-major), written as 8 values (3D: u00 u01 u02 u11 u12 u22; 2D: u00 u01 u11;
+// the rest 0).  Returns NULL, or why L is not a symmetric positive definite matrix.
+const char* noise_factor(const double* L, int d, double* o) {
+  for (int r = 0; r < d; ++r)
+    for (int c = 0; c < r; ++c)
+      if (std::fabs(L[r * d + c] - L[c * d + r]) > 1e-12 * (std::fabs(L[r * d + c]) + std::fabs(L[c * d + r])) + 1e-300)
+        return "a noise matrix is not symmetric";
+  double U[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int r = 0; r < d; ++r) {
+    double s2 = L[r * d + r];
+    for (int k = 0; k < r; ++k) s2 -= U[k][r] * U[k][r];
+    if (!(s2 > 0)) return "a noise matrix is not positive definite";
+    U[r][r] = std::sqrt(s2);
+    for (int c = r + 1; c < d; ++c) {
+      double v = L[r * d + c];
+      for (int k = 0; k < r; ++k) v -= U[k][r] * U[k][c];
+      U[r][c] = v / U[r][r];
+    }
+  }
+  for (int k = 0; k < 8; ++k) o[k] = 0.0;
+  if (d == 3) {
+    o[0] = U[0][0], o[1] = U[0][1], o[2] = U[0][2], o[3] = U[1][1], o[4] = U[1][2], o[5] = U[2][2];
+  } else {
+    o[0] = U[0][0], o[1] = U[0][1], o[2] = U[1][1];
+  }
+  return nullptr;
+}
+}  // namespace purse
+
+extern "C" {
+
 purse_status purse_set_noise(purse_t h, const double* lam) {
   if (!h) return arg_error("purse_set_noise: NULL handle");
   if (h->kind == PURSE_REG) return arg_error("purse_set_noise: regression PURSEs take no noise matrices");
@@ -228,30 +263,8 @@ purse_status purse_set_noise(purse_t h, const double* lam) {
   if (!finite_all(lam, (size_t)n * d * d)) return arg_error("purse_set_noise: non-finite input");
   std::vector<double> u64(8 * (size_t)n, 0.0);
   for (int i = 0; i < n; ++i) {
-    const double* L = lam + (size_t)i * d * d;
-    for (int r = 0; r < d; ++r)
-      for (int c = 0; c < r; ++c)
-        if (std::fabs(L[r * d + c] - L[c * d + r]) > 1e-12 * (std::fabs(L[r * d + c]) + std::fabs(L[c * d + r])) + 1e-300)
-          return arg_error("purse_set_noise: a noise matrix is not symmetric");
-    // Cholesky Lambda = U^T U (U upper triangular, row by row)
-    double U[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    for (int r = 0; r < d; ++r) {
-      double s2 = L[r * d + r];
-      for (int k = 0; k < r; ++k) s2 -= U[k][r] * U[k][r];
-      if (!(s2 > 0)) return arg_error("purse_set_noise: a noise matrix is not positive definite");
-      U[r][r] = std::sqrt(s2);
-      for (int c = r + 1; c < d; ++c) {
-        double v = L[r * d + c];
-        for (int k = 0; k < r; ++k) v -= U[k][r] * U[k][c];
-        U[r][c] = v / U[r][r];
-      }
-    }
-    double* o = &u64[8 * (size_t)i];
-    if (d == 3) {
-      o[0] = U[0][0], o[1] = U[0][1], o[2] = U[0][2], o[3] = U[1][1], o[4] = U[1][2], o[5] = U[2][2];
-    } else {
-      o[0] = U[0][0], o[1] = U[0][1], o[2] = U[1][1];
-    }
+    const char* why = noise_factor(lam + (size_t)i * d * d, d, &u64[8 * (size_t)i]);
+    if (why) return arg_error(std::string("purse_set_noise: ") + why);
   }
   std::vector<float> u32(u64.size());
   for (size_t k = 0; k < u64.size(); ++k) u32[k] = (float)u64[k];

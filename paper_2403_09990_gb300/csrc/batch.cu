@@ -16,6 +16,10 @@ struct purse_batch_s {
   purse::BatchPurseInfo* d_info = nullptr;
   float* d_tab32 = nullptr;
   double* d_tab64 = nullptr;
+  // noise matrices of eq. 4 (purse_batch_set_noise): factors U_i, 8 values per keypoint, or NULL
+  float* d_ell32 = nullptr;
+  double* d_ell64 = nullptr;
+  std::vector<int> kinds, offsets;  // host copies (kind per PURSE, CSR keypoint offsets)
   purse::WalkStats* d_stats = nullptr;
   double* d_seed_data = nullptr;
   unsigned int* d_counter = nullptr;
@@ -69,6 +73,8 @@ static BatchArgs make_args(purse_batch_t b, const purse_params* p3, const purse_
   a.info = b->d_info;
   a.table = b->d_tab32;
   a.table64 = b->d_tab64;
+  a.ell = b->d_ell32;
+  a.ell64 = b->d_ell64;
   a.stats = b->d_stats;
   a.seed_data = b->d_seed_data;
   a.n_purses = b->n_purses;
@@ -139,7 +145,8 @@ static cudaError_t enqueue_batch(purse_batch_t b, const purse_params* p3, const 
   cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_evals, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess)
-    e = launch_stats_batch(b->n_purses, b->d_info, b->d_tab64, d_seeds, sp, b->d_stats, b->d_seed_data, st);
+    e = launch_stats_batch(b->n_purses, b->d_info, b->d_tab64, b->d_ell64, d_seeds, sp, b->d_stats, b->d_seed_data,
+                           st);
   if (e == cudaSuccess) e = launch_batch_walk(a, chunk, warps, b->sm_count, st);
   if (e == cudaSuccess && !walks_only) e = launch_megb_batch(a, n_iters, d_results, b->d_far, st);
   return e;
@@ -207,6 +214,8 @@ purse_status purse_batch_create(int n_purses, const int* kinds, const int* offse
   if (fault_at("alloc")) return injected_fault("alloc", "purse_batch_create");
   purse_batch_s* b = new purse_batch_s();
   b->n_purses = n_purses, b->nmax = nmax, b->total_rows = 2 * total;
+  b->kinds.assign(kinds, kinds + n_purses);
+  b->offsets.assign(offsets, offsets + n_purses + 1);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -240,6 +249,8 @@ purse_status purse_batch_destroy(purse_batch_t b) {
   cudaFree(b->d_info);
   cudaFree(b->d_tab32);
   cudaFree(b->d_tab64);
+  cudaFree(b->d_ell32);
+  cudaFree(b->d_ell64);
   cudaFree(b->d_stats);
   cudaFree(b->d_seed_data);
   cudaFree(b->d_counter);
@@ -250,6 +261,40 @@ purse_status purse_batch_destroy(purse_batch_t b) {
   cudaFree(b->d_cs);
   delete b;
   return PURSE_OK;
+}
+
+purse_status purse_batch_set_noise(purse_batch_t b, const double* lam) {
+  if (!b) return barg("purse_batch_set_noise: NULL batch");
+  if (b->exec) cudaGraphExecDestroy(b->exec);  // the next solve captures a graph with the new tables
+  b->exec = nullptr;
+  b->graph_key.clear();
+  if (!lam) {  // back to the identity norm
+    cudaFree(b->d_ell32);
+    cudaFree(b->d_ell64);
+    b->d_ell32 = nullptr, b->d_ell64 = nullptr;
+    return PURSE_OK;
+  }
+  const int total = b->offsets[b->n_purses];
+  for (size_t k = 0; k < 9 * (size_t)total; ++k)
+    if (!std::isfinite(lam[k])) return barg("purse_batch_set_noise: non-finite input");
+  std::vector<double> u64(8 * (size_t)total, 0.0);
+  for (int p = 0; p < b->n_purses; ++p) {
+    const int d = b->kinds[p] == 0 ? 3 : 2;
+    for (int g = b->offsets[p]; g < b->offsets[p + 1]; ++g) {
+      const double* L9 = lam + 9 * (size_t)g;
+      const double L2[4] = {L9[0], L9[1], L9[3], L9[4]};  // 2D-3D: the top-left 2 x 2 block, row-major
+      const char* why = noise_factor(d == 3 ? L9 : L2, d, &u64[8 * (size_t)g]);
+      if (why) return barg(std::string("purse_batch_set_noise: ") + why);
+    }
+  }
+  std::vector<float> u32(u64.begin(), u64.end());
+  if (fault_at("alloc")) return injected_fault("alloc", "purse_batch_set_noise");
+  cudaError_t e = cudaSuccess;
+  if (!b->d_ell64) e = dev_alloc((void**)&b->d_ell64, u64.size() * sizeof(double));
+  if (e == cudaSuccess && !b->d_ell32) e = dev_alloc((void**)&b->d_ell32, u32.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_ell64, u64.data(), u64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_ell32, u32.data(), u32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? PURSE_OK : cuda_fail(e, "purse_batch_set_noise");
 }
 
 purse_status purse_batch_solve(purse_batch_t b, const purse_params* p3d, const purse_params* p2d, uint64_t seed,
@@ -266,7 +311,8 @@ purse_status purse_batch_solve(purse_batch_t b, const purse_params* p3d, const p
     return barg("purse_batch_solve: too many work items (2 x n_purses x n_samples >= 2^32)");
   if (!d_seeds || !d_results) return barg("purse_batch_solve: NULL buffer");
   if (batch_walk_smem(b->nmax, p3d->n_perturb > p2d->n_perturb ? p3d->n_perturb : p2d->n_perturb,
-                      p3d->n_steps > p2d->n_steps ? p3d->n_steps : p2d->n_steps, b->warps) > 227 * 1024)
+                      p3d->n_steps > p2d->n_steps ? p3d->n_steps : p2d->n_steps, b->warps, b->d_ell32 != nullptr) >
+      227 * 1024)
     return barg("purse_batch_solve: the largest PURSE does not fit the walk kernel's shared memory");
   if (fault_at("launch")) return injected_fault("launch", "purse_batch_solve");
   purse_status s = ensure_batch_buffers(b, n_samples, n_iters);
@@ -338,7 +384,7 @@ purse_status purse_batch_tune(purse_batch_t b, const purse_params* p3d, const pu
   float best = 1e30f;
   int bc = b->chunk, bw = b->warps;
   for (int wi = 0; wi < 2 && e == cudaSuccess; ++wi) {
-    if (batch_walk_smem(b->nmax, np, nt, warps[wi]) > 227 * 1024) continue;
+    if (batch_walk_smem(b->nmax, np, nt, warps[wi], b->d_ell32 != nullptr) > 227 * 1024) continue;
     for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
       float ms = 0.f;
       for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms up

@@ -63,6 +63,8 @@ struct BatchArgs {
   const BatchPurseInfo* info;
   const float* table;  // FP32 tables, rows of 4 floats
   const double* table64;  // the same tables in FP64 (read by the boundary snap)
+  const float* ell;       // NULL, or noise factors U_i of eq. 4: 8 floats per keypoint in CSR order
+  const double* ell64;    // the same in FP64 (statistics, boundary snap)
   const WalkStats* stats;
   const double* seed_data;
   int n_purses, n_samples, nmax;
@@ -174,9 +176,11 @@ void tune_store(int op, int kind, int n, long long samples, int variant, const c
 cudaError_t launch_stats(purse_t h, const double* d_seeds, int s0, const purse_params* p, WalkStats* d_stats,
                          double* d_seed_data, cudaStream_t st);  // takes h->ell64 into the translation scale
 cudaError_t launch_walk(purse_t h, const purse_params* p, const WalkArgs& a, cudaStream_t st);
-cudaError_t launch_stats_batch(int n_purses, const BatchPurseInfo* info, const double* tab64, const double* seeds,
-                               const BatchStatParams& sp, WalkStats* out, double* seed_data, cudaStream_t st);
-size_t batch_walk_smem(int nmax, int n_perturb, int n_steps, int warps);
+cudaError_t launch_stats_batch(int n_purses, const BatchPurseInfo* info, const double* tab64, const double* ell64,
+                               const double* seeds, const BatchStatParams& sp, WalkStats* out, double* seed_data,
+                               cudaStream_t st);
+// lam: the batch carries noise matrices (the tables and slabs of the walks with U_i)
+size_t batch_walk_smem(int nmax, int n_perturb, int n_steps, int warps, bool lam = false);
 cudaError_t launch_batch_walk(const BatchArgs& b, int chunk, int warps, int sm_count, cudaStream_t st);
 cudaError_t launch_megb_batch(const BatchArgs& b, int n_iters, double* d_results, int32_t* d_farthest,
                               cudaStream_t st);
@@ -199,6 +203,7 @@ cudaError_t launch_eval(purse_t h, int precision, const void* d_poses, int n_pos
 cudaError_t launch_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t i, uint32_t w0, int n_streams,
                              int n_words, uint32_t* d_words, int32_t* d_lattice, int unit, cudaStream_t st);
 size_t megb_scratch_bytes(int n_iters, int sm_count);
+const char* noise_factor(const double* L, int d, double* o);
 // navg > 1: the output rule of Alg. 6 (centre from the last navg iterates; megb_solve_mean)
 cudaError_t launch_megb(purse_t h, int precision, int n_iters, const void* d_q, int n_rot, const void* d_t,
                         int n_tr, double* d_result, int32_t* d_farthest, void* scratch, cudaStream_t st,

@@ -158,20 +158,22 @@ __global__ void __launch_bounds__(kStatsThreads)
 
 // One block per PURSE of a batch; one seed pose per PURSE.
 __global__ void __launch_bounds__(kStatsThreads) stats_batch_kernel(const BatchPurseInfo* info, const double* tab64,
-                                                                    const double* seeds, BatchStatParams sp,
-                                                                    WalkStats* out, double* seed_data) {
+                                                                    const double* ell64, const double* seeds,
+                                                                    BatchStatParams sp, WalkStats* out,
+                                                                    double* seed_data) {
   __shared__ double red[12 * kStatsThreads];
   __shared__ WalkStats sh;
   const int p = blockIdx.x;
   const BatchPurseInfo in = info[p];
   stats_block(seeds + 12 * (size_t)p, 1, tab64 + 4 * (size_t)in.table_off, in.n, in.kind, in.fx, in.fy,
               sp.t_p[in.kind], sp.th_p[in.kind], sp.raw[in.kind], out + p, seed_data + (size_t)p * kSeedStride, red,
-              sh);
+              sh, ell64 ? ell64 + 8 * (size_t)(in.table_off / 2) : nullptr);
 }
 
-cudaError_t launch_stats_batch(int n_purses, const BatchPurseInfo* info, const double* tab64, const double* seeds,
-                               const BatchStatParams& sp, WalkStats* out, double* seed_data, cudaStream_t st) {
-  stats_batch_kernel<<<n_purses, kStatsThreads, 0, st>>>(info, tab64, seeds, sp, out, seed_data);
+cudaError_t launch_stats_batch(int n_purses, const BatchPurseInfo* info, const double* tab64, const double* ell64,
+                               const double* seeds, const BatchStatParams& sp, WalkStats* out, double* seed_data,
+                               cudaStream_t st) {
+  stats_batch_kernel<<<n_purses, kStatsThreads, 0, st>>>(info, tab64, ell64, seeds, sp, out, seed_data);
   return cudaGetLastError();
 }
 

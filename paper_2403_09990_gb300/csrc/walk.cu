@@ -1586,26 +1586,27 @@ __global__ void __launch_bounds__(kWalkThreads, sizeof(T) == 4 ? 2 : 1)
 // the dS_t items of 3D-3D PURSEs are skipped (their two balls use the dS_R samples).  Each warp
 // pops chunks of items from one atomic counter; the queue never waits, so the kernel ends when
 // the counter passes the last item.  A warp stages the constraint table and Philox round keys of
-// its current PURSE into its own shared-memory area when the PURSE changes.
-__host__ __device__ inline size_t batch_warp_bytes(int nmax, int n_perturb, int n_steps) {
-  return walk_table_bytes<float>(nmax) + 128 + walk_slab_bytes2<float>(nmax, n_perturb, n_steps);
+// its current PURSE into its own shared-memory area when the PURSE changes.  With noise matrices
+// (LAM) the warp's table holds the PURSE's factors U_i after its 2N rows, as in walk_kernel.
+__host__ __device__ inline size_t batch_warp_bytes(int nmax, int n_perturb, int n_steps, bool lam = false) {
+  return walk_table_bytes<float>(nmax, lam) + 128 + walk_slab_bytes2<float>(nmax, n_perturb, n_steps, lam);
 }
 
-size_t batch_walk_smem(int nmax, int n_perturb, int n_steps, int warps) {
-  return (size_t)warps * batch_warp_bytes(nmax, n_perturb, n_steps);
+size_t batch_walk_smem(int nmax, int n_perturb, int n_steps, int warps, bool lam) {
+  return (size_t)warps * batch_warp_bytes(nmax, n_perturb, n_steps, lam);
 }
 
 // TR3D: the 3D-3D dS_t walks run too (b.tr3d); a separate instantiation so that batches without
-// them keep the smaller kernel.
-template <bool TR3D>
+// them keep the smaller kernel.  LAM: the batch carries noise matrices (eq. 4).
+template <bool TR3D, bool LAM>
 __global__ void __launch_bounds__(kWalkThreads, 2)
     batch_walk_kernel(const __grid_constant__ BatchArgs b, const int chunk, const int np_max, const int nt_max) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* base = smem + (size_t)warp * batch_warp_bytes(b.nmax, np_max, nt_max);
+  unsigned char* base = smem + (size_t)warp * batch_warp_bytes(b.nmax, np_max, nt_max, LAM);
   T4<float>* tab = reinterpret_cast<T4<float>*>(base);
-  uint32_t* rkw = reinterpret_cast<uint32_t*>(base + walk_table_bytes<float>(b.nmax));
-  unsigned char* slab_base = base + walk_table_bytes<float>(b.nmax) + 128;
+  uint32_t* rkw = reinterpret_cast<uint32_t*>(base + walk_table_bytes<float>(b.nmax, LAM));
+  unsigned char* slab_base = base + walk_table_bytes<float>(b.nmax, LAM) + 128;
   const unsigned S = (unsigned)b.n_samples;
   const unsigned long long seed = *b.seed;
   unsigned long long evals = 0;
@@ -1629,6 +1630,10 @@ __global__ void __launch_bounds__(kWalkThreads, 2)
         __syncwarp();
         const T4<float>* src = reinterpret_cast<const T4<float>*>(b.table) + in.table_off;
         for (int r = lane; r < 2 * in.n; r += 32) tab[r] = src[r];
+        if constexpr (LAM) {  // rows [2N, 4N): U_i, two rows of 4 floats per keypoint
+          const T4<float>* us = reinterpret_cast<const T4<float>*>(b.ell) + in.table_off;
+          for (int r = lane; r < 2 * in.n; r += 32) tab[2 * in.n + r] = us[r];
+        }
         const unsigned long long key = seed + (unsigned long long)p;
         if (lane < 10) {
           rkw[2 * lane] = (uint32_t)key + (uint32_t)lane * 0x9E3779B9u;
@@ -1644,8 +1649,9 @@ __global__ void __launch_bounds__(kWalkThreads, 2)
         c.st = b.stats + p, c.seed_data = b.seed_data + (size_t)p * kSeedStride, c.s0 = 1;
         c.key0 = (uint32_t)key, c.key1 = (uint32_t)(key >> 32);
         c.trace = nullptr, c.status = b.status;
-        c.tab64 = b.table64 + 4 * (size_t)in.table_off, c.kd = &b.info[p].fx, c.ell64 = nullptr;
-        sl = carve<float>(slab_base, c.N, c.NP, c.NT);
+        c.tab64 = b.table64 + 4 * (size_t)in.table_off, c.kd = &b.info[p].fx;
+        c.ell64 = LAM ? b.ell64 + 4 * (size_t)in.table_off : nullptr;
+        sl = carve<float, LAM>(slab_base, c.N, c.NP, c.NT);
         cur = p;
         __syncwarp();
       }
@@ -1656,24 +1662,24 @@ __global__ void __launch_bounds__(kWalkThreads, 2)
       float* snap = smp == 0 ? b.snap_rot : b.snap_tr;
       c.out_snap = snap ? snap + (size_t)kSnapStride * off : nullptr;
       if (in.kind == 0 && smp == 0)
-        walk_one<float, 0, 0, false>(c, rk, w, tab, sl, lane, evals);
+        walk_one<float, 0, 0, LAM>(c, rk, w, tab, sl, lane, evals);
       else if (in.kind == 0) {
-        if constexpr (TR3D) walk_one<float, 0, 1, false>(c, rk, w, tab, sl, lane, evals);
+        if constexpr (TR3D) walk_one<float, 0, 1, LAM>(c, rk, w, tab, sl, lane, evals);
       }
       else if (smp == 0)
-        walk_one<float, 1, 0, false>(c, rk, w, tab, sl, lane, evals);
+        walk_one<float, 1, 0, LAM>(c, rk, w, tab, sl, lane, evals);
       else
-        walk_one<float, 1, 1, false>(c, rk, w, tab, sl, lane, evals);
+        walk_one<float, 1, 1, LAM>(c, rk, w, tab, sl, lane, evals);
     }
   }
   if (lane == 0 && evals) atomicAdd(b.evals, evals);
 }
 
-template <bool TR3D>
+template <bool TR3D, bool LAM>
 static cudaError_t launch_batch_walk_t(const BatchArgs& b, int chunk, int warps, int sm_count, cudaStream_t st) {
   const int np_max = max(b.n_perturb[0], b.n_perturb[1]), nt_max = max(b.n_steps[0], b.n_steps[1]);
-  const size_t smem = batch_walk_smem(b.nmax, np_max, nt_max, warps);
-  auto kern = batch_walk_kernel<TR3D>;
+  const size_t smem = batch_walk_smem(b.nmax, np_max, nt_max, warps, LAM);
+  auto kern = batch_walk_kernel<TR3D, LAM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -1685,8 +1691,11 @@ static cudaError_t launch_batch_walk_t(const BatchArgs& b, int chunk, int warps,
 }
 
 cudaError_t launch_batch_walk(const BatchArgs& b, int chunk, int warps, int sm_count, cudaStream_t st) {
-  return b.tr3d ? launch_batch_walk_t<true>(b, chunk, warps, sm_count, st)
-                : launch_batch_walk_t<false>(b, chunk, warps, sm_count, st);
+  if (b.ell)
+    return b.tr3d ? launch_batch_walk_t<true, true>(b, chunk, warps, sm_count, st)
+                  : launch_batch_walk_t<false, true>(b, chunk, warps, sm_count, st);
+  return b.tr3d ? launch_batch_walk_t<true, false>(b, chunk, warps, sm_count, st)
+                : launch_batch_walk_t<false, false>(b, chunk, warps, sm_count, st);
 }
 
 template <typename T, int KIND, int SAMPLER, bool LAM>

@@ -75,6 +75,7 @@ _SIGS = {
     "purse_sync": [_VP, _VP],
     "purse_batch_create": [ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)],
     "purse_batch_destroy": [_VP],
+    "purse_batch_set_noise": [_VP, _VP],
     "purse_batch_solve": [_VP, ctypes.POINTER(purse_params), ctypes.POINTER(purse_params), ctypes.c_uint64, _VP,
                           ctypes.c_int, ctypes.c_int, _VP, _VP],
     "purse_batch_tune": [_VP, ctypes.POINTER(purse_params), ctypes.POINTER(purse_params), ctypes.c_uint64, _VP,
@@ -317,6 +318,30 @@ def purse_batch_create(purses) -> int:
                                     obs.ctypes.data, radii.ctypes.data, ctypes.cast(Ks, _VP), ctypes.byref(h)),
            "purse_batch_create")
     return h.value
+
+
+def purse_batch_set_noise(b, purses):
+    """Noise matrices of every PURSE of the batch from the objects' lam (n x 3 x 3 or n x 2 x 2), in
+    the CSR order of purse_batch_create; None (or PURSEs without lam) clears them."""
+    import numpy as np
+    if purses is None or all(getattr(p, "lam", None) is None for p in purses):
+        _check(lib().purse_batch_set_noise(b, None), "purse_batch_set_noise")
+        return
+    rows = []
+    for p in purses:
+        lam = getattr(p, "lam", None)
+        n = p.radii.shape[0]
+        L = np.zeros((n, 3, 3))
+        if lam is None:
+            L[:] = np.eye(3)
+        else:
+            d = np.asarray(lam).shape[-1]
+            L[:, :d, :d] = lam
+            if d == 2:
+                L[:, 2, 2] = 1.0
+        rows.append(L.reshape(n, 9))
+    arr = np.ascontiguousarray(np.concatenate(rows), dtype=np.float64)
+    _check(lib().purse_batch_set_noise(b, arr.ctypes.data), "purse_batch_set_noise")
 
 
 def purse_batch_destroy(b):

@@ -199,3 +199,81 @@ def test_batch_full_size_sampled():
                 assert parity.rot_angle(qn, so3.quat_from_R(R)).max() <= 1e-5
     finally:
         P.purse_batch_destroy(b)
+
+
+def test_batch_noise_matrices_equal_single_path():
+    """purse_batch_set_noise (eq. 4 over a batch): PURSE p gives exactly the samples, snap records,
+    farthest sequences, balls and gradients of purse_sample / megb_solve / megb_backward on a handle
+    given the same matrices by purse_set_noise; one PURSE without matrices keeps the identity norm."""
+    rng = np.random.default_rng(3)
+    purses = []
+    for p in range(9):
+        n = int(rng.integers(4, 40))
+        purses.append(syn.purse_3d3d_ellipsoidal(n, 100 + p) if p % 2 == 0 else syn.purse_2d3d_ellipsoidal(n, 100 + p))
+    purses.append(syn.purse_2d3d(12, 5))
+    n_purses, S, K, seed = len(purses), 160, 30, 91
+    p3 = closure.preset_3d3d(n_iter=3, v0=0.02, rot_perturb=0.025, trans_perturb=0.00125, perturb_units=1)
+    p2 = closure.preset_2d3d(n_iter=3, rot_perturb=0.002, trans_perturb=0.002, perturb_units=1)
+    seeds = torch.as_tensor(syn.seed_array(purses), dtype=torch.float64, device="cuda")
+    res = torch.full((n_purses, 9), np.nan, dtype=torch.float64, device="cuda")
+    g = torch.as_tensor(rng.normal(size=(n_purses, 9)), device="cuda")
+    total = sum(pu.n for pu in purses)
+    gy = torch.full((total, 3), np.nan, dtype=torch.float64, device="cuda")
+    gr = torch.full((total,), np.nan, dtype=torch.float64, device="cuda")
+    b = P.purse_batch_create(purses)
+    try:
+        bad = [syn.purse_3d3d_ellipsoidal(p.n, 1) if p.kind == 0 else p for p in purses]
+        bad[0].lam = -bad[0].lam  # not positive definite
+        with pytest.raises(P.PurseError):
+            P.purse_batch_set_noise(b, bad)
+        P.purse_batch_set_noise(b, purses)
+        pp3, pp2 = params_from(p3, 0, 0), params_from(p2, 0, 0)
+        P.purse_batch_set_grad(b, 1)
+        P.purse_batch_solve(b, pp3, pp2, seed, seeds, S, K, res)
+        P.purse_batch_backward(b, res, g, gy, gr)
+        P.purse_batch_sync(b)
+        far = torch.empty((n_purses, 2 * K), dtype=torch.int32, device="cuda")
+        P.purse_batch_copy_farthest(b, far)
+        o = 0
+        for p, pu in enumerate(purses):
+            prm = p3 if pu.kind == 0 else p2
+            bq, bt = torch.empty((S, 4), device="cuda"), torch.empty((S, 3), device="cuda")
+            bq2, bt2 = torch.empty((S, 4), device="cuda"), torch.empty((S, 3), device="cuda")
+            P.purse_batch_copy_samples(b, p, bq, bt, bq2, bt2)
+            bsr, bst = torch.empty((S, 12), device="cuda"), torch.empty((S, 12), device="cuda")
+            P.purse_batch_copy_snap(b, p, bsr, bst)
+            with P.Purse(pu) as h:
+                sd = torch.as_tensor(pu.seed_pose()[None], dtype=torch.float64, device="cuda")
+                out = []
+                for sampler in (0, 1):
+                    q = torch.empty((S, 4), device="cuda")
+                    t = torch.empty((S, 3), device="cuda")
+                    sn = torch.empty((S, 12), device="cuda")
+                    P.purse_sample(h.h, params_from(prm, sampler, 0), seed + p, sd, 1, S, q, t, None, snap=sn)
+                    out.append((q, t, sn))
+                r1 = torch.empty(9, dtype=torch.float64, device="cuda")
+                f1 = torch.empty(2 * K, dtype=torch.int32, device="cuda")
+                P.megb_solve(h.h, 0, K, out[0][0], S, out[1][1], S, r1, f1)
+                dim = 3 if pu.kind == 0 else 2
+                y1 = torch.empty((pu.n, dim), dtype=torch.float64, device="cuda")
+                rr1 = torch.empty(pu.n, dtype=torch.float64, device="cuda")
+                P.megb_backward(h.h, 0, K, out[0][0], out[0][2], S, out[1][1], out[1][2], S, f1, r1, g[p].contiguous(),
+                                y1, rr1)
+                P.purse_sync(h.h)
+            torch.cuda.synchronize()
+            assert torch.equal(out[0][0], bq) and torch.equal(out[0][1], bt), p
+            assert torch.equal(out[1][0], bq2) and torch.equal(out[1][1], bt2), p
+            assert torch.equal(out[0][2], bsr) and torch.equal(out[1][2], bst), p
+            assert torch.equal(f1, far[p]), p
+            assert torch.allclose(r1, res[p], rtol=1e-12, atol=1e-15), p
+            gyb, grb = gy[o:o + pu.n], gr[o:o + pu.n]
+            assert torch.allclose(y1, gyb[:, :dim], rtol=1e-10, atol=1e-12 * float(y1.abs().max())), p
+            assert torch.allclose(rr1, grb, rtol=1e-10, atol=1e-12 * float(rr1.abs().max())), p
+            o += pu.n
+        # back to the identity norm: the next solve captures a new graph and runs
+        P.purse_batch_set_noise(b, None)
+        P.purse_batch_solve(b, pp3, pp2, seed, seeds, S, K, res)
+        P.purse_batch_sync(b)
+        assert torch.all(torch.isfinite(res))
+    finally:
+        P.purse_batch_destroy(b)
