@@ -346,6 +346,19 @@ purse_status purse_batch_create(int n_purses, const int* kinds, const int* offse
                                 const double* obs, const double* radii, const purse_intrinsics* K,
                                 purse_batch_t* out);
 
+/* A batch of pose-regression PURSEs (Example 3, eq. PURSEreg): PURSE p has the hypotheses
+ * [offsets[p], offsets[p+1]) (1..256 each) of the host arrays hyp (12 doubles per hypothesis: R_i
+ * row-major, then t_i; as purse_create_regression), beta_rot and beta_t (> 0).  purse_batch_solve
+ * then runs both samplers of every PURSE (reg_walk_one, the walk of the single-PURSE regression
+ * kernel) with the parameter set p3d (p2d must be valid and is not used), one seed pose per PURSE,
+ * and the balls as for the other kinds (rotation ball from the dS_R samples, translation ball from
+ * the dS_t samples): PURSE p gives exactly purse_sample / megb_solve of a regression handle with key
+ * seed + p.  No boundary snap, adjoint or noise matrices (purse_batch_set_grad / _set_noise answer
+ * PURSE_ERR_ARG).  Errors and ownership as for purse_batch_create. */
+purse_status purse_batch_create_regression(int n_purses, const int* offsets, const double* hyp,
+                                           const double* beta_rot, const double* beta_t,
+                                           purse_batch_t* out);
+
 purse_status purse_batch_destroy(purse_batch_t b);
 
 /* Noise bounded in the general norm of eq. 4 for every PURSE of the batch (the batched form of

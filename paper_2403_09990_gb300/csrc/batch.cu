@@ -20,6 +20,7 @@ struct purse_batch_s {
   float* d_ell32 = nullptr;
   double* d_ell64 = nullptr;
   std::vector<int> kinds, offsets;  // host copies (kind per PURSE, CSR keypoint offsets)
+  int reg = 0;  // pose-regression batch (purse_batch_create_regression)
   purse::WalkStats* d_stats = nullptr;
   double* d_seed_data = nullptr;
   unsigned int* d_counter = nullptr;
@@ -97,6 +98,7 @@ static BatchArgs make_args(purse_batch_t b, const purse_params* p3, const purse_
   a.snap_tr = b->grad ? b->d_snap + (size_t)kSnapStride * S : nullptr;
   a.fstar = b->grad ? b->d_fstar : nullptr;
   a.tr3d = p3->v0 > 0.0 ? 1 : 0;
+  a.reg = b->reg;
   a.status = b->d_status;
   a.evals = b->d_evals;
   return a;
@@ -152,6 +154,46 @@ static cudaError_t enqueue_batch(purse_batch_t b, const purse_params* p3, const 
   return e;
 }
 
+}  // namespace purse
+
+namespace purse {
+// Device copies of a batch's per-PURSE records and concatenated tables (FP64 and FP32), statistics
+// and seed-data slots and the status/counter words; the batch handle owns them.
+static purse_status upload_batch(const char* fn, int n_purses, int nmax, int reg, const int* kinds, const int* offsets,
+                                 const std::vector<BatchPurseInfo>& info, const std::vector<double>& t64,
+                                 purse_batch_t* out) {
+  std::vector<float> t32(t64.begin(), t64.end());
+  if (fault_at("alloc")) return injected_fault("alloc", fn);
+  purse_batch_s* b = new purse_batch_s();
+  b->n_purses = n_purses, b->nmax = nmax, b->total_rows = (int)(t64.size() / 4), b->reg = reg;
+  b->kinds.assign(kinds, kinds + n_purses);
+  b->offsets.assign(offsets, offsets + n_purses + 1);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_info, info.size() * sizeof(BatchPurseInfo));
+  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_tab64, t64.size() * sizeof(double));
+  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_tab32, t32.size() * sizeof(float));
+  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_stats, n_purses * sizeof(WalkStats));
+  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_seed_data, (size_t)n_purses * kSeedStride * sizeof(double));
+  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_counter, 256);
+  if (e == cudaSuccess) {
+    b->d_seed = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(b->d_counter) + 64);
+    b->d_evals = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(b->d_counter) + 128);
+    b->d_status = reinterpret_cast<int*>(reinterpret_cast<char*>(b->d_counter) + 192);
+    e = cudaMemset(b->d_counter, 0, 256);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_info, info.data(), info.size() * sizeof(BatchPurseInfo), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_tab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    purse_status s = cuda_fail(e, fn);
+    purse_batch_destroy(b);
+    return s;
+  }
+  *out = b;
+  return PURSE_OK;
+}
 }  // namespace purse
 
 using namespace purse;
@@ -210,37 +252,62 @@ purse_status purse_batch_create(int n_purses, const int* kinds, const int* offse
       bb[3] = radii[g] * radii[g];
     }
   }
-  std::vector<float> t32(t64.begin(), t64.end());
-  if (fault_at("alloc")) return injected_fault("alloc", "purse_batch_create");
-  purse_batch_s* b = new purse_batch_s();
-  b->n_purses = n_purses, b->nmax = nmax, b->total_rows = 2 * total;
-  b->kinds.assign(kinds, kinds + n_purses);
-  b->offsets.assign(offsets, offsets + n_purses + 1);
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_info, info.size() * sizeof(BatchPurseInfo));
-  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_tab64, t64.size() * sizeof(double));
-  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_tab32, t32.size() * sizeof(float));
-  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_stats, n_purses * sizeof(WalkStats));
-  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_seed_data, (size_t)n_purses * kSeedStride * sizeof(double));
-  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_counter, 256);
-  if (e == cudaSuccess) {
-    b->d_seed = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(b->d_counter) + 64);
-    b->d_evals = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(b->d_counter) + 128);
-    b->d_status = reinterpret_cast<int*>(reinterpret_cast<char*>(b->d_counter) + 192);
-    e = cudaMemset(b->d_counter, 0, 256);
+  return upload_batch("purse_batch_create", n_purses, nmax, 0, kinds, offsets, info, t64, out);
+}
+
+purse_status purse_batch_create_regression(int n_purses, const int* offsets, const double* hyp, const double* beta_rot,
+                                           const double* beta_t, purse_batch_t* out) {
+  if (!out) return barg("purse_batch_create_regression: out is NULL");
+  *out = nullptr;
+  if (n_purses < 1) return barg("purse_batch_create_regression: n_purses must be >= 1");
+  if (!offsets || !hyp || !beta_rot || !beta_t) return barg("purse_batch_create_regression: NULL input");
+  if (offsets[0] != 0) return barg("purse_batch_create_regression: offsets[0] must be 0");
+  int nmax = 0;
+  for (int p = 0; p < n_purses; ++p) {
+    const int n = offsets[p + 1] - offsets[p];
+    if (n < 1 || n > 256) return barg("purse_batch_create_regression: every PURSE needs 1..256 hypotheses");
+    nmax = n > nmax ? n : nmax;
   }
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_info, info.data(), info.size() * sizeof(BatchPurseInfo), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_tab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    purse_status s = cuda_fail(e, "purse_batch_create");
-    purse_batch_destroy(b);
-    return s;
+  const int total = offsets[n_purses];
+  for (int i = 0; i < total; ++i) {
+    if (!(beta_rot[i] > 0) || !(beta_t[i] > 0) || !std::isfinite(beta_rot[i]) || !std::isfinite(beta_t[i]))
+      return barg("purse_batch_create_regression: radii must be finite and > 0");
+    const double* R = hyp + 12 * (size_t)i;
+    double err = 0.0;  // |R R^T - I| and det R - 1
+    for (int k = 0; k < 12; ++k)
+      if (!std::isfinite(R[k])) return barg("purse_batch_create_regression: non-finite hypothesis");
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        const double d = R[3 * r] * R[3 * c] + R[3 * r + 1] * R[3 * c + 1] + R[3 * r + 2] * R[3 * c + 2];
+        err = std::max(err, std::fabs(d - (r == c ? 1.0 : 0.0)));
+      }
+    const double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                       R[2] * (R[3] * R[7] - R[4] * R[6]);
+    if (err > 1e-6 || std::fabs(det - 1.0) > 1e-6)
+      return barg("purse_batch_create_regression: a hypothesis rotation is not a rotation matrix");
   }
-  *out = b;
-  return PURSE_OK;
+  // PURSE p: rows [4 offsets[p], 4 offsets[p+1]) in the layout of purse_create_regression -- (t_i, beta_i^t),
+  // then the rows of R_i with beta_i^R in the first
+  std::vector<double> t64(16 * (size_t)total, 0.0);
+  std::vector<BatchPurseInfo> info(n_purses);
+  std::vector<int> kinds(n_purses, PURSE_REG);
+  for (int p = 0; p < n_purses; ++p) {
+    const int n = offsets[p + 1] - offsets[p], o = offsets[p];
+    info[p].kind = PURSE_REG, info[p].n = n, info[p].table_off = 4 * o, info[p].pad = 0;
+    info[p].fx = info[p].fy = info[p].cx = info[p].cy = 0.0;
+    info[p].rho_max = 0.0;
+    double* tp = &t64[16 * (size_t)o];
+    for (int i = 0; i < n; ++i) {
+      const double* H = hyp + 12 * (size_t)(o + i);
+      double* a = tp + 4 * (size_t)i;
+      a[0] = H[9], a[1] = H[10], a[2] = H[11], a[3] = beta_t[o + i];
+      for (int r = 0; r < 3; ++r) {
+        double* row = tp + 4 * ((size_t)(1 + r) * n + i);
+        row[0] = H[3 * r], row[1] = H[3 * r + 1], row[2] = H[3 * r + 2], row[3] = r == 0 ? beta_rot[o + i] : 0.0;
+      }
+    }
+  }
+  return upload_batch("purse_batch_create_regression", n_purses, nmax, 1, kinds.data(), offsets, info, t64, out);
 }
 
 purse_status purse_batch_destroy(purse_batch_t b) {
@@ -265,6 +332,7 @@ purse_status purse_batch_destroy(purse_batch_t b) {
 
 purse_status purse_batch_set_noise(purse_batch_t b, const double* lam) {
   if (!b) return barg("purse_batch_set_noise: NULL batch");
+  if (b->reg) return barg("purse_batch_set_noise: regression PURSEs take no noise matrices");
   if (b->exec) cudaGraphExecDestroy(b->exec);  // the next solve captures a graph with the new tables
   b->exec = nullptr;
   b->graph_key.clear();
@@ -311,8 +379,8 @@ purse_status purse_batch_solve(purse_batch_t b, const purse_params* p3d, const p
     return barg("purse_batch_solve: too many work items (2 x n_purses x n_samples >= 2^32)");
   if (!d_seeds || !d_results) return barg("purse_batch_solve: NULL buffer");
   if (batch_walk_smem(b->nmax, p3d->n_perturb > p2d->n_perturb ? p3d->n_perturb : p2d->n_perturb,
-                      p3d->n_steps > p2d->n_steps ? p3d->n_steps : p2d->n_steps, b->warps, b->d_ell32 != nullptr) >
-      227 * 1024)
+                      p3d->n_steps > p2d->n_steps ? p3d->n_steps : p2d->n_steps, b->warps, b->d_ell32 != nullptr,
+                      b->reg != 0) > 227 * 1024)
     return barg("purse_batch_solve: the largest PURSE does not fit the walk kernel's shared memory");
   if (fault_at("launch")) return injected_fault("launch", "purse_batch_solve");
   purse_status s = ensure_batch_buffers(b, n_samples, n_iters);
@@ -384,7 +452,7 @@ purse_status purse_batch_tune(purse_batch_t b, const purse_params* p3d, const pu
   float best = 1e30f;
   int bc = b->chunk, bw = b->warps;
   for (int wi = 0; wi < 2 && e == cudaSuccess; ++wi) {
-    if (batch_walk_smem(b->nmax, np, nt, warps[wi], b->d_ell32 != nullptr) > 227 * 1024) continue;
+    if (batch_walk_smem(b->nmax, np, nt, warps[wi], b->d_ell32 != nullptr, b->reg != 0) > 227 * 1024) continue;
     for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
       float ms = 0.f;
       for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms up
@@ -441,6 +509,7 @@ purse_status purse_batch_copy_samples(purse_batch_t b, int p, float* d_q_rot, fl
 purse_status purse_batch_set_grad(purse_batch_t b, int enable) {
   if (!b) return barg("purse_batch_set_grad: NULL batch");
   if (enable != 0 && enable != 1) return barg("purse_batch_set_grad: enable must be 0 or 1");
+  if (enable && b->reg) return barg("purse_batch_set_grad: no boundary snap (and no adjoint) for regression PURSEs");
   if (b->grad != enable) {
     b->grad = enable;
     if (b->exec) cudaGraphExecDestroy(b->exec);

@@ -81,6 +81,7 @@ struct BatchArgs {
   float* snap_tr;   // same for the dS_t walks
   int32_t* fstar;   // NULL or n_purses x 2: farthest sample from each final centre
   int tr3d;         // 3D-3D: run the dS_t walks and take the translation ball from them (v0 > 0)
+  int reg;          // every PURSE is a pose-regression PURSE (Example 3), parameters in slot 0
   int* status;
   unsigned long long* evals;
 };
@@ -180,7 +181,7 @@ cudaError_t launch_stats_batch(int n_purses, const BatchPurseInfo* info, const d
                                const double* seeds, const BatchStatParams& sp, WalkStats* out, double* seed_data,
                                cudaStream_t st);
 // lam: the batch carries noise matrices (the tables and slabs of the walks with U_i)
-size_t batch_walk_smem(int nmax, int n_perturb, int n_steps, int warps, bool lam = false);
+size_t batch_walk_smem(int nmax, int n_perturb, int n_steps, int warps, bool lam = false, bool reg = false);
 cudaError_t launch_batch_walk(const BatchArgs& b, int chunk, int warps, int sm_count, cudaStream_t st);
 cudaError_t launch_megb_batch(const BatchArgs& b, int n_iters, double* d_results, int32_t* d_farthest,
                               cudaStream_t st);

@@ -165,8 +165,9 @@ __global__ void __launch_bounds__(kStatsThreads) stats_batch_kernel(const BatchP
   __shared__ WalkStats sh;
   const int p = blockIdx.x;
   const BatchPurseInfo in = info[p];
+  const int pk = in.kind == 1 ? 1 : 0;  // parameter slot: 2D-3D, else 3D-3D or pose regression
   stats_block(seeds + 12 * (size_t)p, 1, tab64 + 4 * (size_t)in.table_off, in.n, in.kind, in.fx, in.fy,
-              sp.t_p[in.kind], sp.th_p[in.kind], sp.raw[in.kind], out + p, seed_data + (size_t)p * kSeedStride, red,
+              sp.t_p[pk], sp.th_p[pk], sp.raw[pk], out + p, seed_data + (size_t)p * kSeedStride, red,
               sh, ell64 ? ell64 + 8 * (size_t)(in.table_off / 2) : nullptr);
 }
 

@@ -1592,8 +1592,13 @@ __host__ __device__ inline size_t batch_warp_bytes(int nmax, int n_perturb, int 
   return walk_table_bytes<float>(nmax, lam) + 128 + walk_slab_bytes2<float>(nmax, n_perturb, n_steps, lam);
 }
 
-size_t batch_walk_smem(int nmax, int n_perturb, int n_steps, int warps, bool lam) {
-  return (size_t)warps * batch_warp_bytes(nmax, n_perturb, n_steps, lam);
+// Pose-regression batches: the warp's hypothesis table (4N rows), round keys, then reg_walk_one's slab.
+__host__ __device__ inline size_t batch_reg_warp_bytes(int nmax, int n_perturb) {
+  return reg_table_bytes<float>(nmax) + 128 + reg_slab_bytes<float>(nmax, n_perturb);
+}
+
+size_t batch_walk_smem(int nmax, int n_perturb, int n_steps, int warps, bool lam, bool reg) {
+  return (size_t)warps * (reg ? batch_reg_warp_bytes(nmax, n_perturb) : batch_warp_bytes(nmax, n_perturb, n_steps, lam));
 }
 
 // TR3D: the 3D-3D dS_t walks run too (b.tr3d); a separate instantiation so that batches without
@@ -1675,6 +1680,85 @@ __global__ void __launch_bounds__(kWalkThreads, 2)
   if (lane == 0 && evals) atomicAdd(b.evals, evals);
 }
 
+// Batches of pose-regression PURSEs (Example 3): the same work queue over (PURSE, sampler, walk)
+// items, both samplers for every PURSE, each walk run by reg_walk_one (the walk of reg_walk_kernel).
+__global__ void __launch_bounds__(kWalkThreads, 2)
+    batch_reg_walk_kernel(const __grid_constant__ BatchArgs b, const int chunk, const int np_max) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* base = smem + (size_t)warp * batch_reg_warp_bytes(b.nmax, np_max);
+  T4<float>* tab = reinterpret_cast<T4<float>*>(base);
+  uint32_t* rkw = reinterpret_cast<uint32_t*>(base + reg_table_bytes<float>(b.nmax));
+  T4<float>* C = reinterpret_cast<T4<float>*>(base + reg_table_bytes<float>(b.nmax) + 128);
+  const unsigned S = (unsigned)b.n_samples;
+  const unsigned long long seed = *b.seed;
+  unsigned long long evals = 0;
+  int cur = -1;
+  WalkCtx<float> c;
+  Slab<float> sl;
+  sl.D = nullptr, sl.L = nullptr, sl.E = nullptr, sl.S = nullptr;
+  const RkPtr rk{rkw};
+  for (;;) {
+    unsigned head = 0;
+    if (lane == 0) head = atomicAdd(b.counter, (unsigned)chunk);
+    head = __shfl_sync(kFullMask, head, 0);
+    if (head >= b.total_items) break;
+    const unsigned end = min(head + (unsigned)chunk, b.total_items);
+    for (unsigned item = head; item < end; ++item) {
+      const int p = (int)(item / (2 * S));
+      const int smp = (int)((item / S) & 1u);
+      const int w = (int)(item % S);
+      if (p != cur) {
+        const BatchPurseInfo in = b.info[p];
+        __syncwarp();
+        const T4<float>* src = reinterpret_cast<const T4<float>*>(b.table) + in.table_off;
+        for (int r = lane; r < 4 * in.n; r += 32) tab[r] = src[r];
+        const unsigned long long key = seed + (unsigned long long)p;
+        if (lane < 10) {
+          rkw[2 * lane] = (uint32_t)key + (uint32_t)lane * 0x9E3779B9u;
+          rkw[2 * lane + 1] = (uint32_t)(key >> 32) + (uint32_t)lane * 0xBB67AE85u;
+        }
+        c.N = in.n, c.NP = b.n_perturb[0], c.K = b.n_keep[0], c.NT = b.n_steps[0], c.n_iter = b.n_iter[0], c.mc = 1;
+        c.fx = c.fy = c.cx = c.cy = 0.0f;
+        c.rho_max = 0.0f;
+        c.omega0 = b.omega0[0], c.v0 = b.v0[0], c.gamma = b.gamma[0];
+        c.om0 = float(b.omega0[0]), c.vv0 = float(b.v0[0]), c.gam = float(b.gamma[0]);
+        c.st = b.stats + p, c.seed_data = b.seed_data + (size_t)p * kSeedStride, c.s0 = 1;
+        c.key0 = (uint32_t)key, c.key1 = (uint32_t)(key >> 32);
+        c.trace = nullptr, c.status = b.status, c.out_snap = nullptr;
+        c.tab64 = nullptr, c.kd = nullptr, c.ell64 = nullptr;
+        sl.P = C + in.n;
+        sl.key = reinterpret_cast<uint32_t*>(sl.P + c.NP);
+        sl.J = reinterpret_cast<int*>(sl.key + c.NP);
+        cur = p;
+        __syncwarp();
+      }
+      c.r_pert = float(smp == 0 ? c.st->r_trans : c.st->r_rot);
+      const size_t off = (size_t)p * S;
+      c.out_q = (smp == 0 ? b.q_rot : b.q_tr) + 4 * off;
+      c.out_t = (smp == 0 ? b.t_rot : b.t_tr) + 3 * off;
+      if (smp == 0)
+        reg_walk_one<float, 0>(c, rk, w, tab, C, sl, lane, evals);
+      else
+        reg_walk_one<float, 1>(c, rk, w, tab, C, sl, lane, evals);
+    }
+  }
+  if (lane == 0 && evals) atomicAdd(b.evals, evals);
+}
+
+static cudaError_t launch_batch_reg_walk(const BatchArgs& b, int chunk, int warps, int sm_count, cudaStream_t st) {
+  const int np_max = b.n_perturb[0];
+  const size_t smem = batch_walk_smem(b.nmax, np_max, b.n_steps[0], warps, false, true);
+  cudaError_t e = cudaFuncSetAttribute(batch_reg_walk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_reg_walk_kernel, 32 * warps, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  batch_reg_walk_kernel<<<per_sm * sm_count, 32 * warps, smem, st>>>(b, chunk, np_max);
+  return cudaGetLastError();
+}
+
 template <bool TR3D, bool LAM>
 static cudaError_t launch_batch_walk_t(const BatchArgs& b, int chunk, int warps, int sm_count, cudaStream_t st) {
   const int np_max = max(b.n_perturb[0], b.n_perturb[1]), nt_max = max(b.n_steps[0], b.n_steps[1]);
@@ -1691,6 +1775,7 @@ static cudaError_t launch_batch_walk_t(const BatchArgs& b, int chunk, int warps,
 }
 
 cudaError_t launch_batch_walk(const BatchArgs& b, int chunk, int warps, int sm_count, cudaStream_t st) {
+  if (b.reg) return launch_batch_reg_walk(b, chunk, warps, sm_count, st);
   if (b.ell)
     return b.tr3d ? launch_batch_walk_t<true, true>(b, chunk, warps, sm_count, st)
                   : launch_batch_walk_t<false, true>(b, chunk, warps, sm_count, st);

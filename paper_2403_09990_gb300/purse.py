@@ -74,6 +74,7 @@ _SIGS = {
                         ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP],
     "purse_sync": [_VP, _VP],
     "purse_batch_create": [ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)],
+    "purse_batch_create_regression": [ctypes.c_int, _VP, _VP, _VP, _VP, _VP],
     "purse_batch_destroy": [_VP],
     "purse_batch_set_noise": [_VP, _VP],
     "purse_batch_solve": [_VP, ctypes.POINTER(purse_params), ctypes.POINTER(purse_params), ctypes.c_uint64, _VP,
@@ -317,6 +318,23 @@ def purse_batch_create(purses) -> int:
     _check(lib().purse_batch_create(len(purses), kinds.ctypes.data, offsets.ctypes.data, model.ctypes.data,
                                     obs.ctypes.data, radii.ctypes.data, ctypes.cast(Ks, _VP), ctypes.byref(h)),
            "purse_batch_create")
+    return h.value
+
+
+def purse_batch_create_regression(purses) -> int:
+    """Batch handle from a list of pose-regression synthetic.Purse-like objects (rot_hyp, obs, radii_rot,
+    radii)."""
+    import numpy as np
+    offsets = np.zeros(len(purses) + 1, dtype=np.int32)
+    offsets[1:] = np.cumsum([p.radii.shape[0] for p in purses])
+    hyp = np.ascontiguousarray(np.concatenate(
+        [np.concatenate([np.asarray(p.rot_hyp).reshape(-1, 9), np.asarray(p.obs).reshape(-1, 3)], axis=1)
+         for p in purses]), dtype=np.float64)
+    br = np.ascontiguousarray(np.concatenate([p.radii_rot for p in purses]), dtype=np.float64)
+    bt = np.ascontiguousarray(np.concatenate([p.radii for p in purses]), dtype=np.float64)
+    h = _VP()
+    _check(lib().purse_batch_create_regression(len(purses), offsets.ctypes.data, hyp.ctypes.data, br.ctypes.data,
+                                               bt.ctypes.data, ctypes.byref(h)), "purse_batch_create_regression")
     return h.value
 
 

@@ -277,3 +277,49 @@ def test_batch_noise_matrices_equal_single_path():
         assert torch.all(torch.isfinite(res))
     finally:
         P.purse_batch_destroy(b)
+
+
+def test_batch_regression_equals_single_path():
+    """purse_batch_create_regression (Example 3 over a batch): PURSE p gives exactly the samples of
+    both samplers, the farthest sequences and the balls of purse_sample / megb_solve on a regression
+    handle with key seed + p; snap, gradients and noise matrices are refused."""
+    rng = np.random.default_rng(4)
+    purses = [syn.purse_reg(int(n), 200 + p) for p, n in enumerate([1, 3, 10, 29, 7, 16, 40])]
+    purses.append(syn.purse_reg_nested(10, 3))
+    n_purses, S, K, seed = len(purses), 300, 40, 123
+    prm = closure.preset_reg(n_iter=4, rot_perturb=0.2, v0=0.02)
+    seeds = torch.as_tensor(syn.seed_array(purses), dtype=torch.float64, device="cuda")
+    res = torch.full((n_purses, 9), np.nan, dtype=torch.float64, device="cuda")
+    b = P.purse_batch_create_regression(purses)
+    try:
+        pp = params_from(prm, 0, 0)
+        with pytest.raises(P.PurseError):
+            P.purse_batch_set_grad(b, 1)
+        with pytest.raises(P.PurseError):
+            P.purse_batch_set_noise(b, None)
+        P.purse_batch_solve(b, pp, pp, seed, seeds, S, K, res)
+        evals = P.purse_batch_sync(b)
+        assert evals > 0
+        far = torch.empty((n_purses, 2 * K), dtype=torch.int32, device="cuda")
+        P.purse_batch_copy_farthest(b, far)
+        for p, pu in enumerate(purses):
+            bq, bt = torch.empty((S, 4), device="cuda"), torch.empty((S, 3), device="cuda")
+            bq2, bt2 = torch.empty((S, 4), device="cuda"), torch.empty((S, 3), device="cuda")
+            P.purse_batch_copy_samples(b, p, bq, bt, bq2, bt2)
+            torch.cuda.synchronize()
+            q, t = single(pu, prm, 0, seed + p, S)
+            q2, t2 = single(pu, prm, 1, seed + p, S)
+            assert torch.equal(q, bq) and torch.equal(t, bt), p
+            assert torch.equal(q2, bq2) and torch.equal(t2, bt2), p
+            r1 = torch.empty(9, dtype=torch.float64, device="cuda")
+            f1 = torch.empty(2 * K, dtype=torch.int32, device="cuda")
+            with P.Purse(pu) as h:
+                P.megb_solve(h.h, 0, K, q, S, t2, S, r1, f1)
+                P.purse_sync(h.h)
+            assert torch.equal(f1, far[p]), p
+            assert torch.allclose(r1, res[p], rtol=1e-12, atol=1e-15), (p, r1, res[p])
+            for qq, tt in ((q, t), (q2, t2)):  # every sample of both samplers inside its PURSE
+                qn, tn = qq.cpu().numpy().astype(np.float64), tt.cpu().numpy().astype(np.float64)
+                assert np.all(parity.classify(pu, so3.R_from_quat(qn), tn, 0) >= 0), p
+    finally:
+        P.purse_batch_destroy(b)
