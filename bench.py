@@ -751,7 +751,98 @@ def sweep_next(P, syn, dev, stream):
     row["isotropic_fused_walks"] = {"ms": iso_ms, "evals_per_s": iso_evals / (iso_ms / 1e3),
                                     "note": "purse_sample on the identity-norm PURSE of the same seed, walks only"}
     lines.append(row)
+    lines.append(sweep_batch_row(P, syn, dev, stream, "batch_lambda", events, cpu))
+    lines.append(sweep_batch_row(P, syn, dev, stream, "batch_reg", events, cpu))
     return lines
+
+
+def sweep_batch_row(P, syn, dev, stream, name, events, cpu, n_purses=1024, S=4096, n_single=16, oracle_walks=32):
+    """One batch solve (graph replay, CUDA events) of n_purses PURSEs with noise matrices (3D-3D / 2D-3D
+    by a fair coin, N ~ U{4..64}, eigenvalues 0.5-2) or of pose-regression PURSEs (N ~ U{3..20}
+    hypotheses), S samples each, N_I = 5, both balls; beside it the single-PURSE path for the first
+    n_single PURSEs (wall clock, create + both samplers + balls + D2H) and the oracle on oracle_walks
+    walks per sampler of the first PURSE (one host core)."""
+    import torch
+    from oracle import closure, megb as om
+    rng = np.random.default_rng(11)
+    if name == "batch_lambda":
+        purses = [syn.purse_3d3d_ellipsoidal(int(rng.integers(4, 65)), 1000 + p) if rng.random() < 0.5 else
+                  syn.purse_2d3d_ellipsoidal(int(rng.integers(4, 65)), 1000 + p) for p in range(n_purses)]
+        p3 = P.make_params(n_iter=5, n_perturb=150, n_keep=10, n_steps=15, omega0=0.5, v0=0.0, gamma=0.5,
+                           rot_perturb=0.0, trans_perturb=0.1)
+        p2 = P.make_params(n_iter=5, n_perturb=150, n_keep=10, n_steps=15, omega0=1.0, v0=2.0, gamma=0.5,
+                           rot_perturb=0.2, trans_perturb=0.1)
+        b = P.purse_batch_create(purses)
+        P.purse_batch_set_noise(b, purses)
+        note = (f"{n_purses} PURSEs with noise matrices (eq. 4; 3D-3D / 2D-3D by a fair coin, N ~ U{{4..64}}, "
+                f"eigenvalues 0.5-2), {S} samples each, N_I = 5, both balls ({K_MEGB} GGD iterations)")
+    else:
+        purses = [syn.purse_reg(int(rng.integers(3, 21)), 2000 + p) for p in range(n_purses)]
+        p3 = P.make_params(n_iter=5, n_perturb=150, n_keep=10, n_steps=10, omega0=0.5, v0=0.02, gamma=0.5,
+                           rot_perturb=0.2, trans_perturb=0.1)
+        p2 = p3
+        b = P.purse_batch_create_regression(purses)
+        note = (f"{n_purses} pose-regression PURSEs (Example 3, N ~ U{{3..20}} hypotheses), {S} samples each, "
+                f"both samplers, N_I = 5, both balls ({K_MEGB} GGD iterations)")
+    seeds = torch.as_tensor(syn.seed_array(purses), dtype=torch.float64, device=dev)
+    res = torch.empty((n_purses, 9), dtype=torch.float64, device=dev)
+    try:
+        ms = events(lambda: P.purse_batch_solve(b, p3, p2, 5, seeds, S, K_MEGB, res, stream), 2)
+        P.purse_batch_sync(b, stream)
+        finite = bool(torch.isfinite(res).all())
+    finally:
+        P.purse_batch_destroy(b)
+
+    def samplers(pu):
+        return (0, 1) if pu.kind != syn.KIND_3D3D else (0,)
+
+    def per_walk(pu, prm):
+        return prm.n_iter * (prm.n_perturb + prm.n_keep * prm.n_steps) * (2 * pu.n if pu.kind == syn.KIND_REG else pu.n)
+    evals = sum(len(samplers(pu)) * S * per_walk(pu, p3 if pu.kind != syn.KIND_2D3D else p2) for pu in purses)
+    # the single-PURSE path for the first PURSEs
+    q = [torch.empty((S, 4), dtype=torch.float32, device=dev) for _ in range(2)]
+    t = [torch.empty((S, 3), dtype=torch.float32, device=dev) for _ in range(2)]
+    r1 = torch.empty(9, dtype=torch.float64, device=dev)
+
+    def single():
+        for p, pu in enumerate(purses[:n_single]):
+            prm = p3 if pu.kind != syn.KIND_2D3D else p2
+            with P.Purse(pu) as h:
+                sd = torch.as_tensor(pu.seed_pose()[None], dtype=torch.float64, device=dev)
+                for smp in samplers(pu):
+                    prm.sampler = smp
+                    P.purse_sample(h.h, prm, 5 + p, sd, 1, S, q[smp], t[smp], None, stream)
+                prm.sampler = 0
+                P.megb_solve(h.h, 0, K_MEGB, q[0], S, t[1] if len(samplers(pu)) == 2 else t[0], S, r1, None, stream)
+                r1.cpu()
+    single()
+    _, sdt = _host_timed(single)
+    # the oracle on a bounded sample of the first PURSE
+    pu = purses[0]
+    oprm = closure.preset_reg(v0=0.02, rot_perturb=0.2) if pu.kind == syn.KIND_REG else (
+        closure.preset_3d3d() if pu.kind == syn.KIND_3D3D else closure.preset_2d3d())
+    ids = np.arange(oracle_walks)
+
+    def oracle_run():
+        R, tt = closure.sample_rotation_boundary(pu, pu.seed_pose()[None], oprm, 5, ids)
+        qs, ts = closure.as_samples(R, tt)
+        if len(samplers(pu)) == 2:
+            R2, tt2 = closure.sample_translation_boundary(pu, pu.seed_pose()[None], oprm, 5, ids)
+            ts = closure.as_samples(R2, tt2)[1]
+        om.megb_rotation(qs, K_MEGB)
+        om.megb_translation(ts, K_MEGB)
+    _, odt = _host_timed(oracle_run)
+    oev = len(samplers(pu)) * oracle_walks * per_walk(pu, oprm)
+    return {"sweep": "next", "row": name, "workload": note,
+            "gpu": {"ms": ms, "purses_per_s": n_purses / (ms / 1e3), "evals_per_s": evals / (ms / 1e3),
+                    "results_finite": finite, "path": "purse_batch_solve (one graph: statistics, persistent walk "
+                    "launch, one block per ball)"},
+            "per_instance": {"purses": n_single, "purses_per_s": n_single / sdt,
+                             "path": "per PURSE: create + purse_sample per sampler + megb_solve + D2H, wall clock"},
+            "speedup_vs_per_instance": (n_purses / (ms / 1e3)) / (n_single / sdt),
+            "cpu_baseline": cpu(oev / odt, "evals/s", f"{oracle_walks} walks per sampler of the first PURSE + both "
+                                "balls"),
+            "gpu_over_oracle": (evals / (ms / 1e3)) / (oev / odt)}
 
 
 def oracle_params(purse):

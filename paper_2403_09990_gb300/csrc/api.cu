@@ -222,10 +222,12 @@ namespace purse {
 // the d x d matrix L (row-major), written as 8 values (3D: u00 u01 u02 u11 u12 u22; 2D: u00 u01 u11;
 // the rest 0).  Returns NULL, or why L is not a symmetric positive definite matrix.
 const char* noise_factor(const double* L, int d, double* o) {
+  double scale = 0.0;  // symmetry is judged against the size of the matrix, not of the entry (an entry
+                      // near 0 formed as a sum of products differs from its transpose by their rounding)
+  for (int k = 0; k < d * d; ++k) scale = std::max(scale, std::fabs(L[k]));
   for (int r = 0; r < d; ++r)
     for (int c = 0; c < r; ++c)
-      if (std::fabs(L[r * d + c] - L[c * d + r]) > 1e-12 * (std::fabs(L[r * d + c]) + std::fabs(L[c * d + r])) + 1e-300)
-        return "a noise matrix is not symmetric";
+      if (std::fabs(L[r * d + c] - L[c * d + r]) > 1e-12 * scale + 1e-300) return "a noise matrix is not symmetric";
   double U[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   for (int r = 0; r < d; ++r) {
     double s2 = L[r * d + r];
