@@ -51,8 +51,8 @@ SM_COUNT_NOMINAL = 152
 # --no-plain --no-grad --no-c1 --no-tune (one pass).  The counters belong to the kernel built from the sources
 # whose SHA-256 (walk.cu, dev.cuh, internal.h concatenated) begins with WALK_DRAM_SRC; any other source gives
 # traffic null.
-WALK_DRAM_BYTES = {"R": 179456 + 1536, "t": 610048 + 1024}
-WALK_DRAM_SRC = "0abdc04772bdf9f1"
+WALK_DRAM_BYTES = {"R": 438272 + 768, "t": 914944 + 0}
+WALK_DRAM_SRC = "20892b8d1bfbb92d"
 FP32_LANES_PER_SM = 128
 # C1: 3D-3D PURSE (N = 8, seed 0) in FP64, |S0| = 2048 RANSAG seeds, N_W = 2 walks each (4096 samples of the
 # dS_R sampler, N_I = 5, 3DMatch preset), both balls with K = 200; flops per 3D-3D evaluation: 26 for in_purse
