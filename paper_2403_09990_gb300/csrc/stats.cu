@@ -374,6 +374,22 @@ __device__ int quartic_real_roots(const double (&A)[5], double (&out)[4]) {
   return nr;
 }
 
+// Orthonormal frame (columns F[.][0..2]) of the triangle X_0 X_1 X_2: e_1 along X_1 - X_0, e_2 the
+// unit part of X_2 - X_0 orthogonal to it, e_3 = e_1 x e_2.  For two congruent triangles the rotation
+// F_X F_P^T maps one onto the other.
+__device__ __forceinline__ void triangle_frame(const double (&X)[3][3], double (&F)[3][3]) {
+  double u[3], v[3];
+  for (int d = 0; d < 3; ++d) u[d] = X[1][d] - X[0][d], v[d] = X[2][d] - X[0][d];
+  const double iu = rsqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  for (int d = 0; d < 3; ++d) u[d] *= iu;
+  const double uv = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+  for (int d = 0; d < 3; ++d) v[d] -= uv * u[d];
+  const double iv = rsqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  for (int d = 0; d < 3; ++d) v[d] *= iv;
+  const double w[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+  for (int d = 0; d < 3; ++d) F[d][0] = u[d], F[d][1] = v[d], F[d][2] = w[d];
+}
+
 // One RANSAG trial of Step I for 2D-3D: three distinct constraints (index words as for 3D-3D), one
 // pixel uniform in each noise disk, bearings f_i = K^-1 (z_i, 1) / |.|, and P3P by Grunert's
 // elimination: the law of cosines on the triangle sides a = |P_2 - P_3|, b = |P_1 - P_3|,
@@ -383,7 +399,13 @@ __device__ int quartic_real_roots(const double (&A)[5], double (&out)[4]) {
 // (a', b', g: the angles between bearings 2-3, 1-3, 1-2).  Per real root v (ascending):
 // s_1 = b / sqrt(Q(v)); u from u^2 - 2 cos(g) u + 1 - (c^2 / b^2) Q(v) = 0, each root kept when
 // u^2 + v^2 - 2 u v cos(a') = (a^2 / b^2) Q(v) holds to 1e-8 relative and every depth is positive;
-// the pose maps P_i onto s_i f_i (Horn's fit).  Candidate slot k of the trial holds the k-th pose
+// the pose maps P_i onto s_i f_i.  Those depths make the camera-frame triangle X_i = s_i f_i congruent
+// to the model triangle (up to the root's rounding), so the rotation taking the orthonormal frame of
+// (P_2 - P_1, P_3 - P_1) onto that of (X_2 - X_1, X_3 - X_1) is the least-squares (Horn / Arun) fit of
+// the three pairs to rounding, formed without an eigen-decomposition (each FP64 instruction is
+// expensive on this part); t = mean X - R mean P.
+// Acceptance is division-free: P_z > 0 and |(y_i - c) X_z - f X_xy|_(Lambda) <= r_i X_z per constraint.
+// Candidate slot k of the trial holds the k-th pose
 // and acc = 1 when it lies in the PURSE (eq. 2/5, FP64).  Up to four slots per trial.
 __global__ void __launch_bounds__(128)
     ransag_p3p_kernel(const double* tab, const double* ell, int n, double fx, double fy, double cx, double cy,
@@ -467,14 +489,12 @@ __global__ void __launch_bounds__(128)
         pbar[d] = (P[0][d] + P[1][d] + P[2][d]) / 3.0;
         xbar[d] = (B3[0][d] + B3[1][d] + B3[2][d]) / 3.0;
       }
-      double M[9];  // sum (x - xbar)(p - pbar)^T
+      double E[3][3], F[3][3];  // orthonormal frames (columns) of the model and camera triangles
+      triangle_frame(P, E);
+      triangle_frame(B3, F);
+      M3<double> R;
       for (int rr = 0; rr < 3; ++rr)
-        for (int cc = 0; cc < 3; ++cc) {
-          double acc_m = 0.0;
-          for (int kk = 0; kk < 3; ++kk) acc_m += (B3[kk][rr] - xbar[rr]) * (P[kk][cc] - pbar[cc]);
-          M[3 * rr + cc] = acc_m;
-        }
-      const M3<double> R = qmat(rotation_maximising_trace(M));
+        for (int cc = 0; cc < 3; ++cc) R.m[3 * rr + cc] = F[rr][0] * E[cc][0] + F[rr][1] * E[cc][1] + F[rr][2] * E[cc][2];
       double t[3];
       for (int rr = 0; rr < 3; ++rr)
         t[rr] = xbar[rr] - (R.m[3 * rr] * pbar[0] + R.m[3 * rr + 1] * pbar[1] + R.m[3 * rr + 2] * pbar[2]);
@@ -488,14 +508,16 @@ __global__ void __launch_bounds__(128)
         if (!(X2 > 0.0)) {
           ok = false;
         } else {
-          const double gu = bi[0] - (fx * X0 / X2 + cx), gv = bi[1] - (fy * X1 / X2 + cy);
+          // the pixel residual times X_z > 0
+          const double gu = (bi[0] - cx) * X2 - fx * X0, gv = (bi[1] - cy) * X2 - fy * X1;
           double g2 = gu * gu + gv * gv;
           if (ell) {
             const double* U = ell + 8 * i;
             const double a = U[0] * gu + U[1] * gv, b = U[2] * gv;
             g2 = a * a + b * b;
           }
-          ok = ai[3] - sqrt(g2) >= 0.0;
+          const double rz = ai[3] * X2;
+          ok = g2 <= rz * rz;
         }
       }
       double* os = o + 12 * slot;
