@@ -58,6 +58,22 @@ __device__ __forceinline__ bool better(double ka, int ia, double kb, int ib) {
   return ka > kb || (ka == kb && ia < ib);
 }
 
+// The same rule on the bit patterns of keys >= 0 (an empty entry is (0, INT_MAX), below every sample).
+__device__ __forceinline__ bool better_bits(unsigned long long ka, int ia, unsigned long long kb, int ib) {
+  return ka > kb || (ka == kb && ia < ib);
+}
+
+// Warp reduction of (key bits, index) by that rule with three integer warp maxima.
+__device__ __forceinline__ void warp_best64(unsigned long long& kb, int& bi) {
+  const bool has = bi != INT_MAX;
+  const uint32_t hw = __reduce_max_sync(kFullMask, has ? (uint32_t)(kb >> 32) : 0u);
+  const uint32_t lw = __reduce_max_sync(kFullMask, has && (uint32_t)(kb >> 32) == hw ? (uint32_t)kb : 0u);
+  const unsigned long long m = ((unsigned long long)hw << 32) | lw;
+  const uint32_t mi = __reduce_max_sync(kFullMask, has && kb == m ? ~(uint32_t)bi : 0u);
+  kb = m;
+  bi = mi ? (int)~mi : INT_MAX;
+}
+
 template <typename T>
 __global__ void megb_init(const T* q, int nq, const T* t, int nt, MegbState* s) {
   if (threadIdx.x != 0) return;
@@ -314,45 +330,39 @@ __device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbSta
     if (!*last) return false;
     if (tid != 0) return true;
   } else {
-  bk = (double)bkt;
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const double ok = __shfl_xor_sync(kFullMask, bk, o);
-    const int oi = __shfl_xor_sync(kFullMask, bi, o);
-    if (better(ok, oi, bk, bi)) bk = ok, bi = oi;
-  }
-  if (lane == 0) wkey[warp] = bk, widx[warp] = bi;
-  __syncthreads();
-  if (tid == 0) {
-    for (int w = 1; w < kMegbThreads / 32; ++w)
-      if (better(wkey[w], widx[w], bk, bi)) bk = wkey[w], bi = widx[w];
-    parts[bid] = Part{bk, bi, 0};
+    // FP64 keys (>= 0) order like their 64-bit patterns: the same rule with integer reductions of
+    // (key bits, index) -- the high word, then the low word, then the complement of the index
+    (void)bk;
+    unsigned long long kb = bi != INT_MAX ? (unsigned long long)__double_as_longlong(bkt) : 0ull;
+    warp_best64(kb, bi);
+    unsigned long long* wpk = reinterpret_cast<unsigned long long*>(wkey);
+    if (lane == 0) wpk[warp] = kb, widx[warp] = bi;
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < kMegbThreads / 32; ++w)
+        if (better_bits(wpk[w], widx[w], kb, bi)) kb = wpk[w], bi = widx[w];
+      parts[bid] = Part{__longlong_as_double((long long)kb), bi, 0};
+      __threadfence();
+      const unsigned ticket = atomicAdd(&s->counter[MODE], 1u);
+      *last = ticket == (unsigned)nb - 1;
+    }
+    __syncthreads();
+    if (!*last) return false;
     __threadfence();
-    const unsigned ticket = atomicAdd(&s->counter[MODE], 1u);
-    *last = ticket == (unsigned)nb - 1;
-  }
-  __syncthreads();
-  if (!*last) return false;
-  __threadfence();
-  bk = -1.0, bi = INT_MAX;
-  for (int b = tid; b < nb; b += blockDim.x) {
-    // partials of other blocks: read from L2, bypassing this SM's L1
-    const double pk = __ldcg(&parts[b].key);
-    const int pi = __ldcg(&parts[b].idx);
-    if (better(pk, pi, bk, bi)) bk = pk, bi = pi;
-  }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const double ok = __shfl_xor_sync(kFullMask, bk, o);
-    const int oi = __shfl_xor_sync(kFullMask, bi, o);
-    if (better(ok, oi, bk, bi)) bk = ok, bi = oi;
-  }
-  __syncthreads();  // every warp has read wkey / widx of the first reduction
-  if (lane == 0) wkey[warp] = bk, widx[warp] = bi;
-  __syncthreads();
-  if (tid != 0) return true;
-  for (int w = 1; w < kMegbThreads / 32; ++w)
-    if (better(wkey[w], widx[w], bk, bi)) bk = wkey[w], bi = widx[w];
+    kb = 0ull, bi = INT_MAX;
+    for (int b = tid; b < nb; b += blockDim.x) {
+      // partials of other blocks: read from L2, bypassing this SM's L1
+      const unsigned long long pk = (unsigned long long)__ldcg(reinterpret_cast<const long long*>(&parts[b].key));
+      const int pi = __ldcg(&parts[b].idx);
+      if (better_bits(pk, pi, kb, bi)) kb = pk, bi = pi;
+    }
+    warp_best64(kb, bi);
+    __syncthreads();  // every warp has read wpk / widx of the first reduction
+    if (lane == 0) wpk[warp] = kb, widx[warp] = bi;
+    __syncthreads();
+    if (tid != 0) return true;
+    for (int w = 1; w < kMegbThreads / 32; ++w)
+      if (better_bits(wpk[w], widx[w], kb, bi)) kb = wpk[w], bi = widx[w];
   }
   s->counter[MODE] = 0;
   auto ld = [](const double* p) { return COHERENT ? __ldcg(p) : *p; };
