@@ -4,11 +4,14 @@
 //                geodesic distance, monotone on [0, pi]),
 //                C_k = SLERP(C_{k-1}, q_{f_k}, 1/k)
 //   translation: f_k = argmax_s |t_s - c_{k-1}|^2,  c_k = c_{k-1} + (t_f - c_{k-1}) / k
-// One launch per iteration: every block reduces its slice to a (key, index)
-// partial (FP32 samples: one 64-bit atomic maximum per block; FP64 samples: an
-// array of partials); the last block to finish (atomic ticket, no waiting) takes
-// the farthest sample and the step in FP64.  A final pass computes the radius from
-// the farthest sample with an FP64 log map.  Ties go to the lowest index.
+// Every block reduces its slice to a (key, index) partial (FP32 samples: one
+// 64-bit atomic maximum per block; FP64 samples: an array of partials).  One
+// launch per iteration (megb_backward, the allocation-free solver): the last block
+// to finish (atomic ticket, no waiting) takes the farthest sample and the step in
+// FP64.  One persistent launch for both balls (megb_solve): after a bounded grid
+// barrier every block takes the same step itself.  A final pass computes the
+// radius from the farthest sample with an FP64 log map.  Ties go to the lowest
+// index.
 #include <climits>
 #include <mutex>
 
@@ -26,8 +29,10 @@ struct MegbState {
   int fstar[2];       // farthest sample from the final centre (rotation, translation)
   unsigned int gen[2];  // iterations published by the persistent kernel
   // FP32 samples: farthest (key bits, complement of the index) of the iteration so far, per ball and
-  // iteration parity; the block that takes the step reads and clears it
-  unsigned long long best[2][2];
+  // iteration mod 2 (one launch per iteration: the block that takes the step reads and clears it) or
+  // mod 3 (persistent kernel: every block reads it after the barrier, block 0 clears the slot of the
+  // iteration after next)
+  unsigned long long best[2][3];
   // output rule of Alg. 6 (megb_solve_mean): sums over the last iterates -- of q q^T (upper triangle of
   // the 4 x 4 matrix, 10 values) for the rotation ball and of c for the translation ball
   double acc[13];
@@ -87,7 +92,7 @@ __global__ void megb_init(const T* q, int nq, const T* t, int nt, MegbState* s) 
   s->c[3] = 0.0;
   s->counter[0] = s->counter[1] = 0;
   s->gen[0] = s->gen[1] = 0;
-  s->best[0][0] = s->best[0][1] = s->best[1][0] = s->best[1][1] = 0ull;
+  for (int i = 0; i < 6; ++i) s->best[i / 3][i % 3] = 0ull;
   for (int i = 0; i < 13; ++i) s->acc[i] = 0.0;
 }
 
@@ -141,12 +146,11 @@ __device__ __forceinline__ Q4<double> slerp_step(const Q4<double>& c, const RelR
 // largest eigenvalue of sum C_t C_t^T.  Called by the thread that takes step k with the previous and
 // the new iterate; adds them to the sums in s->acc and returns, at k == K, the projected mean (the new
 // iterate before).  The translation ball averages its last centres the same way (no projection).
-template <bool COHERENT>
 __device__ __forceinline__ Q4<double> mean_rule_rotation(MegbState* s, const Q4<double>& prev, const Q4<double>& cn,
                                                          int k, int K, int navg) {
   const int first = K - navg + 1;
   double a[10];
-  for (int e = 0; e < 10; ++e) a[e] = COHERENT ? __ldcg(&s->acc[e]) : s->acc[e];
+  for (int e = 0; e < 10; ++e) a[e] = s->acc[e];
   auto add = [&](const Q4<double>& q) {
     const double v[4] = {q.w, q.x, q.y, q.z};
     int e = 0;
@@ -172,12 +176,11 @@ __device__ __forceinline__ Q4<double> mean_rule_rotation(MegbState* s, const Q4<
   return q;
 }
 
-template <bool COHERENT>
 __device__ __forceinline__ void mean_rule_translation(MegbState* s, const double* prev, double* cn, int k, int K,
                                                       int navg) {
   const int first = K - navg + 1;
   double a[3];
-  for (int d = 0; d < 3; ++d) a[d] = COHERENT ? __ldcg(&s->acc[10 + d]) : s->acc[10 + d];
+  for (int d = 0; d < 3; ++d) a[d] = s->acc[10 + d];
   for (int d = 0; d < 3; ++d) {
     if (k == 1 && first <= 0) a[d] += prev[d];
     if (k >= first) a[d] += cn[d];
@@ -213,38 +216,18 @@ __device__ __forceinline__ T sample_key(const T* __restrict__ x, int i, bool vec
   return dx * dx + dy * dy + dz * dz;
 }
 
-// One GGD iteration of a ball over this block's slice of the samples.  MODE 0: rotation ball, MODE 1:
-// translation ball.  k >= 1: GGD step k; k == 0: final radius.  Every block reduces its slice to a
-// (key, index) maximum -- FP32 samples: packed into one 64-bit atomic maximum; FP64 samples: a
-// partial per block -- and the last block to take a ticket takes the farthest sample and the step in
-// FP64 (its thread 0 writes the state).  Returns true in the block that took the step.  COHERENT:
-// the centre is read from L2 (the persistent kernel reads a centre written by another block in the
-// same launch).
-template <typename T, int MODE, bool COHERENT>
-__device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbState* s, Part* parts, int k, int K,
-                                         int navg, int32_t* f_int, int32_t* f_out, double* result, double* wkey,
-                                         int* widx, bool* last, int bid, int nb) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  T c0, c1, c2, c3;
-  if (MODE == 0) {
-    if (COHERENT)
-      c0 = T(__ldcg(&s->C[0])), c1 = T(__ldcg(&s->C[1])), c2 = T(__ldcg(&s->C[2])), c3 = T(__ldcg(&s->C[3]));
-    else
-      c0 = T(s->C[0]), c1 = T(s->C[1]), c2 = T(s->C[2]), c3 = T(s->C[3]);
-  } else {
-    if (COHERENT)
-      c0 = T(__ldcg(&s->c[0])), c1 = T(__ldcg(&s->c[1])), c2 = T(__ldcg(&s->c[2])), c3 = T(0);
-    else
-      c0 = T(s->c[0]), c1 = T(s->c[1]), c2 = T(s->c[2]), c3 = T(0);
-  }
-  // per-thread maximum in the key precision (the conversion to FP64 is exact and keeps the order)
-  T bkt = T(-1);
-  int bi = INT_MAX;
-  const int stride = nb * blockDim.x;
+// This thread's farthest sample of its slice (samples bid * blockDim.x + threadIdx.x + j * stride) from the
+// centre (c0, c1, c2, c3): the largest key in the key precision (its conversion to FP64 is exact and keeps
+// the order), ties to the lowest index; (-1, INT_MAX) when the slice is empty.
+template <typename T, int MODE>
+__device__ __forceinline__ void scan_slice(const T* __restrict__ x, int n, int bid, int stride, T c0, T c1, T c2, T c3,
+                                           T& bkt, int& bi) {
+  bkt = T(-1);
+  bi = INT_MAX;
   // Four samples in flight per thread (indices ascending, so the strict > keeps the lowest index
   // among equal keys); quaternions are read as 16-byte vectors when the array allows it.
   const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
-  int i = bid * blockDim.x + tid;
+  int i = bid * blockDim.x + threadIdx.x;
   const bool grouped = MODE == 1 && sizeof(T) == 4 && vec;
   if (grouped) {
     // FP32 translations: groups of four samples = three 16-byte vectors per thread, two groups in
@@ -296,6 +279,26 @@ __device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbSta
     const T key = sample_key<T, MODE>(x, i, vec, c0, c1, c2, c3);
     if (key > bkt) bkt = key, bi = i;
   }
+}
+
+// One GGD iteration of a ball over this block's slice of the samples.  MODE 0: rotation ball, MODE 1:
+// translation ball.  k >= 1: GGD step k; k == 0: final radius.  Every block reduces its slice to a
+// (key, index) maximum -- FP32 samples: packed into one 64-bit atomic maximum; FP64 samples: a
+// partial per block -- and the last block to take a ticket takes the farthest sample and the step in
+// FP64 (its thread 0 writes the state).  Returns true in the block that took the step.
+template <typename T, int MODE>
+__device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbState* s, Part* parts, int k, int K,
+                                         int navg, int32_t* f_int, int32_t* f_out, double* result, double* wkey,
+                                         int* widx, bool* last, int bid, int nb) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T c0, c1, c2, c3;
+  if (MODE == 0)
+    c0 = T(s->C[0]), c1 = T(s->C[1]), c2 = T(s->C[2]), c3 = T(s->C[3]);
+  else
+    c0 = T(s->c[0]), c1 = T(s->c[1]), c2 = T(s->c[2]), c3 = T(0);
+  T bkt;
+  int bi;
+  scan_slice<T, MODE>(x, n, bid, nb * (int)blockDim.x, c0, c1, c2, c3, bkt, bi);
   double bk;
   if constexpr (sizeof(T) == 4) {
     // FP32 keys are >= 0 (or never taken: NaN fails key > bkt), so their bit patterns order like the
@@ -365,7 +368,7 @@ __device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbSta
       if (better_bits(wpk[w], widx[w], kb, bi)) kb = wpk[w], bi = widx[w];
   }
   s->counter[MODE] = 0;
-  auto ld = [](const double* p) { return COHERENT ? __ldcg(p) : *p; };
+  auto ld = [](const double* p) { return *p; };
   if (MODE == 0) {
     const T* qs = x + 4 * (size_t)bi;
     const Q4<double> c{ld(&s->C[0]), ld(&s->C[1]), ld(&s->C[2]), ld(&s->C[3])};
@@ -373,7 +376,7 @@ __device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbSta
     const RelRot r = rel_rot(c, qf);
     if (k > 0) {
       Q4<double> cn = slerp_step(c, r, k);
-      if (navg > 1) cn = mean_rule_rotation<COHERENT>(s, c, cn, k, K, navg);
+      if (navg > 1) cn = mean_rule_rotation(s, c, cn, k, K, navg);
       s->C[0] = cn.w, s->C[1] = cn.x, s->C[2] = cn.y, s->C[3] = cn.z;
     } else {
       result[0] = c.w, result[1] = c.x, result[2] = c.y, result[3] = c.z;
@@ -387,7 +390,7 @@ __device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbSta
       double cn[3] = {c0d + ((double)p[0] - c0d) * rk, c1d + ((double)p[1] - c1d) * rk, c2d + ((double)p[2] - c2d) * rk};
       if (navg > 1) {
         const double prev[3] = {c0d, c1d, c2d};
-        mean_rule_translation<COHERENT>(s, prev, cn, k, K, navg);
+        mean_rule_translation(s, prev, cn, k, K, navg);
       }
       s->c[0] = cn[0], s->c[1] = cn[1], s->c[2] = cn[2];
     } else {
@@ -413,41 +416,156 @@ __global__ void __launch_bounds__(kMegbThreads)
   __shared__ double wkey[kMegbThreads / 32];
   __shared__ int widx[kMegbThreads / 32];
   __shared__ bool last;
-  ggd_iter<T, MODE, false>(x, n, s, parts, k, K, navg, f_int, f_out, result, wkey, widx, &last, blockIdx.x, gridDim.x);
+  ggd_iter<T, MODE>(x, n, s, parts, k, K, navg, f_int, f_out, result, wkey, widx, &last, blockIdx.x, gridDim.x);
 }
 
-// All K iterations and the radius pass of a ball on blocks [b0, b0 + nb) of a cooperative launch
-// (every block resident).  After each iteration the block that took the step publishes it by
-// bumping s->gen[MODE] (release); the others wait for it with a bounded poll (acquire) and, if the
-// poll limit runs out, flag a timeout in the status word and leave (the result is then not written).
+// All K iterations and the radius pass of a ball on blocks [0, nb) of its group in a cooperative launch
+// (every block resident).  Every block keeps its own copy of the descent state in shared memory and
+// takes every step itself: per iteration it reduces its slice to a farthest (key, index), posts it
+// (FP32 keys: one 64-bit atomic maximum of (key bits, complement of the index) into the iteration's
+// slot of a ring of three; FP64 keys: its partial), arrives on the group's counter (release) and
+// waits (acquire, bounded poll) until all nb blocks of the group have arrived; then it reads the
+// farthest sample and takes the FP64 step.  Every block computes the same step from the same values,
+// so the copies stay identical, and the farthest sample does not depend on the grid (keys descending,
+// indices ascending): the results equal those of the one-launch-per-iteration kernel.  Block 0 writes
+// the farthest sequence, the result and the final state.  If the poll limit runs out the block flags
+// a timeout in the status word and leaves (the result is then not written).
 template <typename T, int MODE>
 __device__ __forceinline__ void ggd_ball(const T* __restrict__ x, int n, MegbState* s, Part* parts, int n_iters,
-                                         int navg, int32_t* f_int, int32_t* f_out, double* result, int* status, int bid, int nb,
-                                         double* wkey, int* widx, bool* last, bool* stop) {
+                                         int navg, int32_t* f_int, int32_t* f_out, double* result, int* status, int bid,
+                                         int nb, MegbState* loc, unsigned long long* wpk, int* widx, int* fsh,
+                                         bool* stop) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) loc->C[i] = __ldcg(&s->C[i]), loc->c[i] = __ldcg(&s->c[i]);
+    for (int i = 0; i < 13; ++i) loc->acc[i] = __ldcg(&s->acc[i]);
+  }
+  __syncthreads();
   for (int it = 1; it <= n_iters + 1; ++it) {
     const int k = it <= n_iters ? it : 0;
-    const bool took =
-        ggd_iter<T, MODE, true>(x, n, s, parts, k, n_iters, navg, f_int, f_out, result, wkey, widx, last, bid, nb);
-    if (it == n_iters + 1) break;
-    if (threadIdx.x == 0) {
-      *stop = false;
-      if (took) {
-        __threadfence();
-        st_release(&s->gen[MODE], (unsigned)it);
-      } else {
-        int polls = 0;
-        while (ld_acquire(&s->gen[MODE]) < (unsigned)it) {
-          if (++polls > (1 << 22)) {
-            atomicOr(status, kDevErrTimeout);
-            *stop = true;
-            break;
-          }
-          __nanosleep(64);
+    T c0, c1, c2, c3 = T(0);
+    if (MODE == 0)
+      c0 = T(loc->C[0]), c1 = T(loc->C[1]), c2 = T(loc->C[2]), c3 = T(loc->C[3]);
+    else
+      c0 = T(loc->c[0]), c1 = T(loc->c[1]), c2 = T(loc->c[2]);
+    T bkt;
+    int bi;
+    scan_slice<T, MODE>(x, n, bid, nb * (int)blockDim.x, c0, c1, c2, c3, bkt, bi);
+    // the block's farthest (key bits, index): keys >= 0 (NaN is never taken) order like their bit
+    // patterns; an empty entry is (0, INT_MAX), below every sample
+    const bool has = bi != INT_MAX;
+    unsigned long long kb;
+    if constexpr (sizeof(T) == 4) {
+      const uint32_t k32 = has ? __float_as_uint(bkt) : 0u;
+      const uint32_t mk = __reduce_max_sync(kFullMask, k32);
+      const uint32_t mi = __reduce_max_sync(kFullMask, has && k32 == mk ? ~(uint32_t)bi : 0u);
+      kb = ((unsigned long long)mk << 32) | mi;
+    } else {
+      kb = has ? (unsigned long long)__double_as_longlong(bkt) : 0ull;
+      warp_best64(kb, bi);
+    }
+    if (lane == 0) wpk[warp] = kb, widx[warp] = bi;
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < kMegbThreads / 32; ++w) {
+        if (sizeof(T) == 4) {
+          kb = wpk[w] > kb ? wpk[w] : kb;
+        } else if (better_bits(wpk[w], widx[w], kb, bi)) {
+          kb = wpk[w], bi = widx[w];
         }
+      }
+      if (sizeof(T) == 4) {
+        atomicMax(&s->best[MODE][it % 3], kb);
+        // the slot of iteration it + 1 was last read after the barrier of iteration it - 2, before
+        // every block arrived at the barrier of iteration it - 1, which this block has passed
+        if (bid == 0) s->best[MODE][(it + 1) % 3] = 0ull;
+      } else {
+        parts[bid] = Part{__longlong_as_double((long long)kb), bi, 0};
+      }
+      __threadfence();
+      atomicAdd(&s->gen[MODE], 1u);
+      const unsigned target = (unsigned)nb * (unsigned)it;
+      int polls = 0;
+      *stop = false;
+      while (ld_acquire(&s->gen[MODE]) < target) {
+        if (++polls > (1 << 22)) {
+          atomicOr(status, kDevErrTimeout);
+          *stop = true;
+          break;
+        }
+        __nanosleep(32);
+      }
+      if (sizeof(T) == 4 && !*stop) {
+        const unsigned long long b = __ldcg(&s->best[MODE][it % 3]);
+        *fsh = b == 0ull ? 0 : (int)~(uint32_t)b;
       }
     }
     __syncthreads();
     if (*stop) return;
+    if constexpr (sizeof(T) == 8) {
+      // the partials of every block of the group (read from L2, bypassing this SM's L1)
+      kb = 0ull, bi = INT_MAX;
+      for (int b = tid; b < nb; b += blockDim.x) {
+        const unsigned long long pk = (unsigned long long)__ldcg(reinterpret_cast<const long long*>(&parts[b].key));
+        const int pi = __ldcg(&parts[b].idx);
+        if (better_bits(pk, pi, kb, bi)) kb = pk, bi = pi;
+      }
+      warp_best64(kb, bi);
+      if (lane == 0) wpk[warp] = kb, widx[warp] = bi;
+      __syncthreads();
+      if (tid == 0) {
+        for (int w = 1; w < kMegbThreads / 32; ++w)
+          if (better_bits(wpk[w], widx[w], kb, bi)) kb = wpk[w], bi = widx[w];
+        *fsh = bi == INT_MAX ? 0 : bi;
+      }
+    }
+    if (tid == 0) {
+      const int f = *fsh;
+      if (MODE == 0) {
+        const T* qs = x + 4 * (size_t)f;
+        const Q4<double> c{loc->C[0], loc->C[1], loc->C[2], loc->C[3]};
+        const Q4<double> qf = qnormalize(Q4<double>{(double)qs[0], (double)qs[1], (double)qs[2], (double)qs[3]});
+        const RelRot r = rel_rot(c, qf);
+        if (k > 0) {
+          Q4<double> cn = slerp_step(c, r, k);
+          if (navg > 1) cn = mean_rule_rotation(loc, c, cn, k, n_iters, navg);
+          loc->C[0] = cn.w, loc->C[1] = cn.x, loc->C[2] = cn.y, loc->C[3] = cn.z;
+        } else if (bid == 0) {
+          result[0] = c.w, result[1] = c.x, result[2] = c.y, result[3] = c.z;
+          result[7] = r.th;
+        }
+      } else {
+        const T* p = x + 3 * (size_t)f;
+        const double c0d = loc->c[0], c1d = loc->c[1], c2d = loc->c[2];
+        if (k > 0) {
+          const double rk = 1.0 / k;
+          double cn[3] = {c0d + ((double)p[0] - c0d) * rk, c1d + ((double)p[1] - c1d) * rk,
+                          c2d + ((double)p[2] - c2d) * rk};
+          if (navg > 1) {
+            const double prev[3] = {c0d, c1d, c2d};
+            mean_rule_translation(loc, prev, cn, k, n_iters, navg);
+          }
+          loc->c[0] = cn[0], loc->c[1] = cn[1], loc->c[2] = cn[2];
+        } else if (bid == 0) {
+          const double dx = (double)p[0] - c0d, dy = (double)p[1] - c1d, dz = (double)p[2] - c2d;
+          result[4] = c0d, result[5] = c1d, result[6] = c2d;
+          result[8] = sqrt(dx * dx + dy * dy + dz * dz);
+        }
+      }
+      if (bid == 0) {
+        if (k > 0) {
+          f_int[k - 1] = f;
+          if (f_out) f_out[k - 1] = f;
+        } else {
+          s->fstar[MODE] = f;
+          for (int i = 0; i < 4; ++i) {
+            if (MODE == 0) s->C[i] = loc->C[i];
+            else s->c[i] = loc->c[i];
+          }
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -458,14 +576,17 @@ __global__ void __launch_bounds__(kMegbThreads)
     ggd_persistent(const T* __restrict__ q, int nq, const T* __restrict__ t, int nt, int gq, MegbState* s,
                    Part* parts_q, Part* parts_t, int n_iters, int navg, int32_t* f_int, int32_t* f_out,
                    double* result, int* status) {
-  __shared__ double wkey[kMegbThreads / 32];
+  __shared__ MegbState loc;
+  __shared__ unsigned long long wpk[kMegbThreads / 32];
   __shared__ int widx[kMegbThreads / 32];
-  __shared__ bool last, stop;
+  __shared__ int fsh;
+  __shared__ bool stop;
   if ((int)blockIdx.x < gq)
-    ggd_ball<T, 0>(q, nq, s, parts_q, n_iters, navg, f_int, f_out, result, status, blockIdx.x, gq, wkey, widx, &last, &stop);
+    ggd_ball<T, 0>(q, nq, s, parts_q, n_iters, navg, f_int, f_out, result, status, blockIdx.x, gq, &loc, wpk, widx, &fsh,
+                   &stop);
   else
     ggd_ball<T, 1>(t, nt, s, parts_t, n_iters, navg, f_int + n_iters, f_out ? f_out + n_iters : nullptr, result, status,
-                   blockIdx.x - gq, gridDim.x - gq, wkey, widx, &last, &stop);
+                   blockIdx.x - gq, gridDim.x - gq, &loc, wpk, widx, &fsh, &stop);
 }
 
 __global__ void megb_zero_result(double* result, int skip_rot, int skip_tr) {
@@ -703,7 +824,7 @@ __global__ void megb_state_from_result(const double* result, MegbState* s) {
   s->c[3] = 0.0;
   s->counter[0] = s->counter[1] = 0;
   s->fstar[0] = s->fstar[1] = 0;
-  s->best[0][0] = s->best[0][1] = s->best[1][0] = s->best[1][1] = 0ull;
+  for (int i = 0; i < 6; ++i) s->best[i / 3][i % 3] = 0ull;
   for (int i = 0; i < 13; ++i) s->acc[i] = 0.0;
 }
 
