@@ -295,7 +295,7 @@ purse_status purse_rng_words(uint64_t seed, uint32_t phase, uint32_t j, uint32_t
  *   0 walk -- warps per walk block, {8, 4, 2}; used by purse_sample (variant = sampler + 2 precision)
  *   1 megb -- samples per thread of the persistent ball kernel, i.e. blocks per ball, FP32
  *             {1 .. 64}, FP64 {1 .. 8}; used by megb_solve (variant = precision)
- *   2 dist -- resident CTAs per SM of the tensor-core distance kernel, {4, 3, 2, 1}; used by
+ *   2 dist -- resident CTAs per SM of the tensor-core distance kernel, {2, 1}; used by
  *             purse_dist modes 1 and 2 (variant = 3 split passes or 1)
  *   3 batch -- reserved (purse_batch_tune keeps its choice in the batch).
  * No shape changes a result.  The cache lives in the process; if the environment variable

@@ -419,6 +419,60 @@ __global__ void __launch_bounds__(kMegbThreads)
   ggd_iter<T, MODE>(x, n, s, parts, k, K, navg, f_int, f_out, result, wkey, widx, &last, blockIdx.x, gridDim.x);
 }
 
+// The slice of this block's thread kept in shared memory for all iterations of the persistent kernel:
+// sample i = bid * blockDim.x + threadIdx.x + j * stride (j < J) in slot j * blockDim.x + threadIdx.x --
+// rotations as 4 values per slot, translations as three planes of J * blockDim.x values.  Every thread
+// reads back only its own slots.
+template <typename T, int MODE>
+__device__ __forceinline__ void cache_slice(const T* __restrict__ x, int n, int bid, int stride, int J, T* cache) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int j = 0; j < J; ++j) {
+    const long i = (long)bid * nt + tid + (long)j * stride;
+    if (i >= n) break;
+    const int slot = j * nt + tid;
+    if (MODE == 0) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) cache[4 * slot + c] = x[4 * i + c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) cache[c * J * nt + slot] = x[3 * i + c];
+    }
+  }
+}
+
+// scan_slice over the cached slice: the same keys in the same order (indices ascending, strict >).
+template <typename T, int MODE>
+__device__ __forceinline__ void scan_cached(const T* cache, int n, int bid, int stride, int J, T c0, T c1, T c2, T c3,
+                                            T& bkt, int& bi) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  bkt = T(-1);
+  bi = INT_MAX;
+  const int i0 = bid * nt + tid;
+  // slots j < jn hold samples of this thread (i0 + j stride < n)
+  const int jn = i0 >= n ? 0 : min(J, (n - 1 - i0) / stride + 1);
+#pragma unroll 4
+  for (int j = 0; j < jn; ++j) {
+    const int slot = j * nt + tid;
+    T key;
+    if (MODE == 0) {
+      T qv[4];
+      if constexpr (sizeof(T) == 4) {
+        const float4 v = reinterpret_cast<const float4*>(cache)[slot];
+        qv[0] = v.x, qv[1] = v.y, qv[2] = v.z, qv[3] = v.w;
+      } else {
+        const double2 a = reinterpret_cast<const double2*>(cache)[2 * slot];
+        const double2 b = reinterpret_cast<const double2*>(cache)[2 * slot + 1];
+        qv[0] = a.x, qv[1] = a.y, qv[2] = b.x, qv[3] = b.y;
+      }
+      key = rot_key(c0, c1, c2, c3, qv);
+    } else {
+      const T dx = cache[slot] - c0, dy = cache[J * nt + slot] - c1, dz = cache[2 * J * nt + slot] - c2;
+      key = dx * dx + dy * dy + dz * dz;
+    }
+    if (key > bkt) bkt = key, bi = i0 + j * stride;
+  }
+}
+
 // All K iterations and the radius pass of a ball on blocks [0, nb) of its group in a cooperative launch
 // (every block resident).  Every block keeps its own copy of the descent state in shared memory and
 // takes every step itself: per iteration it reduces its slice to a farthest (key, index), posts it
@@ -434,12 +488,14 @@ template <typename T, int MODE>
 __device__ __forceinline__ void ggd_ball(const T* __restrict__ x, int n, MegbState* s, Part* parts, int n_iters,
                                          int navg, int32_t* f_int, int32_t* f_out, double* result, int* status, int bid,
                                          int nb, MegbState* loc, unsigned long long* wpk, int* widx, int* fsh,
-                                         bool* stop) {
+                                         bool* stop, T* cache, int J) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int stride = nb * (int)blockDim.x;
   if (tid == 0) {
     for (int i = 0; i < 4; ++i) loc->C[i] = __ldcg(&s->C[i]), loc->c[i] = __ldcg(&s->c[i]);
     for (int i = 0; i < 13; ++i) loc->acc[i] = __ldcg(&s->acc[i]);
   }
+  if (J > 0) cache_slice<T, MODE>(x, n, bid, stride, J, cache);
   __syncthreads();
   for (int it = 1; it <= n_iters + 1; ++it) {
     const int k = it <= n_iters ? it : 0;
@@ -450,7 +506,10 @@ __device__ __forceinline__ void ggd_ball(const T* __restrict__ x, int n, MegbSta
       c0 = T(loc->c[0]), c1 = T(loc->c[1]), c2 = T(loc->c[2]);
     T bkt;
     int bi;
-    scan_slice<T, MODE>(x, n, bid, nb * (int)blockDim.x, c0, c1, c2, c3, bkt, bi);
+    if (J > 0)
+      scan_cached<T, MODE>(cache, n, bid, stride, J, c0, c1, c2, c3, bkt, bi);
+    else
+      scan_slice<T, MODE>(x, n, bid, stride, c0, c1, c2, c3, bkt, bi);
     // the block's farthest (key bits, index): keys >= 0 (NaN is never taken) order like their bit
     // patterns; an empty entry is (0, INT_MAX), below every sample
     const bool has = bi != INT_MAX;
@@ -575,18 +634,20 @@ template <typename T>
 __global__ void __launch_bounds__(kMegbThreads)
     ggd_persistent(const T* __restrict__ q, int nq, const T* __restrict__ t, int nt, int gq, MegbState* s,
                    Part* parts_q, Part* parts_t, int n_iters, int navg, int32_t* f_int, int32_t* f_out,
-                   double* result, int* status) {
+                   double* result, int* status, int jq, int jt) {
   __shared__ MegbState loc;
   __shared__ unsigned long long wpk[kMegbThreads / 32];
   __shared__ int widx[kMegbThreads / 32];
   __shared__ int fsh;
   __shared__ bool stop;
+  extern __shared__ __align__(16) unsigned char slice[];  // jq / jt > 0: the block's samples, kept
+  T* cache = reinterpret_cast<T*>(slice);
   if ((int)blockIdx.x < gq)
     ggd_ball<T, 0>(q, nq, s, parts_q, n_iters, navg, f_int, f_out, result, status, blockIdx.x, gq, &loc, wpk, widx, &fsh,
-                   &stop);
+                   &stop, cache, jq);
   else
     ggd_ball<T, 1>(t, nt, s, parts_t, n_iters, navg, f_int + n_iters, f_out ? f_out + n_iters : nullptr, result, status,
-                   blockIdx.x - gq, gridDim.x - gq, &loc, wpk, widx, &fsh, &stop);
+                   blockIdx.x - gq, gridDim.x - gq, &loc, wpk, widx, &fsh, &stop, cache, jt);
 }
 
 __global__ void megb_zero_result(double* result, int skip_rot, int skip_tr) {
@@ -640,13 +701,37 @@ static cudaError_t launch_megb_t(purse_t h, int n_iters, int navg, const T* q, i
         gt = room;
       }
     }
+    // keep every block's samples in shared memory for all iterations when they fit and every block stays
+    // resident with that much shared memory
+    int jq = gq > 0 ? (int)(((long)nq + gq * kMegbThreads - 1) / (gq * kMegbThreads)) : 0;
+    int jt = gt > 0 ? (int)(((long)nt + gt * kMegbThreads - 1) / (gt * kMegbThreads)) : 0;
+    const size_t bq = (size_t)jq * kMegbThreads * 4 * sizeof(T), bt = (size_t)jt * kMegbThreads * 3 * sizeof(T);
+    size_t dyn = bq > bt ? bq : bt;
+    static int smem_optin = -1;
+    if (smem_optin < 0) {
+      int dev = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if (e != cudaSuccess) return e;
+    }
+    bool keep = dyn > 0 && dyn + 1024 <= (size_t)smem_optin;
+    if (keep) {
+      cudaError_t e = cudaFuncSetAttribute(ggd_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ggd_persistent<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      int nbk = 0;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbk, ggd_persistent<T>, kMegbThreads, dyn);
+      if (e != cudaSuccess) return e;
+      keep = (long)nbk * h->sm_count >= gq + gt;
+    }
+    if (!keep) jq = jt = 0, dyn = 0;
     int gqi = (int)gq, nqi = nq, nti = nt, ni = n_iters, na = navg;
     Part* parts_t = parts + cap;
     int* status = h->d_status;
     void* args[] = {(void*)&q, &nqi, (void*)&t, &nti, &gqi, &s, &parts, &parts_t, &ni, &na, &f_int, &f_out, &result,
-                    &status};
+                    &status, &jq, &jt};
     return cudaLaunchCooperativeKernel((const void*)ggd_persistent<T>, dim3((unsigned)(gq + gt)), dim3(kMegbThreads),
-                                       args, 0, st);
+                                       args, dyn, st);
   }
   if (nq > 0) {
     const long want = ((long)nq + kMegbThreads * 4 - 1) / (kMegbThreads * 4);

@@ -13,15 +13,13 @@
 // hi.hi + hi.lo + lo.hi in FP32 (about 2^-21 relative per product, near FP32); mode 2 takes
 // one TF32 pass (2^-11).  B is split from the FP64 constraint table.
 //
-// Mapping: one CTA of 128 threads per tile of 128 poses (persistent over tiles), M = 128
-// rows in TMEM lanes, constraints in rounds of up to 32 (N <= 96 columns per MMA, 128 TMEM
-// columns at most, so four CTAs fit an SM).  The raw 6 KB pose tiles stream through a ring of
-// four shared-memory stages filled by 1-D bulk copies (cp.async.bulk, one mbarrier per
-// stage); the threads split a landed tile into A (hi, lo).  Shared memory holds A and B in
-// the K-major no-swizzle canonical layout: core matrices of 8 rows x 16 bytes, the four core
-// matrices of a row group along K contiguous (LBO = 128 B), row groups 512 B apart (SBO).
-// One thread issues the MMAs and commits them to an mbarrier; all four warps read their 32
-// TMEM lanes back with tcgen05.ld.
+// Mapping: persistent CTAs of nine warps (two per SM) over tiles of 128 poses, M = 128 rows in
+// TMEM lanes, constraints in rounds of 16 (N = 48 columns per MMA).  Split warps load their pose
+// rows with 16-byte global loads and write A (hi, lo) into a ring of shared-memory slots; one thread
+// issues the MMAs into a ring of TMEM accumulators; epilogue warps read them back with tcgen05.ld.
+// The stages hand over through mbarriers (see tc_dist_kernel).  Shared memory holds A and B in the
+// K-major no-swizzle canonical layout: core matrices of 8 rows x 16 bytes, the four core matrices of
+// a row group along K contiguous (LBO = 128 B), row groups 512 B apart (SBO).
 #include <algorithm>
 #include <cfloat>
 
@@ -30,11 +28,7 @@
 
 namespace purse {
 
-constexpr int kTcThreads = 128;
-constexpr int kTcRoundMax = 32;          // constraints per MMA round (N = 96, 128 TMEM columns)
-constexpr int kTcStages = 4;             // raw pose tiles in flight per CTA
 constexpr uint32_t kTcTileBytes = 8192;  // 128 rows x 16 fp32
-constexpr uint32_t kTcRawBytes = 6144;   // 128 poses x 48 B
 
 __device__ __forceinline__ float rna_tf32(float x) {
   uint32_t r;
@@ -112,199 +106,276 @@ __device__ double tc_coef(int kind, const double* tab, int n, double fx, double 
   return 0.0;
 }
 
+// Byte size of one A slot: hi (and lo for the split passes).
+template <int PASSES>
+__host__ __device__ constexpr uint32_t tc_abuf() {
+  return PASSES == 3 ? 2 * kTcTileBytes : kTcTileBytes;
+}
+
+constexpr int kTcThreads = 288;                // 9 warps
+constexpr int kTcA = 3, kTcAcc = 4;            // A slots, TMEM accumulators of 64 columns
+constexpr int kTcPrefetch = 4;                 // pose tiles in flight per split thread
+constexpr uint32_t kTcCols = 64 * kTcAcc;
+
+// Wait for the phase of the given parity with the thread suspended in between (try_wait with a suspend
+// time hint: the thread resumes when the phase completes, or after the hint), so that waiting warps take
+// no issue slots from the working ones.  Bounded: gives up after about 2^31 SM cycles (about a second)
+// or once another role has raised the failure flag.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(1000000u)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile int* fail) {
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_try_wait_hint(bar, parity)) return true;
+    if (*fail || clock64() - t0 > (1ll << 31)) return false;
+    __nanosleep(32);  // the suspending try_wait alone still left the waiting warps busy on the issue slots
+  }
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Each CTA is persistent over tiles of 128 poses (tile k of the CTA is
+// global tile blockIdx.x + k gridDim.x) and runs each stage on its own warps, linked by mbarrier rings
+// (no CTA-wide barrier in the loop):
+//   warps 0-3  load the poses of tile k with 16-byte global loads (one pose row of 48 B per thread,
+//              kTcPrefetch tiles in flight in registers), split them into A (hi, lo) in a ring of
+//              kTcA slots of shared memory and signal the slot;
+//   warp 4     (one thread) issues the MMAs of each unit (tile, round of 16 constraints, N = 48) into a
+//              ring of kTcAcc accumulators of 64 TMEM columns, committing to the accumulator's barrier
+//              and, after a tile's last round, to its A slot's;
+//   warps 5-8  read an accumulator back (warp w reads TMEM lanes 32 (w mod 4) ..), release it and turn
+//              it into margins, one pose row per thread.
+// Padded constraints (i >= n) get radius +inf and, 2D-3D, P_z = 1, so they never lower the minimum; the
+// margins use FP32 expressions two constraints per paired instruction.  Every wait is bounded; a role
+// that gives up raises a shared flag that ends the others' loops, and the MMAs in flight finish before
+// TMEM is released.
 template <int KIND, int PASSES>
-__global__ void __launch_bounds__(kTcThreads, 4)
+__global__ void __launch_bounds__(kTcThreads)
     tc_dist_kernel(const double* __restrict__ tab, const float* __restrict__ tab32, int n, double fx, double fy,
                    double cx, double cy, const float* __restrict__ poses, long n_poses, float* __restrict__ dist,
-                   uint32_t tmem_cols, int* status) {
+                   int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  // layout: [raw pose tiles, kTcStages x 6 KB][A_hi 8 KB][A_lo 8 KB][B_hi 64 B per column][B_lo][radii]
-  //         [mbarriers: MMA completion, one per raw stage][TMEM address]
+  // layout: [A slots, kTcA x (hi, lo)][B_hi 64 B per column][B_lo][radii]
+  //         [barriers: A full, A empty, acc full, acc empty, MMA done][TMEM address][flag]
+  constexpr uint32_t abuf = tc_abuf<PASSES>();
   const int n_pad = (n + 15) & ~15;
-  const int cols = 3 * n_pad;
-  unsigned char* raw = smem;
-  unsigned char* a_hi = smem + kTcStages * kTcRawBytes;
-  unsigned char* a_lo = a_hi + kTcTileBytes;
-  unsigned char* b_hi = a_lo + kTcTileBytes;
+  const int cols = 3 * n_pad, R = n_pad / 16;
+  unsigned char* a0 = smem;
+  unsigned char* b_hi = a0 + kTcA * abuf;
   unsigned char* b_lo = b_hi + 64 * (size_t)cols;
   float* r_s = reinterpret_cast<float*>(b_lo + 64 * (size_t)cols);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(r_s + n_pad);
-  uint64_t* full = bar + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + kTcStages);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  uint64_t* a_full = reinterpret_cast<uint64_t*>(r_s + n_pad);
+  uint64_t* a_empty = a_full + kTcA;
+  uint64_t* t_full = a_empty + kTcA;
+  uint64_t* t_empty = t_full + kTcAcc;
+  uint64_t* mma_done = t_empty + kTcAcc;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+  volatile int* fail = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // ---- operands that stay: B (hi, lo), radii, the constant column k = 12..15 of A
+  // ---- operands that stay: B (hi, lo), radii, the constant columns k = 12..15 of every A slot
   for (int e = tid; e < cols * 16; e += kTcThreads) {
     const int c = e >> 4, k = e & 15;
     const int i = c / 3, comp = c - 3 * i;
-    const double v = i < n ? tc_coef(KIND, tab, n, fx, fy, cx, cy, i, comp, k) : 0.0;
+    const double v = i < n ? tc_coef(KIND, tab, n, fx, fy, cx, cy, i, comp, k)
+                           : (KIND == 1 && comp == 2 && k == 12 ? 1.0 : 0.0);
     const float hi = rna_tf32((float)v);
     const float lo = rna_tf32((float)(v - (double)hi));
     *reinterpret_cast<float*>(b_hi + kmaj_off(c, k)) = hi;
     *reinterpret_cast<float*>(b_lo + kmaj_off(c, k)) = lo;
   }
-  for (int i = tid; i < n_pad; i += kTcThreads) r_s[i] = i < n ? tab32[4 * i + 3] : 0.f;
-  {
-    const int row = tid;  // k = 12..15: (1, 0, 0, 0) in hi, zeros in lo
-    *reinterpret_cast<float4*>(a_hi + kmaj_off(row, 12)) = make_float4(1.f, 0.f, 0.f, 0.f);
-    *reinterpret_cast<float4*>(a_lo + kmaj_off(row, 12)) = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = tid; i < n_pad; i += kTcThreads) r_s[i] = i < n ? tab32[4 * i + 3] : INFINITY;
+  for (int e = tid; e < kTcA * 128; e += kTcThreads) {
+    unsigned char* ah = a0 + (e >> 7) * abuf;
+    *reinterpret_cast<float4*>(ah + kmaj_off(e & 127, 12)) = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (PASSES == 3)
+      *reinterpret_cast<float4*>(ah + kTcTileBytes + kmaj_off(e & 127, 12)) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   if (tid == 0) {
-    mbar_init(bar, 1);
-    for (int s = 0; s < kTcStages; ++s) mbar_init(full + s, 1);
+    for (int s = 0; s < kTcA; ++s) mbar_init(a_full + s, 4), mbar_init(a_empty + s, 1);
+    for (int s = 0; s < kTcAcc; ++s) mbar_init(t_full + s, 1), mbar_init(t_empty + s, 4);
+    mbar_init(mma_done, 1);
+    *fail = 0;
   }
-  if (warp == 0) {
+  if (warp == 4) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
-                 "r"(tmem_cols)
+                 "r"(kTcCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  fence_async_smem();  // B and the constant columns of A, written by the generic proxy, are read by the MMAs
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t a_hi_s = smem_addr(a_hi), a_lo_s = smem_addr(a_lo);
-  const uint32_t b_hi_s = smem_addr(b_hi), b_lo_s = smem_addr(b_lo);
-  uint32_t phase = 0;
-  bool failed = false;
 
-  // ---- raw pose tiles: tile k of this CTA (global tile blockIdx.x + k gridDim.x, 48 B per pose,
-  //      one 1-D bulk copy) lands in stage k mod kTcStages; thread 0 keeps kTcStages tiles in flight
-  const long n_tiles = (n_poses + 127) / 128;
-  long issued = 0;  // thread 0: bulk copies issued so far
-  auto issue = [&](long k) {
-    const long tile = blockIdx.x + k * (long)gridDim.x;
-    if (tile >= n_tiles) return;
-    const int s = (int)(k % kTcStages);
-    const long rows = n_poses - tile * 128 < 128 ? n_poses - tile * 128 : 128;
-    const uint32_t bytes = (uint32_t)(rows * 48);
-    mbar_arrive_expect_tx(full + s, bytes);
-    bulk_copy_g2s(raw + (size_t)s * kTcRawBytes, poses + 12 * (tile * 128), bytes, full + s);
-    issued = k + 1;
-  };
-  if (tid == 0)
-    for (int k = 0; k < kTcStages; ++k) issue(k);
-  long k = 0;
-  for (;; ++k) {
-    const long tile = blockIdx.x + k * (long)gridDim.x;
-    if (tile >= n_tiles) break;
-    const int st = (int)(k % kTcStages);
-    const bool okf = mbar_wait_bounded(full + st, (uint32_t)((k / kTcStages) & 1), 1 << 24);
-    if (__syncthreads_or(!okf)) {
-      failed = true;
-      break;
-    }
-    const long row0 = tile * 128;
-    const long avail4 = (n_poses - row0) * 3;
-    const float4* src = reinterpret_cast<const float4*>(raw + (size_t)st * kTcRawBytes);
-    // ---- A split into hi and lo (K-major core matrices)
+  // tiles of this CTA (32-bit per-CTA counters: a launch takes fewer than 2^31 tiles)
+  const int n_tiles = (int)((n_poses + 127) / 128);
+  const int T = n_tiles > (int)blockIdx.x ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const long step = (long)gridDim.x * 128;
+
+  if (warp < 4) {
+    // ---- split warps: pose row tid of every tile
+    long row = (long)blockIdx.x * 128 + tid;
+    float4 x[kTcPrefetch][3];
+    auto load = [&](float4 (&d)[3], long r) {
+      const float4* src = reinterpret_cast<const float4*>(poses) + 3 * r;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int q = tid + kTcThreads * j;
-      const int row = q / 3, kb = q - 3 * row;
-      const float4 x = q < avail4 ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 h = make_float4(rna_tf32(x.x), rna_tf32(x.y), rna_tf32(x.z), rna_tf32(x.w));
-      *reinterpret_cast<float4*>(a_hi + kmaj_off(row, 4 * kb)) = h;
-      if (PASSES == 3)
-        *reinterpret_cast<float4*>(a_lo + kmaj_off(row, 4 * kb)) =
-            make_float4(rna_tf32(x.x - h.x), rna_tf32(x.y - h.y), rna_tf32(x.z - h.z), rna_tf32(x.w - h.w));
-    }
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) issue(k + kTcStages);  // every thread has read stage st: refill it
-    float best = INFINITY;
-    for (int c0 = 0; c0 < n_pad && !failed; c0 += kTcRoundMax) {
-      const int nr = min(kTcRoundMax, n_pad - c0);  // constraints of this round (a multiple of 16)
-      const int ncol = 3 * nr;
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t idesc = idesc_tf32(ncol);
-        const uint32_t boff = (uint32_t)(3 * c0 / 8) * 512u;  // first column of the round
+      for (int kb = 0; kb < 3; ++kb) d[kb] = r < n_poses ? __ldg(src + kb) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {  // K = 16 in two steps of 8
-          const uint32_t ko = 256u * s;
-          tc_mma(tmem, smem_desc(a_hi_s + ko), smem_desc(b_hi_s + boff + ko), idesc, s > 0);
-          if (PASSES == 3) {
-            tc_mma(tmem, smem_desc(a_hi_s + ko), smem_desc(b_lo_s + boff + ko), idesc, 1);
-            tc_mma(tmem, smem_desc(a_lo_s + ko), smem_desc(b_hi_s + boff + ko), idesc, 1);
-          }
+    for (int j = 0; j < kTcPrefetch; ++j) load(x[j], row + j * step);
+    int as = 0;
+    uint32_t aph = 0;
+    for (int k0 = 0; k0 < T && !*fail; k0 += kTcPrefetch) {
+#pragma unroll
+      for (int j = 0; j < kTcPrefetch; ++j) {
+        const int k = k0 + j;
+        if (k >= T) break;
+        if (k >= kTcA && !tc_wait(a_empty + as, aph ^ 1u, fail)) {
+          *fail = 1;
+          break;
         }
-        tc_commit(bar);
-      }
-      const bool ok = mbar_wait_bounded(bar, phase, 1 << 24);
-      phase ^= 1u;
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        break;
-      }
-      tc_fence_after();
-      const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-      for (int g = 0; g < nr; g += 16) {
-        float v0[16], v1[16], v2[16];
-        const uint32_t col = (uint32_t)(3 * g);
-        tc_ld16(lane_base + col, v0);
-        tc_ld16(lane_base + col + 16, v1);
-        tc_ld16(lane_base + col + 32, v2);
-        tc_wait_ld();
-        float v[48];
+        unsigned char* ah = a0 + (size_t)as * abuf;
 #pragma unroll
-        for (int u = 0; u < 16; ++u) v[u] = v0[u], v[16 + u] = v1[u], v[32 + u] = v2[u];
+        for (int kb = 0; kb < 3; ++kb) {
+          const float4 v = x[j][kb];
+          const float4 h = make_float4(rna_tf32(v.x), rna_tf32(v.y), rna_tf32(v.z), rna_tf32(v.w));
+          *reinterpret_cast<float4*>(ah + kmaj_off(tid, 4 * kb)) = h;
+          if (PASSES == 3)
+            *reinterpret_cast<float4*>(ah + kTcTileBytes + kmaj_off(tid, 4 * kb)) =
+                make_float4(rna_tf32(v.x - h.x), rna_tf32(v.y - h.y), rna_tf32(v.z - h.z), rna_tf32(v.w - h.w));
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(a_full + as);
+        if (++as == kTcA) as = 0, aph ^= 1u;
+        load(x[j], row + (long)(k + kTcPrefetch) * step);  // the tile kTcPrefetch ahead into the freed registers
+      }
+    }
+  } else if (warp == 4) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      const uint32_t a0_s = smem_addr(a0), b_hi_s = smem_addr(b_hi), b_lo_s = smem_addr(b_lo);
+      const uint32_t idesc = idesc_tf32(48);
+      int as = 0, ts = 0, u = 0;
+      uint32_t aph = 0, tph = 0;
+      for (int k = 0; k < T && !*fail; ++k) {
+        if (!tc_wait(a_full + as, aph, fail)) {
+          *fail = 1;
+          break;
+        }
+        const uint32_t ah = a0_s + (uint32_t)as * abuf, al = ah + kTcTileBytes;
+        for (int r = 0; r < R; ++r, ++u) {
+          if (u >= kTcAcc && !tc_wait(t_empty + ts, tph ^ 1u, fail)) {
+            *fail = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem + 64u * (uint32_t)ts;
+          const uint32_t boff = (uint32_t)(6 * r) * 512u;  // columns 48 r .. 48 r + 47
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int i = c0 + g + u;
-          if (i < n) {
-            const float x = v[3 * u], y = v[3 * u + 1], z = v[3 * u + 2];
-            // margin r - |e| (2D-3D: r - |e| / P_z) without a division: |e| = s2 rsqrt(s2 (P_z^2))
-            float m;
-            if (KIND == 0) {
-              const float s2 = fmaf(z, z, fmaf(y, y, x * x));
-              m = fmaf(-s2, rsqrtf(s2 + 1e-30f), r_s[i]);
-            } else {
-              const float s2 = fmaf(y, y, x * x);
-              m = z > 0.f ? fmaf(-s2, rsqrtf(fmaf(s2, z * z, 1e-30f)), r_s[i]) : -INFINITY;
+          for (int s = 0; s < 2; ++s) {  // K = 16 in two steps of 8
+            const uint32_t ko = 256u * s;
+            tc_mma(d, smem_desc(ah + ko), smem_desc(b_hi_s + boff + ko), idesc, s > 0);
+            if (PASSES == 3) {
+              tc_mma(d, smem_desc(ah + ko), smem_desc(b_lo_s + boff + ko), idesc, 1);
+              tc_mma(d, smem_desc(al + ko), smem_desc(b_hi_s + boff + ko), idesc, 1);
             }
-            best = fminf(best, m);
           }
+          tc_commit(t_full + ts);
+          if (++ts == kTcAcc) ts = 0, tph ^= 1u;
+        }
+        if (*fail) break;
+        tc_commit(a_empty + as);  // the tile's MMAs have read A slot as
+        if (++as == kTcA) as = 0, aph ^= 1u;
+      }
+      // every MMA issued has finished before TMEM is released
+      tc_commit(mma_done);
+      if (!tc_wait(mma_done, 0u, fail)) mbar_wait_bounded(mma_done, 0u, 1 << 24);
+    }
+  } else {
+    // ---- epilogue warps: TMEM lanes 32 (warp mod 4) .. + 31, pose row 32 (warp mod 4) + lane of each tile
+    const int q = warp & 3;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+    long row = (long)blockIdx.x * 128 + 32 * q + lane;
+    const float2 tiny = make_float2(1e-30f, 1e-30f);
+    int ts = 0;
+    uint32_t tph = 0;
+    for (int k = 0; k < T && !*fail; ++k, row += step) {
+      float2 best = make_float2(INFINITY, INFINITY), zmin = best, zsum = make_float2(0.f, 0.f);
+      for (int r = 0; r < R; ++r) {
+        if (!tc_wait(t_full + ts, tph, fail)) {
+          *fail = 1;
+          break;
+        }
+        tc_fence_after();
+        float v[48];
+        {
+          float v0[16], v1[16], v2[16];
+          const uint32_t col = 64u * (uint32_t)ts;
+          tc_ld16(lane_base + col, v0);
+          tc_ld16(lane_base + col + 16, v1);
+          tc_ld16(lane_base + col + 32, v2);
+          tc_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = v0[e], v[16 + e] = v1[e], v[32 + e] = v2[e];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(t_empty + ts);  // this warp has read its lanes of the accumulator
+        if (++ts == kTcAcc) ts = 0, tph ^= 1u;
+        const float2* r2 = reinterpret_cast<const float2*>(r_s + 16 * r);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {  // constraints 16 r + 2 p and 16 r + 2 p + 1
+          const float2 x = make_float2(v[6 * p], v[6 * p + 3]), y = make_float2(v[6 * p + 1], v[6 * p + 4]);
+          const float2 z = make_float2(v[6 * p + 2], v[6 * p + 5]);
+          float2 m;
+          if (KIND == 0) {
+            const float2 s2 = fma2(z, z, fma2(y, y, mul2(x, x)));
+            m = fma2(make_float2(-s2.x, -s2.y), rsq2(add2(s2, tiny)), r2[p]);
+          } else {
+            const float2 s2 = fma2(y, y, mul2(x, x));
+            m = fma2(make_float2(-s2.x, -s2.y), rsq2(fma2(s2, mul2(z, z), tiny)), r2[p]);
+            zmin = min2(zmin, z);
+            zsum = add2(zsum, z);  // NaN if some P_z is NaN
+          }
+          best = min2(best, m);
         }
       }
-      tc_fence_before();
-      __syncthreads();  // every warp has read TMEM before the next round overwrites it
+      if (*fail) break;
+      float b = fminf(best.x, best.y);
+      if (KIND == 1 && !(fminf(zmin.x, zmin.y) > 0.f && zsum.x == zsum.x && zsum.y == zsum.y)) b = -INFINITY;
+      if (row < n_poses) dist[row] = b;
     }
-    if (failed) break;
-    const long row = row0 + tid;
-    if (row < n_poses) dist[row] = best;
-  }
-  if (failed) {
-    if (tid == 0) {
-      atomicOr(status, kDevErrTimeout);
-      // the bulk copies still in flight land before the shared memory is released (bounded)
-      for (long kk = k; kk < issued; ++kk)
-        mbar_wait_bounded(full + (int)(kk % kTcStages), (uint32_t)((kk / kTcStages) & 1), 1 << 24);
-    }
-    // and the MMAs still in flight finish before the accumulator is released (bounded)
-    mbar_wait_bounded(bar, phase ^ 1u, 1 << 24);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+  tc_fence_after();
+  if (tid == 0 && *fail) atomicOr(status, kDevErrTimeout);
+  if (warp == 4)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
 }
 
-size_t tc_dist_smem(int n) {
+size_t tc_dist_smem(int n, int passes) {
   const int n_pad = (n + 15) & ~15;
-  return kTcStages * kTcRawBytes + 2 * kTcTileBytes + 2 * 64 * (size_t)(3 * n_pad) + 4 * (size_t)n_pad +
-         8 * (1 + kTcStages) + 16;
+  return kTcA * (size_t)(passes == 3 ? tc_abuf<3>() : tc_abuf<1>()) + 2 * 64 * (size_t)(3 * n_pad) +
+         4 * (size_t)n_pad + 8 * (2 * kTcA + 2 * kTcAcc + 1) + 16;
 }
 
 cudaError_t launch_tc_dist(purse_t h, int passes, const float* d_poses, long n_poses, float* d_dist, cudaStream_t st) {
   if (n_poses == 0) return cudaSuccess;
-  const int n = h->n, n_pad = (n + 15) & ~15;
-  const int round_cols = 3 * (n_pad < kTcRoundMax ? n_pad : kTcRoundMax);
-  uint32_t tcols = 32;
-  while (tcols < (uint32_t)round_cols) tcols <<= 1;
-  const size_t smem = tc_dist_smem(n);
-  void (*kern)(const double*, const float*, int, double, double, double, double, const float*, long, float*,
-               uint32_t, int*);
+  const int n = h->n;
+  const size_t smem = tc_dist_smem(n, passes);
+  void (*kern)(const double*, const float*, int, double, double, double, double, const float*, long, float*, int*);
   if (h->kind == 0)
     kern = passes == 3 ? tc_dist_kernel<0, 3> : tc_dist_kernel<0, 1>;
   else
@@ -313,8 +384,8 @@ cudaError_t launch_tc_dist(purse_t h, int passes, const float* d_poses, long n_p
   // several CTAs per SM: the whole configurable shared memory for this kernel
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
-  // resident CTAs per SM from the register file, the shared memory and the accumulator columns (every
-  // resident CTA holds its own, at most 512 per SM)
+  // resident CTAs per SM from the register file, the threads, the shared memory and the accumulator
+  // columns (every resident CTA holds its own, at most 512 per SM)
   cudaFuncAttributes fa;
   e = cudaFuncGetAttributes(&fa, kern);
   int dev = 0, smem_sm = 0;
@@ -323,16 +394,16 @@ cudaError_t launch_tc_dist(purse_t h, int passes, const float* d_poses, long n_p
   if (e != cudaSuccess) return e;
   const int regs = (fa.numRegs + 7) & ~7;
   int per_sm = 65536 / (regs * kTcThreads);
-  per_sm = std::min(per_sm, smem_sm / (int)(smem + 1024));
   per_sm = std::min(per_sm, 2048 / kTcThreads);
-  per_sm = std::min(per_sm, (int)(512u / tcols));
+  per_sm = std::min(per_sm, smem_sm / (int)(smem + 1024));
+  per_sm = std::min(per_sm, (int)(512u / kTcCols));
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   per_sm = std::max(1, std::min(per_sm, tuned_config(kTuneDist, h->kind, n, n_poses, passes, per_sm)));
   const long tiles = (n_poses + 127) / 128;
   const long cap = (long)per_sm * h->sm_count;
   const int grid = (int)(tiles < cap ? tiles : cap);
   kern<<<grid, kTcThreads, smem, st>>>(h->tables.f64, h->tables.f32, n, h->K.fx, h->K.fy, h->K.cx, h->K.cy, d_poses,
-                                       n_poses, d_dist, tcols, h->d_status);
+                                       n_poses, d_dist, h->d_status);
   return cudaGetLastError();
 }
 

@@ -226,9 +226,9 @@ purse_status purse_tune_dist(purse_t h, int mode, const float* d_poses, long lon
   if (mode != 1 && mode != 2) return (set_error("purse_tune_dist: mode must be 1 or 2 (tensor cores)"), PURSE_ERR_ARG);
   purse_status s = purse_dist(h, mode, d_poses, n_poses, d_dist, stream);
   if (s != PURSE_OK) return s;
-  const int cands[] = {4, 3, 2, 1};
+  const int cands[] = {2, 1};
   cudaStream_t st = (cudaStream_t)stream;
-  return tune_op(kTuneDist, h->kind, h->n, n_poses, mode == 1 ? 3 : 1, cands, 4, 4, st,
+  return tune_op(kTuneDist, h->kind, h->n, n_poses, mode == 1 ? 3 : 1, cands, 2, 2, st,
                  [&](int) {
                    const purse_status r = purse_dist(h, mode, d_poses, n_poses, d_dist, stream);
                    return r == PURSE_OK ? cudaSuccess : cudaErrorLaunchFailure;

@@ -90,7 +90,7 @@ def test_tensor_core_shapes_give_identical_distances():
     poses = torch.as_tensor(np.concatenate([R, t], axis=1), dtype=torch.float32).cuda().contiguous()
     with P.Purse(p) as h:
         outs = []
-        for cta in (4, 3, 2, 1):
+        for cta in (2, 1):
             P.purse_tune_cache_put(P.TUNE_DIST, 1, p.n, n, 3, None, cta)
             d = torch.empty(n, dtype=torch.float32, device="cuda")
             P.purse_dist(h.h, 1, poses, n, d)
@@ -101,4 +101,4 @@ def test_tensor_core_shapes_give_identical_distances():
         P.purse_tune_cache_clear()
         d = torch.empty(n, dtype=torch.float32, device="cuda")
         r = P.purse_tune_dist(h.h, 1, poses, n, d)
-        assert r["config"] in (4, 3, 2, 1) and torch.equal(d, outs[0])
+        assert r["config"] in (2, 1) and torch.equal(d, outs[0])
