@@ -59,11 +59,8 @@ size_t megb_scratch_bytes(int n_iters, int sm_count) {
   return sizeof(MegbState) + 2 * megb_blocks_cap(sm_count) * sizeof(Part) + 2 * (size_t)n_iters * sizeof(int32_t) + 256;
 }
 
-__device__ __forceinline__ bool better(double ka, int ia, double kb, int ib) {
-  return ka > kb || (ka == kb && ia < ib);
-}
-
-// The same rule on the bit patterns of keys >= 0 (an empty entry is (0, INT_MAX), below every sample).
+// The farthest-sample rule (larger key, ties to the lower index) on the bit patterns of keys >= 0, which
+// order like the values (an empty entry is (0, INT_MAX), below every sample).
 __device__ __forceinline__ bool better_bits(unsigned long long ka, int ia, unsigned long long kb, int ib) {
   return ka > kb || (ka == kb && ia < ib);
 }
@@ -299,11 +296,10 @@ __device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbSta
   T bkt;
   int bi;
   scan_slice<T, MODE>(x, n, bid, nb * (int)blockDim.x, c0, c1, c2, c3, bkt, bi);
-  double bk;
   if constexpr (sizeof(T) == 4) {
     // FP32 keys are >= 0 (or never taken: NaN fails key > bkt), so their bit patterns order like the
     // values; (key bits, complement of the index) packed in 64 bits is largest for the farthest
-    // sample, ties to the lowest index -- the rule of better(), reduced with integer operations only
+    // sample, ties to the lowest index -- the rule of better_bits(), reduced with integer operations only
     // (each FP64 instruction of a warp occupies this part's FP64 unit for tens of cycles).  An empty
     // thread packs 0, below every sample.
     const bool has = bi != INT_MAX;
@@ -335,7 +331,6 @@ __device__ __forceinline__ bool ggd_iter(const T* __restrict__ x, int n, MegbSta
   } else {
     // FP64 keys (>= 0) order like their 64-bit patterns: the same rule with integer reductions of
     // (key bits, index) -- the high word, then the low word, then the complement of the index
-    (void)bk;
     unsigned long long kb = bi != INT_MAX ? (unsigned long long)__double_as_longlong(bkt) : 0ull;
     warp_best64(kb, bi);
     unsigned long long* wpk = reinterpret_cast<unsigned long long*>(wkey);
