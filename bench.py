@@ -334,7 +334,8 @@ def run_gpu(args, rank, world):
     out["megb_exact"] = run_exact(hR, qR, tT, res, dev)
     out["ransag"] = run_ransag(dev)
     if not args.no_c1:
-        out["c1"] = run_c1(dev, sms, clock_mhz, with_oracle=rank == 0 and not args.no_cpu_baseline)
+        out["c1"] = run_c1(dev, sms, clock_mhz, with_oracle=rank == 0 and not args.no_cpu_baseline,
+                           tune=not args.no_tune)
     if not args.no_plain:
         out["plain_gpu"] = run_plain(args, p, dev, seeds, value / world, t_step)
     if rank == 0 and not args.no_e2e:
@@ -398,11 +399,13 @@ def run_tune(hR, hT, seeds, qR, tR, qT, tT, res, stream):
     return out
 
 
-def run_c1(dev, sms, clock_mhz, with_oracle):
+def run_c1(dev, sms, clock_mhz, with_oracle, tune=True):
     """Config C1 end to end in FP64 on the GPU: RANSAG to |S0| = 2048 seeds (wall clock around its
     synchronising call), 4096 dS_R walks of N_I = 5 and both balls with K = 200 (CUDA events), per solve;
     the walk kernel's executed evaluations (28 / 26 FLOP) against the FP64 FMA rate of the part; beside it
-    the oracle on the same workload (one host core, FP64) with its balls."""
+    the oracle on the same workload (one host core, FP64) with its balls.  With tune, the autotuner first
+    picks the walk's warps per block and the balls' blocks for this workload (reported beside the
+    defaults)."""
     import torch
     import paper_2403_09990_gb300.purse as P
     from paper_2403_09990_gb300 import synthetic as syn
@@ -416,7 +419,16 @@ def run_c1(dev, sms, clock_mhz, with_oracle):
     t = torch.empty((S, 3), dtype=torch.float64, device=dev)
     res = torch.empty(9, dtype=torch.float64, device=dev)
     rows = []
+    tuning = None
     with P.Purse(p) as h:
+        if tune:
+            s0 = P.purse_ransag(h.h, 1, 1 << 20, C1_SEEDS, seeds)
+            rw = P.purse_tune_walk(h.h, prm, 3, seeds, s0, S, q, t, stream)
+            rb = P.purse_tune_megb(h.h, 1, C1_K, q, S, t, S, res, stream)
+            tuning = {"walk": {"shape": "warps per block", "config": rw["config"], "ms": rw["ms"],
+                               "default_config": rw["default_config"], "default_ms": rw["default_ms"]},
+                      "megb": {"shape": "samples per thread (blocks per ball)", "config": rb["config"], "ms": rb["ms"],
+                               "default_config": rb["default_config"], "default_ms": rb["default_ms"]}}
         for r in range(4):
             t0 = time.perf_counter()
             s0 = P.purse_ransag(h.h, 1, 1 << 20, C1_SEEDS, seeds)
@@ -452,6 +464,8 @@ def run_c1(dev, sms, clock_mhz, with_oracle):
                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                         "flops_per_eval": {"dist": FLOPS_DIST_3D, "in_purse": FLOPS_INPURSE_3D},
                         "peak_source": f"{sms} SMs x {FP64_FMA_PER_SM} FP64 FMA x 2 x {clock_mhz:.0f} MHz"}}
+    if tuning is not None:
+        out["tuning"] = tuning
     if with_oracle:
         from oracle import closure, megb as om, ransag
         t0 = time.perf_counter()
